@@ -1,0 +1,178 @@
+/*
+ * tmr.h -- C ABI of libtmr, GB300 (sm_103a) reference-less transmission-matrix
+ * (TM) retrieval with FFT-structured probing, after Zhong et al.,
+ * "Efficient reference-less transmission matrix retrieval for a multimode
+ * fiber using fast Fourier transform" (arXiv 2302.13524).
+ *
+ * Problem (Sec. 2.2).  The TM has M rows (output pixels, on an ny x nx grid,
+ * row = a*nx + b) of N complex entries (input modes).  Row t is probed by
+ * Q = [F D_1; ...; F D_J] (Eq. probingmatrix), F the unnormalised N-point DFT
+ * F x[k] = sum_n x[n] exp(-2 pi i k n / N) and D_j = diag(d_j), |d_j[n]| = 1.
+ * Each row yields K = J*N intensities y[j*N + k] = |(F (d_j .* t))[k]|^2
+ * (Eq. forwardmodel / Eq. optTMsmall2).  Retrieval minimises, independently
+ * per row, f(t) = ||y - |Q t|^2||^2 (Eq. optTMsmall2) by L-BFGS (Algorithm 1),
+ * then fits one phase offset per row from defocus intensities (Sec. 2.3,
+ * Eq. optphase) and returns diag(e^{i phi}) T_est (Eq. phaseoffset).
+ *
+ * Data layout (all row-major, complex values interleaved re,im):
+ *   masks  complex64 [J][N]
+ *   T      complex64 [M][N]
+ *   y      float32   [M][J][N]   (pattern index i = j*N + k within a row)
+ *   y_def  float32   [n_defocus][M]
+ *   G      complex64 [M][N]      gradient packed as df/dRe t + i df/dIm t
+ *
+ * Pointers.  Unless stated otherwise an array argument may be a device
+ * pointer or a host pointer (pinned or pageable); the library checks with
+ * cudaPointerGetAttributes and stages host arrays through device buffers it
+ * owns, copying results back before the call returns.  With device pointers
+ * every call is asynchronous on the handle's stream; argument errors are
+ * returned synchronously; numerical trouble of a single row is reported in
+ * row_status.  The caller owns every array it passes; the library never
+ * keeps a caller pointer past the call (masks and H are copied at create).
+ *
+ * Errors.  Every entry point returns a tmr_status; on failure
+ * tmr_last_error() returns a message for the calling thread.  No entry point
+ * falls back to the CPU: sizes without a GPU path return TMR_ERR_UNSUPPORTED.
+ * A handle is not thread-safe.
+ */
+#ifndef TMR_H
+#define TMR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tmr_handle tmr_handle; /* opaque, owned by the library */
+
+typedef enum {
+    TMR_OK = 0,
+    TMR_ERR_INVALID_ARG = 1, /* bad size, NULL where not allowed, bad option     */
+    TMR_ERR_UNSUPPORTED = 2, /* no GPU path for this N, J or option              */
+    TMR_ERR_OOM = 3,         /* device allocation failed or over workspace_limit */
+    TMR_ERR_CUDA = 4,        /* a CUDA runtime call failed                       */
+    TMR_ERR_TIMEOUT = 5,     /* tmr_sync gave up waiting                         */
+    TMR_ERR_NUMERIC = 6      /* a row reported non-finite values (tmr_sync)      */
+} tmr_status;
+
+/* Initial value of each row (Algorithm 1, first step). */
+enum {
+    TMR_INIT_RANDOM = 0,   /* Philox4x32-10 complex normal, scaled to ||t||^2 = sum(y)/(J N) */
+    TMR_INIT_BP = 1,       /* back-propagation t0 = Q^H sqrt(y) / (J N), Eq. backpropagation */
+    TMR_INIT_SPECTRAL = 2  /* power iteration on Q^H diag(min(y/mean y, clip)) Q / (J N)    */
+};
+
+/* Per-row outcome written to row_status. */
+enum {
+    TMR_ROW_MAXITER = 0,   /* ran all iterations                                   */
+    TMR_ROW_CONVERGED = 1, /* stopped early: tolerance met, zero loss or gradient  */
+    TMR_ROW_ZERO = 2,      /* all intensities zero: t = 0, no iteration (Sec. 2.2,
+                              rows outside the fiber mask)                        */
+    TMR_ROW_NUMERIC = 3    /* non-finite intensity or iterate; t = 0 or last value */
+};
+
+enum { TMR_PREC_FP32 = 0 };
+
+/* Defocus operator of the phase-offset fit (Sec. 2.3).  The defocus field
+ * of pattern n is D c_n with c_n[row] = (Q t_row)[n] (the first n_defocus
+ * probe patterns) and D x = ifft2(H .* fft2(x)) on the ny x nx pixel grid.
+ * H: device or host complex64 [ny][nx], or NULL for the quadratic phase
+ * H[a][b] = exp(-i coef (ky_a^2 + kx_b^2)) on signed integer frequencies
+ * (k = idx for 2 idx < n, else idx - n). */
+typedef struct {
+    int ny, nx;      /* ny * nx == M                                   */
+    const void *H;   /* copied at tmr_create; NULL = quadratic(coef)   */
+    double coef;     /* quadratic coefficient (0.05 in the workloads)  */
+    int n_defocus;   /* number of defocus patterns, 1 <= n_defocus <= J*N */
+} tmr_defocus_op;
+
+typedef struct {
+    int m;                  /* L-BFGS memory, 1..8 (default 5)                       */
+    int init;               /* TMR_INIT_* (default spectral)                         */
+    unsigned long long seed;/* Philox key for random/spectral starts (default 0)     */
+    int power_iters;        /* spectral power iterations (default 100)               */
+    double clip;            /* spectral intensity clip, <= 0: none (default 2.0)     */
+    double tol;             /* early exit when |f_prev - f| / f_prev < tol; 0 = off  */
+    int phase_iters;        /* L-BFGS iterations of the phase-offset fit (default 100) */
+    int precision;          /* TMR_PREC_FP32                                         */
+    int use_graph;          /* capture tmr_retrieve into a CUDA graph (default 0)    */
+    size_t workspace_limit; /* max device bytes the handle may allocate; 0 = no cap  */
+} tmr_options;
+
+/* Fill *opt with the defaults above. */
+void tmr_default_options(tmr_options *opt);
+
+/* Create a handle for M rows of length N probed with J masks.
+ *   masks      complex64 [J][N], |d| = 1 (not checked), copied.
+ *   defocus_op NULL: no phase-offset fit; else copied (H copied).
+ *   opt        NULL: defaults.
+ *   stream     cudaStream_t for all work; NULL = the legacy default stream.
+ * Supported on the GPU: N a power of two with 64 <= N <= 4096, 1 <= J <= 8.
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
+                      const tmr_defocus_op *defocus_op, const tmr_options *opt,
+                      void *stream);
+
+/* Forward model (Eq. optTMsmall2): Y[r][j][k] = |F(d_j .* T[r])[k]|^2.
+ *   T complex64 [M][N] in, Y float32 [M][J][N] out. */
+tmr_status tmr_forward(tmr_handle *h, const void *T, float *Y);
+
+/* Loss and gradient (Eq. optTMsmall2, Eq. derivative, App. A):
+ *   loss[r] = ||Y[r] - |Q T[r]|^2||^2,
+ *   G[r]    = -4 Q^H diag(Q T[r]) (Y[r] - |Q T[r]|^2).
+ * loss float32 [M] (may be NULL), G complex64 [M][N] (may be NULL). */
+tmr_status tmr_grad(tmr_handle *h, const void *T, const float *Y, float *loss, void *G);
+
+/* The whole path: initialise every row (opt.init), run `iters` L-BFGS
+ * iterations of Algorithm 1 with an exact line search on the quartic
+ * f(t + alpha p), then, when y_def != NULL and the handle has a defocus
+ * operator, fit the phase offsets (Eq. optphase) from phi = 0 and write
+ * T_out = diag(e^{i phi}) T_est (Eq. phaseoffset), phi shifted so that
+ * arg(sum_r ||t_r||^2 e^{i phi_r}) = 0.
+ *   y          float32 [M][J][N]
+ *   y_def      float32 [n_defocus][M] or NULL (skip the phase fit)
+ *   iters      >= 0
+ *   T_out      complex64 [M][N]
+ *   row_status int32 [M], row_iters int32 [M], row_loss float32 [M]: each may
+ *              be NULL.
+ * Rows whose intensities are all zero come back as t = 0 with status ZERO. */
+tmr_status tmr_retrieve(tmr_handle *h, const float *y, const float *y_def, int iters,
+                        void *T_out, int *row_status, int *row_iters, float *row_loss);
+
+/* As tmr_retrieve, starting every row from T_init (complex64 [M][N]) with an
+ * empty L-BFGS history (restart or resume from a checkpoint). */
+tmr_status tmr_retrieve_from(tmr_handle *h, const void *T_init, const float *y,
+                             const float *y_def, int iters, void *T_out, int *row_status,
+                             int *row_iters, float *row_loss);
+
+/* Defocus intensities of T (Eq. forwarddefocusImage with the handle's
+ * operator): Y_def[n][r] = |(D c_n)[r]|^2, c_n[r] = (Q T[r])[n].
+ *   Y_def float32 [n_defocus][M].  UNSUPPORTED without a defocus operator. */
+tmr_status tmr_defocus_forward(tmr_handle *h, const void *T, float *Y_def);
+
+/* Phase-offset fit alone (Sec. 2.3): given T_est and y_def, run the L-BFGS /
+ * Armijo fit of Eq. optphase from phi = 0, write phi (float64 [M], may be
+ * NULL) and T_out = diag(e^{i phi}) T_est (complex64 [M][N], may be NULL). */
+tmr_status tmr_defocus_fit(tmr_handle *h, const void *T_est, const float *y_def, double *phi,
+                           void *T_out);
+
+/* Wait for the handle's stream, at most timeout_s seconds (<= 0: no limit),
+ * polling.  Returns TMR_ERR_TIMEOUT when the work is still running,
+ * TMR_ERR_NUMERIC when a row of the last retrieve reported non-finite values. */
+tmr_status tmr_sync(tmr_handle *h, double timeout_s);
+
+/* Message describing the calling thread's last error ("" if none). */
+const char *tmr_last_error(void);
+
+/* Device bytes currently held by the handle. */
+size_t tmr_workspace_bytes(const tmr_handle *h);
+
+/* Release the handle and everything it allocated.  NULL is allowed. */
+void tmr_destroy(tmr_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TMR_H */

@@ -1,0 +1,234 @@
+"""ctypes binding of libtmr (include/tmr.h): argument marshalling only.
+
+Every function takes the same arguments as its C counterpart; arrays may be
+torch tensors (CUDA or CPU) or numpy arrays, passed by their data pointers
+after dtype/contiguity/size checks.  Errors raise TMRError.  There is no
+fallback: if libtmr.so is missing or cannot be loaded, importing fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtmr.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "tmr.h")
+
+TMR_OK, TMR_ERR_INVALID_ARG, TMR_ERR_UNSUPPORTED, TMR_ERR_OOM = 0, 1, 2, 3
+TMR_ERR_CUDA, TMR_ERR_TIMEOUT, TMR_ERR_NUMERIC = 4, 5, 6
+TMR_INIT_RANDOM, TMR_INIT_BP, TMR_INIT_SPECTRAL = 0, 1, 2
+TMR_ROW_MAXITER, TMR_ROW_CONVERGED, TMR_ROW_ZERO, TMR_ROW_NUMERIC = 0, 1, 2, 3
+TMR_PREC_FP32 = 0
+INIT = {"random": TMR_INIT_RANDOM, "bp": TMR_INIT_BP, "spectral": TMR_INIT_SPECTRAL}
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "TIMEOUT",
+                6: "NUMERIC"}
+
+
+class TMRError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class tmr_options(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("init", ctypes.c_int), ("seed", ctypes.c_ulonglong),
+                ("power_iters", ctypes.c_int), ("clip", ctypes.c_double), ("tol", ctypes.c_double),
+                ("phase_iters", ctypes.c_int), ("precision", ctypes.c_int),
+                ("use_graph", ctypes.c_int), ("workspace_limit", ctypes.c_size_t)]
+
+
+class tmr_defocus_op(ctypes.Structure):
+    _fields_ = [("ny", ctypes.c_int), ("nx", ctypes.c_int), ("H", ctypes.c_void_p),
+                ("coef", ctypes.c_double), ("n_defocus", ctypes.c_int)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libtmr.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, ip, fp, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p
+    H = ctypes.c_void_p
+    sigs = {
+        "tmr_default_options": ([ctypes.POINTER(tmr_options)], None),
+        "tmr_create": ([ctypes.POINTER(H), ip, ip, ip, vp, ctypes.POINTER(tmr_defocus_op),
+                        ctypes.POINTER(tmr_options), vp], ctypes.c_int),
+        "tmr_forward": ([H, vp, fp], ctypes.c_int),
+        "tmr_grad": ([H, vp, fp, fp, vp], ctypes.c_int),
+        "tmr_retrieve": ([H, fp, fp, ip, vp, vp, vp, fp], ctypes.c_int),
+        "tmr_retrieve_from": ([H, vp, fp, fp, ip, vp, vp, vp, fp], ctypes.c_int),
+        "tmr_defocus_forward": ([H, vp, fp], ctypes.c_int),
+        "tmr_defocus_fit": ([H, vp, fp, dp, vp], ctypes.c_int),
+        "tmr_sync": ([H, ctypes.c_double], ctypes.c_int),
+        "tmr_last_error": ([], ctypes.c_char_p),
+        "tmr_workspace_bytes": ([H], ctypes.c_size_t),
+        "tmr_destroy": ([H], None),
+    }
+    for name, (args, res) in sigs.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
+lib = _load()
+
+
+def header_symbols(path: str = HEADER):
+    """Function names declared in include/tmr.h."""
+    with open(path) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(tmr_\w+)\s*\(", text, re.M)))
+
+
+def _check(st: int):
+    if st != TMR_OK:
+        raise TMRError(st, lib.tmr_last_error().decode())
+
+
+def _ptr(x, dtype=None, count=None, name="array"):
+    """Data pointer of a torch tensor / numpy array (None -> NULL), with checks."""
+    if x is None:
+        return None
+    mod = type(x).__module__
+    if mod.startswith("torch"):
+        import torch
+        if dtype is not None:
+            want = {"c64": torch.complex64, "f32": torch.float32, "i32": torch.int32,
+                    "f64": torch.float64}[dtype]
+            if x.dtype != want:
+                raise TypeError(f"{name}: dtype {x.dtype}, expected {want}")
+        if not x.is_contiguous():
+            raise ValueError(f"{name}: not contiguous")
+        if count is not None and x.numel() != count:
+            raise ValueError(f"{name}: {x.numel()} elements, expected {count}")
+        return ctypes.c_void_p(x.data_ptr())
+    import numpy as np
+    if isinstance(x, np.ndarray):
+        if dtype is not None:
+            want = {"c64": np.complex64, "f32": np.float32, "i32": np.int32, "f64": np.float64}[dtype]
+            if x.dtype != want:
+                raise TypeError(f"{name}: dtype {x.dtype}, expected {want}")
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{name}: not contiguous")
+        if count is not None and x.size != count:
+            raise ValueError(f"{name}: {x.size} elements, expected {count}")
+        return ctypes.c_void_p(x.ctypes.data)
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    raise TypeError(f"{name}: unsupported array type {type(x)}")
+
+
+def tmr_default_options(**overrides) -> tmr_options:
+    o = tmr_options()
+    lib.tmr_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        if k == "init" and isinstance(v, str):
+            v = INIT[v]
+        setattr(o, k, v)
+    return o
+
+
+class Handle:
+    """Owns a tmr_handle; sizes are kept for argument checks."""
+
+    def __init__(self, raw, N, M, J, n_defocus):
+        self.raw = raw
+        self.N, self.M, self.J, self.n_defocus = N, M, J, n_defocus
+        self._keep = []
+
+    def close(self):
+        if self.raw:
+            lib.tmr_destroy(self.raw)
+            self.raw = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def tmr_create(N, M, J, masks, defocus_op=None, opt=None, stream=None) -> Handle:
+    """defocus_op: None or dict(ny, nx, n_defocus, coef=0.05, H=None)."""
+    dop = None
+    keep = []
+    if defocus_op is not None:
+        Hp = _ptr(defocus_op.get("H"), "c64", M, "H")
+        dop = tmr_defocus_op(int(defocus_op["ny"]), int(defocus_op["nx"]),
+                             Hp.value if Hp is not None else None,
+                             float(defocus_op.get("coef", 0.05)), int(defocus_op["n_defocus"]))
+        keep.append(defocus_op.get("H"))
+    if opt is None:
+        opt = tmr_default_options()
+    elif isinstance(opt, dict):
+        opt = tmr_default_options(**opt)
+    raw = ctypes.c_void_p()
+    st = lib.tmr_create(ctypes.byref(raw), int(N), int(M), int(J), _ptr(masks, "c64", J * N, "masks"),
+                        ctypes.byref(dop) if dop is not None else None, ctypes.byref(opt),
+                        ctypes.c_void_p(stream) if stream else None)
+    _check(st)
+    return Handle(raw, N, M, J, dop.n_defocus if dop is not None else 0)
+
+
+def tmr_forward(h: Handle, T, Y):
+    _check(lib.tmr_forward(h.raw, _ptr(T, "c64", h.M * h.N, "T"), _ptr(Y, "f32", h.M * h.J * h.N, "Y")))
+
+
+def tmr_grad(h: Handle, T, Y, loss=None, G=None):
+    _check(lib.tmr_grad(h.raw, _ptr(T, "c64", h.M * h.N, "T"), _ptr(Y, "f32", h.M * h.J * h.N, "Y"),
+                        _ptr(loss, "f32", h.M, "loss"), _ptr(G, "c64", h.M * h.N, "G")))
+
+
+def tmr_retrieve(h: Handle, y, y_def, iters, T_out, row_status=None, row_iters=None,
+                 row_loss=None):
+    _check(lib.tmr_retrieve(h.raw, _ptr(y, "f32", h.M * h.J * h.N, "y"),
+                            _ptr(y_def, "f32", h.n_defocus * h.M, "y_def"), int(iters),
+                            _ptr(T_out, "c64", h.M * h.N, "T_out"),
+                            _ptr(row_status, "i32", h.M, "row_status"),
+                            _ptr(row_iters, "i32", h.M, "row_iters"),
+                            _ptr(row_loss, "f32", h.M, "row_loss")))
+
+
+def tmr_retrieve_from(h: Handle, T_init, y, y_def, iters, T_out, row_status=None, row_iters=None,
+                      row_loss=None):
+    _check(lib.tmr_retrieve_from(h.raw, _ptr(T_init, "c64", h.M * h.N, "T_init"),
+                                 _ptr(y, "f32", h.M * h.J * h.N, "y"),
+                                 _ptr(y_def, "f32", h.n_defocus * h.M, "y_def"), int(iters),
+                                 _ptr(T_out, "c64", h.M * h.N, "T_out"),
+                                 _ptr(row_status, "i32", h.M, "row_status"),
+                                 _ptr(row_iters, "i32", h.M, "row_iters"),
+                                 _ptr(row_loss, "f32", h.M, "row_loss")))
+
+
+def tmr_defocus_forward(h: Handle, T, Y_def):
+    _check(lib.tmr_defocus_forward(h.raw, _ptr(T, "c64", h.M * h.N, "T"),
+                                   _ptr(Y_def, "f32", h.n_defocus * h.M, "Y_def")))
+
+
+def tmr_defocus_fit(h: Handle, T_est, y_def, phi=None, T_out=None):
+    _check(lib.tmr_defocus_fit(h.raw, _ptr(T_est, "c64", h.M * h.N, "T_est"),
+                               _ptr(y_def, "f32", h.n_defocus * h.M, "y_def"),
+                               _ptr(phi, "f64", h.M, "phi"), _ptr(T_out, "c64", h.M * h.N, "T_out")))
+
+
+def tmr_sync(h: Handle, timeout_s: float = 0.0):
+    _check(lib.tmr_sync(h.raw, float(timeout_s)))
+
+
+def tmr_last_error() -> str:
+    return lib.tmr_last_error().decode()
+
+
+def tmr_workspace_bytes(h: Handle) -> int:
+    return int(lib.tmr_workspace_bytes(h.raw))
+
+
+def tmr_destroy(h: Handle):
+    h.close()

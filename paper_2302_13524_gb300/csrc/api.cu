@@ -1,0 +1,508 @@
+// api.cu -- the C ABI of libtmr (declared in include/tmr.h).
+//
+// Owns the handle (sizes, options, the device copies of the masks, the FFT
+// twiddle table and the defocus transfer function, and every scratch buffer),
+// validates arguments, stages host arrays through device buffers, and
+// sequences the kernels of one retrieval on the handle's stream:
+//   solver (per-row Algorithm 1, persistent cluster kernel) -> row energies ->
+//   phase-offset fit (cooperative kernel) -> T_out = diag(e^{i phi}) T_est.
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tmr.h"
+
+using namespace tmr;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+tmr_status fail(tmr_status st, const std::string &msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+tmr_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? TMR_ERR_OOM : TMR_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define TMR_CUDA(call, what)                      \
+    do {                                          \
+        cudaError_t e__ = (call);                 \
+        if (e__ != cudaSuccess) return cuda_fail(e__, what); \
+    } while (0)
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct tmr_handle {
+    int N = 0, M = 0, J = 0;
+    tmr_options opt{};
+    bool has_defocus = false;
+    int ny = 0, nx = 0, Nd = 0;
+    cudaStream_t stream = nullptr;
+    size_t held = 0;
+    // persistent device state
+    float2 *masks = nullptr, *tw = nullptr, *H = nullptr, *Zd = nullptr;
+    double *phi = nullptr, *pf_ws = nullptr, *pf_loss = nullptr;
+    float *wts = nullptr;
+    unsigned *queue = nullptr, *pf_sync = nullptr;
+    int *pf_err = nullptr, *pf_iters = nullptr;
+    int *status_scratch = nullptr, *iters_scratch = nullptr;
+    float *loss_scratch = nullptr;
+    // staging buffers for host arrays, keyed by slot
+    DevBuf stage[8];
+    // last retrieve, for tmr_sync's numeric check
+    const int *last_status = nullptr;
+    bool last_had_fit = false;
+};
+
+namespace {
+
+enum { ST_Y = 0, ST_YDEF, ST_TOUT, ST_TIN, ST_STATUS, ST_ITERS, ST_LOSS, ST_PHI };
+
+tmr_status halloc(tmr_handle *h, void **p, size_t bytes, const char *what)
+{
+    if (h->opt.workspace_limit && h->held + bytes > h->opt.workspace_limit)
+        return fail(TMR_ERR_OOM, std::string(what) + ": workspace_limit exceeded");
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TMR_ERR_OOM, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+    h->held += bytes;
+    return TMR_OK;
+}
+
+void hfree(tmr_handle *h, void *p, size_t bytes)
+{
+    if (p) {
+        cudaFree(p);
+        h->held -= bytes;
+    }
+}
+
+// Device view of a caller array: the pointer itself when it is device memory,
+// otherwise a staging buffer (copied in when `in`).
+tmr_status stage(tmr_handle *h, int slot, const void *src, size_t bytes, bool in, void **dev)
+{
+    if (is_device_ptr(src)) {
+        *dev = const_cast<void *>(src);
+        return TMR_OK;
+    }
+    DevBuf &b = h->stage[slot];
+    if (b.bytes < bytes) {
+        hfree(h, b.p, b.bytes);
+        b.p = nullptr;
+        b.bytes = 0;
+        tmr_status st = halloc(h, &b.p, bytes, "staging buffer");
+        if (st != TMR_OK) return st;
+        b.bytes = bytes;
+    }
+    if (in) TMR_CUDA(cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, h->stream), "copy in");
+    *dev = b.p;
+    return TMR_OK;
+}
+
+tmr_status unstage(tmr_handle *h, void *host, const void *dev, size_t bytes, bool *synced)
+{
+    if (host && dev != host) {
+        TMR_CUDA(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, h->stream), "copy out");
+        *synced = true;
+    }
+    return TMR_OK;
+}
+
+tmr_status check_launch(cudaError_t e, const char *what)
+{
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return TMR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void tmr_default_options(tmr_options *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->m = 5;
+    o->init = TMR_INIT_SPECTRAL;
+    o->seed = 0;
+    o->power_iters = 100;
+    o->clip = 2.0;
+    o->tol = 0.0;
+    o->phase_iters = 100;
+    o->precision = TMR_PREC_FP32;
+    o->use_graph = 0;
+    o->workspace_limit = 0;
+}
+
+const char *tmr_last_error(void) { return g_last_error.c_str(); }
+
+size_t tmr_workspace_bytes(const tmr_handle *h) { return h ? h->held : 0; }
+
+void tmr_destroy(tmr_handle *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    void *ptrs[] = {h->masks, h->tw, h->H, h->Zd, h->phi, h->pf_ws, h->pf_loss, h->wts, h->queue,
+                    h->pf_sync, h->pf_err, h->pf_iters, h->status_scratch, h->iters_scratch,
+                    h->loss_scratch};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (auto &b : h->stage)
+        if (b.p) cudaFree(b.p);
+    delete h;
+}
+
+tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
+                      const tmr_defocus_op *dop, const tmr_options *opt, void *stream)
+{
+    g_last_error.clear();
+    if (!out) return fail(TMR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (N <= 0 || M < 0 || J <= 0) return fail(TMR_ERR_INVALID_ARG, "N, J must be positive and M >= 0");
+    if (!masks) return fail(TMR_ERR_INVALID_ARG, "masks is NULL");
+    tmr_options o;
+    tmr_default_options(&o);
+    if (opt) o = *opt;
+    if (o.m < 1 || o.m > kMaxMem) return fail(TMR_ERR_INVALID_ARG, "opt.m must be in 1..8");
+    if (o.init < TMR_INIT_RANDOM || o.init > TMR_INIT_SPECTRAL) return fail(TMR_ERR_INVALID_ARG, "opt.init");
+    if (o.power_iters < 0 || o.phase_iters < 0 || o.tol < 0) return fail(TMR_ERR_INVALID_ARG, "negative option");
+    if (o.precision != TMR_PREC_FP32) return fail(TMR_ERR_UNSUPPORTED, "only TMR_PREC_FP32 is available");
+    if (!fft_supported(N)) return fail(TMR_ERR_UNSUPPORTED, "N must be a power of two in 64..4096");
+    if (J > kMaxMasks) return fail(TMR_ERR_UNSUPPORTED, "J must be at most 8");
+    int dev = 0;
+    TMR_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dop) {
+        if (dop->ny <= 0 || dop->nx <= 0 || (long long)dop->ny * dop->nx != M)
+            return fail(TMR_ERR_INVALID_ARG, "defocus grid ny*nx must equal M");
+        if (dop->n_defocus < 1 || dop->n_defocus > J * N)
+            return fail(TMR_ERR_INVALID_ARG, "n_defocus must be in 1..J*N");
+        if (!defocus_supported(dop->ny, dop->nx))
+            return fail(TMR_ERR_UNSUPPORTED, "defocus grid sides must be powers of two, grid <= 160 KB");
+    }
+
+    tmr_handle *h = new tmr_handle();
+    h->N = N;
+    h->M = M;
+    h->J = J;
+    h->opt = o;
+    h->stream = (cudaStream_t)stream;
+    tmr_status st;
+#define TRY(x)                    \
+    do {                          \
+        st = (x);                 \
+        if (st != TMR_OK) {       \
+            tmr_destroy(h);       \
+            return st;            \
+        }                         \
+    } while (0)
+    TRY(halloc(h, (void **)&h->masks, sizeof(float2) * (size_t)J * N, "masks"));
+    {
+        cudaError_t e = cudaMemcpy(h->masks, masks, sizeof(float2) * (size_t)J * N, cudaMemcpyDefault);
+        if (e != cudaSuccess) {
+            tmr_destroy(h);
+            return cuda_fail(e, "copy masks");
+        }
+    }
+    const int twn = fft_table_len(N);
+    std::vector<float2> tw(twn > 0 ? twn : 1);
+    fft_table(N, tw.data());
+    TRY(halloc(h, (void **)&h->tw, sizeof(float2) * tw.size(), "twiddles"));
+    if (cudaMemcpy(h->tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        tmr_destroy(h);
+        return fail(TMR_ERR_CUDA, "copy twiddles");
+    }
+    TRY(halloc(h, (void **)&h->queue, sizeof(unsigned) * 4, "queue"));
+    TRY(halloc(h, (void **)&h->status_scratch, sizeof(int) * (M > 0 ? M : 1), "status"));
+    TRY(halloc(h, (void **)&h->iters_scratch, sizeof(int) * (M > 0 ? M : 1), "iters"));
+    TRY(halloc(h, (void **)&h->loss_scratch, sizeof(float) * (M > 0 ? M : 1), "loss"));
+    if (dop) {
+        h->has_defocus = true;
+        h->ny = dop->ny;
+        h->nx = dop->nx;
+        h->Nd = dop->n_defocus;
+        const size_t P = (size_t)M;
+        TRY(halloc(h, (void **)&h->H, sizeof(float2) * P, "H"));
+        if (dop->H) {
+            if (cudaMemcpy(h->H, dop->H, sizeof(float2) * P, cudaMemcpyDefault) != cudaSuccess) {
+                tmr_destroy(h);
+                return fail(TMR_ERR_CUDA, "copy H");
+            }
+        } else {
+            cudaError_t e = launch_make_quadratic_H(h->ny, h->nx, dop->coef, h->H, nullptr);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) {
+                tmr_destroy(h);
+                return cuda_fail(e, "make H");
+            }
+        }
+        TRY(halloc(h, (void **)&h->Zd, sizeof(float2) * (size_t)h->Nd * P, "defocus fields"));
+        TRY(halloc(h, (void **)&h->phi, sizeof(double) * P, "phi"));
+        TRY(halloc(h, (void **)&h->wts, sizeof(float) * P, "weights"));
+        const int grid = phase_fit_grid(h->ny, h->nx, h->Nd);
+        TRY(halloc(h, (void **)&h->pf_ws, sizeof(double) * phase_fit_workspace_doubles((int)P, h->Nd, o.m, grid),
+                   "phase-fit workspace"));
+        TRY(halloc(h, (void **)&h->pf_sync, sizeof(unsigned) * 4, "barrier"));
+        TRY(halloc(h, (void **)&h->pf_err, sizeof(int) * 4, "error flag"));
+        TRY(halloc(h, (void **)&h->pf_iters, sizeof(int) * 4, "phase iters"));
+        TRY(halloc(h, (void **)&h->pf_loss, sizeof(double) * 4, "phase loss"));
+        cudaMemset(h->pf_err, 0, sizeof(int) * 4);
+    }
+#undef TRY
+    *out = h;
+    return TMR_OK;
+}
+
+tmr_status tmr_forward(tmr_handle *h, const void *T, float *Y)
+{
+    g_last_error.clear();
+    if (!h || !T || !Y) return fail(TMR_ERR_INVALID_ARG, "NULL argument");
+    const size_t MN = (size_t)h->M * h->N, MK = MN * h->J;
+    void *dT, *dY;
+    tmr_status st;
+    if ((st = stage(h, ST_TIN, T, sizeof(float2) * MN, true, &dT)) != TMR_OK) return st;
+    if ((st = stage(h, ST_Y, Y, sizeof(float) * MK, false, &dY)) != TMR_OK) return st;
+    if ((st = check_launch(launch_forward(h->N, h->M, h->J, (const float2 *)dT, h->masks, h->tw,
+                                          (float *)dY, h->stream), "forward kernel")) != TMR_OK)
+        return st;
+    bool synced = false;
+    if ((st = unstage(h, Y, dY, sizeof(float) * MK, &synced)) != TMR_OK) return st;
+    if (synced) TMR_CUDA(cudaStreamSynchronize(h->stream), "sync");
+    return TMR_OK;
+}
+
+tmr_status tmr_grad(tmr_handle *h, const void *T, const float *Y, float *loss, void *G)
+{
+    g_last_error.clear();
+    if (!h || !T || !Y) return fail(TMR_ERR_INVALID_ARG, "NULL argument");
+    const size_t MN = (size_t)h->M * h->N, MK = MN * h->J;
+    void *dT, *dY, *dL = nullptr, *dG = nullptr;
+    tmr_status st;
+    if ((st = stage(h, ST_TIN, T, sizeof(float2) * MN, true, &dT)) != TMR_OK) return st;
+    if ((st = stage(h, ST_Y, Y, sizeof(float) * MK, true, &dY)) != TMR_OK) return st;
+    if (loss && (st = stage(h, ST_LOSS, loss, sizeof(float) * h->M, false, &dL)) != TMR_OK) return st;
+    if (G && (st = stage(h, ST_TOUT, G, sizeof(float2) * MN, false, &dG)) != TMR_OK) return st;
+    if ((st = check_launch(launch_grad(h->N, h->M, h->J, (const float2 *)dT, h->masks, h->tw,
+                                       (const float *)dY, (float *)dL, (float2 *)dG, h->stream),
+                           "gradient kernel")) != TMR_OK)
+        return st;
+    bool synced = false;
+    if (loss && (st = unstage(h, loss, dL, sizeof(float) * h->M, &synced)) != TMR_OK) return st;
+    if (G && (st = unstage(h, G, dG, sizeof(float2) * MN, &synced)) != TMR_OK) return st;
+    if (synced) TMR_CUDA(cudaStreamSynchronize(h->stream), "sync");
+    return TMR_OK;
+}
+
+static tmr_status run_phase_fit(tmr_handle *h, const float2 *Tin, const float *dYdef, double *dphi,
+                                float2 *Tout)
+{
+    // weights of the constant-phase normalisation: row energies of T_est
+    TMR_CUDA(launch_row_energy(h->N, h->M, Tin, h->wts, h->stream), "row energy");
+    TMR_CUDA(cudaMemsetAsync(h->pf_sync, 0, sizeof(unsigned) * 4, h->stream), "memset");
+    TMR_CUDA(cudaMemsetAsync(h->pf_err, 0, sizeof(int) * 4, h->stream), "memset");
+    PhaseFitParams p{};
+    p.Zd = h->Zd;
+    p.Ydef = dYdef;
+    p.H = h->H;
+    p.wts = h->wts;
+    p.phi = dphi;
+    p.Nd = h->Nd;
+    p.ny = h->ny;
+    p.nx = h->nx;
+    p.iters = h->opt.phase_iters;
+    p.m = h->opt.m;
+    p.ws = h->pf_ws;
+    p.sync = h->pf_sync;
+    p.err = h->pf_err;
+    p.iters_done = h->pf_iters;
+    p.loss_out = h->pf_loss;
+    TMR_CUDA(launch_phase_fit(p, h->stream), "phase-fit kernel");
+    if (Tout) TMR_CUDA(launch_apply_phase(h->N, h->M, dphi, Tin, Tout, h->stream), "apply phase");
+    return TMR_OK;
+}
+
+static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *y, const float *y_def,
+                                int iters, void *T_out, int *row_status, int *row_iters,
+                                float *row_loss)
+{
+    g_last_error.clear();
+    if (!h || !y || !T_out) return fail(TMR_ERR_INVALID_ARG, "NULL argument");
+    if (iters < 0) return fail(TMR_ERR_INVALID_ARG, "iters must be >= 0");
+    const bool fit = y_def != nullptr;
+    if (fit && !h->has_defocus) return fail(TMR_ERR_INVALID_ARG, "y_def given but the handle has no defocus operator");
+    {
+        int dev = 0, smem_optin = 0;
+        TMR_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+        TMR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
+        if (solver_smem_bytes(h->N, h->J, h->opt.m) > (size_t)smem_optin)
+            return fail(TMR_ERR_UNSUPPORTED, "per-row state of this (N, J, m) does not fit in shared memory");
+    }
+    const size_t MN = (size_t)h->M * h->N, MK = MN * h->J;
+    tmr_status st;
+    void *dy, *dT, *dTin = nullptr, *dYd = nullptr, *dS, *dI, *dL;
+    if ((st = stage(h, ST_Y, y, sizeof(float) * MK, true, &dy)) != TMR_OK) return st;
+    if (T_init && (st = stage(h, ST_TIN, T_init, sizeof(float2) * MN, true, &dTin)) != TMR_OK) return st;
+    if (fit && (st = stage(h, ST_YDEF, y_def, sizeof(float) * (size_t)h->Nd * h->M, true, &dYd)) != TMR_OK)
+        return st;
+    if ((st = stage(h, ST_TOUT, T_out, sizeof(float2) * MN, false, &dT)) != TMR_OK) return st;
+    dS = h->status_scratch;
+    dI = h->iters_scratch;
+    dL = h->loss_scratch;
+    if (row_status && (st = stage(h, ST_STATUS, row_status, sizeof(int) * h->M, false, &dS)) != TMR_OK) return st;
+    if (row_iters && (st = stage(h, ST_ITERS, row_iters, sizeof(int) * h->M, false, &dI)) != TMR_OK) return st;
+    if (row_loss && (st = stage(h, ST_LOSS, row_loss, sizeof(float) * h->M, false, &dL)) != TMR_OK) return st;
+
+    TMR_CUDA(cudaMemsetAsync(h->queue, 0, sizeof(unsigned) * 4, h->stream), "memset");
+    SolverParams p{};
+    p.masks = h->masks;
+    p.tw = h->tw;
+    p.y = (const float *)dy;
+    p.T_init = (const float2 *)dTin;
+    p.T_out = (float2 *)dT;
+    p.row_status = (int *)dS;
+    p.row_iters = (int *)dI;
+    p.row_loss = (float *)dL;
+    p.Zd = fit ? h->Zd : nullptr;
+    p.queue = h->queue;
+    p.Nd = fit ? h->Nd : 0;
+    p.M = h->M;
+    p.J = h->J;
+    p.iters = iters;
+    p.m = h->opt.m;
+    p.init = h->opt.init;
+    p.power_iters = h->opt.power_iters;
+    p.seed = h->opt.seed;
+    p.clip = (float)h->opt.clip;
+    p.tol = h->opt.tol;
+    int clusters = 0;
+    TMR_CUDA(launch_solver(h->N, p, h->stream, &clusters), "solver kernel");
+    if (fit) {
+        if ((st = run_phase_fit(h, (const float2 *)dT, (const float *)dYd, h->phi, (float2 *)dT)) != TMR_OK)
+            return st;
+    }
+    h->last_status = (const int *)dS;
+    h->last_had_fit = fit;
+    bool synced = false;
+    if ((st = unstage(h, T_out, dT, sizeof(float2) * MN, &synced)) != TMR_OK) return st;
+    if (row_status && (st = unstage(h, row_status, dS, sizeof(int) * h->M, &synced)) != TMR_OK) return st;
+    if (row_iters && (st = unstage(h, row_iters, dI, sizeof(int) * h->M, &synced)) != TMR_OK) return st;
+    if (row_loss && (st = unstage(h, row_loss, dL, sizeof(float) * h->M, &synced)) != TMR_OK) return st;
+    if (synced) TMR_CUDA(cudaStreamSynchronize(h->stream), "sync");
+    return TMR_OK;
+}
+
+tmr_status tmr_retrieve(tmr_handle *h, const float *y, const float *y_def, int iters, void *T_out,
+                        int *row_status, int *row_iters, float *row_loss)
+{
+    return retrieve_impl(h, nullptr, y, y_def, iters, T_out, row_status, row_iters, row_loss);
+}
+
+tmr_status tmr_retrieve_from(tmr_handle *h, const void *T_init, const float *y, const float *y_def,
+                             int iters, void *T_out, int *row_status, int *row_iters, float *row_loss)
+{
+    if (!T_init) return fail(TMR_ERR_INVALID_ARG, "T_init is NULL");
+    return retrieve_impl(h, T_init, y, y_def, iters, T_out, row_status, row_iters, row_loss);
+}
+
+tmr_status tmr_defocus_forward(tmr_handle *h, const void *T, float *Y_def)
+{
+    g_last_error.clear();
+    if (!h || !T || !Y_def) return fail(TMR_ERR_INVALID_ARG, "NULL argument");
+    if (!h->has_defocus) return fail(TMR_ERR_UNSUPPORTED, "handle has no defocus operator");
+    const size_t MN = (size_t)h->M * h->N;
+    void *dT, *dY;
+    tmr_status st;
+    if ((st = stage(h, ST_TIN, T, sizeof(float2) * MN, true, &dT)) != TMR_OK) return st;
+    if ((st = stage(h, ST_YDEF, Y_def, sizeof(float) * (size_t)h->Nd * h->M, false, &dY)) != TMR_OK) return st;
+    TMR_CUDA(launch_fields(h->N, h->M, h->J, h->Nd, (const float2 *)dT, h->masks, h->tw, h->Zd, h->stream),
+             "fields kernel");
+    TMR_CUDA(launch_defocus_forward(h->ny, h->nx, h->Nd, h->Zd, h->H, nullptr, nullptr, (float *)dY, h->stream),
+             "defocus kernel");
+    bool synced = false;
+    if ((st = unstage(h, Y_def, dY, sizeof(float) * (size_t)h->Nd * h->M, &synced)) != TMR_OK) return st;
+    if (synced) TMR_CUDA(cudaStreamSynchronize(h->stream), "sync");
+    return TMR_OK;
+}
+
+tmr_status tmr_defocus_fit(tmr_handle *h, const void *T_est, const float *y_def, double *phi, void *T_out)
+{
+    g_last_error.clear();
+    if (!h || !T_est || !y_def) return fail(TMR_ERR_INVALID_ARG, "NULL argument");
+    if (!h->has_defocus) return fail(TMR_ERR_UNSUPPORTED, "handle has no defocus operator");
+    const size_t MN = (size_t)h->M * h->N;
+    void *dT, *dY, *dP = nullptr, *dO = nullptr;
+    tmr_status st;
+    if ((st = stage(h, ST_TIN, T_est, sizeof(float2) * MN, true, &dT)) != TMR_OK) return st;
+    if ((st = stage(h, ST_YDEF, y_def, sizeof(float) * (size_t)h->Nd * h->M, true, &dY)) != TMR_OK) return st;
+    if (phi && (st = stage(h, ST_PHI, phi, sizeof(double) * h->M, false, &dP)) != TMR_OK) return st;
+    if (T_out && (st = stage(h, ST_TOUT, T_out, sizeof(float2) * MN, false, &dO)) != TMR_OK) return st;
+    TMR_CUDA(launch_fields(h->N, h->M, h->J, h->Nd, (const float2 *)dT, h->masks, h->tw, h->Zd, h->stream),
+             "fields kernel");
+    if ((st = run_phase_fit(h, (const float2 *)dT, (const float *)dY, dP ? (double *)dP : h->phi,
+                            (float2 *)dO)) != TMR_OK)
+        return st;
+    bool synced = false;
+    if (phi && (st = unstage(h, phi, dP, sizeof(double) * h->M, &synced)) != TMR_OK) return st;
+    if (T_out && (st = unstage(h, T_out, dO, sizeof(float2) * MN, &synced)) != TMR_OK) return st;
+    if (synced) TMR_CUDA(cudaStreamSynchronize(h->stream), "sync");
+    return TMR_OK;
+}
+
+tmr_status tmr_sync(tmr_handle *h, double timeout_s)
+{
+    g_last_error.clear();
+    if (!h) return fail(TMR_ERR_INVALID_ARG, "NULL handle");
+    const auto t0 = std::chrono::steady_clock::now();
+    while (true) {
+        cudaError_t e = cudaStreamQuery(h->stream);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "stream");
+        if (timeout_s > 0) {
+            const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (el > timeout_s) return fail(TMR_ERR_TIMEOUT, "work still running after the timeout");
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    if (h->last_had_fit && h->pf_err) {
+        int err = 0;
+        TMR_CUDA(cudaMemcpy(&err, h->pf_err, sizeof(int), cudaMemcpyDeviceToHost), "read error flag");
+        if (err) return fail(TMR_ERR_TIMEOUT, "phase-offset fit: grid barrier timed out");
+    }
+    if (h->last_status && h->M > 0 && is_device_ptr(h->last_status)) {
+        std::vector<int> st(h->M);
+        TMR_CUDA(cudaMemcpy(st.data(), h->last_status, sizeof(int) * h->M, cudaMemcpyDeviceToHost), "read status");
+        for (int v : st)
+            if (v == TMR_ROW_NUMERIC) return fail(TMR_ERR_NUMERIC, "a row reported non-finite values");
+    }
+    return TMR_OK;
+}
+
+}  // extern "C"

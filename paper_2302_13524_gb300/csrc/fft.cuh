@@ -1,0 +1,161 @@
+// fft.cuh -- block-level complex FFT of length N = 2^L held in registers.
+//
+// A team of T threads computes one length-N transform; thread `tid` holds
+// E = N / T elements in the "thread-strided" layout: register e <-> index
+// tid + e*T.  Input and output both use this layout, so a forward transform's
+// output can be consumed elementwise and fed straight into an inverse
+// transform without a shared-memory round trip.
+//
+// Passes follow the Stockham autosort formulation: N = R_0 * E^(P-1) with the
+// small remainder radix first.  In pass p (radix R, stride Ns = product of the
+// earlier radices) butterfly b reads x[b + r N/R], multiplies by
+// W_{Ns R}^{r (b mod Ns)}, takes an R-point DFT and writes its outputs to
+// (b div Ns) Ns R + (b mod Ns) + q Ns.  Every pass but the last exchanges
+// through a padded shared buffer (one float2 of padding per 16, which keeps the
+// strided writes of the early passes free of bank conflicts); the last pass's
+// outputs land in the thread-strided layout directly.
+//
+// Twiddles come from a table with one block per pass p >= 1:
+// tw_p[(r-1) Ns + j] = exp(-2 pi i r j / (Ns R)), r = 1..R-1, j = 0..Ns-1,
+// computed in FP64 on the host and rounded to FP32 (no device trig).  A
+// thread reads its row j contiguously across the warp.
+#pragma once
+
+#include "common.cuh"
+
+namespace tmr {
+
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x / 2); }
+__host__ __device__ constexpr int ipowc(int b, int e) { return e == 0 ? 1 : b * ipowc(b, e - 1); }
+
+// Threads per transform for length N: one warp at least, eight points each
+// above that.
+__host__ __device__ constexpr int fft_threads(int N) { return N / 8 < 32 ? 32 : N / 8; }
+
+template <int N, int E>
+struct FftPlan {
+    static constexpr int LN = ilog2c(N), LE = ilog2c(E);
+    static constexpr int P = (LN + LE - 1) / LE;  // number of passes
+    static constexpr int LR0 = LN - (P - 1) * LE; // log2 of the first radix
+    __host__ __device__ static constexpr int radix(int p) { return p == 0 ? (1 << LR0) : E; }
+    __host__ __device__ static constexpr int ns(int p) { return p == 0 ? 1 : (1 << LR0) * ipowc(E, p - 1); }
+    // offset (in float2) of pass p's twiddle block in the table
+    __host__ __device__ static constexpr int tw_off(int p)
+    {
+        return p <= 1 ? 0 : tw_off(p - 1) + (radix(p - 1) - 1) * ns(p - 1);
+    }
+    static constexpr int TW_SIZE = tw_off(P);  // total table length
+};
+
+__host__ __device__ __forceinline__ constexpr int fft_pad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int fft_buf_len(int N) { return N + N / 16; }
+
+// Multiply by the quarter turn W_4 = exp(SIGN i pi / 2): -i for the forward sign.
+template <int SIGN>
+__device__ __forceinline__ float2 rot4(float2 a)
+{
+    return SIGN < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+// In-place R-point DFT, X[k] = sum_n x[n] exp(SIGN 2 pi i k n / R), natural order.
+template <int R, int SIGN>
+__device__ __forceinline__ void dft_small(float2 (&x)[R])
+{
+    if constexpr (R == 1) {
+    } else if constexpr (R == 2) {
+        const float2 a = x[0], b = x[1];
+        x[0] = cadd(a, b);
+        x[1] = csub(a, b);
+    } else if constexpr (R == 4) {
+        const float2 a0 = cadd(x[0], x[2]), a1 = csub(x[0], x[2]);
+        const float2 a2 = cadd(x[1], x[3]), a3 = rot4<SIGN>(csub(x[1], x[3]));
+        x[0] = cadd(a0, a2);
+        x[2] = csub(a0, a2);
+        x[1] = cadd(a1, a3);
+        x[3] = csub(a1, a3);
+    } else if constexpr (R == 8) {
+        // decimation in time: two 4-point DFTs of the even and odd samples
+        float2 e[4] = {x[0], x[2], x[4], x[6]};
+        float2 o[4] = {x[1], x[3], x[5], x[7]};
+        dft_small<4, SIGN>(e);
+        dft_small<4, SIGN>(o);
+        constexpr float h = 0.70710678118654752440f;
+        // W_8^k o_k for k = 1, 2, 3
+        const float2 o1 = SIGN < 0 ? make_float2(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x))
+                                   : make_float2(h * (o[1].x - o[1].y), h * (o[1].y + o[1].x));
+        const float2 o2 = rot4<SIGN>(o[2]);
+        const float2 o3 = SIGN < 0 ? make_float2(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y))
+                                   : make_float2(-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y));
+        x[0] = cadd(e[0], o[0]);
+        x[4] = csub(e[0], o[0]);
+        x[1] = cadd(e[1], o1);
+        x[5] = csub(e[1], o1);
+        x[2] = cadd(e[2], o2);
+        x[6] = csub(e[2], o2);
+        x[3] = cadd(e[3], o3);
+        x[7] = csub(e[3], o3);
+    } else {
+        static_assert(R == 1 || R == 2 || R == 4 || R == 8, "unsupported radix");
+    }
+}
+
+// One Stockham pass (see file comment).  buf: shared, fft_buf_len(N) float2.
+template <int N, int T, int R, int NS, int TWOFF, int SIGN, bool LAST>
+__device__ __forceinline__ void fft_pass(float2 (&v)[N / T], float2 *buf, const float2 *tw, int tid)
+{
+    constexpr int E = N / T, BPT = E / R;
+    static_assert(BPT * R == E, "radix must divide the points per thread");
+#pragma unroll
+    for (int i = 0; i < BPT; i++) {
+        const int b = tid + i * T;
+        const int j = b & (NS - 1);
+        float2 x[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) x[r] = v[i + r * BPT];
+        if constexpr (NS > 1) {
+#pragma unroll
+            for (int r = 1; r < R; r++) {
+                float2 w = tw[TWOFF + (r - 1) * NS + j];
+                if constexpr (SIGN > 0) w.y = -w.y;
+                x[r] = cmul(x[r], w);
+            }
+        }
+        dft_small<R, SIGN>(x);
+        if constexpr (LAST) {
+#pragma unroll
+            for (int q = 0; q < R; q++) v[i + q * BPT] = x[q];
+        } else {
+            const int base = (b - j) * R + j;
+#pragma unroll
+            for (int q = 0; q < R; q++) buf[fft_pad(base + q * NS)] = x[q];
+        }
+    }
+    if constexpr (!LAST) {
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; e++) v[e] = buf[fft_pad(tid + e * T)];
+        __syncthreads();
+    }
+}
+
+template <int N, int T, int SIGN, int p>
+__device__ __forceinline__ void fft_passes(float2 (&v)[N / T], float2 *buf, const float2 *tw, int tid)
+{
+    using Pl = FftPlan<N, N / T>;
+    if constexpr (p < Pl::P) {
+        fft_pass<N, T, Pl::radix(p), Pl::ns(p), Pl::tw_off(p), SIGN, p == Pl::P - 1>(v, buf, tw, tid);
+        fft_passes<N, T, SIGN, p + 1>(v, buf, tw, tid);
+    }
+}
+
+// Unnormalised length-N transform of the thread-strided registers v:
+// SIGN = -1: X[k] = sum_n x[n] exp(-2 pi i k n / N); SIGN = +1: the conjugate
+// kernel (N * ifft).  All T threads of the team must call it (it
+// synchronises the block); buf and tw are shared memory.
+template <int N, int T, int SIGN>
+__device__ __forceinline__ void block_fft(float2 (&v)[N / T], float2 *buf, const float2 *tw, int tid)
+{
+    fft_passes<N, T, SIGN, 0>(v, buf, tw, tid);
+}
+
+}  // namespace tmr

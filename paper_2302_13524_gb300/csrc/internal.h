@@ -1,0 +1,74 @@
+// internal.h -- launchers shared between the C-ABI layer and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace tmr {
+
+// Twiddle table of the block FFT for length N (FP64 on the host, rounded to
+// FP32); returns its length in float2, writes it to out when out != NULL.
+int fft_table(int N, float2 *out);
+int fft_table_len(int N);
+bool fft_supported(int N);
+
+// ---- fused forward model and gradient (kernels.cu) -------------------------
+cudaError_t launch_forward(int N, int M, int J, const float2 *T, const float2 *masks,
+                           const float2 *tw, float *Y, cudaStream_t s);
+cudaError_t launch_grad(int N, int M, int J, const float2 *T, const float2 *masks,
+                        const float2 *tw, const float *Y, float *loss, float2 *G, cudaStream_t s);
+// c_n[r] = (Q T[r])[n] for n < Nd, written as Zd[n][r] (the defocus fields).
+cudaError_t launch_fields(int N, int M, int J, int Nd, const float2 *T, const float2 *masks,
+                          const float2 *tw, float2 *Zd, cudaStream_t s);
+// T[r] *= exp(i phi[r])
+cudaError_t launch_apply_phase(int N, int M, const double *phi, const float2 *Tin, float2 *Tout,
+                               cudaStream_t s);
+
+// ---- persistent per-row solver (solver.cu) ---------------------------------
+struct SolverParams {
+    const float2 *masks;  // [J][N]
+    const float2 *tw;     // FFT twiddle table
+    const float *y;       // [M][J][N]
+    const float2 *T_init; // [M][N] or NULL
+    float2 *T_out;        // [M][N]
+    int *row_status;      // [M]
+    int *row_iters;       // [M]
+    float *row_loss;      // [M]
+    float2 *Zd;           // [Nd][M] defocus fields of the final iterate, or NULL
+    unsigned *queue;      // row work counter, zeroed before the launch
+    int Nd, M, J, iters, m, init, power_iters;
+    unsigned long long seed;
+    float clip;
+    double tol;
+};
+size_t solver_smem_bytes(int N, int J, int m);
+cudaError_t launch_solver(int N, const SolverParams &p, cudaStream_t s, int *clusters_out);
+
+// ---- defocus operator and phase-offset fit (defocus.cu) --------------------
+struct PhaseFitParams {
+    const float2 *Zd;    // [Nd][P] fields c_n (P = ny*nx = M)
+    const float *Ydef;   // [Nd][P]
+    const float2 *H;     // [P] transfer function
+    const float2 *twy;   // FFT table for ny
+    const float2 *twx;   // FFT table for nx
+    const float *wts;    // [P] weights of the constant-phase normalisation
+    double *phi;         // [P] out
+    int Nd, ny, nx, iters, m;
+    // workspace (allocated by the caller, see phase_fit_workspace)
+    double *ws;
+    unsigned *sync;      // grid barrier words (2), zeroed before the launch
+    int *err;            // error flag, zeroed before the launch
+    int *iters_done;     // [1]
+    double *loss_out;    // [1]
+};
+size_t phase_fit_workspace_doubles(int P, int Nd, int m, int grid);
+int phase_fit_grid(int ny, int nx, int Nd);
+bool defocus_supported(int ny, int nx);
+cudaError_t launch_phase_fit(const PhaseFitParams &p, cudaStream_t s);
+cudaError_t launch_defocus_forward(int ny, int nx, int Nd, const float2 *Zd, const float2 *H,
+                                   const float2 *twy, const float2 *twx, float *Ydef,
+                                   cudaStream_t s);
+cudaError_t launch_make_quadratic_H(int ny, int nx, double coef, float2 *H, cudaStream_t s);
+cudaError_t launch_row_energy(int N, int M, const float2 *T, float *w, cudaStream_t s);
+
+}  // namespace tmr
