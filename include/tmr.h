@@ -171,6 +171,36 @@ size_t tmr_workspace_bytes(const tmr_handle *h);
 /* Release the handle and everything it allocated.  NULL is allowed. */
 void tmr_destroy(tmr_handle *h);
 
+/* Per-row retrieval without any allocation and without a handle.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not call cudaMalloc: code running under an allocator that owns
+ * the whole device memory budget, loops that cannot afford the device-wide
+ * synchronisation a first cudaMalloc may cause, or hosts that forbid device
+ * allocation after start-up.  It runs the same persistent solver as
+ * tmr_retrieve (initialisation, `iters` L-BFGS iterations of Algorithm 1;
+ * no phase-offset fit) with the caller's arrays, all of which must be device
+ * memory: masks complex64 [J][N], y float32 [M][J][N], T_out complex64 [M][N],
+ * row_status / row_iters int32 [M] and row_loss float32 [M] (each may be NULL).
+ * opt: NULL for the defaults; opt->workspace_limit and use_graph are ignored.
+ * stream: cudaStream_t, NULL for the legacy default stream.
+ *
+ * Its only scratch (a row work counter and the FFT twiddle table) lives in
+ * one static 64 KiB device array that every GPU which loads the library holds
+ * until the process exits.  Limits: N a power of two in 64..4096, J <= 8,
+ * 1 <= opt->m <= 8; larger sizes return TMR_ERR_UNSUPPORTED with a message.
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  The first
+ * call on a device looks up the array's device address (once per device, with
+ * that device current); make that first call before any stream capture.
+ * Every call on a device shares the array and rewrites it (the counter is
+ * cleared, the table refilled), so calls whose work overlaps on the GPU -- on
+ * different streams, or from different threads -- race and must be ordered
+ * by the caller.  Asynchronous on `stream`; errors via tmr_last_error(). */
+tmr_status tmr_retrieve_rows_static(int N, int M, int J, const void *masks, const float *y,
+                                    int iters, const tmr_options *opt, void *T_out,
+                                    int *row_status, int *row_iters, float *row_loss,
+                                    void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -63,6 +63,8 @@ def _load():
         "tmr_last_error": ([], ctypes.c_char_p),
         "tmr_workspace_bytes": ([H], ctypes.c_size_t),
         "tmr_destroy": ([H], None),
+        "tmr_retrieve_rows_static": ([ip, ip, ip, vp, fp, ip, ctypes.POINTER(tmr_options), vp, vp,
+                                      vp, fp, vp], ctypes.c_int),
     }
     for name, (args, res) in sigs.items():
         f = getattr(L, name)
@@ -232,3 +234,18 @@ def tmr_workspace_bytes(h: Handle) -> int:
 
 def tmr_destroy(h: Handle):
     h.close()
+
+
+def tmr_retrieve_rows_static(N, M, J, masks, y, iters, opt, T_out, row_status=None,
+                             row_iters=None, row_loss=None, stream=None):
+    """Allocation-free per-row retrieval (device arrays only, no handle)."""
+    if opt is None:
+        opt = tmr_default_options()
+    elif isinstance(opt, dict):
+        opt = tmr_default_options(**opt)
+    _check(lib.tmr_retrieve_rows_static(
+        int(N), int(M), int(J), _ptr(masks, "c64", J * N, "masks"),
+        _ptr(y, "f32", M * J * N, "y"), int(iters), ctypes.byref(opt),
+        _ptr(T_out, "c64", M * N, "T_out"), _ptr(row_status, "i32", M, "row_status"),
+        _ptr(row_iters, "i32", M, "row_iters"), _ptr(row_loss, "f32", M, "row_loss"),
+        ctypes.c_void_p(stream) if stream else None))

@@ -20,12 +20,20 @@
 using namespace tmr;
 
 namespace {
+thread_local char g_last_error_buf[512];
+}
 
-thread_local std::string g_last_error;
+void tmr::set_last_error(const char *msg)
+{
+    if (!msg) msg = "";
+    snprintf(g_last_error_buf, sizeof(g_last_error_buf), "%s", msg);
+}
+
+namespace {
 
 tmr_status fail(tmr_status st, const std::string &msg)
 {
-    g_last_error = msg;
+    tmr::set_last_error(msg.c_str());
     return st;
 }
 
@@ -163,7 +171,7 @@ void tmr_default_options(tmr_options *o)
     o->workspace_limit = 0;
 }
 
-const char *tmr_last_error(void) { return g_last_error.c_str(); }
+const char *tmr_last_error(void) { return g_last_error_buf; }
 
 size_t tmr_workspace_bytes(const tmr_handle *h) { return h ? h->held : 0; }
 
@@ -184,7 +192,7 @@ void tmr_destroy(tmr_handle *h)
 tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
                       const tmr_defocus_op *dop, const tmr_options *opt, void *stream)
 {
-    g_last_error.clear();
+    tmr::set_last_error("");
     if (!out) return fail(TMR_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (N <= 0 || M < 0 || J <= 0) return fail(TMR_ERR_INVALID_ARG, "N, J must be positive and M >= 0");
@@ -283,7 +291,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
 
 tmr_status tmr_forward(tmr_handle *h, const void *T, float *Y)
 {
-    g_last_error.clear();
+    tmr::set_last_error("");
     if (!h || !T || !Y) return fail(TMR_ERR_INVALID_ARG, "NULL argument");
     const size_t MN = (size_t)h->M * h->N, MK = MN * h->J;
     void *dT, *dY;
@@ -301,7 +309,7 @@ tmr_status tmr_forward(tmr_handle *h, const void *T, float *Y)
 
 tmr_status tmr_grad(tmr_handle *h, const void *T, const float *Y, float *loss, void *G)
 {
-    g_last_error.clear();
+    tmr::set_last_error("");
     if (!h || !T || !Y) return fail(TMR_ERR_INVALID_ARG, "NULL argument");
     const size_t MN = (size_t)h->M * h->N, MK = MN * h->J;
     void *dT, *dY, *dL = nullptr, *dG = nullptr;
@@ -353,7 +361,7 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
                                 int iters, void *T_out, int *row_status, int *row_iters,
                                 float *row_loss)
 {
-    g_last_error.clear();
+    tmr::set_last_error("");
     if (!h || !y || !T_out) return fail(TMR_ERR_INVALID_ARG, "NULL argument");
     if (iters < 0) return fail(TMR_ERR_INVALID_ARG, "iters must be >= 0");
     const bool fit = y_def != nullptr;
@@ -434,7 +442,7 @@ tmr_status tmr_retrieve_from(tmr_handle *h, const void *T_init, const float *y, 
 
 tmr_status tmr_defocus_forward(tmr_handle *h, const void *T, float *Y_def)
 {
-    g_last_error.clear();
+    tmr::set_last_error("");
     if (!h || !T || !Y_def) return fail(TMR_ERR_INVALID_ARG, "NULL argument");
     if (!h->has_defocus) return fail(TMR_ERR_UNSUPPORTED, "handle has no defocus operator");
     const size_t MN = (size_t)h->M * h->N;
@@ -454,7 +462,7 @@ tmr_status tmr_defocus_forward(tmr_handle *h, const void *T, float *Y_def)
 
 tmr_status tmr_defocus_fit(tmr_handle *h, const void *T_est, const float *y_def, double *phi, void *T_out)
 {
-    g_last_error.clear();
+    tmr::set_last_error("");
     if (!h || !T_est || !y_def) return fail(TMR_ERR_INVALID_ARG, "NULL argument");
     if (!h->has_defocus) return fail(TMR_ERR_UNSUPPORTED, "handle has no defocus operator");
     const size_t MN = (size_t)h->M * h->N;
@@ -478,7 +486,7 @@ tmr_status tmr_defocus_fit(tmr_handle *h, const void *T_est, const float *y_def,
 
 tmr_status tmr_sync(tmr_handle *h, double timeout_s)
 {
-    g_last_error.clear();
+    tmr::set_last_error("");
     if (!h) return fail(TMR_ERR_INVALID_ARG, "NULL handle");
     const auto t0 = std::chrono::steady_clock::now();
     while (true) {
