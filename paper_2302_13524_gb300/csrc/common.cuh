@@ -93,9 +93,9 @@ __device__ __forceinline__ float2 philox_cnormal(unsigned long long seed, uint32
 {
     const uint4 o = philox4x32_10(make_uint4(n, row, 0u, 0u),
                                   make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-    const double u0 = ((double)o.x + 0.5) * 0x1p-32;
-    const float u1 = (float)(((double)o.y + 0.5) * 0x1p-32);
-    const float rho = sqrtf(-2.0f * (float)log(u0));
+    const float u0 = fmaf((float)o.x, 0x1p-32f, 0x1p-33f);  // (x + 1/2) 2^-32, rounded to FP32
+    const float u1 = fmaf((float)o.y, 0x1p-32f, 0x1p-33f);
+    const float rho = sqrtf(-2.0f * logf(u0));
     float s, c;
     sincospif(2.0f * u1, &s, &c);
     return make_float2(rho * c, rho * s);

@@ -158,4 +158,66 @@ __device__ __forceinline__ void block_fft(float2 (&v)[N / T], float2 *buf, const
     fft_passes<N, T, SIGN, 0>(v, buf, tw, tid);
 }
 
+
+// ---------------------------------------------------------------------------
+// Variant whose last pass takes its twiddles from a per-thread base instead of
+// the table: in the last pass (Ns = N/R, R = E) butterfly b = tid has
+// j = tid, so its twiddles are w^r with w = exp(-2 pi i tid / N); the thread
+// keeps w in two registers (wb, made once) and forms the powers by complex
+// multiplication.  The table then only needs passes 1 .. P-2 (tw_off(P-1)
+// entries), which is what lets the solver keep it in shared memory cheaply.
+template <int N, int T>
+struct FftSmall {
+    using Pl = FftPlan<N, N / T>;
+    static constexpr int TW_SMALL = Pl::P >= 2 ? Pl::tw_off(Pl::P - 1) : 0;
+};
+
+template <int R, int SIGN>
+__device__ __forceinline__ void twiddle_powers(float2 (&x)[R], float2 wb)
+{
+    if constexpr (SIGN > 0) wb.y = -wb.y;
+    if constexpr (R >= 2) x[1] = cmul(x[1], wb);
+    if constexpr (R >= 4) {
+        const float2 w2 = cmul(wb, wb), w3 = cmul(w2, wb);
+        x[2] = cmul(x[2], w2);
+        x[3] = cmul(x[3], w3);
+        if constexpr (R >= 8) {
+            const float2 w4 = cmul(w2, w2);
+            x[4] = cmul(x[4], w4);
+            x[5] = cmul(x[5], cmul(w4, wb));
+            x[6] = cmul(x[6], cmul(w4, w2));
+            x[7] = cmul(x[7], cmul(w4, w3));
+        }
+    }
+}
+
+template <int N, int T, int SIGN, int p>
+__device__ __forceinline__ void fft_passes_rb(float2 (&v)[N / T], float2 *buf, const float2 *tw, float2 wb,
+                                              int tid)
+{
+    using Pl = FftPlan<N, N / T>;
+    if constexpr (p < Pl::P - 1) {
+        fft_pass<N, T, Pl::radix(p), Pl::ns(p), Pl::tw_off(p), SIGN, false>(v, buf, tw, tid);
+        fft_passes_rb<N, T, SIGN, p + 1>(v, buf, tw, wb, tid);
+    } else if constexpr (p == Pl::P - 1) {
+        constexpr int R = Pl::radix(p), E = N / T;
+        static_assert(R == E, "last pass must use the full radix");
+        float2 x[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) x[r] = v[r];
+        if constexpr (Pl::ns(p) > 1) twiddle_powers<R, SIGN>(x, wb);
+        dft_small<R, SIGN>(x);
+#pragma unroll
+        for (int q = 0; q < R; q++) v[q] = x[q];
+    }
+}
+
+// As block_fft; wb = exp(-2 pi i tid / N) for this thread.
+template <int N, int T, int SIGN>
+__device__ __forceinline__ void block_fft_rb(float2 (&v)[N / T], float2 *buf, const float2 *tw, float2 wb,
+                                             int tid)
+{
+    fft_passes_rb<N, T, SIGN, 0>(v, buf, tw, wb, tid);
+}
+
 }  // namespace tmr

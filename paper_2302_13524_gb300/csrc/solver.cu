@@ -3,29 +3,39 @@
 // One cluster of J CTAs solves one TM row at a time; rows come from an atomic
 // work counter, so a launch of (clusters x J) CTAs walks the whole matrix.
 // CTA j owns mask j:
-//   registers: z_j = F(d_j .* t) (the current fields), y_j, and w_j = F(d_j .* p)
-//              in the FFT's thread-strided layout -- never leave the chip;
-//   shared:    d_j, the twiddle table, the FFT exchange buffer, and a 1/J
-//              slice of every length-N vector: t, g, p and the L-BFGS pairs.
-// Length-N vectors are all-gathered and sums over masks are reduced through
-// distributed shared memory (DSMEM) between the CTAs of the cluster.
+//   registers: d_j, z_j = F(d_j .* t) (the current fields), y_j and
+//              w_j = F(d_j .* p), all in the FFT's thread-strided layout, and the
+//              twiddle base of the last FFT pass;
+//   shared:    the FFT exchange buffer and the small-pass twiddles, a 1/J slice
+//              of every length-N vector (t, g and the L-BFGS pairs), and two
+//              receive areas.
+// Exchanges between the CTAs of a cluster are pushes: a CTA stores its data
+// into its peers' shared memory (distributed shared memory) and then arrives at
+// the cluster barrier, so that after the barrier every read is local.
+//   X[N]      full direction p (or t), assembled from the owners' slices; once
+//             a CTA has read X into registers, X serves as its FFT exchange
+//             buffer until the next gather;
+//   Y[J][SL]  the J masks' adjoint outputs for my slice (summed into g);
+//   part[2][J][32]  reduction partials (two buffers used alternately).
 //
-// One iteration (Algorithm 1: f and its gradient by FFT, L-BFGS step):
-//   A  direction p = -H g on the slice from the compact L-BFGS form
-//      H = gamma I + [S gamma Y] M [S^T; gamma Y^T]   (Byrd, Nocedal & Schnabel
-//      1994; Nocedal & Wright eq. 7.24), coefficients from FP64 Gram scalars;
-//   B1 cluster barrier, gather p;
-//   C  w_j = F(d_j .* p)                                   (J FFTs per row)
-//   D  quartic line-search sums of phi(a) = f(t + a p) = sum_i (r_i - 2 a Re(conj z_i w_i)
-//      - a^2 |w_i|^2)^2; B2; exact minimiser from the cubic phi'(a) = 0 (FP64);
-//   E  t += a p, z += a w, r = y - |z|^2, u = z .* r (registers);
-//   F  v_j = conj(d_j) .* F^H u_j                          (J inverse FFTs)
-//   B3; g = -4 sum_j v_j on the slice (Eq. derivative); new pair s = a p,
-//      y = g_new - g_old;
-//   G  all Gram dot products of the new vectors with the history in one batched
-//      reduction; B4.
-// Four cluster barriers and two FFT batches per iteration; the f and gradient
-// of Algorithm 1 are those of the iterate produced by the previous step.
+// One iteration (Algorithm 1: f and its gradient by FFT, then the L-BFGS step):
+//   A  p = -H g on my slice from the compact L-BFGS form
+//      H = gamma I + [S gamma Y] M [S^T; gamma Y^T] (Byrd, Nocedal & Schnabel
+//      1994), coefficients from the Gram scalars; push the slice into X.  B1.
+//   C  w_j = F(d_j .* p)                                     (J FFTs per row)
+//   D  sums of the quartic phi(a) = f(t + a p) = sum_i (r_i - 2 a Re(conj z_i w_i)
+//      - a^2 |w_i|^2)^2; push.  B2.  Exact minimiser from phi'(a) = 0.
+//   E  t += a p, z += a w, r = y - |z|^2, u = z .* r (registers)
+//   F  v_j = conj(d_j) .* F^H u_j; push each slice to its owner.  B3.
+//   G  g = -4 sum_j v_j on my slice (Eq. derivative), pair s = a p,
+//      y = g_new - g_old, every Gram dot product in one batched reduction.  B4.
+// Four cluster barriers and two FFT batches per iteration.
+//
+// Buffer reuse across barriers: X is read (step C) before its reader arrives at
+// B2 and written again only after B4; Y is written after B2 and read before
+// B4; a part buffer is read right after the barrier that completes it and
+// rewritten two reductions later.  No CTA touches a peer's shared memory after
+// the barrier that hands out the final (past-the-end) row, so CTAs may exit.
 #include <cooperative_groups.h>
 
 #include <cmath>
@@ -41,194 +51,218 @@ namespace tmr {
 enum { ROW_MAXITER = 0, ROW_CONVERGED = 1, ROW_ZERO = 2, ROW_NUMERIC = 3 };
 enum { INIT_RANDOM = 0, INIT_BP = 1, INIT_SPECTRAL = 2 };
 
-constexpr int kSlots = kMaxMem + 1;  // ring of m+1 slots: the new pair never overwrites a live one
-constexpr int kMaxNV = 4 * kSlots + 4;
+constexpr int kSlots = kMaxMem + 1;  // m+1 slots: the new pair never overwrites a live one
+constexpr int kParts = 40;           // reduction width (values per CTA and reduction)
+static_assert(4 * kSlots + 3 <= kParts, "reduction width");
 
-// FP64 L-BFGS scalars, replicated in every CTA of the cluster (each CTA computes
-// them from identical reduced sums, so they agree bit for bit).
+// L-BFGS scalars, replicated in every CTA of the cluster: each CTA computes
+// them from identical sums added in the same order, so they agree bit for bit
+// and every CTA takes the same branches.  FP32 like the rest of the path (the
+// FP64 pipe of this part is a small fraction of its FP32 rate, and these
+// scalars sit on the critical path of every iteration).
 struct Gram {
-    double SY[kSlots][kSlots];  // s_a^T y_b for slot a no newer than slot b
-    double YY[kSlots][kSlots];  // y_a^T y_b, same convention
-    double Sg[kSlots], Yg[kSlots];
-    double c1[kSlots], c2[kSlots];  // direction coefficients per slot
-    double gamma, gg, f, f_prev;
-    double alpha;
+    float SY[kSlots][kSlots];  // s_a^T y_b for slot a no newer than slot b
+    float YY[kSlots][kSlots];  // y_a^T y_b, same convention
+    float rD[kSlots];          // 1 / s_a^T y_a
+    float Sg[kSlots], Yg[kSlots];
+    float c1[kSlots], c2[kSlots];  // direction coefficients per slot (c2 includes gamma)
+    float gamma, gg, f, sumy, alpha;
+    float red[kParts];  // the last cluster-wide sums
     int order[kSlots];  // live slots, oldest first
-    int np;             // number of live pairs
-    int newslot;
-    int status, done, stop, early;
+    int np, newslot;
+    int status, done, stop, early, row;
 };
 
-__device__ __forceinline__ double quartic_val(const double *c, double a)
-{
-    return (((c[4] * a + c[3]) * a + c[2]) * a + c[1]) * a + c[0];
-}
-
-// Global minimiser over the real line of c0 + c1 a + ... + c4 a^4 (c4 > 0),
-// among the real roots of the cubic derivative; ties go to the smallest
+// Global minimiser of phi(a) = c0 + c1 a + c2 a^2 + c3 a^3 + c4 a^4 (c4 > 0)
+// over the real line.  phi' = g(a) = c1 + 2 c2 a + 3 c3 a^2 + 4 c4 a^3 rises at
+// both ends; with three real roots the middle one is a local maximum of phi,
+// so the minimiser is the leftmost or the rightmost root.  The critical
+// points r1 < r2 of g (roots of a quadratic) say which case holds; each
+// needed root is bracketed (expanding outwards from a point of known sign)
+// and found by Newton steps kept inside the bracket.  Ties go to the smallest
 // positive root.  c4 == 0 means w == 0: no step.
-__device__ double quartic_argmin(const double *c)
+__device__ float quartic_argmin(const float *c)
 {
-    if (!(c[4] > 0.0)) {
-        if (c[2] > 0.0 && c[3] == 0.0) return -c[1] / (2.0 * c[2]);
-        return 0.0;
+    const float c1 = c[1], c2 = c[2], c3 = c[3], c4 = c[4];
+    if (!(c4 > 0.f)) {
+        if (c2 > 0.f && c3 == 0.f) return -c1 / (2.f * c2);
+        return 0.f;
     }
-    const double B = 3.0 * c[3] / (4.0 * c[4]), C = 2.0 * c[2] / (4.0 * c[4]), D = c[1] / (4.0 * c[4]);
-    const double p = C - B * B / 3.0;
-    const double q = 2.0 * B * B * B / 27.0 - B * C / 3.0 + D;
-    double roots[3];
-    int nr = 0;
-    const double disc = q * q / 4.0 + p * p * p / 27.0;
-    if (disc > 0.0) {
-        const double sq = sqrt(disc);
-        const double u = cbrt(-q / 2.0 + (q > 0.0 ? -sq : sq));
-        const double x = (u != 0.0) ? u - p / (3.0 * u) : 0.0;
-        roots[nr++] = x - B / 3.0;
-    } else if (p == 0.0) {
-        roots[nr++] = -B / 3.0;
-    } else {
-        const double m = 2.0 * sqrt(-p / 3.0);
-        double arg = 3.0 * q / (p * m);
-        arg = arg > 1.0 ? 1.0 : (arg < -1.0 ? -1.0 : arg);
-        const double th = acos(arg) / 3.0;
-        for (int k = 0; k < 3; k++) roots[nr++] = m * cos(th - 2.0 * M_PI * k / 3.0) - B / 3.0;
-    }
-    double best = 0.0, bestv = 0.0;
-    bool have = false;
-    for (int k = 0; k < nr; k++) {
-        double a = roots[k];
-        for (int it = 0; it < 3; it++) {  // Newton polish on phi'
-            const double f1 = ((4.0 * c[4] * a + 3.0 * c[3]) * a + 2.0 * c[2]) * a + c[1];
-            const double f2 = (12.0 * c[4] * a + 6.0 * c[3]) * a + 2.0 * c[2];
-            if (f2 == 0.0) break;
-            const double na = a - f1 / f2;
-            if (!isfinite(na)) break;
+    auto g = [&](float a) { return fmaf(fmaf(fmaf(4.f * c4, a, 3.f * c3), a, 2.f * c2), a, c1); };
+    auto dg = [&](float a) { return fmaf(fmaf(12.f * c4, a, 6.f * c3), a, 2.f * c2); };
+    auto phi = [&](float a) { return a * fmaf(fmaf(fmaf(c4, a, c3), a, c2), a, c1); };
+    // a root in [lo, hi] with g(lo) <= 0 <= g(hi)
+    auto solve = [&](float lo, float hi, float glo, float ghi) {
+        float a = (ghi != glo) ? lo - glo * (hi - lo) / (ghi - glo) : 0.5f * (lo + hi);
+        if (!(a >= lo && a <= hi)) a = 0.5f * (lo + hi);
+        for (int it = 0; it < 60; it++) {
+            const float ga = g(a);
+            if (ga == 0.f) break;
+            if (ga < 0.f) lo = a;
+            else hi = a;
+            const float d = dg(a);
+            float na = (d != 0.f) ? a - ga / d : 0.5f * (lo + hi);
+            if (!(na > lo && na < hi)) na = 0.5f * (lo + hi);
+            if (na == a || hi - lo <= 4e-7f * fmaxf(fabsf(lo), fabsf(hi))) {
+                a = na;
+                break;
+            }
             a = na;
         }
-        const double v = quartic_val(c, a);
-        if (!have || v < bestv || (v == bestv && a > 0.0 && (best <= 0.0 || a < best))) {
-            best = a;
+        return a;
+    };
+    // walk from x0 (sign of g known) in direction dir until g changes sign
+    auto bracket = [&](float x0, float dir, float &lo, float &hi, float &glo, float &ghi) {
+        const float g0 = g(x0);
+        float step = fmaxf(1.f, fabsf(x0));
+        float x = x0, gx = g0;
+        for (int it = 0; it < 80; it++) {
+            const float xn = x + dir * step;
+            const float gn = g(xn);
+            if ((dir > 0.f && gn >= 0.f) || (dir < 0.f && gn <= 0.f)) {
+                if (dir > 0.f) { lo = x; glo = gx; hi = xn; ghi = gn; }
+                else { lo = xn; glo = gn; hi = x; ghi = gx; }
+                return;
+            }
+            x = xn;
+            gx = gn;
+            step *= 2.f;
+        }
+        lo = hi = x;
+        glo = ghi = gx;
+    };
+    float cand[2];
+    int nc = 0;
+    const float qa = 12.f * c4, qb = 6.f * c3, qc = 2.f * c2;
+    const float disc = qb * qb - 4.f * qa * qc;
+    bool three = false;
+    float r1 = 0.f, r2 = 0.f;
+    if (disc > 0.f) {
+        const float sq = sqrtf(disc);
+        const float q = -0.5f * (qb + (qb >= 0.f ? sq : -sq));
+        r1 = q / qa;
+        r2 = (q != 0.f) ? qc / q : r1;
+        if (r1 > r2) {
+            const float t = r1;
+            r1 = r2;
+            r2 = t;
+        }
+        three = g(r1) >= 0.f && g(r2) <= 0.f;
+    }
+    float lo, hi, glo, ghi;
+    if (three) {
+        bracket(r1, -1.f, lo, hi, glo, ghi);
+        cand[nc++] = solve(lo, hi, glo, ghi);
+        bracket(r2, +1.f, lo, hi, glo, ghi);
+        cand[nc++] = solve(lo, hi, glo, ghi);
+    } else {
+        const float g0 = g(0.f);
+        if (g0 == 0.f) return 0.f;
+        bracket(0.f, g0 < 0.f ? +1.f : -1.f, lo, hi, glo, ghi);
+        cand[nc++] = solve(lo, hi, glo, ghi);
+    }
+    float best = cand[0], bestv = phi(cand[0]);
+    for (int k = 1; k < nc; k++) {
+        const float v = phi(cand[k]);
+        if (v < bestv || (v == bestv && cand[k] > 0.f && (best <= 0.f || cand[k] < best))) {
+            best = cand[k];
             bestv = v;
-            have = true;
         }
     }
     return best;
 }
 
-// Compact-form coefficients (run by one thread): p = -(gamma g + sum c1_i s_i
-// + gamma sum c2_i y_i).  Falls back to p = -g (and clears the history) when
-// there is no pair or the result is not a descent direction.
+// Compact-form coefficients (one thread): p = -(gamma g + sum c1_i s_i +
+// sum c2_i y_i) with c2 already scaled by gamma.  Falls back to p = -g
+// (clearing the history) when there is no pair or the result is not a descent
+// direction.
 __device__ void lbfgs_coefficients(Gram &G)
 {
     const int np = G.np;
-    for (int a = 0; a < kSlots; a++) G.c1[a] = G.c2[a] = 0.0;
+    for (int a = 0; a < kSlots; a++) G.c1[a] = G.c2[a] = 0.f;
     if (np > 0) {
         const int nw = G.order[np - 1];
-        const double gamma = G.SY[nw][nw] / G.YY[nw][nw];
-        double av[kSlots], bv[kSlots], c2[kSlots], c1[kSlots];
-        for (int i = 0; i < np; i++) {
-            av[i] = G.Sg[G.order[i]];
-            bv[i] = G.Yg[G.order[i]];
-        }
-        // R c2 = -a (R upper triangular in age order, R_ij = s_i^T y_j, i <= j)
+        const float gamma = G.SY[nw][nw] / G.YY[nw][nw];
+        float c2[kSlots], c1[kSlots];
+        // R c2 = -S^T g  (R upper triangular in age order, R_ij = s_i^T y_j, i <= j)
         for (int i = np - 1; i >= 0; i--) {
-            double s = -av[i];
-            for (int j = i + 1; j < np; j++) s -= G.SY[G.order[i]][G.order[j]] * c2[j];
-            c2[i] = s / G.SY[G.order[i]][G.order[i]];
+            const int oi = G.order[i];
+            float s = -G.Sg[oi];
+            for (int j = i + 1; j < np; j++) s = fmaf(-G.SY[oi][G.order[j]], c2[j], s);
+            c2[i] = s * G.rD[oi];
         }
-        // R^T c1 = -(D + gamma Y^T Y) c2 - gamma b
+        // R^T c1 = -(D + gamma Y^T Y) c2 - gamma Y^T g
         for (int i = 0; i < np; i++) {
-            double rhs = -G.SY[G.order[i]][G.order[i]] * c2[i] - gamma * bv[i];
+            const int oi = G.order[i];
+            float yc = 0.f;
             for (int j = 0; j < np; j++) {
                 const int a = G.order[i < j ? i : j], b = G.order[i < j ? j : i];
-                rhs -= gamma * G.YY[a][b] * c2[j];
+                yc = fmaf(G.YY[a][b], c2[j], yc);
             }
-            for (int j = 0; j < i; j++) rhs -= G.SY[G.order[j]][G.order[i]] * c1[j];
-            c1[i] = rhs / G.SY[G.order[i]][G.order[i]];
+            float rhs = -G.SY[oi][oi] * c2[i] - gamma * (G.Yg[oi] + yc);
+            for (int j = 0; j < i; j++) rhs = fmaf(-G.SY[G.order[j]][oi], c1[j], rhs);
+            c1[i] = rhs * G.rD[oi];
         }
-        double pg = gamma * G.gg;
-        for (int i = 0; i < np; i++) pg += c1[i] * av[i] + gamma * c2[i] * bv[i];
-        // <p, g> = -pg must be negative
-        if (pg > 0.0 && isfinite(pg)) {
+        float pg = gamma * G.gg;  // <g, H g> = -<p, g>
+        for (int i = 0; i < np; i++) pg += c1[i] * G.Sg[G.order[i]] + gamma * c2[i] * G.Yg[G.order[i]];
+        if (pg > 0.f && isfinite(pg)) {
             G.gamma = gamma;
             for (int i = 0; i < np; i++) {
                 G.c1[G.order[i]] = c1[i];
-                G.c2[G.order[i]] = c2[i];
+                G.c2[G.order[i]] = gamma * c2[i];
             }
             return;
         }
         G.np = 0;
     }
-    G.gamma = 1.0;
+    G.gamma = 1.f;
 }
 
 template <int N>
 struct SolverCfg {
     static constexpr int NT = fft_threads(N);
     static constexpr int E = N / NT;
-    static constexpr int TWN = FftPlan<N, E>::TW_SIZE;
     static constexpr int NW = NT / 32;
-};
-
-// Shared-memory carve-up (dynamic part).  SL = ceil(N / J) slice length.
-template <int N>
-struct SmemLayout {
-    float2 *buf, *tw, *dm, *ps, *ts, *gs, *hs;  // hs: S slots then Y slots, each SL
-    float *red, *pub;  // pub: two buffers of kMaxNV, used alternately
-    Gram *gram;
-    int *rowslot;
+    static constexpr int TWS = FftSmall<N, NT>::TW_SMALL;
 };
 
 template <int N>
 __host__ __device__ size_t solver_smem(int J, int m)
 {
     using C = SolverCfg<N>;
-    const int SL = (N + J - 1) / J;
-    size_t f2 = (size_t)fft_buf_len(N) + C::TWN + N + 3 * (size_t)SL + 2 * (size_t)(m + 1) * SL;
+    const size_t SL = (N + J - 1) / J;
+    size_t f2 = (size_t)fft_buf_len(N) /*X and FFT exchange*/ + C::TWS + (size_t)J * SL /*Y*/ +
+                2 * SL /*t, g*/ + 2 * (size_t)(m + 1) * SL /*pairs*/;
     size_t bytes = f2 * sizeof(float2);
-    bytes += sizeof(float) * (kMaxNV * C::NW + 2 * kMaxNV);
+    bytes += sizeof(float) * ((size_t)kParts * C::NW + 2 * (size_t)J * kParts);
     bytes = (bytes + 15) & ~(size_t)15;
-    bytes += sizeof(Gram) + 16;
-    return bytes;
+    return bytes + sizeof(Gram);
+}
+
+// Block sums of NV per-thread values: value k ends in out[k], written by
+// thread k mod blockDim.x.  Partials are added warp by warp in a fixed order.
+template <int NV>
+__device__ __forceinline__ void block_partials(float (&v)[NV], float *red, float *out, int nw)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        const float s = warp_sum(v[k]);
+        if (lane == 0) red[k * nw + warp] = s;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < NV; k += blockDim.x) {  // NV may exceed the block size
+        float s = 0.f;
+        for (int w = 0; w < nw; w++) s += red[k * nw + w];
+        out[k] = s;
+    }
 }
 
 template <int N>
-__device__ __forceinline__ SmemLayout<N> carve(unsigned char *base, int J, int m)
+__global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 : 1) k_solver(SolverParams P)
 {
     using C = SolverCfg<N>;
-    const int SL = (N + J - 1) / J;
-    SmemLayout<N> L;
-    float2 *f = reinterpret_cast<float2 *>(base);
-    L.buf = f;
-    f += fft_buf_len(N);
-    L.tw = f;
-    f += C::TWN;
-    L.dm = f;
-    f += N;
-    L.ps = f;
-    f += SL;
-    L.ts = f;
-    f += SL;
-    L.gs = f;
-    f += SL;
-    L.hs = f;
-    f += 2 * (size_t)(m + 1) * SL;
-    float *fl = reinterpret_cast<float *>(f);
-    L.red = fl;
-    fl += kMaxNV * C::NW;
-    L.pub = fl;
-    fl += 2 * kMaxNV;
-    size_t off = (reinterpret_cast<unsigned char *>(fl) - base + 15) & ~(size_t)15;
-    L.gram = reinterpret_cast<Gram *>(base + off);
-    L.rowslot = reinterpret_cast<int *>(base + off + sizeof(Gram));
-    return L;
-}
-
-template <int N>
-__global__ void __launch_bounds__(SolverCfg<N>::NT) k_solver(SolverParams P)
-{
-    using C = SolverCfg<N>;
-    constexpr int NT = C::NT, E = C::E;
+    constexpr int NT = C::NT, E = C::E, NW = C::NW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cg::cluster_group cluster = cg::this_cluster();
     const int J = P.J, m = P.m, M = P.M;
@@ -236,96 +270,112 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT) k_solver(SolverParams P)
     const int tid = threadIdx.x;
     const int SL = (N + J - 1) / J;
     const int lo = (jr * N) / J, hi = ((jr + 1) * N) / J;  // my slice [lo, hi)
+    const int nmine = hi - lo;
     const size_t K = (size_t)J * N;
-    SmemLayout<N> L = carve<N>(smem_raw, J, m);
-    float2 *S_slot = L.hs;                                  // S slot a at S_slot + a*SL
-    float2 *Y_slot = L.hs + (size_t)(m + 1) * SL;           // Y slot a at Y_slot + a*SL
-    Gram &G = *L.gram;
+    const bool even = (N % J) == 0;  // slices of equal length SL = N / J
 
-    // slice owner of index n: the largest o with (o N) / J <= n
+    // ---- shared memory ----
+    float2 *X = reinterpret_cast<float2 *>(smem_raw);
+    float2 *buf = X;  // exchange buffer of every FFT: X is free once gathered
+    float2 *tws = X + fft_buf_len(N);
+    float2 *Yr = tws + C::TWS;  // [J][SL]
+    float2 *ts = Yr + (size_t)J * SL;
+    float2 *gs = ts + SL;
+    float2 *Ss = gs + SL;  // slot a at Ss + a*SL
+    float2 *Ys = Ss + (size_t)(m + 1) * SL;
+    float *red = reinterpret_cast<float *>(Ys + (size_t)(m + 1) * SL);
+    float *part = red + kParts * NW;  // [2][J][kParts]
+    Gram &G = *reinterpret_cast<Gram *>(
+        smem_raw + ((reinterpret_cast<unsigned char *>(part + 2 * J * kParts) - smem_raw + 15) &
+                    ~(size_t)15));
+
+    for (int i = tid; i < C::TWS; i += NT) tws[i] = P.tw[i];
+    float2 dm[E];
+#pragma unroll
+    for (int e = 0; e < E; e++) dm[e] = P.masks[(size_t)jr * N + tid + e * NT];
+    float2 wb;
+    {
+        double s, c;
+        sincospi(-2.0 * (double)tid / (double)N, &s, &c);
+        wb = make_float2((float)c, (float)s);
+    }
     auto owner = [&](int n) {
+        if (even) return n / SL;
         int o = (int)(((long long)n * J) / N);
         while (o + 1 < J && ((o + 1) * N) / J <= n) o++;
         while (o > 0 && (o * N) / J > n) o--;
         return o;
     };
+    cluster.sync();  // every CTA of the cluster runs before anyone touches its shared memory
 
-    for (int i = tid; i < C::TWN; i += NT) L.tw[i] = P.tw[i];
-    for (int i = tid; i < N; i += NT) L.dm[i] = P.masks[(size_t)jr * N + i];
-    __syncthreads();
-
-    // gather one thread-strided vector x[e] = dm[n] * v[n] from the peers' slices
-    auto gather_masked = [&](float2 (&x)[E], float2 *slice_buf) {
+    // Cluster-wide sum of nv per-thread values: the block sums are written to
+    // part[sel][jr][:] of every CTA (own copy local, peers' by DSMEM stores),
+    // one barrier, then thread 0 adds the J partials in rank order into
+    // G.red (the caller synchronises before reading it).
+    int sel = 0;
+    auto cluster_sum = [&](auto &vals, int nv) {
+        float *pb = part + sel * J * kParts;
+        sel ^= 1;
+        block_partials(vals, red, pb + jr * kParts, NW);
+        for (int k = tid; k < nv; k += NT) {  // the same thread wrote value k above
+            const float s = pb[jr * kParts + k];
+            for (int o = 0; o < J; o++)
+                if (o != jr) cluster.map_shared_rank(pb, o)[jr * kParts + k] = s;
+        }
+        cluster.sync();
+        if (tid == 0) {
+            for (int k = 0; k < nv; k++) {
+                float s = 0.f;
+                for (int o = 0; o < J; o++) s += pb[o * kParts + k];
+                G.red[k] = s;
+            }
+        }
+    };
+    // my slice (length nmine) into X of every CTA
+    auto push_slice_to_X = [&](const float2 *src) {
+        for (int i = tid; i < nmine; i += NT) {
+            const float2 v = src[i];
+            for (int o = 0; o < J; o++) cluster.map_shared_rank(X, o)[lo + i] = v;
+        }
+    };
+    // thread-strided natural-order vector v to the owners' Y[jr][:]
+    auto push_to_owners = [&](const float2 (&v)[E]) {
 #pragma unroll
         for (int e = 0; e < E; e++) {
             const int n = tid + e * NT;
             const int o = owner(n);
-            const int olo = (o * N) / J;
-            const float2 *rp = cluster.map_shared_rank(slice_buf, o);
-            x[e] = cmul(rp[n - olo], L.dm[n]);
+            cluster.map_shared_rank(Yr, o)[(size_t)jr * SL + (n - (o * N) / J)] = v[e];
         }
     };
-    // publish NV block sums in L.pub, barrier, and return the cluster totals in
-    // FP64 summed in rank order (identical in every CTA)
-    // The two publication buffers alternate: a peer may still be reading the
-    // previous reduction's sums when this CTA publishes the next ones, but not
-    // the ones before that (each reduction ends in a cluster barrier).
-    int pub_sel = 0;
-    auto cluster_sum = [&](auto &vals, double *out, int nv) {
-        float *pb = L.pub + pub_sel * kMaxNV;
-        pub_sel ^= 1;
-        block_sum(vals, L.red, pb);
-        cluster.sync();
-        for (int k = 0; k < nv; k++) out[k] = 0.0;
-        for (int o = 0; o < J; o++) {
-            const float *rp = cluster.map_shared_rank(pb, o);
-            for (int k = 0; k < nv; k++) out[k] += (double)rp[k];
-        }
-    };
-    // v_j = conj(d_j) .* F^H u into L.buf (natural order, unpadded), barrier,
-    // and return sum_j v_j on my slice via the callback
-    auto adjoint_to_buf = [&](float2 (&u)[E]) {
-        block_fft<N, NT, +1>(u, L.buf, L.tw, tid);
-        __syncthreads();
-#pragma unroll
-        for (int e = 0; e < E; e++) {
-            const int n = tid + e * NT;
-            L.buf[n] = cmulc(u[e], L.dm[n]);
-        }
-        cluster.sync();
-    };
-    auto slice_sum = [&](int n) {
-        float2 s = make_float2(0.f, 0.f);
-        for (int o = 0; o < J; o++) {
-            const float2 *rp = cluster.map_shared_rank(L.buf, o);
-            s = cadd(s, rp[n]);
-        }
-        return s;
+    // element i of my slice of sum_j Y[j], times s
+    auto slice_sum = [&](int i, float s) {
+        float2 acc = Yr[i];
+        for (int o = 1; o < J; o++) acc = cadd(acc, Yr[(size_t)o * SL + i]);
+        return cscale(acc, s);
     };
 
     while (true) {
-        if (jr == 0 && tid == 0) *L.rowslot = (int)atomicAdd(P.queue, 1u);
+        if (jr == 0 && tid == 0) {
+            const int r = (int)atomicAdd(P.queue, 1u);
+            for (int o = 0; o < J; o++) cluster.map_shared_rank(&G.row, o)[0] = r;
+        }
         cluster.sync();
-        const int row = *cluster.map_shared_rank(L.rowslot, 0);
-        // every peer has read rank 0's slot before rank 0 may rewrite it or any
-        // CTA exits (a CTA's shared memory must outlive its peers' accesses)
-        cluster.sync();
-        if (row >= M) break;
+        const int row = G.row;
+        if (row >= M) break;  // nobody touches another CTA's shared memory after this barrier
 
         // ---- intensities of mask jr, their sum and finiteness ----
         float yv[E];
         float2 z[E];
         {
-            float part[2] = {0.f, 0.f};
+            float pv[2] = {0.f, 0.f};
             const float *yr = P.y + (size_t)row * K + (size_t)jr * N;
 #pragma unroll
             for (int e = 0; e < E; e++) {
                 yv[e] = yr[tid + e * NT];
-                if (isfinite(yv[e])) part[0] += yv[e];
-                else part[1] += 1.f;
+                if (isfinite(yv[e])) pv[0] += yv[e];
+                else pv[1] += 1.f;
             }
-            double tot[2];
-            cluster_sum(part, tot, 2);
+            cluster_sum(pv, 2);
             if (tid == 0) {
                 G.status = ROW_MAXITER;
                 G.done = 0;
@@ -333,30 +383,34 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT) k_solver(SolverParams P)
                 G.f = 0.0;
                 G.stop = 0;
                 G.early = 0;
-                if (tot[1] > 0.0) { G.status = ROW_NUMERIC; G.stop = 1; G.early = 1; }
-                else if (tot[0] == 0.0) { G.status = ROW_ZERO; G.stop = 1; G.early = 1; }
-                G.f_prev = tot[0];  // sum(y), kept for the init scaling
+                G.sumy = G.red[0];
+                if (G.red[1] > 0.0) { G.status = ROW_NUMERIC; G.stop = 1; G.early = 1; }
+                else if (G.red[0] == 0.0) { G.status = ROW_ZERO; G.stop = 1; G.early = 1; }
             }
             __syncthreads();
         }
-        const double sumy = G.f_prev;
+        const float sumy = G.sumy;
+        const float JN = (float)J * N;
 
         if (!G.stop) {
             // ---- initialisation ----
-            const double JN = (double)J * N;
             if (P.T_init) {
-                for (int n = lo + tid; n < hi; n += NT) L.ts[n - lo] = P.T_init[(size_t)row * N + n];
+                for (int i = tid; i < nmine; i += NT) ts[i] = P.T_init[(size_t)row * N + lo + i];
             } else if (P.init == INIT_BP) {
                 float2 u[E];
 #pragma unroll
                 for (int e = 0; e < E; e++) u[e] = make_float2(sqrtf(fmaxf(yv[e], 0.f)), 0.f);
-                adjoint_to_buf(u);
-                for (int n = lo + tid; n < hi; n += NT) L.ts[n - lo] = cscale(slice_sum(n), (float)(1.0 / JN));
+                block_fft_rb<N, NT, +1>(u, buf, tws, wb, tid);
+#pragma unroll
+                for (int e = 0; e < E; e++) u[e] = cmulc(u[e], dm[e]);
+                push_to_owners(u);
+                cluster.sync();
+                for (int i = tid; i < nmine; i += NT) ts[i] = slice_sum(i, 1.f / JN);
             } else {
-                for (int n = lo + tid; n < hi; n += NT)
-                    L.ts[n - lo] = philox_cnormal(P.seed, (uint32_t)row, (uint32_t)n);
+                for (int i = tid; i < nmine; i += NT)
+                    ts[i] = philox_cnormal(P.seed, (uint32_t)row, (uint32_t)(lo + i));
                 if (P.init == INIT_SPECTRAL) {
-                    const float mean = (float)(sumy / (double)K);
+                    const float mean = sumy / (float)K;
                     float tau[E];
 #pragma unroll
                     for (int e = 0; e < E; e++) {
@@ -365,131 +419,148 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT) k_solver(SolverParams P)
                         tau[e] = tv;
                     }
                     for (int it = 0; it < P.power_iters; it++) {
-                        for (int n = lo + tid; n < hi; n += NT) L.ps[n - lo] = L.ts[n - lo];
+                        // t <- A t, A = Q^H diag(tau) Q / (J N); the norm is restored
+                        // every 8th step and at the end (only the direction matters
+                        // to the power iteration, and |A| <= clip bounds the growth)
+                        __syncthreads();
+                        push_slice_to_X(ts);
                         cluster.sync();
                         float2 x[E];
-                        gather_masked(x, L.ps);
-                        block_fft<N, NT, -1>(x, L.buf, L.tw, tid);
+#pragma unroll
+                        for (int e = 0; e < E; e++) x[e] = cmul(X[tid + e * NT], dm[e]);
+                        __syncthreads();  // X is read before the FFT reuses it
+                        block_fft_rb<N, NT, -1>(x, buf, tws, wb, tid);
 #pragma unroll
                         for (int e = 0; e < E; e++) x[e] = cscale(x[e], tau[e]);
-                        adjoint_to_buf(x);
-                        float part[1] = {0.f};
-                        for (int n = lo + tid; n < hi; n += NT) {
-                            const float2 s = cscale(slice_sum(n), (float)(1.0 / JN));
-                            L.ts[n - lo] = s;
-                            part[0] += cabs2(s);
+                        block_fft_rb<N, NT, +1>(x, buf, tws, wb, tid);
+#pragma unroll
+                        for (int e = 0; e < E; e++) x[e] = cmulc(x[e], dm[e]);
+                        push_to_owners(x);
+                        cluster.sync();
+                        const bool renorm = ((it & 7) == 7) || (it == P.power_iters - 1);
+                        float pv[1] = {0.f};
+                        for (int i = tid; i < nmine; i += NT) {
+                            const float2 s = slice_sum(i, 1.f / JN);
+                            ts[i] = s;
+                            pv[0] = fmaf(s.x, s.x, fmaf(s.y, s.y, pv[0]));
                         }
-                        double nrm;
-                        cluster_sum(part, &nrm, 1);
-                        const float inv = nrm > 0.0 ? (float)(1.0 / sqrt(nrm)) : 0.f;
-                        for (int n = lo + tid; n < hi; n += NT) L.ts[n - lo] = cscale(L.ts[n - lo], inv);
+                        if (renorm) {
+                            cluster_sum(pv, 1);
+                            __syncthreads();
+                            const float nrm = G.red[0];
+                            const float inv = nrm > 0.f ? rsqrtf(nrm) : 0.f;
+                            for (int i = tid; i < nmine; i += NT) ts[i] = cscale(ts[i], inv);
+                        }
                     }
                 }
                 // rescale to the Parseval norm ||t||^2 = sum(y) / (J N)
-                float part[1] = {0.f};
-                for (int n = lo + tid; n < hi; n += NT) part[0] += cabs2(L.ts[n - lo]);
-                double nrm;
-                cluster_sum(part, &nrm, 1);
-                const float sc = nrm > 0.0 ? (float)(sqrt(sumy / JN) / sqrt(nrm)) : 0.f;
-                for (int n = lo + tid; n < hi; n += NT) L.ts[n - lo] = cscale(L.ts[n - lo], sc);
+                float pv[1] = {0.f};
+                for (int i = tid; i < nmine; i += NT) pv[0] += cabs2(ts[i]);
+                cluster_sum(pv, 1);
+                __syncthreads();
+                const float nrm = G.red[0];
+                const float sc = nrm > 0.f ? sqrtf(sumy / JN) / sqrtf(nrm) : 0.f;
+                for (int i = tid; i < nmine; i += NT) ts[i] = cscale(ts[i], sc);
             }
 
             // ---- f and gradient at t0 ----
             {
-                for (int n = lo + tid; n < hi; n += NT) L.ps[n - lo] = L.ts[n - lo];
+                __syncthreads();
+                push_slice_to_X(ts);
                 cluster.sync();
-                gather_masked(z, L.ps);
-                block_fft<N, NT, -1>(z, L.buf, L.tw, tid);
+#pragma unroll
+                for (int e = 0; e < E; e++) z[e] = cmul(X[tid + e * NT], dm[e]);
+                __syncthreads();  // X is read before the FFT reuses it
+                block_fft_rb<N, NT, -1>(z, buf, tws, wb, tid);
                 float2 u[E];
-                float part[2] = {0.f, 0.f};
+                float pv[2] = {0.f, 0.f};
 #pragma unroll
                 for (int e = 0; e < E; e++) {
                     const float r = yv[e] - cabs2(z[e]);
-                    part[0] = fmaf(r, r, part[0]);
+                    pv[0] = fmaf(r, r, pv[0]);
                     u[e] = cscale(z[e], r);
                 }
-                adjoint_to_buf(u);
-                for (int n = lo + tid; n < hi; n += NT) {
-                    const float2 g = cscale(slice_sum(n), -4.f);
-                    L.gs[n - lo] = g;
-                    part[1] += cabs2(g);
+                block_fft_rb<N, NT, +1>(u, buf, tws, wb, tid);
+#pragma unroll
+                for (int e = 0; e < E; e++) u[e] = cmulc(u[e], dm[e]);
+                push_to_owners(u);
+                cluster.sync();
+                for (int i = tid; i < nmine; i += NT) {
+                    const float2 g = slice_sum(i, -4.f);
+                    gs[i] = g;
+                    pv[1] += cabs2(g);
                 }
-                double tot[2];
-                cluster_sum(part, tot, 2);
+                cluster_sum(pv, 2);
                 if (tid == 0) {
-                    G.f = tot[0];
-                    G.gg = tot[1];
+                    G.f = G.red[0];
+                    G.gg = G.red[1];
                     G.np = 0;
-                    if (!isfinite(tot[0]) || !isfinite(tot[1])) { G.status = ROW_NUMERIC; G.stop = 1; }
+                    if (!isfinite(G.f) || !isfinite(G.gg)) { G.status = ROW_NUMERIC; G.stop = 1; }
+                    else if (P.iters > 0 && (G.f == 0.f || G.gg == 0.f)) { G.status = ROW_CONVERGED; G.stop = 1; }
+                    else {
+                        lbfgs_coefficients(G);
+                        G.newslot = 0;
+                    }
                 }
                 __syncthreads();
             }
 
             // ---- L-BFGS iterations ----
             for (int it = 0; it < P.iters && !G.stop; it++) {
-                // A: direction
-                if (tid == 0) {
-                    if (G.f == 0.0 || G.gg == 0.0) {
-                        G.status = ROW_CONVERGED;
-                        G.stop = 1;
-                    } else {
-                        lbfgs_coefficients(G);
-                        // free slot for the new pair
-                        bool used[kSlots] = {false};
-                        for (int i = 0; i < G.np; i++) used[G.order[i]] = true;
-                        int ns = 0;
-                        while (used[ns]) ns++;
-                        G.newslot = ns;
-                    }
-                }
-                __syncthreads();
-                if (G.stop) break;
+                const int ns = G.newslot;
+                float2 *Sn = Ss + (size_t)ns * SL;
+                float2 *Yn = Ys + (size_t)ns * SL;
+                // A: direction on my slice, parked in the new S slot until the step is known
                 {
-                    const float gam = (float)G.gamma;
+                    const float gam = G.gamma;
                     const int np = G.np;
-                    for (int n = lo + tid; n < hi; n += NT) {
-                        const int i = n - lo;
-                        float2 acc = cscale(L.gs[i], gam);
+                    for (int i = tid; i < nmine; i += NT) {
+                        float2 acc = cscale(gs[i], gam);
                         for (int k = 0; k < np; k++) {
                             const int a = G.order[k];
-                            acc = cadd(acc, cscale(S_slot[(size_t)a * SL + i], (float)G.c1[a]));
-                            acc = cadd(acc, cscale(Y_slot[(size_t)a * SL + i], (float)(G.gamma * G.c2[a])));
+                            const float c1 = G.c1[a], c2 = G.c2[a];
+                            const float2 sa = Ss[(size_t)a * SL + i], ya = Ys[(size_t)a * SL + i];
+                            acc.x = fmaf(c1, sa.x, fmaf(c2, ya.x, acc.x));
+                            acc.y = fmaf(c1, sa.y, fmaf(c2, ya.y, acc.y));
                         }
-                        L.ps[i] = cscale(acc, -1.f);
+                        const float2 p = make_float2(-acc.x, -acc.y);
+                        Sn[i] = p;
+                        for (int o = 0; o < J; o++) cluster.map_shared_rank(X, o)[lo + i] = p;
                     }
                 }
                 cluster.sync();  // B1
                 // C: w = F(d .* p)
                 float2 w[E];
-                gather_masked(w, L.ps);
-                block_fft<N, NT, -1>(w, L.buf, L.tw, tid);
+#pragma unroll
+                for (int e = 0; e < E; e++) w[e] = cmul(X[tid + e * NT], dm[e]);
+                __syncthreads();  // X is read before the FFT reuses it
+                block_fft_rb<N, NT, -1>(w, buf, tws, wb, tid);
                 // D: quartic coefficients
                 {
-                    float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+                    float pv[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                     for (int e = 0; e < E; e++) {
                         const float a = cdotr(z[e], w[e]);
                         const float b = cabs2(w[e]);
                         const float r = yv[e] - cabs2(z[e]);
-                        part[0] = fmaf(r, r, part[0]);
-                        part[1] = fmaf(-4.f * r, a, part[1]);
-                        part[2] += fmaf(4.f * a, a, -2.f * r * b);
-                        part[3] = fmaf(4.f * a, b, part[3]);
-                        part[4] = fmaf(b, b, part[4]);
+                        pv[0] = fmaf(r, r, pv[0]);
+                        pv[1] = fmaf(-4.f * r, a, pv[1]);
+                        pv[2] += fmaf(4.f * a, a, -2.f * r * b);
+                        pv[3] = fmaf(4.f * a, b, pv[3]);
+                        pv[4] = fmaf(b, b, pv[4]);
                     }
-                    double c[5];
-                    cluster_sum(part, c, 5);  // B2
+                    cluster_sum(pv, 5);  // B2
                     if (tid == 0) {
-                        const double al = quartic_argmin(c);
+                        const float al = quartic_argmin(G.red);
                         G.alpha = al;
                         if (!isfinite(al)) { G.status = ROW_NUMERIC; G.stop = 1; }
-                        else if (al == 0.0) { G.status = ROW_CONVERGED; G.stop = 1; }
+                        else if (al == 0.f) { G.status = ROW_CONVERGED; G.stop = 1; }
                     }
                     __syncthreads();
                 }
                 if (G.stop) break;
-                const float al = (float)G.alpha;
-                // E: update
+                const float al = G.alpha;
+                // E: update fields, residual and the step
                 float2 u[E];
                 float fpart = 0.f;
 #pragma unroll
@@ -499,49 +570,48 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT) k_solver(SolverParams P)
                     fpart = fmaf(r, r, fpart);
                     u[e] = cscale(z[e], r);
                 }
-                const int ns = G.newslot;
-                for (int n = lo + tid; n < hi; n += NT) {
-                    const int i = n - lo;
-                    const float2 s = cscale(L.ps[i], al);
-                    S_slot[(size_t)ns * SL + i] = s;
-                    L.ts[i] = cadd(L.ts[i], s);
+                for (int i = tid; i < nmine; i += NT) {
+                    const float2 s = cscale(Sn[i], al);
+                    Sn[i] = s;
+                    ts[i] = cadd(ts[i], s);
                 }
-                // F: adjoint
-                adjoint_to_buf(u);  // B3
-                // new gradient, new y, and the batched dot products
+                // F: adjoint, pushed to the slice owners
+                block_fft_rb<N, NT, +1>(u, buf, tws, wb, tid);
+#pragma unroll
+                for (int e = 0; e < E; e++) u[e] = cmulc(u[e], dm[e]);
+                push_to_owners(u);
+                cluster.sync();  // B3
+                // G: new gradient, new pair, batched dot products
                 {
                     const int np = G.np;
-                    float part[kMaxNV];
+                    float pv[kParts];
 #pragma unroll
-                    for (int k = 0; k < kMaxNV; k++) part[k] = 0.f;
-                    for (int n = lo + tid; n < hi; n += NT) {
-                        const int i = n - lo;
-                        const float2 gn = cscale(slice_sum(n), -4.f);
-                        const float2 yn = csub(gn, L.gs[i]);
-                        L.gs[i] = gn;
-                        Y_slot[(size_t)ns * SL + i] = yn;
-                        const float2 sn = S_slot[(size_t)ns * SL + i];
-                        // slots: live ones in age order, then the new slot (index np)
+                    for (int k = 0; k < kParts; k++) pv[k] = 0.f;
+                    for (int i = tid; i < nmine; i += NT) {
+                        const float2 gn = slice_sum(i, -4.f);
+                        const float2 yn = csub(gn, gs[i]);
+                        gs[i] = gn;
+                        Yn[i] = yn;
+                        const float2 sn = Sn[i];
 #pragma unroll
                         for (int k = 0; k < kSlots; k++) {
                             if (k <= np) {
                                 const int a = (k < np) ? G.order[k] : ns;
-                                const float2 sa = S_slot[(size_t)a * SL + i];
-                                const float2 ya = Y_slot[(size_t)a * SL + i];
-                                part[4 * k + 0] += cdotr(sa, yn);
-                                part[4 * k + 1] += cdotr(ya, yn);
-                                part[4 * k + 2] += cdotr(sa, gn);
-                                part[4 * k + 3] += cdotr(ya, gn);
+                                const float2 sa = Ss[(size_t)a * SL + i];
+                                const float2 ya = Ys[(size_t)a * SL + i];
+                                pv[4 * k + 0] += cdotr(sa, yn);
+                                pv[4 * k + 1] += cdotr(ya, yn);
+                                pv[4 * k + 2] += cdotr(sa, gn);
+                                pv[4 * k + 3] += cdotr(ya, gn);
                             }
                         }
-                        part[4 * kSlots + 0] += cabs2(sn);
-                        part[4 * kSlots + 1] += cabs2(gn);
+                        pv[4 * kSlots + 0] += cabs2(sn);
+                        pv[4 * kSlots + 1] += cabs2(gn);
                     }
-                    part[4 * kSlots + 2] = fpart;
-                    double tot[kMaxNV];
-                    cluster_sum(part, tot, kMaxNV);  // B4
+                    pv[4 * kSlots + 2] = fpart;
+                    cluster_sum(pv, 4 * kSlots + 3);  // B4
                     if (tid == 0) {
-                        // Gram update for the new pair (slot ns)
+                        const float *tot = G.red;
                         for (int k = 0; k <= np; k++) {
                             const int a = (k < np) ? G.order[k] : ns;
                             G.SY[a][ns] = tot[4 * k + 0];
@@ -549,22 +619,32 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT) k_solver(SolverParams P)
                             G.Sg[a] = tot[4 * k + 2];
                             G.Yg[a] = tot[4 * k + 3];
                         }
-                        const double sy = tot[4 * np + 0], yy = tot[4 * np + 1];
-                        const double ss = tot[4 * kSlots + 0];
-                        const double fnew = tot[4 * kSlots + 2];
+                        const float sy = tot[4 * np + 0], yy = tot[4 * np + 1];
+                        const float ss = tot[4 * kSlots + 0];
+                        const float fnew = tot[4 * kSlots + 2];
                         G.gg = tot[4 * kSlots + 1];
-                        if (sy > 1e-10 * sqrt(ss) * sqrt(yy) && sy > 0.0) {
+                        if (sy > 1e-10f * sqrtf(ss) * sqrtf(yy) && sy > 0.f) {
+                            G.rD[ns] = 1.f / sy;
                             G.order[G.np++] = ns;
                             if (G.np > m) {
                                 for (int k = 0; k + 1 < G.np; k++) G.order[k] = G.order[k + 1];
                                 G.np--;
                             }
                         }
-                        const double rel = fabs(G.f - fnew) / fmax(G.f, 1e-30);
+                        const float rel = fabsf(G.f - fnew) / fmaxf(G.f, 1e-30f);
                         G.f = fnew;
                         G.done = it + 1;
                         if (!isfinite(fnew) || !isfinite(G.gg)) { G.status = ROW_NUMERIC; G.stop = 1; }
-                        else if (P.tol > 0.0 && rel < P.tol) { G.status = ROW_CONVERGED; G.stop = 1; }
+                        else if (P.tol > 0.0 && rel < (float)P.tol) { G.status = ROW_CONVERGED; G.stop = 1; }
+                        else if (it + 1 < P.iters && (fnew == 0.f || G.gg == 0.f)) { G.status = ROW_CONVERGED; G.stop = 1; }
+                        if (!G.stop && it + 1 < P.iters) {
+                            lbfgs_coefficients(G);
+                            bool used[kSlots] = {false};
+                            for (int i = 0; i < G.np; i++) used[G.order[i]] = true;
+                            int nsl = 0;
+                            while (used[nsl]) nsl++;
+                            G.newslot = nsl;
+                        }
                     }
                     __syncthreads();
                 }
@@ -573,13 +653,13 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT) k_solver(SolverParams P)
 
         // ---- outputs (rows decided before initialisation come back as zero) ----
         const bool early = G.early != 0;
-        for (int n = lo + tid; n < hi; n += NT)
-            P.T_out[(size_t)row * N + n] = early ? make_float2(0.f, 0.f) : L.ts[n - lo];
+        for (int i = tid; i < nmine; i += NT)
+            P.T_out[(size_t)row * N + lo + i] = early ? make_float2(0.f, 0.f) : ts[i];
         if (jr == 0 && tid == 0) {
             if (P.row_status) P.row_status[row] = G.status;
             if (P.row_iters) P.row_iters[row] = G.done;
-            if (P.row_loss) P.row_loss[row] = early ? (G.status == ROW_ZERO ? 0.f : __int_as_float(0x7fc00000))
-                                                    : (float)G.f;
+            if (P.row_loss)
+                P.row_loss[row] = early ? (G.status == ROW_ZERO ? 0.f : __int_as_float(0x7fc00000)) : (float)G.f;
         }
         if (P.Zd) {
 #pragma unroll
@@ -588,7 +668,7 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT) k_solver(SolverParams P)
                 if (pat < P.Nd) P.Zd[(size_t)pat * M + row] = early ? make_float2(0.f, 0.f) : z[e];
             }
         }
-        cluster.sync();  // all peers done with this row's shared data
+        __syncthreads();
     }
 }
 
@@ -599,10 +679,6 @@ static cudaError_t launch_solver_t(const SolverParams &p, cudaStream_t s, int *c
     const size_t sm = solver_smem<N>(p.J, p.m);
     cudaError_t e = cudaFuncSetAttribute(k_solver<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    if (p.J > 8) {
-        e = cudaFuncSetAttribute(k_solver<N>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-    }
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
