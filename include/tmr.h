@@ -88,7 +88,7 @@ typedef struct {
 } tmr_defocus_op;
 
 typedef struct {
-    int m;                  /* L-BFGS memory, 1..8 (default 5)                       */
+    int m;                  /* L-BFGS memory, 1..6 (default 5)                       */
     int init;               /* TMR_INIT_* (default spectral)                         */
     unsigned long long seed;/* Philox key for random/spectral starts (default 0)     */
     int power_iters;        /* spectral power iterations (default 100)               */
@@ -188,7 +188,7 @@ void tmr_destroy(tmr_handle *h);
  * Its only scratch (a row work counter and the FFT twiddle table) lives in
  * one static 64 KiB device array that every GPU which loads the library holds
  * until the process exits.  Limits: N a power of two in 64..4096, J <= 8,
- * 1 <= opt->m <= 8; larger sizes return TMR_ERR_UNSUPPORTED with a message.
+ * 1 <= opt->m <= 6; larger sizes return TMR_ERR_UNSUPPORTED with a message.
  * It calls no cudaMalloc, cudaFree or other allocating routine.  The first
  * call on a device looks up the array's device address (once per device, with
  * that device current); make that first call before any stream capture.

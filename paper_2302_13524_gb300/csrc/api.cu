@@ -200,7 +200,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     tmr_options o;
     tmr_default_options(&o);
     if (opt) o = *opt;
-    if (o.m < 1 || o.m > kMaxMem) return fail(TMR_ERR_INVALID_ARG, "opt.m must be in 1..8");
+    if (o.m < 1 || o.m > kMaxMem) return fail(TMR_ERR_INVALID_ARG, "opt.m must be in 1..6");
     if (o.init < TMR_INIT_RANDOM || o.init > TMR_INIT_SPECTRAL) return fail(TMR_ERR_INVALID_ARG, "opt.init");
     if (o.power_iters < 0 || o.phase_iters < 0 || o.tol < 0) return fail(TMR_ERR_INVALID_ARG, "negative option");
     if (o.precision != TMR_PREC_FP32) return fail(TMR_ERR_UNSUPPORTED, "only TMR_PREC_FP32 is available");

@@ -7,7 +7,7 @@
 namespace tmr {
 
 constexpr int kMaxMasks = 8;  // J <= 8: one CTA per mask inside a portable cluster
-constexpr int kMaxMem = 8;    // L-BFGS memory m <= 8
+constexpr int kMaxMem = 6;    // L-BFGS memory m <= 6: 4 (m + 1) + 3 reduced values fit one warp
 
 __host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }

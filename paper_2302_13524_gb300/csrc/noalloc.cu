@@ -89,7 +89,7 @@ extern "C" tmr_status tmr_retrieve_rows_static(int N, int M, int J, const void *
     if (!masks || !y || !T_out) return fail(TMR_ERR_INVALID_ARG, "NULL array");
     if (!tmr::fft_supported(N)) return fail(TMR_ERR_UNSUPPORTED, "N must be a power of two in 64..4096");
     if (J > tmr::kMaxMasks) return fail(TMR_ERR_UNSUPPORTED, "J must be at most 8");
-    if (o.m < 1 || o.m > tmr::kMaxMem) return fail(TMR_ERR_INVALID_ARG, "opt.m must be in 1..8");
+    if (o.m < 1 || o.m > tmr::kMaxMem) return fail(TMR_ERR_INVALID_ARG, "opt.m must be in 1..6");
     if (o.init < TMR_INIT_RANDOM || o.init > TMR_INIT_SPECTRAL || o.power_iters < 0 || o.tol < 0)
         return fail(TMR_ERR_INVALID_ARG, "bad option");
     const int twn = tmr::fft_table_len(N);

@@ -52,24 +52,29 @@ enum { ROW_MAXITER = 0, ROW_CONVERGED = 1, ROW_ZERO = 2, ROW_NUMERIC = 3 };
 enum { INIT_RANDOM = 0, INIT_BP = 1, INIT_SPECTRAL = 2 };
 
 constexpr int kSlots = kMaxMem + 1;  // m+1 slots: the new pair never overwrites a live one
-constexpr int kParts = 40;           // reduction width (values per CTA and reduction)
+constexpr int kParts = 32;           // values per reduction: one per lane of a warp
 static_assert(4 * kSlots + 3 <= kParts, "reduction width");
+// layout of the per-iteration dot products: 4 per age k (s_k.y, y_k.y, s_k.g,
+// y_k.g with the new y and g), then these three
+constexpr int kIdxSS = 4 * kSlots, kIdxGG = 4 * kSlots + 1, kIdxF = 4 * kSlots + 2;
 
 // L-BFGS scalars, replicated in every CTA of the cluster: each CTA computes
 // them from identical sums added in the same order, so they agree bit for bit
 // and every CTA takes the same branches.  FP32 like the rest of the path (the
 // FP64 pipe of this part is a small fraction of its FP32 rate, and these
-// scalars sit on the critical path of every iteration).
+// scalars sit on the critical path of every iteration).  Pairs are indexed by
+// age (0 = oldest); slot[] maps an age to its physical vector slot, and
+// slot[np] is the free slot that receives the next pair.
 struct Gram {
-    float SY[kSlots][kSlots];  // s_a^T y_b for slot a no newer than slot b
-    float YY[kSlots][kSlots];  // y_a^T y_b, same convention
-    float rD[kSlots];          // 1 / s_a^T y_a
+    float SY[kSlots][kSlots];  // s_i^T y_j, ages i <= j
+    float YY[kSlots][kSlots];  // y_i^T y_j, ages i <= j
+    float rD[kSlots];          // 1 / s_i^T y_i
     float Sg[kSlots], Yg[kSlots];
-    float c1[kSlots], c2[kSlots];  // direction coefficients per slot (c2 includes gamma)
+    float c1[kSlots], c2[kSlots];  // direction coefficients by age (c2 includes gamma)
     float gamma, gg, f, sumy, alpha;
     float red[kParts];  // the last cluster-wide sums
-    int order[kSlots];  // live slots, oldest first
-    int np, newslot;
+    int slot[kSlots];
+    int np;
     int status, done, stop, early, row;
 };
 
@@ -172,50 +177,68 @@ __device__ float quartic_argmin(const float *c)
     return best;
 }
 
-// Compact-form coefficients (one thread): p = -(gamma g + sum c1_i s_i +
-// sum c2_i y_i) with c2 already scaled by gamma.  Falls back to p = -g
-// (clearing the history) when there is no pair or the result is not a descent
+// Compact-form coefficients, run by one warp (lane i owns age i):
+// p = -(gamma g + sum_i c1_i s_i + sum_i c2_i y_i), c2 already scaled by gamma.
+// R c2 = -S^T g is solved by back substitution and R^T c1 =
+// -(D + gamma Y^T Y) c2 - gamma Y^T g by forward substitution, each step
+// broadcasting the new unknown with a shuffle.  Falls back to p = -g (and
+// clears the history) when there is no pair or the result is not a descent
 // direction.
-__device__ void lbfgs_coefficients(Gram &G)
+__device__ void lbfgs_coefficients_warp(Gram &G, int lane)
 {
     const int np = G.np;
-    for (int a = 0; a < kSlots; a++) G.c1[a] = G.c2[a] = 0.f;
+    float c1 = 0.f, c2 = 0.f, gamma = 1.f;
+    bool ok = false;
     if (np > 0) {
-        const int nw = G.order[np - 1];
-        const float gamma = G.SY[nw][nw] / G.YY[nw][nw];
-        float c2[kSlots], c1[kSlots];
-        // R c2 = -S^T g  (R upper triangular in age order, R_ij = s_i^T y_j, i <= j)
-        for (int i = np - 1; i >= 0; i--) {
-            const int oi = G.order[i];
-            float s = -G.Sg[oi];
-            for (int j = i + 1; j < np; j++) s = fmaf(-G.SY[oi][G.order[j]], c2[j], s);
-            c2[i] = s * G.rD[oi];
+        gamma = G.SY[np - 1][np - 1] / G.YY[np - 1][np - 1];
+        const bool mine = lane < np;
+        float acc = mine ? -G.Sg[lane] : 0.f;
+        for (int j = np - 1; j >= 0; j--) {
+            if (lane == j) c2 = acc * G.rD[j];
+            const float cj = __shfl_sync(0xffffffffu, c2, j);
+            if (lane < j) acc = fmaf(-G.SY[lane][j], cj, acc);
         }
-        // R^T c1 = -(D + gamma Y^T Y) c2 - gamma Y^T g
-        for (int i = 0; i < np; i++) {
-            const int oi = G.order[i];
-            float yc = 0.f;
-            for (int j = 0; j < np; j++) {
-                const int a = G.order[i < j ? i : j], b = G.order[i < j ? j : i];
-                yc = fmaf(G.YY[a][b], c2[j], yc);
-            }
-            float rhs = -G.SY[oi][oi] * c2[i] - gamma * (G.Yg[oi] + yc);
-            for (int j = 0; j < i; j++) rhs = fmaf(-G.SY[G.order[j]][oi], c1[j], rhs);
-            c1[i] = rhs * G.rD[oi];
+        float yc = 0.f;
+        for (int j = 0; j < np; j++) {
+            const float cj = __shfl_sync(0xffffffffu, c2, j);
+            if (mine) yc = fmaf(G.YY[lane < j ? lane : j][lane < j ? j : lane], cj, yc);
         }
-        float pg = gamma * G.gg;  // <g, H g> = -<p, g>
-        for (int i = 0; i < np; i++) pg += c1[i] * G.Sg[G.order[i]] + gamma * c2[i] * G.Yg[G.order[i]];
-        if (pg > 0.f && isfinite(pg)) {
-            G.gamma = gamma;
-            for (int i = 0; i < np; i++) {
-                G.c1[G.order[i]] = c1[i];
-                G.c2[G.order[i]] = gamma * c2[i];
-            }
-            return;
+        float acc1 = mine ? -G.SY[lane][lane] * c2 - gamma * (G.Yg[lane] + yc) : 0.f;
+        for (int j = 0; j < np; j++) {
+            if (lane == j) c1 = acc1 * G.rD[j];
+            const float cj = __shfl_sync(0xffffffffu, c1, j);
+            if (mine && lane > j) acc1 = fmaf(-G.SY[j][lane], cj, acc1);
         }
-        G.np = 0;
+        float t = mine ? fmaf(c1, G.Sg[lane], gamma * c2 * G.Yg[lane]) : 0.f;
+        const float pg = gamma * G.gg + warp_sum(t);  // <g, H g> = -<p, g>
+        ok = pg > 0.f && isfinite(pg);
     }
-    G.gamma = 1.f;
+    __syncwarp();
+    if (lane < kSlots) {
+        G.c1[lane] = (ok && lane < np) ? c1 : 0.f;
+        G.c2[lane] = (ok && lane < np) ? gamma * c2 : 0.f;
+    }
+    if (lane == 0) {
+        G.gamma = ok ? gamma : 1.f;
+        if (!ok) G.np = 0;
+    }
+    __syncwarp();
+}
+
+// Sum of up to 32 values over a warp by recursive halving: after the call,
+// lane l of the warp holds the warp-wide sum of value l in v[0].
+__device__ __forceinline__ void warp_reduce32(float (&v)[32], int lane)
+{
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+        const bool upper = (lane & h) != 0;
+#pragma unroll
+        for (int i = 0; i < h; i++) {
+            const float send = upper ? v[i] : v[i + h];
+            const float keep = upper ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+        }
+    }
 }
 
 template <int N>
@@ -234,28 +257,9 @@ __host__ __device__ size_t solver_smem(int J, int m)
     size_t f2 = (size_t)fft_buf_len(N) /*X and FFT exchange*/ + C::TWS + (size_t)J * SL /*Y*/ +
                 2 * SL /*t, g*/ + 2 * (size_t)(m + 1) * SL /*pairs*/;
     size_t bytes = f2 * sizeof(float2);
-    bytes += sizeof(float) * ((size_t)kParts * C::NW + 2 * (size_t)J * kParts);
+    bytes += sizeof(float) * (2 * (size_t)J * C::NW * kParts);
     bytes = (bytes + 15) & ~(size_t)15;
     return bytes + sizeof(Gram);
-}
-
-// Block sums of NV per-thread values: value k ends in out[k], written by
-// thread k mod blockDim.x.  Partials are added warp by warp in a fixed order.
-template <int NV>
-__device__ __forceinline__ void block_partials(float (&v)[NV], float *red, float *out, int nw)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NV; k++) {
-        const float s = warp_sum(v[k]);
-        if (lane == 0) red[k * nw + warp] = s;
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < NV; k += blockDim.x) {  // NV may exceed the block size
-        float s = 0.f;
-        for (int w = 0; w < nw; w++) s += red[k * nw + w];
-        out[k] = s;
-    }
 }
 
 template <int N>
@@ -283,10 +287,9 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
     float2 *gs = ts + SL;
     float2 *Ss = gs + SL;  // slot a at Ss + a*SL
     float2 *Ys = Ss + (size_t)(m + 1) * SL;
-    float *red = reinterpret_cast<float *>(Ys + (size_t)(m + 1) * SL);
-    float *part = red + kParts * NW;  // [2][J][kParts]
+    float *part = reinterpret_cast<float *>(Ys + (size_t)(m + 1) * SL);  // [2][J][NW][kParts]
     Gram &G = *reinterpret_cast<Gram *>(
-        smem_raw + ((reinterpret_cast<unsigned char *>(part + 2 * J * kParts) - smem_raw + 15) &
+        smem_raw + ((reinterpret_cast<unsigned char *>(part + 2 * J * NW * kParts) - smem_raw + 15) &
                     ~(size_t)15));
 
     for (int i = tid; i < C::TWS; i += NT) tws[i] = P.tw[i];
@@ -299,7 +302,9 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
         sincospi(-2.0 * (double)tid / (double)N, &s, &c);
         wb = make_float2((float)c, (float)s);
     }
+    const int sl_shift = (even && (SL & (SL - 1)) == 0) ? __ffs(SL) - 1 : -1;
     auto owner = [&](int n) {
+        if (sl_shift >= 0) return n >> sl_shift;
         if (even) return n / SL;
         int o = (int)(((long long)n * J) / N);
         while (o + 1 < J && ((o + 1) * N) / J <= n) o++;
@@ -308,28 +313,30 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
     };
     cluster.sync();  // every CTA of the cluster runs before anyone touches its shared memory
 
-    // Cluster-wide sum of nv per-thread values: the block sums are written to
-    // part[sel][jr][:] of every CTA (own copy local, peers' by DSMEM stores),
-    // one barrier, then thread 0 adds the J partials in rank order into
-    // G.red (the caller synchronises before reading it).
+    // Cluster-wide sums of nv <= 32 per-thread values (v padded with zeros):
+    // each warp reduces its 32 values by recursive halving, lane k stores the
+    // warp sum of value k into part[sel][jr][warp][k] of every CTA (its own
+    // copy locally, the peers' by DSMEM stores), one barrier, then thread k adds
+    // the J * NW partials in a fixed order into G.red[k] and the block
+    // synchronises.  The two part buffers alternate: a peer may still read
+    // the previous one after this barrier but not the one before.
+    const int lane = tid & 31, warp = tid >> 5;
     int sel = 0;
-    auto cluster_sum = [&](auto &vals, int nv) {
-        float *pb = part + sel * J * kParts;
+    auto cluster_sum = [&](float (&v)[32], int nv) {
+        float *pb = part + (size_t)sel * J * NW * kParts;
         sel ^= 1;
-        block_partials(vals, red, pb + jr * kParts, NW);
-        for (int k = tid; k < nv; k += NT) {  // the same thread wrote value k above
-            const float s = pb[jr * kParts + k];
-            for (int o = 0; o < J; o++)
-                if (o != jr) cluster.map_shared_rank(pb, o)[jr * kParts + k] = s;
+        warp_reduce32(v, lane);
+        if (lane < nv) {
+            const size_t at = ((size_t)jr * NW + warp) * kParts + lane;
+            for (int o = 0; o < J; o++) cluster.map_shared_rank(pb, o)[at] = v[0];
         }
         cluster.sync();
-        if (tid == 0) {
-            for (int k = 0; k < nv; k++) {
-                float s = 0.f;
-                for (int o = 0; o < J; o++) s += pb[o * kParts + k];
-                G.red[k] = s;
-            }
+        if (tid < nv) {
+            float acc = 0.f;
+            for (int q = 0; q < J * NW; q++) acc += pb[(size_t)q * kParts + tid];
+            G.red[tid] = acc;
         }
+        __syncthreads();
     };
     // my slice (length nmine) into X of every CTA
     auto push_slice_to_X = [&](const float2 *src) {
@@ -367,7 +374,7 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
         float yv[E];
         float2 z[E];
         {
-            float pv[2] = {0.f, 0.f};
+            float pv[32] = {0.f};
             const float *yr = P.y + (size_t)row * K + (size_t)jr * N;
 #pragma unroll
             for (int e = 0; e < E; e++) {
@@ -438,7 +445,7 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
                         push_to_owners(x);
                         cluster.sync();
                         const bool renorm = ((it & 7) == 7) || (it == P.power_iters - 1);
-                        float pv[1] = {0.f};
+                        float pv[32] = {0.f};
                         for (int i = tid; i < nmine; i += NT) {
                             const float2 s = slice_sum(i, 1.f / JN);
                             ts[i] = s;
@@ -446,7 +453,6 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
                         }
                         if (renorm) {
                             cluster_sum(pv, 1);
-                            __syncthreads();
                             const float nrm = G.red[0];
                             const float inv = nrm > 0.f ? rsqrtf(nrm) : 0.f;
                             for (int i = tid; i < nmine; i += NT) ts[i] = cscale(ts[i], inv);
@@ -454,10 +460,9 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
                     }
                 }
                 // rescale to the Parseval norm ||t||^2 = sum(y) / (J N)
-                float pv[1] = {0.f};
+                float pv[32] = {0.f};
                 for (int i = tid; i < nmine; i += NT) pv[0] += cabs2(ts[i]);
                 cluster_sum(pv, 1);
-                __syncthreads();
                 const float nrm = G.red[0];
                 const float sc = nrm > 0.f ? sqrtf(sumy / JN) / sqrtf(nrm) : 0.f;
                 for (int i = tid; i < nmine; i += NT) ts[i] = cscale(ts[i], sc);
@@ -473,7 +478,7 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
                 __syncthreads();  // X is read before the FFT reuses it
                 block_fft_rb<N, NT, -1>(z, buf, tws, wb, tid);
                 float2 u[E];
-                float pv[2] = {0.f, 0.f};
+                float pv[32] = {0.f};
 #pragma unroll
                 for (int e = 0; e < E; e++) {
                     const float r = yv[e] - cabs2(z[e]);
@@ -491,23 +496,24 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
                     pv[1] += cabs2(g);
                 }
                 cluster_sum(pv, 2);
-                if (tid == 0) {
-                    G.f = G.red[0];
-                    G.gg = G.red[1];
-                    G.np = 0;
-                    if (!isfinite(G.f) || !isfinite(G.gg)) { G.status = ROW_NUMERIC; G.stop = 1; }
-                    else if (P.iters > 0 && (G.f == 0.f || G.gg == 0.f)) { G.status = ROW_CONVERGED; G.stop = 1; }
-                    else {
-                        lbfgs_coefficients(G);
-                        G.newslot = 0;
+                if (warp == 0) {
+                    if (lane == 0) {
+                        G.f = G.red[0];
+                        G.gg = G.red[1];
+                        G.np = 0;
+                        if (!isfinite(G.f) || !isfinite(G.gg)) { G.status = ROW_NUMERIC; G.stop = 1; }
+                        else if (P.iters > 0 && (G.f == 0.f || G.gg == 0.f)) { G.status = ROW_CONVERGED; G.stop = 1; }
                     }
+                    if (lane < kSlots) G.slot[lane] = lane;
+                    __syncwarp();
+                    if (!G.stop) lbfgs_coefficients_warp(G, lane);
                 }
                 __syncthreads();
             }
 
             // ---- L-BFGS iterations ----
             for (int it = 0; it < P.iters && !G.stop; it++) {
-                const int ns = G.newslot;
+                const int ns = G.slot[G.np];  // free slot for the new pair
                 float2 *Sn = Ss + (size_t)ns * SL;
                 float2 *Yn = Ys + (size_t)ns * SL;
                 // A: direction on my slice, parked in the new S slot until the step is known
@@ -517,8 +523,8 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
                     for (int i = tid; i < nmine; i += NT) {
                         float2 acc = cscale(gs[i], gam);
                         for (int k = 0; k < np; k++) {
-                            const int a = G.order[k];
-                            const float c1 = G.c1[a], c2 = G.c2[a];
+                            const int a = G.slot[k];
+                            const float c1 = G.c1[k], c2 = G.c2[k];
                             const float2 sa = Ss[(size_t)a * SL + i], ya = Ys[(size_t)a * SL + i];
                             acc.x = fmaf(c1, sa.x, fmaf(c2, ya.x, acc.x));
                             acc.y = fmaf(c1, sa.y, fmaf(c2, ya.y, acc.y));
@@ -537,7 +543,7 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
                 block_fft_rb<N, NT, -1>(w, buf, tws, wb, tid);
                 // D: quartic coefficients
                 {
-                    float pv[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+                    float pv[32] = {0.f};
 #pragma unroll
                     for (int e = 0; e < E; e++) {
                         const float a = cdotr(z[e], w[e]);
@@ -584,9 +590,9 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
                 // G: new gradient, new pair, batched dot products
                 {
                     const int np = G.np;
-                    float pv[kParts];
+                    float pv[32];
 #pragma unroll
-                    for (int k = 0; k < kParts; k++) pv[k] = 0.f;
+                    for (int k = 0; k < 32; k++) pv[k] = 0.f;
                     for (int i = tid; i < nmine; i += NT) {
                         const float2 gn = slice_sum(i, -4.f);
                         const float2 yn = csub(gn, gs[i]);
@@ -595,8 +601,8 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
                         const float2 sn = Sn[i];
 #pragma unroll
                         for (int k = 0; k < kSlots; k++) {
-                            if (k <= np) {
-                                const int a = (k < np) ? G.order[k] : ns;
+                            if (k <= np) {  // live pairs by age, then the new one (age np)
+                                const int a = G.slot[k];
                                 const float2 sa = Ss[(size_t)a * SL + i];
                                 const float2 ya = Ys[(size_t)a * SL + i];
                                 pv[4 * k + 0] += cdotr(sa, yn);
@@ -605,46 +611,73 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
                                 pv[4 * k + 3] += cdotr(ya, gn);
                             }
                         }
-                        pv[4 * kSlots + 0] += cabs2(sn);
-                        pv[4 * kSlots + 1] += cabs2(gn);
+                        pv[kIdxSS] += cabs2(sn);
+                        pv[kIdxGG] += cabs2(gn);
                     }
-                    pv[4 * kSlots + 2] = fpart;
-                    cluster_sum(pv, 4 * kSlots + 3);  // B4
-                    if (tid == 0) {
+                    pv[kIdxF] = fpart;
+                    cluster_sum(pv, kParts);  // B4
+                    if (warp == 0) {
                         const float *tot = G.red;
-                        for (int k = 0; k <= np; k++) {
-                            const int a = (k < np) ? G.order[k] : ns;
-                            G.SY[a][ns] = tot[4 * k + 0];
-                            G.YY[a][ns] = tot[4 * k + 1];
-                            G.Sg[a] = tot[4 * k + 2];
-                            G.Yg[a] = tot[4 * k + 3];
+                        if (lane <= np) {
+                            G.SY[lane][np] = tot[4 * lane + 0];
+                            G.YY[lane][np] = tot[4 * lane + 1];
+                            G.Sg[lane] = tot[4 * lane + 2];
+                            G.Yg[lane] = tot[4 * lane + 3];
                         }
                         const float sy = tot[4 * np + 0], yy = tot[4 * np + 1];
-                        const float ss = tot[4 * kSlots + 0];
-                        const float fnew = tot[4 * kSlots + 2];
-                        G.gg = tot[4 * kSlots + 1];
-                        if (sy > 1e-10f * sqrtf(ss) * sqrtf(yy) && sy > 0.f) {
-                            G.rD[ns] = 1.f / sy;
-                            G.order[G.np++] = ns;
-                            if (G.np > m) {
-                                for (int k = 0; k + 1 < G.np; k++) G.order[k] = G.order[k + 1];
-                                G.np--;
+                        const float fnew = tot[kIdxF];
+                        const bool accept = sy > 1e-10f * sqrtf(tot[kIdxSS]) * sqrtf(yy) && sy > 0.f;
+                        int np2 = np + (accept ? 1 : 0);
+                        __syncwarp();
+                        if (accept && lane == 0) G.rD[np] = 1.f / sy;
+                        __syncwarp();
+                        if (np2 > m) {
+                            // drop the oldest pair: age i + 1 becomes age i
+                            float sy_r[kSlots], yy_r[kSlots], sg = 0.f, yg = 0.f, rd = 0.f;
+                            int sl = 0;
+                            const bool mine = lane < np2 - 1;
+                            const int src = lane + 1;
+#pragma unroll
+                            for (int j = 0; j < kSlots; j++) {
+                                sy_r[j] = (mine && j + 1 < kSlots) ? G.SY[src][j + 1 < kSlots ? j + 1 : 0] : 0.f;
+                                yy_r[j] = (mine && j + 1 < kSlots) ? G.YY[src][j + 1 < kSlots ? j + 1 : 0] : 0.f;
                             }
+                            if (mine) {
+                                sg = G.Sg[src];
+                                yg = G.Yg[src];
+                                rd = G.rD[src];
+                            }
+                            // the m + 1 allocated slots rotate: the oldest pair's slot
+                            // becomes the free one at position m
+                            const int sl_old0 = G.slot[0];
+                            if (lane < m) sl = G.slot[lane + 1];
+                            __syncwarp();
+                            if (mine) {
+#pragma unroll
+                                for (int j = 0; j < kSlots; j++) {
+                                    G.SY[lane][j] = sy_r[j];
+                                    G.YY[lane][j] = yy_r[j];
+                                }
+                                G.Sg[lane] = sg;
+                                G.Yg[lane] = yg;
+                                G.rD[lane] = rd;
+                            }
+                            if (lane < m) G.slot[lane] = sl;
+                            if (lane == m) G.slot[lane] = sl_old0;
+                            np2 = m;
                         }
-                        const float rel = fabsf(G.f - fnew) / fmaxf(G.f, 1e-30f);
-                        G.f = fnew;
-                        G.done = it + 1;
-                        if (!isfinite(fnew) || !isfinite(G.gg)) { G.status = ROW_NUMERIC; G.stop = 1; }
-                        else if (P.tol > 0.0 && rel < (float)P.tol) { G.status = ROW_CONVERGED; G.stop = 1; }
-                        else if (it + 1 < P.iters && (fnew == 0.f || G.gg == 0.f)) { G.status = ROW_CONVERGED; G.stop = 1; }
-                        if (!G.stop && it + 1 < P.iters) {
-                            lbfgs_coefficients(G);
-                            bool used[kSlots] = {false};
-                            for (int i = 0; i < G.np; i++) used[G.order[i]] = true;
-                            int nsl = 0;
-                            while (used[nsl]) nsl++;
-                            G.newslot = nsl;
+                        if (lane == 0) {
+                            G.np = np2;
+                            G.gg = tot[kIdxGG];
+                            const float rel = fabsf(G.f - fnew) / fmaxf(G.f, 1e-30f);
+                            G.f = fnew;
+                            G.done = it + 1;
+                            if (!isfinite(fnew) || !isfinite(G.gg)) { G.status = ROW_NUMERIC; G.stop = 1; }
+                            else if (P.tol > 0.0 && rel < (float)P.tol) { G.status = ROW_CONVERGED; G.stop = 1; }
+                            else if (it + 1 < P.iters && (fnew == 0.f || G.gg == 0.f)) { G.status = ROW_CONVERGED; G.stop = 1; }
                         }
+                        __syncwarp();
+                        if (!G.stop && it + 1 < P.iters) lbfgs_coefficients_warp(G, lane);
                     }
                     __syncthreads();
                 }
