@@ -257,7 +257,7 @@ __host__ __device__ size_t solver_smem(int J, int m)
     size_t f2 = (size_t)fft_buf_len(N) /*X and FFT exchange*/ + C::TWS + (size_t)J * SL /*Y*/ +
                 2 * SL /*t, g*/ + 2 * (size_t)(m + 1) * SL /*pairs*/;
     size_t bytes = f2 * sizeof(float2);
-    bytes += sizeof(float) * (2 * (size_t)J * C::NW * kParts);
+    bytes += sizeof(float) * ((size_t)kParts * C::NW + 2 * (size_t)J * kParts);
     bytes = (bytes + 15) & ~(size_t)15;
     return bytes + sizeof(Gram);
 }
@@ -287,9 +287,10 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
     float2 *gs = ts + SL;
     float2 *Ss = gs + SL;  // slot a at Ss + a*SL
     float2 *Ys = Ss + (size_t)(m + 1) * SL;
-    float *part = reinterpret_cast<float *>(Ys + (size_t)(m + 1) * SL);  // [2][J][NW][kParts]
+    float *red = reinterpret_cast<float *>(Ys + (size_t)(m + 1) * SL);  // [kParts][NW]
+    float *part = red + kParts * NW;                                      // [2][J][kParts]
     Gram &G = *reinterpret_cast<Gram *>(
-        smem_raw + ((reinterpret_cast<unsigned char *>(part + 2 * J * NW * kParts) - smem_raw + 15) &
+        smem_raw + ((reinterpret_cast<unsigned char *>(part + 2 * J * kParts) - smem_raw + 15) &
                     ~(size_t)15));
 
     for (int i = tid; i < C::TWS; i += NT) tws[i] = P.tw[i];
@@ -314,26 +315,38 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
     cluster.sync();  // every CTA of the cluster runs before anyone touches its shared memory
 
     // Cluster-wide sums of nv <= 32 per-thread values (v padded with zeros):
-    // each warp reduces its 32 values by recursive halving, lane k stores the
-    // warp sum of value k into part[sel][jr][warp][k] of every CTA (its own
-    // copy locally, the peers' by DSMEM stores), one barrier, then thread k adds
-    // the J * NW partials in a fixed order into G.red[k] and the block
-    // synchronises.  The two part buffers alternate: a peer may still read
-    // the previous one after this barrier but not the one before.
+    // each warp reduces its values (recursive halving for many values, plain
+    // shuffle sums for a few), the NW warp sums are added in warp order by
+    // thread k, which stores the CTA's sum of value k into part[sel][jr][k]
+    // of every CTA (its own copy locally, the peers' by DSMEM stores); one
+    // cluster barrier; thread k adds the J partials in rank order into
+    // G.red[k] and the block synchronises.  The two part buffers alternate: a
+    // peer may still read the previous one after this barrier but not the one
+    // before.
     const int lane = tid & 31, warp = tid >> 5;
     int sel = 0;
     auto cluster_sum = [&](float (&v)[32], int nv) {
-        float *pb = part + (size_t)sel * J * NW * kParts;
+        float *pb = part + (size_t)sel * J * kParts;
         sel ^= 1;
-        warp_reduce32(v, lane);
-        if (lane < nv) {
-            const size_t at = ((size_t)jr * NW + warp) * kParts + lane;
-            for (int o = 0; o < J; o++) cluster.map_shared_rank(pb, o)[at] = v[0];
+        if (nv <= 6) {
+            for (int k = 0; k < nv; k++) {
+                const float t = warp_sum(v[k]);
+                if (lane == 0) red[k * NW + warp] = t;
+            }
+        } else {
+            warp_reduce32(v, lane);
+            if (lane < nv) red[lane * NW + warp] = v[0];
+        }
+        __syncthreads();
+        if (tid < nv) {
+            float acc = 0.f;
+            for (int w = 0; w < NW; w++) acc += red[tid * NW + w];
+            for (int o = 0; o < J; o++) cluster.map_shared_rank(pb, o)[jr * kParts + tid] = acc;
         }
         cluster.sync();
         if (tid < nv) {
             float acc = 0.f;
-            for (int q = 0; q < J * NW; q++) acc += pb[(size_t)q * kParts + tid];
+            for (int o = 0; o < J; o++) acc += pb[o * kParts + tid];
             G.red[tid] = acc;
         }
         __syncthreads();
@@ -520,14 +533,25 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
                 {
                     const float gam = G.gamma;
                     const int np = G.np;
+                    float c1r[kSlots], c2r[kSlots];
+                    const float2 *sp[kSlots], *yp[kSlots];
+#pragma unroll
+                    for (int k = 0; k < kSlots; k++) {
+                        const int a = G.slot[k < np ? k : 0];
+                        c1r[k] = k < np ? G.c1[k] : 0.f;
+                        c2r[k] = k < np ? G.c2[k] : 0.f;
+                        sp[k] = Ss + (size_t)a * SL;
+                        yp[k] = Ys + (size_t)a * SL;
+                    }
                     for (int i = tid; i < nmine; i += NT) {
                         float2 acc = cscale(gs[i], gam);
-                        for (int k = 0; k < np; k++) {
-                            const int a = G.slot[k];
-                            const float c1 = G.c1[k], c2 = G.c2[k];
-                            const float2 sa = Ss[(size_t)a * SL + i], ya = Ys[(size_t)a * SL + i];
-                            acc.x = fmaf(c1, sa.x, fmaf(c2, ya.x, acc.x));
-                            acc.y = fmaf(c1, sa.y, fmaf(c2, ya.y, acc.y));
+#pragma unroll
+                        for (int k = 0; k < kSlots; k++) {
+                            if (k < np) {
+                                const float2 sa = sp[k][i], ya = yp[k][i];
+                                acc.x = fmaf(c1r[k], sa.x, fmaf(c2r[k], ya.x, acc.x));
+                                acc.y = fmaf(c1r[k], sa.y, fmaf(c2r[k], ya.y, acc.y));
+                            }
                         }
                         const float2 p = make_float2(-acc.x, -acc.y);
                         Sn[i] = p;
@@ -593,6 +617,13 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
                     float pv[32];
 #pragma unroll
                     for (int k = 0; k < 32; k++) pv[k] = 0.f;
+                    const float2 *sp[kSlots], *yp[kSlots];
+#pragma unroll
+                    for (int k = 0; k < kSlots; k++) {
+                        const int a = G.slot[k <= np ? k : 0];
+                        sp[k] = Ss + (size_t)a * SL;
+                        yp[k] = Ys + (size_t)a * SL;
+                    }
                     for (int i = tid; i < nmine; i += NT) {
                         const float2 gn = slice_sum(i, -4.f);
                         const float2 yn = csub(gn, gs[i]);
@@ -602,9 +633,8 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
 #pragma unroll
                         for (int k = 0; k < kSlots; k++) {
                             if (k <= np) {  // live pairs by age, then the new one (age np)
-                                const int a = G.slot[k];
-                                const float2 sa = Ss[(size_t)a * SL + i];
-                                const float2 ya = Ys[(size_t)a * SL + i];
+                                const float2 sa = sp[k][i];
+                                const float2 ya = yp[k][i];
                                 pv[4 * k + 0] += cdotr(sa, yn);
                                 pv[4 * k + 1] += cdotr(ya, yn);
                                 pv[4 * k + 2] += cdotr(sa, gn);
