@@ -216,6 +216,7 @@ def main():
                phase_iters=args.phase_iters, seed=seed)
     dop = dict(ny=ny, nx=nx, n_defocus=Nd, coef=0.05)
     h = tmr.tmr_create(N, M, J, dg, dop, opt, stream=stream.cuda_stream)
+    sched = tmr.tmr_schedule(h)
     y = torch.empty((M, J, N), dtype=torch.float32, device="cuda")
     y_def = torch.empty((Nd, M), dtype=torch.float32, device="cuda")
     with torch.cuda.stream(stream):
@@ -337,6 +338,7 @@ def main():
                            "n_defocus": Nd, "phase_iters": args.phase_iters,
                            "l2": "inputs larger than L2 (y is 256 MB)",
                            "parallelism": f"{world} independent TMs, one per GPU"},
+                "schedule": {"masks_per_cta": sched, "autotuned": True},
                 "fidelity": {"mean": float(fid.mean()), "p1": float(np.percentile(fid, 1)),
                              "frac_ge_0.99": float(np.mean(fid >= 0.99)),
                              "matrix_after_phase_fit": mfid},

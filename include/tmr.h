@@ -96,18 +96,28 @@ typedef struct {
     double tol;             /* early exit when |f_prev - f| / f_prev < tol; 0 = off  */
     int phase_iters;        /* L-BFGS iterations of the phase-offset fit (default 100) */
     int precision;          /* TMR_PREC_FP32                                         */
-    int use_graph;          /* capture tmr_retrieve into a CUDA graph (default 0)    */
+    int use_graph;          /* replay tmr_retrieve from a captured CUDA graph (default 0) */
     size_t workspace_limit; /* max device bytes the handle may allocate; 0 = no cap  */
+    int schedule;           /* masks per CTA of the solver: 1, 2 or 4 (must divide J);
+                               0 = chosen by the autotuner (default)                 */
+    const char *tune_cache; /* JSON file caching autotuned schedules per device, N, J,
+                               m; NULL = this process only                           */
 } tmr_options;
 
 /* Fill *opt with the defaults above. */
 void tmr_default_options(tmr_options *opt);
 
-/* Create a handle for M rows of length N probed with J masks.
+/* Create a handle for M rows of length N probed with J masks.  With
+ * opt->schedule == 0 the first handle for a (device, N, J, m) times every
+ * solver schedule (G masks per CTA, a cluster of J/G CTAs per row) on
+ * synthetic rows and keeps the fastest; the choice is cached in memory and,
+ * when opt->tune_cache names a file, in that JSON file.
  *   masks      complex64 [J][N], |d| = 1 (not checked), copied.
  *   defocus_op NULL: no phase-offset fit; else copied (H copied).
  *   opt        NULL: defaults.
- *   stream     cudaStream_t for all work; NULL = the legacy default stream.
+ *   stream     cudaStream_t for all work; NULL = the legacy default stream (with
+ *              use_graph, a blocking stream the handle creates, which orders
+ *              itself with the legacy default stream).
  * Supported on the GPU: N a power of two with 64 <= N <= 4096, 1 <= J <= 8.
  * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
 tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
@@ -168,6 +178,10 @@ const char *tmr_last_error(void);
 /* Device bytes currently held by the handle. */
 size_t tmr_workspace_bytes(const tmr_handle *h);
 
+/* Masks per CTA of the solver schedule the handle uses (after autotuning),
+ * or 0 for a NULL handle. */
+int tmr_schedule(const tmr_handle *h);
+
 /* Release the handle and everything it allocated.  NULL is allowed. */
 void tmr_destroy(tmr_handle *h);
 
@@ -182,7 +196,8 @@ void tmr_destroy(tmr_handle *h);
  * no phase-offset fit) with the caller's arrays, all of which must be device
  * memory: masks complex64 [J][N], y float32 [M][J][N], T_out complex64 [M][N],
  * row_status / row_iters int32 [M] and row_loss float32 [M] (each may be NULL).
- * opt: NULL for the defaults; opt->workspace_limit and use_graph are ignored.
+ * opt: NULL for the defaults; workspace_limit, use_graph, schedule and tune_cache
+ * are ignored (one mask per CTA).
  * stream: cudaStream_t, NULL for the legacy default stream.
  *
  * Its only scratch (a row work counter and the FFT twiddle table) lives in

@@ -11,4 +11,4 @@ from ._lib import (  # noqa: F401
     TMR_PREC_FP32, TMR_ROW_CONVERGED, TMR_ROW_MAXITER, TMR_ROW_NUMERIC, TMR_ROW_ZERO, Handle,
     LIB_PATH, TMRError, header_symbols, lib, tmr_create, tmr_default_options, tmr_defocus_fit,
     tmr_defocus_forward, tmr_destroy, tmr_forward, tmr_grad, tmr_last_error, tmr_retrieve,
-    tmr_retrieve_from, tmr_retrieve_rows_static, tmr_sync, tmr_workspace_bytes)
+    tmr_retrieve_from, tmr_retrieve_rows_static, tmr_schedule, tmr_sync, tmr_workspace_bytes)

@@ -35,7 +35,8 @@ class tmr_options(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("init", ctypes.c_int), ("seed", ctypes.c_ulonglong),
                 ("power_iters", ctypes.c_int), ("clip", ctypes.c_double), ("tol", ctypes.c_double),
                 ("phase_iters", ctypes.c_int), ("precision", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("workspace_limit", ctypes.c_size_t)]
+                ("use_graph", ctypes.c_int), ("workspace_limit", ctypes.c_size_t),
+                ("schedule", ctypes.c_int), ("tune_cache", ctypes.c_char_p)]
 
 
 class tmr_defocus_op(ctypes.Structure):
@@ -62,6 +63,7 @@ def _load():
         "tmr_sync": ([H, ctypes.c_double], ctypes.c_int),
         "tmr_last_error": ([], ctypes.c_char_p),
         "tmr_workspace_bytes": ([H], ctypes.c_size_t),
+        "tmr_schedule": ([H], ctypes.c_int),
         "tmr_destroy": ([H], None),
         "tmr_retrieve_rows_static": ([ip, ip, ip, vp, fp, ip, ctypes.POINTER(tmr_options), vp, vp,
                                       vp, fp, vp], ctypes.c_int),
@@ -127,6 +129,8 @@ def tmr_default_options(**overrides) -> tmr_options:
     for k, v in overrides.items():
         if k == "init" and isinstance(v, str):
             v = INIT[v]
+        if k == "tune_cache" and isinstance(v, str):
+            v = v.encode()
         setattr(o, k, v)
     return o
 
@@ -230,6 +234,10 @@ def tmr_last_error() -> str:
 
 def tmr_workspace_bytes(h: Handle) -> int:
     return int(lib.tmr_workspace_bytes(h.raw))
+
+
+def tmr_schedule(h: Handle) -> int:
+    return int(lib.tmr_schedule(h.raw))
 
 
 def tmr_destroy(h: Handle):

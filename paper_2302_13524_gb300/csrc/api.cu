@@ -9,6 +9,10 @@
 #include <chrono>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
 #include <string>
 #include <thread>
 #include <vector>
@@ -87,6 +91,12 @@ struct tmr_handle {
     // last retrieve, for tmr_sync's numeric check
     const int *last_status = nullptr;
     bool last_had_fit = false;
+    int G = 1;  // solver schedule: masks per CTA
+    cudaStream_t own_stream = nullptr;  // created for graph capture when the caller gave none
+    // captured retrieve graph and the arguments it was captured with
+    cudaGraphExec_t gexec = nullptr;
+    const void *gkey[9] = {};
+    int giters = -1;
 };
 
 namespace {
@@ -151,6 +161,135 @@ tmr_status check_launch(cudaError_t e, const char *what)
     return TMR_OK;
 }
 
+// ---- schedule autotuner -----------------------------------------------------
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune_mem;
+
+std::map<std::string, int> read_tune_file(const char *path)
+{
+    std::map<std::string, int> out;
+    if (!path) return out;
+    std::ifstream f(path);
+    if (!f) return out;
+    std::stringstream ss;
+    ss << f.rdbuf();
+    const std::string t = ss.str();
+    size_t pos = 0;
+    while ((pos = t.find('"', pos)) != std::string::npos) {
+        const size_t end = t.find('"', pos + 1);
+        if (end == std::string::npos) break;
+        const std::string key = t.substr(pos + 1, end - pos - 1);
+        const size_t colon = t.find(':', end);
+        if (colon == std::string::npos) break;
+        out[key] = std::atoi(t.c_str() + colon + 1);
+        pos = colon + 1;
+    }
+    return out;
+}
+
+void write_tune_file(const char *path, const std::map<std::string, int> &m)
+{
+    if (!path) return;
+    std::ofstream f(path);
+    f << "{";
+    bool first = true;
+    for (auto &kv : m) {
+        f << (first ? "\n  " : ",\n  ") << '"' << kv.first << "\": " << kv.second;
+        first = false;
+    }
+    f << "\n}\n";
+}
+
+bool schedule_ok(int N, int J, int m, int G, int smem_optin)
+{
+    if (J % G != 0 || !solver_variant_exists(N, G)) return false;
+    const size_t b = solver_smem_bytes(N, J, m, G);
+    return b > 0 && b <= (size_t)smem_optin;
+}
+
+// Time every valid schedule on synthetic rows (spectral start, a few power
+// and L-BFGS iterations) and return the fastest.
+tmr_status autotune(tmr_handle *h, int smem_optin, int *G_out)
+{
+    int cand[3], nc = 0;
+    for (int G : {1, 2, 4})
+        if (schedule_ok(h->N, h->J, h->opt.m, G, smem_optin)) cand[nc++] = G;
+    if (nc == 0) return fail(TMR_ERR_UNSUPPORTED, "no solver schedule fits this (N, J, m)");
+    if (nc == 1) {
+        *G_out = cand[0];
+        return TMR_OK;
+    }
+    const int R = 608;
+    const size_t K = (size_t)h->J * h->N;
+    float *y = nullptr;
+    float2 *T = nullptr;
+    if (cudaMalloc(&y, sizeof(float) * R * K) != cudaSuccess ||
+        cudaMalloc(&T, sizeof(float2) * R * h->N) != cudaSuccess) {
+        cudaGetLastError();
+        if (y) cudaFree(y);
+        return fail(TMR_ERR_OOM, "autotuner buffers");
+    }
+    cudaStream_t s = h->stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    launch_fill_synthetic(y, R * K, 12345u, s);
+    SolverParams p{};
+    p.masks = h->masks;
+    p.tw = h->tw;
+    p.y = y;
+    p.T_out = T;
+    p.queue = h->queue;
+    p.M = R;
+    p.J = h->J;
+    p.iters = 6;
+    p.m = h->opt.m;
+    p.init = TMR_INIT_SPECTRAL;
+    p.power_iters = 4;
+    p.clip = 2.f;
+    float best = 1e30f;
+    int bestG = cand[0];
+    tmr_status st = TMR_OK;
+    for (int c = 0; c < nc && st == TMR_OK; c++) {
+        float ms = 0.f;
+        for (int rep = 0; rep < 3; rep++) {
+            cudaMemsetAsync(h->queue, 0, sizeof(unsigned) * 4, s);
+            cudaEventRecord(e0, s);
+            cudaError_t e = launch_solver(h->N, cand[c], p, s, nullptr);
+            cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                st = cuda_fail(e, "autotuner run");
+                break;
+            }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) ms += t;  // the first run warms up
+        }
+        if (st == TMR_OK && ms < best) {
+            best = ms;
+            bestG = cand[c];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(y);
+    cudaFree(T);
+    *G_out = bestG;
+    return st;
+}
+
+std::string tune_key(int dev, int N, int J, int m)
+{
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, dev);
+    char k[320];
+    snprintf(k, sizeof(k), "%s|sm%d%d|N%d|J%d|m%d", prop.name, prop.major, prop.minor, N, J, m);
+    for (char *c = k; *c; c++)
+        if (*c == '"' || *c == '\\') *c = '_';
+    return k;
+}
+
 }  // namespace
 
 extern "C" {
@@ -169,16 +308,22 @@ void tmr_default_options(tmr_options *o)
     o->precision = TMR_PREC_FP32;
     o->use_graph = 0;
     o->workspace_limit = 0;
+    o->schedule = 0;
+    o->tune_cache = nullptr;
 }
+
+int tmr_schedule(const tmr_handle *h) { return h ? h->G : 0; }
 
 const char *tmr_last_error(void) { return g_last_error_buf; }
 
 size_t tmr_workspace_bytes(const tmr_handle *h) { return h ? h->held : 0; }
 
+
 void tmr_destroy(tmr_handle *h)
 {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
     void *ptrs[] = {h->masks, h->tw, h->H, h->Zd, h->phi, h->pf_ws, h->pf_loss, h->wts, h->queue,
                     h->pf_sync, h->pf_err, h->pf_iters, h->status_scratch, h->iters_scratch,
                     h->loss_scratch};
@@ -186,6 +331,8 @@ void tmr_destroy(tmr_handle *h)
         if (p) cudaFree(p);
     for (auto &b : h->stage)
         if (b.p) cudaFree(b.p);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
 }
 
@@ -217,12 +364,28 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
             return fail(TMR_ERR_UNSUPPORTED, "defocus grid sides must be powers of two, grid <= 160 KB");
     }
 
+    int smem_optin = 0;
+    TMR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
+    if (o.schedule != 0 && !schedule_ok(N, J, o.m, o.schedule, smem_optin))
+        return fail(TMR_ERR_UNSUPPORTED, "opt.schedule must be 1, 2 or 4, divide J and fit the device");
+
     tmr_handle *h = new tmr_handle();
     h->N = N;
     h->M = M;
     h->J = J;
     h->opt = o;
+    h->opt.tune_cache = nullptr;  // the caller's string is not kept
     h->stream = (cudaStream_t)stream;
+    if (!h->stream && o.use_graph) {
+        // the legacy default stream cannot be captured: use a blocking stream
+        // of our own, which orders itself with the legacy default stream
+        if (cudaStreamCreate(&h->own_stream) != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return fail(TMR_ERR_CUDA, "stream for graph capture");
+        }
+        h->stream = h->own_stream;
+    }
     tmr_status st;
 #define TRY(x)                    \
     do {                          \
@@ -283,6 +446,34 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
         TRY(halloc(h, (void **)&h->pf_iters, sizeof(int) * 4, "phase iters"));
         TRY(halloc(h, (void **)&h->pf_loss, sizeof(double) * 4, "phase loss"));
         cudaMemset(h->pf_err, 0, sizeof(int) * 4);
+    }
+    // solver schedule: given, cached, or autotuned
+    if (o.schedule != 0) {
+        h->G = o.schedule;
+    } else {
+        const std::string key = tune_key(dev, N, J, o.m);
+        int G = 0;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_mem.find(key);
+            if (it != g_tune_mem.end()) G = it->second;
+            if (!G && o.tune_cache) {
+                auto fm = read_tune_file(o.tune_cache);
+                auto f = fm.find(key);
+                if (f != fm.end() && schedule_ok(N, J, o.m, f->second, smem_optin)) G = f->second;
+            }
+        }
+        if (!G) {
+            TRY(autotune(h, smem_optin, &G));
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune_mem[key] = G;
+            if (o.tune_cache) {
+                auto fm = read_tune_file(o.tune_cache);
+                fm[key] = G;
+                write_tune_file(o.tune_cache, fm);
+            }
+        }
+        h->G = G;
     }
 #undef TRY
     *out = h;
@@ -370,7 +561,7 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
         int dev = 0, smem_optin = 0;
         TMR_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
         TMR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
-        if (solver_smem_bytes(h->N, h->J, h->opt.m) > (size_t)smem_optin)
+        if (!schedule_ok(h->N, h->J, h->opt.m, h->G, smem_optin))
             return fail(TMR_ERR_UNSUPPORTED, "per-row state of this (N, J, m) does not fit in shared memory");
     }
     const size_t MN = (size_t)h->M * h->N, MK = MN * h->J;
@@ -388,7 +579,6 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
     if (row_iters && (st = stage(h, ST_ITERS, row_iters, sizeof(int) * h->M, false, &dI)) != TMR_OK) return st;
     if (row_loss && (st = stage(h, ST_LOSS, row_loss, sizeof(float) * h->M, false, &dL)) != TMR_OK) return st;
 
-    TMR_CUDA(cudaMemsetAsync(h->queue, 0, sizeof(unsigned) * 4, h->stream), "memset");
     SolverParams p{};
     p.masks = h->masks;
     p.tw = h->tw;
@@ -410,11 +600,49 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
     p.seed = h->opt.seed;
     p.clip = (float)h->opt.clip;
     p.tol = h->opt.tol;
-    int clusters = 0;
-    TMR_CUDA(launch_solver(h->N, p, h->stream, &clusters), "solver kernel");
-    if (fit) {
-        if ((st = run_phase_fit(h, (const float2 *)dT, (const float *)dYd, h->phi, (float2 *)dT)) != TMR_OK)
-            return st;
+    // the whole retrieve on the stream: solver, then the phase-offset fit
+    auto enqueue = [&]() -> tmr_status {
+        TMR_CUDA(cudaMemsetAsync(h->queue, 0, sizeof(unsigned) * 4, h->stream), "memset");
+        TMR_CUDA(launch_solver(h->N, h->G, p, h->stream, nullptr), "solver kernel");
+        if (fit) {
+            tmr_status s2 = run_phase_fit(h, (const float2 *)dT, (const float *)dYd, h->phi, (float2 *)dT);
+            if (s2 != TMR_OK) return s2;
+        }
+        return TMR_OK;
+    };
+    const bool all_device = dy == y && dT == T_out && (!T_init || dTin == T_init) &&
+                            (!fit || dYd == y_def) && (!row_status || dS == row_status) &&
+                            (!row_iters || dI == row_iters) && (!row_loss || dL == row_loss);
+    if (h->opt.use_graph && all_device) {
+        const void *key[9] = {dy, dT, dTin, dYd, dS, dI, dL, (const void *)(size_t)fit, nullptr};
+        bool same = h->gexec && h->giters == iters;
+        for (int i = 0; i < 9 && same; i++) same = h->gkey[i] == key[i];
+        if (!same) {
+            if (h->gexec) {
+                cudaGraphExecDestroy(h->gexec);
+                h->gexec = nullptr;
+            }
+            TMR_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            const tmr_status sc = enqueue();
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(h->stream, &graph);
+            if (sc != TMR_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return sc;
+            }
+            if (ec != cudaSuccess) return cuda_fail(ec, "end capture");
+            const cudaError_t ei = cudaGraphInstantiate(&h->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ei != cudaSuccess) {
+                h->gexec = nullptr;
+                return cuda_fail(ei, "graph instantiate");
+            }
+            for (int i = 0; i < 9; i++) h->gkey[i] = key[i];
+            h->giters = iters;
+        }
+        TMR_CUDA(cudaGraphLaunch(h->gexec, h->stream), "graph launch");
+    } else {
+        if ((st = enqueue()) != TMR_OK) return st;
     }
     h->last_status = (const int *)dS;
     h->last_had_fit = fit;

@@ -216,16 +216,21 @@ int phase_fit_grid(int ny, int nx, int Nd)
     return g < 1 ? 1 : g;
 }
 
-// workspace layout (doubles): phi, p, g, gn, phit, (S, Y)[m], part[grid][P], fpart[grid],
-// scal[64], then u[grid][P] as float2 (one e^{i phi} table per CTA)
+constexpr int kPfSlots = kMaxMem + 1;
+constexpr int kPfDots = 4 * kPfSlots + 4;  // per age 4 dots, then ss, gg, gmax, spare
+
+// workspace (in doubles): phi, p, g, phit, S[m+1], Y[m+1] (P each, chunk-owned),
+// fpart[grid], pdot[grid][kPfDots], part[grid][P] (floats), u[P] (float2)
 size_t phase_fit_workspace_doubles(int P, int Nd, int m, int grid)
 {
     (void)Nd;
-    return (size_t)P * (5 + 2 * m) + 2 * (size_t)grid * P + grid + 64;
+    return (size_t)P * (4 + 2 * (m + 1)) + grid + (size_t)grid * kPfDots + ((size_t)grid * P + 1) / 2 +
+           (size_t)P + 64;
 }
 
 struct PFWork {
-    double *phi, *p, *g, *gn, *phit, *S, *Y, *part, *fpart, *scal;
+    double *phi, *p, *g, *phit, *S, *Y, *fpart, *pdot;
+    float *part;
     float2 *u;
 };
 
@@ -235,73 +240,110 @@ __device__ PFWork pf_carve(double *ws, int P, int m, int grid)
     w.phi = ws;
     w.p = w.phi + P;
     w.g = w.p + P;
-    w.gn = w.g + P;
-    w.phit = w.gn + P;
+    w.phit = w.g + P;
     w.S = w.phit + P;
-    w.Y = w.S + (size_t)m * P;
-    w.part = w.Y + (size_t)m * P;
-    w.fpart = w.part + (size_t)grid * P;
-    w.scal = w.fpart + grid;
-    w.u = reinterpret_cast<float2 *>(w.scal + 64);
+    w.Y = w.S + (size_t)(m + 1) * P;
+    w.fpart = w.Y + (size_t)(m + 1) * P;
+    w.pdot = w.fpart + grid;
+    w.part = reinterpret_cast<float *>(w.pdot + (size_t)grid * kPfDots);
+    w.u = reinterpret_cast<float2 *>(w.pdot + (size_t)grid * kPfDots + ((size_t)grid * P + 1) / 2);
     return w;
 }
 
-// scal slots
-enum { SC_F = 0, SC_GP, SC_A, SC_NP, SC_FT, SC_ACCEPT, SC_STOP, SC_ITERS, SC_HEAD };
+// L-BFGS scalars of the phase fit (FP64), replicated in every CTA; pairs by age.
+struct PFGram {
+    double SY[kPfSlots][kPfSlots], YY[kPfSlots][kPfSlots];
+    double rD[kPfSlots], Sg[kPfSlots], Yg[kPfSlots], c1[kPfSlots], c2[kPfSlots];
+    double gamma, gg, gmax, f, gp, a;
+    double red[kPfDots];
+    int slot[kPfSlots];
+    int np, restart;
+};
 
-template <int NV>
-__device__ __forceinline__ void block_sum_d(double (&v)[NV], double *red, double *out)
+// compact-form coefficients (one thread); restart = 1 selects p = -g / max|g|
+__device__ void pf_coefficients(PFGram &G)
 {
-    block_sum<NV, double>(v, red, out);
+    const int np = G.np;
+    for (int i = 0; i < kPfSlots; i++) G.c1[i] = G.c2[i] = 0.0;
+    G.restart = 1;
+    if (np > 0) {
+        const double gamma = G.SY[np - 1][np - 1] / G.YY[np - 1][np - 1];
+        double c1[kPfSlots], c2[kPfSlots];
+        for (int i = np - 1; i >= 0; i--) {
+            double s = -G.Sg[i];
+            for (int j = i + 1; j < np; j++) s -= G.SY[i][j] * c2[j];
+            c2[i] = s * G.rD[i];
+        }
+        for (int i = 0; i < np; i++) {
+            double rhs = -G.SY[i][i] * c2[i] - gamma * G.Yg[i];
+            for (int j = 0; j < np; j++) rhs -= gamma * G.YY[i < j ? i : j][i < j ? j : i] * c2[j];
+            for (int j = 0; j < i; j++) rhs -= G.SY[j][i] * c1[j];
+            c1[i] = rhs * G.rD[i];
+        }
+        double pg = gamma * G.gg;
+        for (int i = 0; i < np; i++) pg += c1[i] * G.Sg[i] + gamma * c2[i] * G.Yg[i];
+        if (pg > 0.0 && isfinite(pg)) {
+            G.gamma = gamma;
+            for (int i = 0; i < np; i++) {
+                G.c1[i] = c1[i];
+                G.c2[i] = gamma * c2[i];
+            }
+            G.gp = -pg;
+            G.restart = 0;
+            return;
+        }
+        G.np = 0;
+    }
+    G.gamma = 1.0;
+    G.gp = G.gmax > 0.0 ? -G.gg / G.gmax : 0.0;
 }
 
-// Loss and gradient partials of this CTA's patterns at phase phi_src into
-// part[blockIdx.x][:] and fpart[blockIdx.x].
-__device__ void pf_eval(const PhaseFitParams &Pp, const PFWork &W, const double *phi_src, float2 *g,
-                        const float2 *twy, const float2 *twx, double *red, double *out)
+// Loss and gradient partials of this CTA's patterns for the phase table u:
+// part[blockIdx.x][:] (FP32, at most a few patterns per CTA) and fpart (FP64).
+__device__ void pf_eval(const PhaseFitParams &Pp, const PFWork &W, float2 *g, const float2 *twy,
+                        const float2 *twx, double *red, double *out)
 {
     const int ny = Pp.ny, nx = Pp.nx, P = ny * nx, pitch = nx + 1;
-    double *part = W.part + (size_t)blockIdx.x * P;
-    float2 *uu = W.u + (size_t)blockIdx.x * P;
-    for (int k = threadIdx.x; k < P; k += blockDim.x) {
-        part[k] = 0.0;
-        float s, c;
-        sincosf((float)remainder(__ldcg(phi_src + k), 2.0 * M_PI), &s, &c);
-        uu[k] = make_float2(c, s);
-    }
-    __syncthreads();
+    float *part = W.part + (size_t)blockIdx.x * P;
+    for (int k = threadIdx.x; k < P; k += blockDim.x) part[k] = 0.f;
     double fl = 0.0;
     for (int n = blockIdx.x; n < Pp.Nd; n += gridDim.x) {
         const float2 *cn = Pp.Zd + (size_t)n * P;
         const float *In = Pp.Ydef + (size_t)n * P;
-        for (int k = threadIdx.x; k < P; k += blockDim.x) g[(k / nx) * pitch + k % nx] = cmul(cn[k], uu[k]);
+        for (int k = threadIdx.x; k < P; k += blockDim.x)
+            g[(k / nx) * pitch + k % nx] = cmul(cn[k], __ldcg(W.u + k));
         __syncthreads();
         defocus_apply_smem(g, ny, nx, Pp.H, false, twy, twx);
         float fpl = 0.f;
         for (int k = threadIdx.x; k < P; k += blockDim.x) {
             const int gi = (k / nx) * pitch + k % nx;
             const float2 w = g[gi];
-            const float G = In[k] - cabs2(w);
-            fpl = fmaf(G, G, fpl);
-            g[gi] = cscale(w, G);
+            const float Gv = In[k] - cabs2(w);
+            fpl = fmaf(Gv, Gv, fpl);
+            g[gi] = cscale(w, Gv);
         }
         fl += (double)fpl;
         __syncthreads();
         defocus_apply_smem(g, ny, nx, Pp.H, true, twy, twx);
         for (int k = threadIdx.x; k < P; k += blockDim.x) {
             const float2 v = cmulc(g[(k / nx) * pitch + k % nx], cn[k]);  // conj(c_n) D^H(w G)
-            // -4 Im(conj(u) v)
-            const float2 cu = uu[k];
-            const float im = fmaf(cu.x, v.y, -cu.y * v.x);
-            part[k] += -4.0 * (double)im;
+            const float2 cu = __ldcg(W.u + k);
+            part[k] += -4.f * fmaf(cu.x, v.y, -cu.y * v.x);  // -4 Im(conj(u) v)
         }
         __syncthreads();
     }
     double fv[1] = {fl};
-    block_sum_d<1>(fv, red, out);
+    block_sum<1, double>(fv, red, out);
     if (threadIdx.x == 0) W.fpart[blockIdx.x] = out[0];
 }
 
+// The phase-offset fit: L-BFGS over phi from phi = 0 with Armijo backtracking.
+// CTA b owns the chunk [k0, k1) of every length-P vector (phi, g, p, the
+// pairs); the cross-CTA traffic is the phase table u (written by chunks, read
+// whole by every CTA's pattern evaluations), the gradient partials and one
+// batched FP64 reduction of dot products per accepted step.  Every CTA holds
+// the same FP64 L-BFGS scalars (identical sums in identical order), so all
+// take the same decisions.
 __global__ void __launch_bounds__(512) k_phase_fit(PhaseFitParams Pp)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -309,199 +351,206 @@ __global__ void __launch_bounds__(512) k_phase_fit(PhaseFitParams Pp)
     float2 *g = reinterpret_cast<float2 *>(smem_raw);
     float2 *twy = g + (size_t)ny * (nx + 1), *twx = twy + ny / 2;
     double *red = reinterpret_cast<double *>(twx + nx / 2 + 1);
-    double *out = red + 32 * 4;
+    double *out = red + 32 * kPfDots;
+    __shared__ PFGram G;
     PFWork W = pf_carve(Pp.ws, P, m, nb);
     make_tw(twy, ny);
     make_tw(twx, nx);
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int chunk = (P + nb - 1) / nb, k0 = blockIdx.x * chunk, k1 = min(P, k0 + chunk);
+    const int chunk = (P + nb - 1) / nb, k0 = min(P, blockIdx.x * chunk), k1 = min(P, k0 + chunk);
+    double *Sg_ = W.S, *Yg_ = W.Y;
 
-    for (int k = k0 + tid; k < k1; k += nt) W.phi[k] = 0.0;
-    if (!grid_sync(Pp.sync, Pp.err)) return;
-    pf_eval(Pp, W, W.phi, g, twy, twx, red, out);
-    if (!grid_sync(Pp.sync, Pp.err)) return;
+    // reduce kPfDots per-thread values over the grid: block sums to pdot[b], a
+    // grid barrier, then every CTA adds the nb partials in order into G.red
+    auto grid_dots = [&](double (&v)[kPfDots], double vmax) -> bool {
+        block_sum<kPfDots, double>(v, red, out);
+        __shared__ double mx[32];
+        double mv = vmax;
+        for (int o = 16; o > 0; o >>= 1) mv = fmax(mv, __shfl_xor_sync(0xffffffffu, mv, o));
+        if ((tid & 31) == 0) mx[tid >> 5] = mv;
+        __syncthreads();
+        if (tid < kPfDots) {
+            double val = out[tid];
+            if (tid == kPfDots - 2) {
+                val = 0.0;
+                for (int w = 0; w < nt / 32; w++) val = fmax(val, mx[w]);
+            }
+            W.pdot[(size_t)blockIdx.x * kPfDots + tid] = val;
+        }
+        if (!grid_sync(Pp.sync, Pp.err)) return false;
+        if (tid < kPfDots) {
+            double acc = 0.0;
+            for (int b = 0; b < nb; b++) {
+                const double x = __ldcg(W.pdot + (size_t)b * kPfDots + tid);
+                acc = (tid == kPfDots - 2) ? fmax(acc, x) : acc + x;
+            }
+            G.red[tid] = acc;
+        }
+        __syncthreads();
+        return true;
+    };
+    // phase table of phit for my chunk
+    auto write_u = [&](const double *ph) {
+        for (int k = k0 + tid; k < k1; k += nt) {
+            float s, c;
+            sincosf((float)ph[k], &s, &c);
+            W.u[k] = make_float2(c, s);
+        }
+    };
+
+    // ---- phi = 0: loss and gradient ----
     for (int k = k0 + tid; k < k1; k += nt) {
-        double s = 0.0;
-        for (int b = 0; b < nb; b++) s += __ldcg(W.part + (size_t)b * P + k);
-        W.g[k] = s;
+        W.phi[k] = 0.0;
+        W.phit[k] = 0.0;
     }
-    if (blockIdx.x == 0 && tid == 0) {
+    write_u(W.phit);
+    if (!grid_sync(Pp.sync, Pp.err)) return;
+    pf_eval(Pp, W, g, twy, twx, red, out);
+    if (!grid_sync(Pp.sync, Pp.err)) return;
+    {
+        double v[kPfDots] = {0.0};
+        double vmax = 0.0;
+        for (int k = k0 + tid; k < k1; k += nt) {
+            double s = 0.0;
+            for (int b = 0; b < nb; b++) s += (double)__ldcg(W.part + (size_t)b * P + k);
+            W.g[k] = s;
+            v[4 * kPfSlots + 1] += s * s;
+            vmax = fmax(vmax, fabs(s));
+        }
+        if (!grid_dots(v, vmax)) return;
+    }
+    if (tid == 0) {
         double f = 0.0;
         for (int b = 0; b < nb; b++) f += __ldcg(W.fpart + b);
-        W.scal[SC_F] = f;
-        W.scal[SC_NP] = 0;
-        W.scal[SC_HEAD] = 0;
-        W.scal[SC_ITERS] = 0;
-        W.scal[SC_STOP] = 0;
+        G.f = f;
+        G.gg = G.red[4 * kPfSlots + 1];
+        G.gmax = G.red[kPfDots - 2];
+        G.np = 0;
+        for (int i = 0; i < kPfSlots; i++) G.slot[i] = i;
+        pf_coefficients(G);
     }
-    if (!grid_sync(Pp.sync, Pp.err)) return;
+    __syncthreads();
 
+    int done = 0;
     for (int it = 0; it < Pp.iters; it++) {
-        // ---- direction (CTA 0, FP64 two-loop over the ring of pairs) ----
-        if (blockIdx.x == 0) {
-            const int np = (int)__ldcg(W.scal + SC_NP), head = (int)__ldcg(W.scal + SC_HEAD);  // head: slot of the oldest pair
-            __shared__ double alph[kMaxMem];
-            for (int k = tid; k < P; k += nt) W.p[k] = __ldcg(W.g + k);
-            __syncthreads();
-            for (int q = np - 1; q >= 0; q--) {
-                const int sl = (head + q) % m;
-                const double *s = W.S + (size_t)sl * P, *y = W.Y + (size_t)sl * P;
-                double v[2] = {0.0, 0.0};
-                for (int k = tid; k < P; k += nt) {
-                    v[0] += s[k] * y[k];
-                    v[1] += s[k] * W.p[k];
+        if (!(G.gmax > 0.0)) break;
+        // ---- direction on my chunk ----
+        {
+            const double gam = G.gamma, ig = 1.0 / G.gmax;
+            const int np = G.np, rs = G.restart;
+            for (int k = k0 + tid; k < k1; k += nt) {
+                double acc;
+                if (rs) {
+                    acc = W.g[k] * ig;
+                } else {
+                    acc = gam * W.g[k];
+                    for (int i = 0; i < np; i++) {
+                        const size_t sl = (size_t)G.slot[i] * P + k;
+                        acc += G.c1[i] * Sg_[sl] + G.c2[i] * Yg_[sl];
+                    }
                 }
-                block_sum_d<2>(v, red, out);
-                const double a = out[1] / out[0];
-                if (tid == 0) alph[q] = a;
-                for (int k = tid; k < P; k += nt) W.p[k] -= a * y[k];
-                __syncthreads();
-            }
-            if (np > 0) {
-                const int sl = (head + np - 1) % m;
-                const double *s = W.S + (size_t)sl * P, *y = W.Y + (size_t)sl * P;
-                double v[2] = {0.0, 0.0};
-                for (int k = tid; k < P; k += nt) {
-                    v[0] += s[k] * y[k];
-                    v[1] += y[k] * y[k];
-                }
-                block_sum_d<2>(v, red, out);
-                const double gam = out[0] / out[1];
-                for (int k = tid; k < P; k += nt) W.p[k] *= gam;
-                __syncthreads();
-            }
-            for (int q = 0; q < np; q++) {
-                const int sl = (head + q) % m;
-                const double *s = W.S + (size_t)sl * P, *y = W.Y + (size_t)sl * P;
-                double v[2] = {0.0, 0.0};
-                for (int k = tid; k < P; k += nt) {
-                    v[0] += s[k] * y[k];
-                    v[1] += y[k] * W.p[k];
-                }
-                block_sum_d<2>(v, red, out);
-                const double b = out[1] / out[0];
-                const double a = alph[q];
-                for (int k = tid; k < P; k += nt) W.p[k] += s[k] * (a - b);
-                __syncthreads();
-            }
-            double v[2] = {0.0, 0.0};
-            for (int k = tid; k < P; k += nt) {
-                W.p[k] = -W.p[k];
-                v[0] += W.g[k] * W.p[k];
-                v[1] = fmax(v[1], fabs(W.g[k]));
-            }
-            // max via a separate pass: reuse block_sum on the sum, max below
-            __shared__ double gmaxs[32];
-            double mx = v[1];
-            for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            if ((tid & 31) == 0) gmaxs[tid >> 5] = mx;
-            double sv[1] = {v[0]};
-            block_sum_d<1>(sv, red, out);
-            double gmax = 0.0;
-            for (int w = 0; w < nt / 32; w++) gmax = fmax(gmax, gmaxs[w]);
-            double gp = out[0];
-            __syncthreads();
-            if (gmax == 0.0) {
-                if (tid == 0) W.scal[SC_STOP] = 1;
-            } else if (np == 0 || !(gp < 0.0)) {
-                for (int k = tid; k < P; k += nt) W.p[k] = -W.g[k] / gmax;
-                double s2[1] = {0.0};
-                for (int k = tid; k < P; k += nt) s2[0] += W.g[k] * W.p[k];
-                block_sum_d<1>(s2, red, out);
-                gp = out[0];
-                if (tid == 0) W.scal[SC_NP] = 0;
-            }
-            if (tid == 0) {
-                W.scal[SC_GP] = gp;
-                W.scal[SC_A] = 1.0;
+                W.p[k] = -acc;
             }
         }
-        if (!grid_sync(Pp.sync, Pp.err)) return;
-        if (__ldcg(W.scal + SC_STOP) != 0.0) break;
-
         // ---- Armijo backtracking ----
+        const double f0 = G.f, gp = G.gp;
+        double a = 1.0, ft = 0.0;
         bool accepted = false;
         for (int h = 0; h <= 30; h++) {
-            const double a = __ldcg(W.scal + SC_A);
-            // every CTA evaluates at phit = phi + a p; CTA b writes its chunk of phit
-            for (int k = k0 + tid; k < k1; k += nt) W.phit[k] = __ldcg(W.phi + k) + a * __ldcg(W.p + k);
+            for (int k = k0 + tid; k < k1; k += nt) W.phit[k] = W.phi[k] + a * W.p[k];
+            write_u(W.phit);
             if (!grid_sync(Pp.sync, Pp.err)) return;
-            pf_eval(Pp, W, W.phit, g, twy, twx, red, out);
+            pf_eval(Pp, W, g, twy, twx, red, out);
             if (!grid_sync(Pp.sync, Pp.err)) return;
-            double ft = 0.0;
+            ft = 0.0;
             for (int b = 0; b < nb; b++) ft += __ldcg(W.fpart + b);
-            const double f = __ldcg(W.scal + SC_F), gp = __ldcg(W.scal + SC_GP);
-            if (ft <= f + 1e-4 * a * gp) {
+            if (ft <= f0 + 1e-4 * a * gp) {
                 accepted = true;
-                for (int k = k0 + tid; k < k1; k += nt) {
-                    double s = 0.0;
-                    for (int b = 0; b < nb; b++) s += __ldcg(W.part + (size_t)b * P + k);
-                    W.gn[k] = s;
-                }
-                if (blockIdx.x == 0 && tid == 0) W.scal[SC_FT] = ft;
                 break;
             }
-            // all CTAs agree on the decision; CTA 0 halves the step after everyone read it
-            if (!grid_sync(Pp.sync, Pp.err)) return;
-            if (blockIdx.x == 0 && tid == 0) W.scal[SC_A] = 0.5 * a;
-            if (!grid_sync(Pp.sync, Pp.err)) return;
+            a *= 0.5;
         }
         if (!accepted) break;
-        if (!grid_sync(Pp.sync, Pp.err)) return;
-
-        // ---- new pair, accept step (CTA 0) ----
-        if (blockIdx.x == 0) {
-            const int np = (int)__ldcg(W.scal + SC_NP), head = (int)__ldcg(W.scal + SC_HEAD);
-            const int sl = (head + np) % m;  // next slot (overwrites the oldest when full)
-            double *s = W.S + (size_t)sl * P, *y = W.Y + (size_t)sl * P;
-            double v[3] = {0.0, 0.0, 0.0};
-            for (int k = tid; k < P; k += nt) {
-                const double sv = __ldcg(W.phit + k) - W.phi[k], yv = __ldcg(W.gn + k) - __ldcg(W.g + k);
-                v[0] += sv * yv;
-                v[1] += sv * sv;
-                v[2] += yv * yv;
-            }
-            block_sum_d<3>(v, red, out);
-            const bool ok = out[0] > 1e-10 * sqrt(out[1]) * sqrt(out[2]) && out[0] > 0.0;
-            if (ok) {
-                for (int k = tid; k < P; k += nt) {
-                    s[k] = __ldcg(W.phit + k) - W.phi[k];
-                    y[k] = __ldcg(W.gn + k) - __ldcg(W.g + k);
+        // ---- accept: new gradient, pair and dot products on my chunk ----
+        {
+            const int np = G.np, ns = G.slot[np];
+            double v[kPfDots] = {0.0};
+            double vmax = 0.0;
+            for (int k = k0 + tid; k < k1; k += nt) {
+                double gn = 0.0;
+                for (int b = 0; b < nb; b++) gn += (double)__ldcg(W.part + (size_t)b * P + k);
+                const double sv = W.phit[k] - W.phi[k], yv = gn - W.g[k];
+                Sg_[(size_t)ns * P + k] = sv;
+                Yg_[(size_t)ns * P + k] = yv;
+                W.phi[k] = W.phit[k];
+                W.g[k] = gn;
+                for (int i = 0; i <= np; i++) {
+                    const size_t sl = (size_t)G.slot[i] * P + k;
+                    const double si = Sg_[sl], yi = Yg_[sl];
+                    v[4 * i + 0] += si * yv;
+                    v[4 * i + 1] += yi * yv;
+                    v[4 * i + 2] += si * gn;
+                    v[4 * i + 3] += yi * gn;
                 }
+                v[4 * kPfSlots + 0] += sv * sv;
+                v[4 * kPfSlots + 1] += gn * gn;
+                vmax = fmax(vmax, fabs(gn));
+            }
+            if (!grid_dots(v, vmax)) return;
+            if (tid == 0) {
+                const double *t = G.red;
+                for (int i = 0; i <= np; i++) {
+                    G.SY[i][np] = t[4 * i + 0];
+                    G.YY[i][np] = t[4 * i + 1];
+                    G.Sg[i] = t[4 * i + 2];
+                    G.Yg[i] = t[4 * i + 3];
+                }
+                const double sy = t[4 * np + 0], yy = t[4 * np + 1], ss = t[4 * kPfSlots + 0];
+                G.gg = t[4 * kPfSlots + 1];
+                G.gmax = t[kPfDots - 2];
+                G.f = ft;
+                if (sy > 1e-10 * sqrt(ss) * sqrt(yy) && sy > 0.0) {
+                    G.rD[np] = 1.0 / sy;
+                    G.np = np + 1;
+                    if (G.np > m) {  // drop the oldest pair; its slot becomes the free one
+                        const int s0 = G.slot[0];
+                        for (int i = 0; i < m; i++) {
+                            for (int j = i; j < m; j++) {
+                                G.SY[i][j] = G.SY[i + 1][j + 1];
+                                G.YY[i][j] = G.YY[i + 1][j + 1];
+                            }
+                            G.Sg[i] = G.Sg[i + 1];
+                            G.Yg[i] = G.Yg[i + 1];
+                            G.rD[i] = G.rD[i + 1];
+                            G.slot[i] = G.slot[i + 1];
+                        }
+                        G.slot[m] = s0;
+                        G.np = m;
+                    }
+                }
+                pf_coefficients(G);
             }
             __syncthreads();
-            for (int k = tid; k < P; k += nt) {
-                W.phi[k] = __ldcg(W.phit + k);
-                W.g[k] = __ldcg(W.gn + k);
-            }
-            if (tid == 0) {
-                if (ok) {
-                    if (np == m) W.scal[SC_HEAD] = (head + 1) % m;
-                    else W.scal[SC_NP] = np + 1;
-                }
-                W.scal[SC_F] = __ldcg(W.scal + SC_FT);
-                W.scal[SC_ITERS] = it + 1;
-            }
         }
-        if (!grid_sync(Pp.sync, Pp.err)) return;
+        done = it + 1;
     }
 
-    // ---- remove the free constant: arg(sum_k w_k e^{i phi_k}) = 0; write phi ----
-    if (blockIdx.x == 0) {
-        double v[2] = {0.0, 0.0};
-        for (int k = tid; k < P; k += nt) {
+    // ---- remove the free constant: arg(sum_k w_k e^{i phi_k}) = 0 ----
+    {
+        double v[kPfDots] = {0.0};
+        for (int k = k0 + tid; k < k1; k += nt) {
             double s, c;
             sincos(W.phi[k], &s, &c);
             const double wk = Pp.wts ? (double)Pp.wts[k] : 1.0;
             v[0] += wk * c;
             v[1] += wk * s;
         }
-        block_sum_d<2>(v, red, out);
-        const double shift = atan2(out[1], out[0]);
-        for (int k = tid; k < P; k += nt) Pp.phi[k] = W.phi[k] - shift;
-        if (tid == 0) {
-            if (Pp.iters_done) *Pp.iters_done = (int)W.scal[SC_ITERS];
-            if (Pp.loss_out) *Pp.loss_out = W.scal[SC_F];
+        if (!grid_dots(v, 0.0)) return;
+        const double shift = atan2(G.red[1], G.red[0]);
+        for (int k = k0 + tid; k < k1; k += nt) Pp.phi[k] = W.phi[k] - shift;
+        if (blockIdx.x == 0 && tid == 0) {
+            if (Pp.iters_done) *Pp.iters_done = done;
+            if (Pp.loss_out) *Pp.loss_out = G.f;
         }
     }
 }
@@ -510,7 +559,7 @@ cudaError_t launch_phase_fit(const PhaseFitParams &p, cudaStream_t s)
 {
     const int grid = phase_fit_grid(p.ny, p.nx, p.Nd);
     const int P = p.ny * p.nx;
-    const size_t sm = defocus_smem(p.ny, p.nx) + sizeof(double) * (32 * 4 + 16) + 2 * sizeof(float2);
+    const size_t sm = defocus_smem(p.ny, p.nx) + sizeof(double) * (32 * kPfDots + kPfDots + 8) + 2 * sizeof(float2);
     (void)P;
     cudaError_t e = cudaFuncSetAttribute(k_phase_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;

@@ -44,8 +44,12 @@ struct SolverParams {
     float clip;
     double tol;
 };
-size_t solver_smem_bytes(int N, int J, int m);
-cudaError_t launch_solver(int N, const SolverParams &p, cudaStream_t s, int *clusters_out);
+// Variants: G masks per CTA (G in {1, 2, 4}, G divides J), cluster of J/G CTAs.
+bool solver_variant_exists(int N, int G);
+size_t solver_smem_bytes(int N, int J, int m, int G);
+cudaError_t launch_solver(int N, int G, const SolverParams &p, cudaStream_t s, int *clusters_out);
+// Synthetic positive intensities for timing runs (autotuner).
+cudaError_t launch_fill_synthetic(float *y, size_t n, unsigned seed, cudaStream_t s);
 
 // ---- defocus operator and phase-offset fit (defocus.cu) --------------------
 struct PhaseFitParams {

@@ -164,16 +164,22 @@ __global__ void __launch_bounds__(fft_threads(N)) k_fields(const float2 *__restr
     }
 }
 
+// T[r] *= e^{i phi[r]}: one CTA per row (strided), the phase factor made once per row.
 __global__ void k_apply_phase(int N, int M, const double *__restrict__ phi,
                               const float2 *__restrict__ Tin, float2 *__restrict__ Tout)
 {
-    const size_t total = (size_t)M * N;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int r = (int)(i / N);
-        double s, c;
-        sincos(phi[r], &s, &c);
-        Tout[i] = cmul(Tin[i], make_float2((float)c, (float)s));
+    __shared__ float2 u;
+    for (int r = blockIdx.x; r < M; r += gridDim.x) {
+        if (threadIdx.x == 0) {
+            double s, c;
+            sincos(phi[r], &s, &c);
+            u = make_float2((float)c, (float)s);
+        }
+        __syncthreads();
+        const float2 ur = u;
+        for (int n = threadIdx.x; n < N; n += blockDim.x)
+            Tout[(size_t)r * N + n] = cmul(Tin[(size_t)r * N + n], ur);
+        __syncthreads();
     }
 }
 
@@ -233,10 +239,25 @@ cudaError_t launch_apply_phase(int N, int M, const double *phi, const float2 *Ti
                                cudaStream_t s)
 {
     if (M == 0) return cudaSuccess;
-    const size_t total = (size_t)M * N;
-    int blocks = (int)((total + 255) / 256);
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    const int blocks = M < 152 * 16 ? M : 152 * 16;
     k_apply_phase<<<blocks, 256, 0, s>>>(N, M, phi, Tin, Tout);
+    return cudaGetLastError();
+}
+
+// y[i] = -ln(u) with u uniform in (0, 1] from a counter hash: exponential
+// intensities with mean 1, like fully developed speckle.
+__global__ void k_fill_synthetic(float *y, size_t n, unsigned seed)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const uint4 o = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(i >> 32), seed, 7u), make_uint2(seed, 11u));
+        const float u = fmaf((float)o.x, 0x1p-32f, 0x1p-33f);
+        y[i] = -logf(u);
+    }
+}
+
+cudaError_t launch_fill_synthetic(float *y, size_t n, unsigned seed, cudaStream_t s)
+{
+    k_fill_synthetic<<<512, 256, 0, s>>>(y, n, seed);
     return cudaGetLastError();
 }
 

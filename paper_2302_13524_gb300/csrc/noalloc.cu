@@ -104,7 +104,8 @@ extern "C" tmr_status tmr_retrieve_rows_static(int N, int M, int J, const void *
         return fail(TMR_ERR_CUDA, "cudaGetDevice failed or device ordinal too large");
     if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return fail(TMR_ERR_CUDA, "cudaDeviceGetAttribute failed");
-    if (tmr::solver_smem_bytes(N, J, o.m) > (size_t)smem_optin)
+    const size_t smem = tmr::solver_smem_bytes(N, J, o.m, 1);
+    if (smem == 0 || smem > (size_t)smem_optin)
         return fail(TMR_ERR_UNSUPPORTED, "per-row state of this (N, J, m) does not fit in shared memory");
 
     void *base = nullptr;
@@ -149,7 +150,7 @@ extern "C" tmr_status tmr_retrieve_rows_static(int N, int M, int J, const void *
     p.seed = o.seed;
     p.clip = (float)o.clip;
     p.tol = o.tol;
-    const cudaError_t e = tmr::launch_solver(N, p, s, nullptr);
+    const cudaError_t e = tmr::launch_solver(N, 1, p, s, nullptr);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(TMR_ERR_CUDA, "solver launch failed");

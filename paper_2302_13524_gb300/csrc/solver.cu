@@ -241,75 +241,83 @@ __device__ __forceinline__ void warp_reduce32(float (&v)[32], int lane)
     }
 }
 
-template <int N>
+// G masks per CTA (G teams of NT threads, one FFT each); the cluster has J/G CTAs.
+template <int N, int G>
 struct SolverCfg {
-    static constexpr int NT = fft_threads(N);
+    static constexpr int NT = fft_threads(N);  // threads per team (one FFT)
+    static constexpr int BT = G * NT;          // threads per CTA
     static constexpr int E = N / NT;
-    static constexpr int NW = NT / 32;
+    static constexpr int NW = BT / 32;
     static constexpr int TWS = FftSmall<N, NT>::TW_SMALL;
 };
 
-template <int N>
+template <int N, int G>
 __host__ __device__ size_t solver_smem(int J, int m)
 {
-    using C = SolverCfg<N>;
-    const size_t SL = (N + J - 1) / J;
-    size_t f2 = (size_t)fft_buf_len(N) /*X and FFT exchange*/ + C::TWS + (size_t)J * SL /*Y*/ +
-                2 * SL /*t, g*/ + 2 * (size_t)(m + 1) * SL /*pairs*/;
+    using C = SolverCfg<N, G>;
+    const int JC = J / G;
+    const size_t SL = (N + JC - 1) / JC;
+    size_t f2 = (size_t)G * fft_buf_len(N) /*X (team 0's exchange) and the others' exchange*/ + C::TWS +
+                (size_t)J * SL /*Y*/ + 2 * SL /*t, g*/ + 2 * (size_t)(m + 1) * SL /*pairs*/;
     size_t bytes = f2 * sizeof(float2);
-    bytes += sizeof(float) * ((size_t)kParts * C::NW + 2 * (size_t)J * kParts);
+    bytes += sizeof(float) * ((size_t)kParts * C::NW + 2 * (size_t)JC * kParts);
     bytes = (bytes + 15) & ~(size_t)15;
     return bytes + sizeof(Gram);
 }
 
-template <int N>
-__global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 : 1) k_solver(SolverParams P)
+template <int N, int G>
+__global__ void __launch_bounds__(SolverCfg<N, G>::BT, (SolverCfg<N, G>::BT <= 256 && N >= 256) ? 2 : 1)
+    k_solver(SolverParams P)
 {
-    using C = SolverCfg<N>;
-    constexpr int NT = C::NT, E = C::E, NW = C::NW;
+    using C = SolverCfg<N, G>;
+    constexpr int NT = C::NT, BT = C::BT, E = C::E, NW = C::NW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cg::cluster_group cluster = cg::this_cluster();
     const int J = P.J, m = P.m, M = P.M;
+    const int JC = J / G;  // CTAs in the cluster
     const int jr = (int)cluster.block_rank();
     const int tid = threadIdx.x;
-    const int SL = (N + J - 1) / J;
-    const int lo = (jr * N) / J, hi = ((jr + 1) * N) / J;  // my slice [lo, hi)
+    const int team = tid / NT, ttid = tid - team * NT;
+    const int jm = jr * G + team;  // the mask of this thread's team
+    const int SL = (N + JC - 1) / JC;
+    const int lo = (jr * N) / JC, hi = ((jr + 1) * N) / JC;  // my slice [lo, hi)
     const int nmine = hi - lo;
     const size_t K = (size_t)J * N;
-    const bool even = (N % J) == 0;  // slices of equal length SL = N / J
+    const bool even = (N % JC) == 0;  // slices of equal length SL = N / JC
 
     // ---- shared memory ----
     float2 *X = reinterpret_cast<float2 *>(smem_raw);
-    float2 *buf = X;  // exchange buffer of every FFT: X is free once gathered
-    float2 *tws = X + fft_buf_len(N);
+    // exchange buffer of this team's FFTs: team 0 reuses X (free once gathered)
+    float2 *buf = X + (size_t)team * fft_buf_len(N);
+    float2 *tws = X + (size_t)G * fft_buf_len(N);
     float2 *Yr = tws + C::TWS;  // [J][SL]
     float2 *ts = Yr + (size_t)J * SL;
     float2 *gs = ts + SL;
     float2 *Ss = gs + SL;  // slot a at Ss + a*SL
     float2 *Ys = Ss + (size_t)(m + 1) * SL;
     float *red = reinterpret_cast<float *>(Ys + (size_t)(m + 1) * SL);  // [kParts][NW]
-    float *part = red + kParts * NW;                                      // [2][J][kParts]
-    Gram &G = *reinterpret_cast<Gram *>(
-        smem_raw + ((reinterpret_cast<unsigned char *>(part + 2 * J * kParts) - smem_raw + 15) &
+    float *part = red + kParts * NW;                                      // [2][JC][kParts]
+    Gram &Gm = *reinterpret_cast<Gram *>(
+        smem_raw + ((reinterpret_cast<unsigned char *>(part + 2 * JC * kParts) - smem_raw + 15) &
                     ~(size_t)15));
 
-    for (int i = tid; i < C::TWS; i += NT) tws[i] = P.tw[i];
+    for (int i = tid; i < C::TWS; i += BT) tws[i] = P.tw[i];
     float2 dm[E];
 #pragma unroll
-    for (int e = 0; e < E; e++) dm[e] = P.masks[(size_t)jr * N + tid + e * NT];
+    for (int e = 0; e < E; e++) dm[e] = P.masks[(size_t)jm * N + ttid + e * NT];
     float2 wb;
     {
         double s, c;
-        sincospi(-2.0 * (double)tid / (double)N, &s, &c);
+        sincospi(-2.0 * (double)ttid / (double)N, &s, &c);
         wb = make_float2((float)c, (float)s);
     }
     const int sl_shift = (even && (SL & (SL - 1)) == 0) ? __ffs(SL) - 1 : -1;
     auto owner = [&](int n) {
         if (sl_shift >= 0) return n >> sl_shift;
         if (even) return n / SL;
-        int o = (int)(((long long)n * J) / N);
-        while (o + 1 < J && ((o + 1) * N) / J <= n) o++;
-        while (o > 0 && (o * N) / J > n) o--;
+        int o = (int)(((long long)n * JC) / N);
+        while (o + 1 < JC && ((o + 1) * N) / JC <= n) o++;
+        while (o > 0 && (o * N) / JC > n) o--;
         return o;
     };
     cluster.sync();  // every CTA of the cluster runs before anyone touches its shared memory
@@ -320,13 +328,13 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
     // thread k, which stores the CTA's sum of value k into part[sel][jr][k]
     // of every CTA (its own copy locally, the peers' by DSMEM stores); one
     // cluster barrier; thread k adds the J partials in rank order into
-    // G.red[k] and the block synchronises.  The two part buffers alternate: a
+    // Gm.red[k] and the block synchronises.  The two part buffers alternate: a
     // peer may still read the previous one after this barrier but not the one
     // before.
     const int lane = tid & 31, warp = tid >> 5;
     int sel = 0;
     auto cluster_sum = [&](float (&v)[32], int nv) {
-        float *pb = part + (size_t)sel * J * kParts;
+        float *pb = part + (size_t)sel * JC * kParts;
         sel ^= 1;
         if (nv <= 6) {
             for (int k = 0; k < nv; k++) {
@@ -341,30 +349,30 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
         if (tid < nv) {
             float acc = 0.f;
             for (int w = 0; w < NW; w++) acc += red[tid * NW + w];
-            for (int o = 0; o < J; o++) cluster.map_shared_rank(pb, o)[jr * kParts + tid] = acc;
+            for (int o = 0; o < JC; o++) cluster.map_shared_rank(pb, o)[jr * kParts + tid] = acc;
         }
         cluster.sync();
         if (tid < nv) {
             float acc = 0.f;
-            for (int o = 0; o < J; o++) acc += pb[o * kParts + tid];
-            G.red[tid] = acc;
+            for (int o = 0; o < JC; o++) acc += pb[o * kParts + tid];
+            Gm.red[tid] = acc;
         }
         __syncthreads();
     };
     // my slice (length nmine) into X of every CTA
     auto push_slice_to_X = [&](const float2 *src) {
-        for (int i = tid; i < nmine; i += NT) {
+        for (int i = tid; i < nmine; i += BT) {
             const float2 v = src[i];
-            for (int o = 0; o < J; o++) cluster.map_shared_rank(X, o)[lo + i] = v;
+            for (int o = 0; o < JC; o++) cluster.map_shared_rank(X, o)[lo + i] = v;
         }
     };
-    // thread-strided natural-order vector v to the owners' Y[jr][:]
+    // this team's thread-strided natural-order vector v to the owners' Y[jm][:]
     auto push_to_owners = [&](const float2 (&v)[E]) {
 #pragma unroll
         for (int e = 0; e < E; e++) {
-            const int n = tid + e * NT;
+            const int n = ttid + e * NT;
             const int o = owner(n);
-            cluster.map_shared_rank(Yr, o)[(size_t)jr * SL + (n - (o * N) / J)] = v[e];
+            cluster.map_shared_rank(Yr, o)[(size_t)jm * SL + (n - (o * N) / JC)] = v[e];
         }
     };
     // element i of my slice of sum_j Y[j], times s
@@ -377,57 +385,57 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
     while (true) {
         if (jr == 0 && tid == 0) {
             const int r = (int)atomicAdd(P.queue, 1u);
-            for (int o = 0; o < J; o++) cluster.map_shared_rank(&G.row, o)[0] = r;
+            for (int o = 0; o < JC; o++) cluster.map_shared_rank(&Gm.row, o)[0] = r;
         }
         cluster.sync();
-        const int row = G.row;
+        const int row = Gm.row;
         if (row >= M) break;  // nobody touches another CTA's shared memory after this barrier
 
-        // ---- intensities of mask jr, their sum and finiteness ----
+        // ---- intensities of mask jm, their sum and finiteness ----
         float yv[E];
         float2 z[E];
         {
             float pv[32] = {0.f};
-            const float *yr = P.y + (size_t)row * K + (size_t)jr * N;
+            const float *yr = P.y + (size_t)row * K + (size_t)jm * N;
 #pragma unroll
             for (int e = 0; e < E; e++) {
-                yv[e] = yr[tid + e * NT];
+                yv[e] = yr[ttid + e * NT];
                 if (isfinite(yv[e])) pv[0] += yv[e];
                 else pv[1] += 1.f;
             }
             cluster_sum(pv, 2);
             if (tid == 0) {
-                G.status = ROW_MAXITER;
-                G.done = 0;
-                G.np = 0;
-                G.f = 0.0;
-                G.stop = 0;
-                G.early = 0;
-                G.sumy = G.red[0];
-                if (G.red[1] > 0.0) { G.status = ROW_NUMERIC; G.stop = 1; G.early = 1; }
-                else if (G.red[0] == 0.0) { G.status = ROW_ZERO; G.stop = 1; G.early = 1; }
+                Gm.status = ROW_MAXITER;
+                Gm.done = 0;
+                Gm.np = 0;
+                Gm.f = 0.0;
+                Gm.stop = 0;
+                Gm.early = 0;
+                Gm.sumy = Gm.red[0];
+                if (Gm.red[1] > 0.0) { Gm.status = ROW_NUMERIC; Gm.stop = 1; Gm.early = 1; }
+                else if (Gm.red[0] == 0.0) { Gm.status = ROW_ZERO; Gm.stop = 1; Gm.early = 1; }
             }
             __syncthreads();
         }
-        const float sumy = G.sumy;
+        const float sumy = Gm.sumy;
         const float JN = (float)J * N;
 
-        if (!G.stop) {
+        if (!Gm.stop) {
             // ---- initialisation ----
             if (P.T_init) {
-                for (int i = tid; i < nmine; i += NT) ts[i] = P.T_init[(size_t)row * N + lo + i];
+                for (int i = tid; i < nmine; i += BT) ts[i] = P.T_init[(size_t)row * N + lo + i];
             } else if (P.init == INIT_BP) {
                 float2 u[E];
 #pragma unroll
                 for (int e = 0; e < E; e++) u[e] = make_float2(sqrtf(fmaxf(yv[e], 0.f)), 0.f);
-                block_fft_rb<N, NT, +1>(u, buf, tws, wb, tid);
+                block_fft_rb<N, NT, +1>(u, buf, tws, wb, ttid);
 #pragma unroll
                 for (int e = 0; e < E; e++) u[e] = cmulc(u[e], dm[e]);
                 push_to_owners(u);
                 cluster.sync();
-                for (int i = tid; i < nmine; i += NT) ts[i] = slice_sum(i, 1.f / JN);
+                for (int i = tid; i < nmine; i += BT) ts[i] = slice_sum(i, 1.f / JN);
             } else {
-                for (int i = tid; i < nmine; i += NT)
+                for (int i = tid; i < nmine; i += BT)
                     ts[i] = philox_cnormal(P.seed, (uint32_t)row, (uint32_t)(lo + i));
                 if (P.init == INIT_SPECTRAL) {
                     const float mean = sumy / (float)K;
@@ -447,38 +455,38 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
                         cluster.sync();
                         float2 x[E];
 #pragma unroll
-                        for (int e = 0; e < E; e++) x[e] = cmul(X[tid + e * NT], dm[e]);
+                        for (int e = 0; e < E; e++) x[e] = cmul(X[ttid + e * NT], dm[e]);
                         __syncthreads();  // X is read before the FFT reuses it
-                        block_fft_rb<N, NT, -1>(x, buf, tws, wb, tid);
+                        block_fft_rb<N, NT, -1>(x, buf, tws, wb, ttid);
 #pragma unroll
                         for (int e = 0; e < E; e++) x[e] = cscale(x[e], tau[e]);
-                        block_fft_rb<N, NT, +1>(x, buf, tws, wb, tid);
+                        block_fft_rb<N, NT, +1>(x, buf, tws, wb, ttid);
 #pragma unroll
                         for (int e = 0; e < E; e++) x[e] = cmulc(x[e], dm[e]);
                         push_to_owners(x);
                         cluster.sync();
                         const bool renorm = ((it & 7) == 7) || (it == P.power_iters - 1);
                         float pv[32] = {0.f};
-                        for (int i = tid; i < nmine; i += NT) {
+                        for (int i = tid; i < nmine; i += BT) {
                             const float2 s = slice_sum(i, 1.f / JN);
                             ts[i] = s;
                             pv[0] = fmaf(s.x, s.x, fmaf(s.y, s.y, pv[0]));
                         }
                         if (renorm) {
                             cluster_sum(pv, 1);
-                            const float nrm = G.red[0];
+                            const float nrm = Gm.red[0];
                             const float inv = nrm > 0.f ? rsqrtf(nrm) : 0.f;
-                            for (int i = tid; i < nmine; i += NT) ts[i] = cscale(ts[i], inv);
+                            for (int i = tid; i < nmine; i += BT) ts[i] = cscale(ts[i], inv);
                         }
                     }
                 }
                 // rescale to the Parseval norm ||t||^2 = sum(y) / (J N)
                 float pv[32] = {0.f};
-                for (int i = tid; i < nmine; i += NT) pv[0] += cabs2(ts[i]);
+                for (int i = tid; i < nmine; i += BT) pv[0] += cabs2(ts[i]);
                 cluster_sum(pv, 1);
-                const float nrm = G.red[0];
+                const float nrm = Gm.red[0];
                 const float sc = nrm > 0.f ? sqrtf(sumy / JN) / sqrtf(nrm) : 0.f;
-                for (int i = tid; i < nmine; i += NT) ts[i] = cscale(ts[i], sc);
+                for (int i = tid; i < nmine; i += BT) ts[i] = cscale(ts[i], sc);
             }
 
             // ---- f and gradient at t0 ----
@@ -487,9 +495,9 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
                 push_slice_to_X(ts);
                 cluster.sync();
 #pragma unroll
-                for (int e = 0; e < E; e++) z[e] = cmul(X[tid + e * NT], dm[e]);
+                for (int e = 0; e < E; e++) z[e] = cmul(X[ttid + e * NT], dm[e]);
                 __syncthreads();  // X is read before the FFT reuses it
-                block_fft_rb<N, NT, -1>(z, buf, tws, wb, tid);
+                block_fft_rb<N, NT, -1>(z, buf, tws, wb, ttid);
                 float2 u[E];
                 float pv[32] = {0.f};
 #pragma unroll
@@ -498,12 +506,12 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
                     pv[0] = fmaf(r, r, pv[0]);
                     u[e] = cscale(z[e], r);
                 }
-                block_fft_rb<N, NT, +1>(u, buf, tws, wb, tid);
+                block_fft_rb<N, NT, +1>(u, buf, tws, wb, ttid);
 #pragma unroll
                 for (int e = 0; e < E; e++) u[e] = cmulc(u[e], dm[e]);
                 push_to_owners(u);
                 cluster.sync();
-                for (int i = tid; i < nmine; i += NT) {
+                for (int i = tid; i < nmine; i += BT) {
                     const float2 g = slice_sum(i, -4.f);
                     gs[i] = g;
                     pv[1] += cabs2(g);
@@ -511,39 +519,39 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
                 cluster_sum(pv, 2);
                 if (warp == 0) {
                     if (lane == 0) {
-                        G.f = G.red[0];
-                        G.gg = G.red[1];
-                        G.np = 0;
-                        if (!isfinite(G.f) || !isfinite(G.gg)) { G.status = ROW_NUMERIC; G.stop = 1; }
-                        else if (P.iters > 0 && (G.f == 0.f || G.gg == 0.f)) { G.status = ROW_CONVERGED; G.stop = 1; }
+                        Gm.f = Gm.red[0];
+                        Gm.gg = Gm.red[1];
+                        Gm.np = 0;
+                        if (!isfinite(Gm.f) || !isfinite(Gm.gg)) { Gm.status = ROW_NUMERIC; Gm.stop = 1; }
+                        else if (P.iters > 0 && (Gm.f == 0.f || Gm.gg == 0.f)) { Gm.status = ROW_CONVERGED; Gm.stop = 1; }
                     }
-                    if (lane < kSlots) G.slot[lane] = lane;
+                    if (lane < kSlots) Gm.slot[lane] = lane;
                     __syncwarp();
-                    if (!G.stop) lbfgs_coefficients_warp(G, lane);
+                    if (!Gm.stop) lbfgs_coefficients_warp(Gm, lane);
                 }
                 __syncthreads();
             }
 
             // ---- L-BFGS iterations ----
-            for (int it = 0; it < P.iters && !G.stop; it++) {
-                const int ns = G.slot[G.np];  // free slot for the new pair
+            for (int it = 0; it < P.iters && !Gm.stop; it++) {
+                const int ns = Gm.slot[Gm.np];  // free slot for the new pair
                 float2 *Sn = Ss + (size_t)ns * SL;
                 float2 *Yn = Ys + (size_t)ns * SL;
                 // A: direction on my slice, parked in the new S slot until the step is known
                 {
-                    const float gam = G.gamma;
-                    const int np = G.np;
+                    const float gam = Gm.gamma;
+                    const int np = Gm.np;
                     float c1r[kSlots], c2r[kSlots];
                     const float2 *sp[kSlots], *yp[kSlots];
 #pragma unroll
                     for (int k = 0; k < kSlots; k++) {
-                        const int a = G.slot[k < np ? k : 0];
-                        c1r[k] = k < np ? G.c1[k] : 0.f;
-                        c2r[k] = k < np ? G.c2[k] : 0.f;
+                        const int a = Gm.slot[k < np ? k : 0];
+                        c1r[k] = k < np ? Gm.c1[k] : 0.f;
+                        c2r[k] = k < np ? Gm.c2[k] : 0.f;
                         sp[k] = Ss + (size_t)a * SL;
                         yp[k] = Ys + (size_t)a * SL;
                     }
-                    for (int i = tid; i < nmine; i += NT) {
+                    for (int i = tid; i < nmine; i += BT) {
                         float2 acc = cscale(gs[i], gam);
 #pragma unroll
                         for (int k = 0; k < kSlots; k++) {
@@ -555,16 +563,16 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
                         }
                         const float2 p = make_float2(-acc.x, -acc.y);
                         Sn[i] = p;
-                        for (int o = 0; o < J; o++) cluster.map_shared_rank(X, o)[lo + i] = p;
+                        for (int o = 0; o < JC; o++) cluster.map_shared_rank(X, o)[lo + i] = p;
                     }
                 }
                 cluster.sync();  // B1
                 // C: w = F(d .* p)
                 float2 w[E];
 #pragma unroll
-                for (int e = 0; e < E; e++) w[e] = cmul(X[tid + e * NT], dm[e]);
+                for (int e = 0; e < E; e++) w[e] = cmul(X[ttid + e * NT], dm[e]);
                 __syncthreads();  // X is read before the FFT reuses it
-                block_fft_rb<N, NT, -1>(w, buf, tws, wb, tid);
+                block_fft_rb<N, NT, -1>(w, buf, tws, wb, ttid);
                 // D: quartic coefficients
                 {
                     float pv[32] = {0.f};
@@ -581,15 +589,15 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
                     }
                     cluster_sum(pv, 5);  // B2
                     if (tid == 0) {
-                        const float al = quartic_argmin(G.red);
-                        G.alpha = al;
-                        if (!isfinite(al)) { G.status = ROW_NUMERIC; G.stop = 1; }
-                        else if (al == 0.f) { G.status = ROW_CONVERGED; G.stop = 1; }
+                        const float al = quartic_argmin(Gm.red);
+                        Gm.alpha = al;
+                        if (!isfinite(al)) { Gm.status = ROW_NUMERIC; Gm.stop = 1; }
+                        else if (al == 0.f) { Gm.status = ROW_CONVERGED; Gm.stop = 1; }
                     }
                     __syncthreads();
                 }
-                if (G.stop) break;
-                const float al = G.alpha;
+                if (Gm.stop) break;
+                const float al = Gm.alpha;
                 // E: update fields, residual and the step
                 float2 u[E];
                 float fpart = 0.f;
@@ -600,31 +608,31 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
                     fpart = fmaf(r, r, fpart);
                     u[e] = cscale(z[e], r);
                 }
-                for (int i = tid; i < nmine; i += NT) {
+                for (int i = tid; i < nmine; i += BT) {
                     const float2 s = cscale(Sn[i], al);
                     Sn[i] = s;
                     ts[i] = cadd(ts[i], s);
                 }
                 // F: adjoint, pushed to the slice owners
-                block_fft_rb<N, NT, +1>(u, buf, tws, wb, tid);
+                block_fft_rb<N, NT, +1>(u, buf, tws, wb, ttid);
 #pragma unroll
                 for (int e = 0; e < E; e++) u[e] = cmulc(u[e], dm[e]);
                 push_to_owners(u);
                 cluster.sync();  // B3
                 // G: new gradient, new pair, batched dot products
                 {
-                    const int np = G.np;
+                    const int np = Gm.np;
                     float pv[32];
 #pragma unroll
                     for (int k = 0; k < 32; k++) pv[k] = 0.f;
                     const float2 *sp[kSlots], *yp[kSlots];
 #pragma unroll
                     for (int k = 0; k < kSlots; k++) {
-                        const int a = G.slot[k <= np ? k : 0];
+                        const int a = Gm.slot[k <= np ? k : 0];
                         sp[k] = Ss + (size_t)a * SL;
                         yp[k] = Ys + (size_t)a * SL;
                     }
-                    for (int i = tid; i < nmine; i += NT) {
+                    for (int i = tid; i < nmine; i += BT) {
                         const float2 gn = slice_sum(i, -4.f);
                         const float2 yn = csub(gn, gs[i]);
                         gs[i] = gn;
@@ -647,19 +655,19 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
                     pv[kIdxF] = fpart;
                     cluster_sum(pv, kParts);  // B4
                     if (warp == 0) {
-                        const float *tot = G.red;
+                        const float *tot = Gm.red;
                         if (lane <= np) {
-                            G.SY[lane][np] = tot[4 * lane + 0];
-                            G.YY[lane][np] = tot[4 * lane + 1];
-                            G.Sg[lane] = tot[4 * lane + 2];
-                            G.Yg[lane] = tot[4 * lane + 3];
+                            Gm.SY[lane][np] = tot[4 * lane + 0];
+                            Gm.YY[lane][np] = tot[4 * lane + 1];
+                            Gm.Sg[lane] = tot[4 * lane + 2];
+                            Gm.Yg[lane] = tot[4 * lane + 3];
                         }
                         const float sy = tot[4 * np + 0], yy = tot[4 * np + 1];
                         const float fnew = tot[kIdxF];
                         const bool accept = sy > 1e-10f * sqrtf(tot[kIdxSS]) * sqrtf(yy) && sy > 0.f;
                         int np2 = np + (accept ? 1 : 0);
                         __syncwarp();
-                        if (accept && lane == 0) G.rD[np] = 1.f / sy;
+                        if (accept && lane == 0) Gm.rD[np] = 1.f / sy;
                         __syncwarp();
                         if (np2 > m) {
                             // drop the oldest pair: age i + 1 becomes age i
@@ -669,45 +677,45 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
                             const int src = lane + 1;
 #pragma unroll
                             for (int j = 0; j < kSlots; j++) {
-                                sy_r[j] = (mine && j + 1 < kSlots) ? G.SY[src][j + 1 < kSlots ? j + 1 : 0] : 0.f;
-                                yy_r[j] = (mine && j + 1 < kSlots) ? G.YY[src][j + 1 < kSlots ? j + 1 : 0] : 0.f;
+                                sy_r[j] = (mine && j + 1 < kSlots) ? Gm.SY[src][j + 1 < kSlots ? j + 1 : 0] : 0.f;
+                                yy_r[j] = (mine && j + 1 < kSlots) ? Gm.YY[src][j + 1 < kSlots ? j + 1 : 0] : 0.f;
                             }
                             if (mine) {
-                                sg = G.Sg[src];
-                                yg = G.Yg[src];
-                                rd = G.rD[src];
+                                sg = Gm.Sg[src];
+                                yg = Gm.Yg[src];
+                                rd = Gm.rD[src];
                             }
                             // the m + 1 allocated slots rotate: the oldest pair's slot
                             // becomes the free one at position m
-                            const int sl_old0 = G.slot[0];
-                            if (lane < m) sl = G.slot[lane + 1];
+                            const int sl_old0 = Gm.slot[0];
+                            if (lane < m) sl = Gm.slot[lane + 1];
                             __syncwarp();
                             if (mine) {
 #pragma unroll
                                 for (int j = 0; j < kSlots; j++) {
-                                    G.SY[lane][j] = sy_r[j];
-                                    G.YY[lane][j] = yy_r[j];
+                                    Gm.SY[lane][j] = sy_r[j];
+                                    Gm.YY[lane][j] = yy_r[j];
                                 }
-                                G.Sg[lane] = sg;
-                                G.Yg[lane] = yg;
-                                G.rD[lane] = rd;
+                                Gm.Sg[lane] = sg;
+                                Gm.Yg[lane] = yg;
+                                Gm.rD[lane] = rd;
                             }
-                            if (lane < m) G.slot[lane] = sl;
-                            if (lane == m) G.slot[lane] = sl_old0;
+                            if (lane < m) Gm.slot[lane] = sl;
+                            if (lane == m) Gm.slot[lane] = sl_old0;
                             np2 = m;
                         }
                         if (lane == 0) {
-                            G.np = np2;
-                            G.gg = tot[kIdxGG];
-                            const float rel = fabsf(G.f - fnew) / fmaxf(G.f, 1e-30f);
-                            G.f = fnew;
-                            G.done = it + 1;
-                            if (!isfinite(fnew) || !isfinite(G.gg)) { G.status = ROW_NUMERIC; G.stop = 1; }
-                            else if (P.tol > 0.0 && rel < (float)P.tol) { G.status = ROW_CONVERGED; G.stop = 1; }
-                            else if (it + 1 < P.iters && (fnew == 0.f || G.gg == 0.f)) { G.status = ROW_CONVERGED; G.stop = 1; }
+                            Gm.np = np2;
+                            Gm.gg = tot[kIdxGG];
+                            const float rel = fabsf(Gm.f - fnew) / fmaxf(Gm.f, 1e-30f);
+                            Gm.f = fnew;
+                            Gm.done = it + 1;
+                            if (!isfinite(fnew) || !isfinite(Gm.gg)) { Gm.status = ROW_NUMERIC; Gm.stop = 1; }
+                            else if (P.tol > 0.0 && rel < (float)P.tol) { Gm.status = ROW_CONVERGED; Gm.stop = 1; }
+                            else if (it + 1 < P.iters && (fnew == 0.f || Gm.gg == 0.f)) { Gm.status = ROW_CONVERGED; Gm.stop = 1; }
                         }
                         __syncwarp();
-                        if (!G.stop && it + 1 < P.iters) lbfgs_coefficients_warp(G, lane);
+                        if (!Gm.stop && it + 1 < P.iters) lbfgs_coefficients_warp(Gm, lane);
                     }
                     __syncthreads();
                 }
@@ -715,19 +723,19 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
         }
 
         // ---- outputs (rows decided before initialisation come back as zero) ----
-        const bool early = G.early != 0;
-        for (int i = tid; i < nmine; i += NT)
+        const bool early = Gm.early != 0;
+        for (int i = tid; i < nmine; i += BT)
             P.T_out[(size_t)row * N + lo + i] = early ? make_float2(0.f, 0.f) : ts[i];
         if (jr == 0 && tid == 0) {
-            if (P.row_status) P.row_status[row] = G.status;
-            if (P.row_iters) P.row_iters[row] = G.done;
+            if (P.row_status) P.row_status[row] = Gm.status;
+            if (P.row_iters) P.row_iters[row] = Gm.done;
             if (P.row_loss)
-                P.row_loss[row] = early ? (G.status == ROW_ZERO ? 0.f : __int_as_float(0x7fc00000)) : (float)G.f;
+                P.row_loss[row] = early ? (Gm.status == ROW_ZERO ? 0.f : __int_as_float(0x7fc00000)) : (float)Gm.f;
         }
         if (P.Zd) {
 #pragma unroll
             for (int e = 0; e < E; e++) {
-                const int pat = jr * N + tid + e * NT;
+                const int pat = jm * N + ttid + e * NT;
                 if (pat < P.Nd) P.Zd[(size_t)pat * M + row] = early ? make_float2(0.f, 0.f) : z[e];
             }
         }
@@ -735,63 +743,81 @@ __global__ void __launch_bounds__(SolverCfg<N>::NT, (N >= 256 && N <= 2048) ? 2 
     }
 }
 
-template <int N>
+template <int N, int G>
 static cudaError_t launch_solver_t(const SolverParams &p, cudaStream_t s, int *clusters_out)
 {
-    using C = SolverCfg<N>;
-    const size_t sm = solver_smem<N>(p.J, p.m);
-    cudaError_t e = cudaFuncSetAttribute(k_solver<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    using C = SolverCfg<N, G>;
+    const int JC = p.J / G;
+    const size_t sm = solver_smem<N, G>(p.J, p.m);
+    cudaError_t e = cudaFuncSetAttribute(k_solver<N, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = p.J;
+    attr[0].val.clusterDim.x = JC;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(C::NT);
+    cfg.blockDim = dim3(C::BT);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cfg.gridDim = dim3(p.J);
+    cfg.gridDim = dim3(JC);
     int maxc = 0;
-    e = cudaOccupancyMaxActiveClusters(&maxc, k_solver<N>, &cfg);
+    e = cudaOccupancyMaxActiveClusters(&maxc, k_solver<N, G>, &cfg);
     if (e != cudaSuccess) return e;
     if (maxc < 1) return cudaErrorInvalidConfiguration;
     int nc = maxc < p.M ? maxc : p.M;
     if (nc < 1) nc = 1;
-    cfg.gridDim = dim3(nc * p.J);
+    cfg.gridDim = dim3(nc * JC);
     if (clusters_out) *clusters_out = nc;
-    return cudaLaunchKernelEx(&cfg, k_solver<N>, p);
+    return cudaLaunchKernelEx(&cfg, k_solver<N, G>, p);
 }
 
-size_t solver_smem_bytes(int N, int J, int m)
+// Masks per CTA that have a kernel for length N: G * threads(N) <= 512.
+bool solver_variant_exists(int N, int G)
 {
-    switch (N) {
-    case 64: return solver_smem<64>(J, m);
-    case 128: return solver_smem<128>(J, m);
-    case 256: return solver_smem<256>(J, m);
-    case 512: return solver_smem<512>(J, m);
-    case 1024: return solver_smem<1024>(J, m);
-    case 2048: return solver_smem<2048>(J, m);
-    case 4096: return solver_smem<4096>(J, m);
-    default: return 0;
-    }
+    if (G != 1 && G != 2 && G != 4) return false;
+    return fft_supported(N) && G * fft_threads(N) <= 512;
 }
 
-cudaError_t launch_solver(int N, const SolverParams &p, cudaStream_t s, int *clusters_out)
+#define TMR_SOLVER_N_G(NN, GG)                                                        \
+    if (N == NN && G == GG) {                                                         \
+        if constexpr (GG * fft_threads(NN) <= 512) {                                  \
+            if (what == 0) return (long long)solver_smem<NN, GG>(p->J, p->m);          \
+            return (long long)launch_solver_t<NN, GG>(*p, s, clusters_out);            \
+        }                                                                             \
+    }
+#define TMR_SOLVER_N(NN) TMR_SOLVER_N_G(NN, 1) TMR_SOLVER_N_G(NN, 2) TMR_SOLVER_N_G(NN, 4)
+
+// what == 0: shared-memory bytes of the variant; what == 1: launch it.
+static long long solver_dispatch(int N, int G, int what, const SolverParams *p, cudaStream_t s,
+                                 int *clusters_out)
+{
+    TMR_SOLVER_N(64)
+    TMR_SOLVER_N(128)
+    TMR_SOLVER_N(256)
+    TMR_SOLVER_N(512)
+    TMR_SOLVER_N(1024)
+    TMR_SOLVER_N(2048)
+    TMR_SOLVER_N(4096)
+    return what == 0 ? 0 : (long long)cudaErrorInvalidValue;
+}
+
+size_t solver_smem_bytes(int N, int J, int m, int G)
+{
+    SolverParams p{};
+    p.J = J;
+    p.m = m;
+    if (!solver_variant_exists(N, G) || J % G != 0) return 0;
+    return (size_t)solver_dispatch(N, G, 0, &p, nullptr, nullptr);
+}
+
+cudaError_t launch_solver(int N, int G, const SolverParams &p, cudaStream_t s, int *clusters_out)
 {
     if (p.M == 0) return cudaSuccess;
-    switch (N) {
-    case 64: return launch_solver_t<64>(p, s, clusters_out);
-    case 128: return launch_solver_t<128>(p, s, clusters_out);
-    case 256: return launch_solver_t<256>(p, s, clusters_out);
-    case 512: return launch_solver_t<512>(p, s, clusters_out);
-    case 1024: return launch_solver_t<1024>(p, s, clusters_out);
-    case 2048: return launch_solver_t<2048>(p, s, clusters_out);
-    case 4096: return launch_solver_t<4096>(p, s, clusters_out);
-    default: return cudaErrorInvalidValue;
-    }
+    if (!solver_variant_exists(N, G) || p.J % G != 0) return cudaErrorInvalidValue;
+    return (cudaError_t)solver_dispatch(N, G, 1, &p, s, clusters_out);
 }
 
 }  // namespace tmr
