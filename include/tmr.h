@@ -60,7 +60,11 @@ typedef enum {
 enum {
     TMR_INIT_RANDOM = 0,   /* Philox4x32-10 complex normal, scaled to ||t||^2 = sum(y)/(J N) */
     TMR_INIT_BP = 1,       /* back-propagation t0 = Q^H sqrt(y) / (J N), Eq. backpropagation */
-    TMR_INIT_SPECTRAL = 2  /* power iteration on Q^H diag(min(y/mean y, clip)) Q / (J N)    */
+    TMR_INIT_SPECTRAL = 2, /* power iteration on Q^H diag(min(y/mean y, clip)) Q / (J N)    */
+    TMR_INIT_LEARNED = 3   /* the network of tmr_set_init_model proposes t0 from sqrt(y); per
+                              row it is kept only if its loss is below that of the spectral
+                              start (power_iters; 0 = the random start), which is used
+                              otherwise                                                   */
 };
 
 /* Per-row outcome written to row_status. */
@@ -177,6 +181,41 @@ const char *tmr_last_error(void);
 
 /* Device bytes currently held by the handle. */
 size_t tmr_workspace_bytes(const tmr_handle *h);
+
+/* ---- learned initialiser (not in the paper: a network proposes t0) ----
+ * A perceptron x -> GELU(W1 x + b1) -> GELU(W2 h1 + b2) -> W3 h2 + b3 with
+ * FP32 master weights, BF16 copies feeding tensor-core products and FP32
+ * accumulation.  Parameters are one flat FP32 vector W1 [h1][in], b1,
+ * W2 [h2][h1], b2, W3 [out][h2], b3 (row-major).  For tmr_retrieve the input
+ * is the row's sqrt(y) / sqrt(mean y) (in = J*N) and the output the real and
+ * imaginary parts of t0 (out = 2*N), rescaled to ||t0||^2 = sum(y) / (J N).
+ * X, T, Y, loss and grad are device arrays; all work runs on `stream`. */
+typedef struct tmr_mlp tmr_mlp;
+
+/* Weights drawn from U(-sqrt(3/fan_in), sqrt(3/fan_in)) by Philox(seed), biases 0. */
+tmr_status tmr_mlp_create(tmr_mlp **out, int n_in, int n_h1, int n_h2, int n_out,
+                          unsigned long long seed, void *stream);
+size_t tmr_mlp_num_params(const tmr_mlp *m);
+/* Copy (host or device) parameters in; resets the Adam state. */
+tmr_status tmr_mlp_set_params(tmr_mlp *m, const float *params);
+tmr_status tmr_mlp_get_params(tmr_mlp *m, float *params);
+/* Y[B][out] = network(X[B][in]). */
+tmr_status tmr_mlp_forward(tmr_mlp *m, const float *X, int B, float *Y);
+/* Mean squared error L = sum (Y - T)^2 / (B out) of the batch into *loss
+ * (may be NULL) and its gradient w.r.t. every parameter into grad (may be NULL). */
+tmr_status tmr_mlp_grad(tmr_mlp *m, const float *X, const float *T, int B, float *loss,
+                        float *grad);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the batch. */
+tmr_status tmr_mlp_train_step(tmr_mlp *m, const float *X, const float *T, int B, float lr,
+                              float *loss);
+void tmr_mlp_destroy(tmr_mlp *m);
+
+/* Network used by TMR_INIT_LEARNED (not owned; keep it alive while the handle
+ * uses it).  Its sizes must be in = J*N and out = 2*N. */
+tmr_status tmr_set_init_model(tmr_handle *h, tmr_mlp *model);
+/* Rows of the last completed learned-start retrieve whose proposed start was
+ * kept (synchronises the handle's stream), or -1. */
+long long tmr_learned_rows(tmr_handle *h);
 
 /* Masks per CTA of the solver schedule the handle uses (after autotuning),
  * or 0 for a NULL handle. */

@@ -17,10 +17,11 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "tmr.h")
 
 TMR_OK, TMR_ERR_INVALID_ARG, TMR_ERR_UNSUPPORTED, TMR_ERR_OOM = 0, 1, 2, 3
 TMR_ERR_CUDA, TMR_ERR_TIMEOUT, TMR_ERR_NUMERIC = 4, 5, 6
-TMR_INIT_RANDOM, TMR_INIT_BP, TMR_INIT_SPECTRAL = 0, 1, 2
+TMR_INIT_RANDOM, TMR_INIT_BP, TMR_INIT_SPECTRAL, TMR_INIT_LEARNED = 0, 1, 2, 3
 TMR_ROW_MAXITER, TMR_ROW_CONVERGED, TMR_ROW_ZERO, TMR_ROW_NUMERIC = 0, 1, 2, 3
 TMR_PREC_FP32 = 0
-INIT = {"random": TMR_INIT_RANDOM, "bp": TMR_INIT_BP, "spectral": TMR_INIT_SPECTRAL}
+INIT = {"random": TMR_INIT_RANDOM, "bp": TMR_INIT_BP, "spectral": TMR_INIT_SPECTRAL,
+        "learned": TMR_INIT_LEARNED}
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "TIMEOUT",
                 6: "NUMERIC"}
 
@@ -64,6 +65,16 @@ def _load():
         "tmr_last_error": ([], ctypes.c_char_p),
         "tmr_workspace_bytes": ([H], ctypes.c_size_t),
         "tmr_schedule": ([H], ctypes.c_int),
+        "tmr_mlp_create": ([ctypes.POINTER(vp), ip, ip, ip, ip, ctypes.c_ulonglong, vp], ctypes.c_int),
+        "tmr_mlp_num_params": ([vp], ctypes.c_size_t),
+        "tmr_mlp_set_params": ([vp, fp], ctypes.c_int),
+        "tmr_mlp_get_params": ([vp, fp], ctypes.c_int),
+        "tmr_mlp_forward": ([vp, fp, ip, fp], ctypes.c_int),
+        "tmr_mlp_grad": ([vp, fp, fp, ip, fp, fp], ctypes.c_int),
+        "tmr_mlp_train_step": ([vp, fp, fp, ip, ctypes.c_float, fp], ctypes.c_int),
+        "tmr_mlp_destroy": ([vp], None),
+        "tmr_set_init_model": ([H, vp], ctypes.c_int),
+        "tmr_learned_rows": ([H], ctypes.c_longlong),
         "tmr_destroy": ([H], None),
         "tmr_retrieve_rows_static": ([ip, ip, ip, vp, fp, ip, ctypes.POINTER(tmr_options), vp, vp,
                                       vp, fp, vp], ctypes.c_int),
@@ -242,6 +253,75 @@ def tmr_schedule(h: Handle) -> int:
 
 def tmr_destroy(h: Handle):
     h.close()
+
+
+class MLP:
+    """Owns a tmr_mlp (the learned initialiser's network)."""
+
+    def __init__(self, raw, dims):
+        self.raw = raw
+        self.dims = dims
+        self.n_params = int(lib.tmr_mlp_num_params(raw))
+
+    def close(self):
+        if self.raw:
+            lib.tmr_mlp_destroy(self.raw)
+            self.raw = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def tmr_mlp_create(n_in, n_h1, n_h2, n_out, seed=0, stream=None) -> MLP:
+    raw = ctypes.c_void_p()
+    _check(lib.tmr_mlp_create(ctypes.byref(raw), int(n_in), int(n_h1), int(n_h2), int(n_out),
+                              int(seed), ctypes.c_void_p(stream) if stream else None))
+    return MLP(raw, (n_in, n_h1, n_h2, n_out))
+
+
+def tmr_mlp_set_params(m: MLP, params):
+    _check(lib.tmr_mlp_set_params(m.raw, _ptr(params, "f32", m.n_params, "params")))
+
+
+def tmr_mlp_get_params(m: MLP, params):
+    _check(lib.tmr_mlp_get_params(m.raw, _ptr(params, "f32", m.n_params, "params")))
+
+
+def tmr_mlp_forward(m: MLP, X, B, Y):
+    _check(lib.tmr_mlp_forward(m.raw, _ptr(X, "f32", B * m.dims[0], "X"), int(B),
+                               _ptr(Y, "f32", B * m.dims[3], "Y")))
+
+
+def tmr_mlp_grad(m: MLP, X, T, B, loss=None, grad=None):
+    _check(lib.tmr_mlp_grad(m.raw, _ptr(X, "f32", B * m.dims[0], "X"), _ptr(T, "f32", B * m.dims[3], "T"),
+                            int(B), _ptr(loss, "f32", 1, "loss"), _ptr(grad, "f32", m.n_params, "grad")))
+
+
+def tmr_mlp_train_step(m: MLP, X, T, B, lr, loss=None):
+    _check(lib.tmr_mlp_train_step(m.raw, _ptr(X, "f32", B * m.dims[0], "X"),
+                                  _ptr(T, "f32", B * m.dims[3], "T"), int(B), float(lr),
+                                  _ptr(loss, "f32", 1, "loss")))
+
+
+def tmr_mlp_destroy(m: MLP):
+    m.close()
+
+
+def tmr_set_init_model(h: Handle, m):
+    _check(lib.tmr_set_init_model(h.raw, m.raw if m is not None else None))
+
+
+def tmr_learned_rows(h: Handle) -> int:
+    return int(lib.tmr_learned_rows(h.raw))
 
 
 def tmr_retrieve_rows_static(N, M, J, masks, y, iters, opt, T_out, row_status=None,

@@ -95,6 +95,10 @@ struct tmr_handle {
     cudaStream_t own_stream = nullptr;  // created for graph capture when the caller gave none
     // captured retrieve graph and the arguments it was captured with
     cudaGraphExec_t gexec = nullptr;
+    // learned initialiser
+    tmr_mlp *model = nullptr;
+    float2 *Tcand = nullptr;
+    unsigned *wins = nullptr;
     const void *gkey[9] = {};
     int giters = -1;
 };
@@ -314,6 +318,28 @@ void tmr_default_options(tmr_options *o)
 
 int tmr_schedule(const tmr_handle *h) { return h ? h->G : 0; }
 
+tmr_status tmr_set_init_model(tmr_handle *h, tmr_mlp *model)
+{
+    tmr::set_last_error("");
+    if (!h) return fail(TMR_ERR_INVALID_ARG, "NULL handle");
+    if (model && (mlp_in(model) != h->J * h->N || mlp_out(model) != 2 * h->N))
+        return fail(TMR_ERR_INVALID_ARG, "network sizes must be in = J*N, out = 2*N");
+    h->model = model;
+    return TMR_OK;
+}
+
+long long tmr_learned_rows(tmr_handle *h)
+{
+    if (!h || !h->wins) return -1;
+    unsigned v = 0;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess ||
+        cudaMemcpy(&v, h->wins, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return (long long)v;
+}
+
 const char *tmr_last_error(void) { return g_last_error_buf; }
 
 size_t tmr_workspace_bytes(const tmr_handle *h) { return h ? h->held : 0; }
@@ -326,7 +352,7 @@ void tmr_destroy(tmr_handle *h)
     else cudaDeviceSynchronize();
     void *ptrs[] = {h->masks, h->tw, h->H, h->Zd, h->phi, h->pf_ws, h->pf_loss, h->wts, h->queue,
                     h->pf_sync, h->pf_err, h->pf_iters, h->status_scratch, h->iters_scratch,
-                    h->loss_scratch};
+                    h->loss_scratch, h->Tcand, h->wins};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &b : h->stage)
@@ -348,7 +374,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     tmr_default_options(&o);
     if (opt) o = *opt;
     if (o.m < 1 || o.m > kMaxMem) return fail(TMR_ERR_INVALID_ARG, "opt.m must be in 1..6");
-    if (o.init < TMR_INIT_RANDOM || o.init > TMR_INIT_SPECTRAL) return fail(TMR_ERR_INVALID_ARG, "opt.init");
+    if (o.init < TMR_INIT_RANDOM || o.init > TMR_INIT_LEARNED) return fail(TMR_ERR_INVALID_ARG, "opt.init");
     if (o.power_iters < 0 || o.phase_iters < 0 || o.tol < 0) return fail(TMR_ERR_INVALID_ARG, "negative option");
     if (o.precision != TMR_PREC_FP32) return fail(TMR_ERR_UNSUPPORTED, "only TMR_PREC_FP32 is available");
     if (!fft_supported(N)) return fail(TMR_ERR_UNSUPPORTED, "N must be a power of two in 64..4096");
@@ -579,7 +605,26 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
     if (row_iters && (st = stage(h, ST_ITERS, row_iters, sizeof(int) * h->M, false, &dI)) != TMR_OK) return st;
     if (row_loss && (st = stage(h, ST_LOSS, row_loss, sizeof(float) * h->M, false, &dL)) != TMR_OK) return st;
 
+    const bool learned = h->opt.init == TMR_INIT_LEARNED && !T_init;
+    if (learned) {
+        if (!h->model) return fail(TMR_ERR_INVALID_ARG, "TMR_INIT_LEARNED needs tmr_set_init_model");
+        if (!h->Tcand) {
+            if ((st = halloc(h, (void **)&h->Tcand, sizeof(float2) * (MN ? MN : 1), "proposed starts")) != TMR_OK)
+                return st;
+            if ((st = halloc(h, (void **)&h->wins, sizeof(unsigned) * 4, "win counter")) != TMR_OK) return st;
+        }
+        TMR_CUDA(cudaMemsetAsync(h->wins, 0, sizeof(unsigned) * 4, h->stream), "memset");
+        const int CH = 2048;  // rows per network batch
+        for (int r0 = 0; r0 < h->M; r0 += CH) {
+            const int B = h->M - r0 < CH ? h->M - r0 : CH;
+            TMR_CUDA(mlp_propose(h->model, (const float *)dy + (size_t)r0 * h->J * h->N, B, h->N, h->J,
+                                 h->Tcand + (size_t)r0 * h->N, h->stream),
+                     "learned proposals");
+        }
+    }
     SolverParams p{};
+    p.T_cand = learned ? h->Tcand : nullptr;
+    p.cand_wins = learned ? h->wins : nullptr;
     p.masks = h->masks;
     p.tw = h->tw;
     p.y = (const float *)dy;
@@ -595,7 +640,7 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
     p.J = h->J;
     p.iters = iters;
     p.m = h->opt.m;
-    p.init = h->opt.init;
+    p.init = learned ? (h->opt.power_iters > 0 ? TMR_INIT_SPECTRAL : TMR_INIT_RANDOM) : h->opt.init;
     p.power_iters = h->opt.power_iters;
     p.seed = h->opt.seed;
     p.clip = (float)h->opt.clip;

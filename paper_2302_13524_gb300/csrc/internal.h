@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+struct tmr_mlp;
+
 namespace tmr {
 
 // Message returned by tmr_last_error() on this thread (fixed buffer, no heap).
@@ -38,6 +40,8 @@ struct SolverParams {
     int *row_iters;       // [M]
     float *row_loss;      // [M]
     float2 *Zd;           // [Nd][M] defocus fields of the final iterate, or NULL
+    const float2 *T_cand; // [M][N] proposed starts judged against the init, or NULL
+    unsigned *cand_wins;  // rows whose proposed start was kept
     unsigned *queue;      // row work counter, zeroed before the launch
     int Nd, M, J, iters, m, init, power_iters;
     unsigned long long seed;
@@ -50,6 +54,13 @@ size_t solver_smem_bytes(int N, int J, int m, int G);
 cudaError_t launch_solver(int N, int G, const SolverParams &p, cudaStream_t s, int *clusters_out);
 // Synthetic positive intensities for timing runs (autotuner).
 cudaError_t launch_fill_synthetic(float *y, size_t n, unsigned seed, cudaStream_t s);
+
+// ---- learned initialiser (mlp.cu) --------------------------------------------
+// rows of y (B of them) -> features -> network -> starts T scaled to the
+// Parseval norm
+cudaError_t mlp_propose(tmr_mlp *m, const float *y, int B, int N, int J, float2 *T, cudaStream_t s);
+int mlp_in(const tmr_mlp *m);
+int mlp_out(const tmr_mlp *m);
 
 // ---- defocus operator and phase-offset fit (defocus.cu) --------------------
 struct PhaseFitParams {

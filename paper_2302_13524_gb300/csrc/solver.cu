@@ -489,6 +489,34 @@ __global__ void __launch_bounds__(SolverCfg<N, G>::BT, (SolverCfg<N, G>::BT <= 2
                 for (int i = tid; i < nmine; i += BT) ts[i] = cscale(ts[i], sc);
             }
 
+            // ---- judge a proposed start (learned initialiser) against this one ----
+            if (P.T_cand) {
+                for (int i = tid; i < nmine; i += BT) gs[i] = P.T_cand[(size_t)row * N + lo + i];
+                float fv[2];
+                for (int c = 0; c < 2; c++) {  // f at the start above, then at the proposal
+                    __syncthreads();
+                    push_slice_to_X(c == 0 ? ts : gs);
+                    cluster.sync();
+                    float2 x[E];
+#pragma unroll
+                    for (int e = 0; e < E; e++) x[e] = cmul(X[ttid + e * NT], dm[e]);
+                    __syncthreads();  // X is read before the FFT reuses it
+                    block_fft_rb<N, NT, -1>(x, buf, tws, wb, ttid);
+                    float pv[32] = {0.f};
+#pragma unroll
+                    for (int e = 0; e < E; e++) {
+                        const float r = yv[e] - cabs2(x[e]);
+                        pv[0] = fmaf(r, r, pv[0]);
+                    }
+                    cluster_sum(pv, 1);
+                    fv[c] = Gm.red[0];
+                }
+                if (fv[1] < fv[0]) {  // NaN proposals lose
+                    for (int i = tid; i < nmine; i += BT) ts[i] = gs[i];
+                    if (jr == 0 && tid == 0 && P.cand_wins) atomicAdd(P.cand_wins, 1u);
+                }
+            }
+
             // ---- f and gradient at t0 ----
             {
                 __syncthreads();

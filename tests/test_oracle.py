@@ -381,3 +381,44 @@ def test_phase_fit_recovers_planted_offsets():
     T_fix = np.exp(1j * phi)[:, None] * T_est
     assert oracle.matrix_fidelity(T_fix, T) > 1 - 1e-10
     assert oracle.matrix_fidelity(T_est, T) < 0.5
+
+
+# ---------------------------------------------------------- learned-init MLP
+def test_mlp_gelu_matches_erf_definition():
+    import math
+    from oracle import mlp
+    xs = np.linspace(-6, 6, 49)
+    np.testing.assert_allclose(mlp.gelu(xs), [0.5 * x * (1 + math.erf(x / math.sqrt(2))) for x in xs],
+                               atol=1e-15)
+    h = 1e-6
+    np.testing.assert_allclose(mlp.gelu_grad(xs), (mlp.gelu(xs + h) - mlp.gelu(xs - h)) / (2 * h),
+                               atol=1e-8)
+
+
+def test_mlp_gradient_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(30)
+    dims = (8, 6, 6, 4)
+    n = sum(int(np.prod(s)) for s in mlp.shapes(*dims))
+    theta = rng.standard_normal(n) * 0.4
+    X = rng.standard_normal((5, 8))
+    T = rng.standard_normal((5, 4))
+    L, g = mlp.loss_grad(theta, dims, X, T)
+    # the loss is the mean squared error of the forward pass
+    Y, _ = mlp.forward(theta, dims, X)
+    assert abs(L - np.mean((Y - T) ** 2)) < 1e-14
+    h = 1e-6
+    fd = np.empty(n)
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = h
+        fd[i] = (mlp.loss_grad(theta + e, dims, X, T)[0] - mlp.loss_grad(theta - e, dims, X, T)[0]) / (2 * h)
+    assert np.max(abs(fd - g)) < 1e-8 * max(1.0, np.max(abs(g)))
+
+
+def test_adam_first_step_is_signed_lr():
+    from oracle import mlp
+    g = np.array([0.3, -2.0, 1e-3, 0.0])
+    th, m, v = mlp.adam_step(np.zeros(4), g, np.zeros(4), np.zeros(4), 1, lr=0.01)
+    # first bias-corrected step: m_hat = g, v_hat = g^2 -> -lr g / (|g| + eps)
+    np.testing.assert_allclose(th, -0.01 * g / (np.abs(g) + 1e-8), atol=1e-15)
