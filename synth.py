@@ -43,6 +43,10 @@ CONFIGS = {
                      defocus_coef=0.05, tol=1e-7),
     "precision": dict(N=4096, M=16384, grid=(128, 128), J=4, tm="modes", R=2200, photons=1e4,
                       n_defocus=50, iters=100, init="spectral", defocus_coef=0.05),
+    "learned": dict(N=2048, M=8192, grid=(128, 64), J=4, tm="family", R=1100, photons=1e4,
+                    n_defocus=50, iters=100, init="learned", defocus_coef=0.05,
+                    train_fibers=list(range(1, 26)), test_fibers=list(range(101, 106)),
+                    widths=(1024, 1024)),
 }
 
 
@@ -70,6 +74,21 @@ def tm_modes(M: int, N: int, R: int, seed: int = 0, dtype=np.complex128) -> np.n
     U = np.linalg.qr(rng.standard_normal((M, R)) + 1j * rng.standard_normal((M, R)))[0]
     V = np.linalg.qr(rng.standard_normal((N, R)) + 1j * rng.standard_normal((N, R)))[0].conj().T
     theta = rng.uniform(0.0, 2.0 * np.pi, size=R)
+    T = (U * np.exp(1j * theta)) @ V
+    return (T * np.sqrt(M / R)).astype(dtype)
+
+
+def tm_family(M: int, N: int, R: int, fiber_seed: int, basis_seed: int = 0,
+              dtype=np.complex64) -> np.ndarray:
+    """A fiber of a family: the input mode basis V (the guided modes seen from
+    the input plane, fixed by the fiber type) comes from basis_seed; the mode
+    coupling U and phases theta come from fiber_seed.  Scaled so E||row||^2 = 1."""
+    rb = np.random.default_rng([basis_seed, STREAM_TM, 1])
+    rf = np.random.default_rng([fiber_seed, STREAM_TM, 2])
+    R = min(R, M, N)
+    V = np.linalg.qr(rb.standard_normal((N, R)) + 1j * rb.standard_normal((N, R)))[0].conj().T
+    U = np.linalg.qr(rf.standard_normal((M, R)) + 1j * rf.standard_normal((M, R)))[0]
+    theta = rf.uniform(0.0, 2.0 * np.pi, size=R)
     T = (U * np.exp(1j * theta)) @ V
     return (T * np.sqrt(M / R)).astype(dtype)
 
