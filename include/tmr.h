@@ -122,7 +122,13 @@ void tmr_default_options(tmr_options *opt);
  *   stream     cudaStream_t for all work; NULL = the legacy default stream (with
  *              use_graph, a blocking stream the handle creates, which orders
  *              itself with the legacy default stream).
- * Supported on the GPU: N a power of two with 64 <= N <= 4096, 1 <= J <= 8.
+ * Supported on the GPU: 1 <= J <= 8 and N a power of two with
+ * 64 <= N <= 4096 (one register FFT of length N), or any other N with
+ * 16 <= N <= 4096 (Bluestein's chirp-z form of the same DFT through FFTs of
+ * a power-of-two length L >= 2N - 1, one mask per CTA).  When no solver
+ * schedule fits the per-row state of (N, J, opt->m) in shared memory the
+ * handle is still made (tmr_forward, tmr_grad and tmr_defocus_forward work),
+ * tmr_schedule reports 0 and tmr_retrieve returns UNSUPPORTED.
  * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
 tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
                       const tmr_defocus_op *defocus_op, const tmr_options *opt,
@@ -218,7 +224,7 @@ tmr_status tmr_set_init_model(tmr_handle *h, tmr_mlp *model);
 long long tmr_learned_rows(tmr_handle *h);
 
 /* Masks per CTA of the solver schedule the handle uses (after autotuning),
- * or 0 for a NULL handle. */
+ * or 0 for a NULL handle or when no schedule fits (see tmr_create). */
 int tmr_schedule(const tmr_handle *h);
 
 /* Release the handle and everything it allocated.  NULL is allowed. */

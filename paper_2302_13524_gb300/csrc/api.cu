@@ -206,7 +206,7 @@ void write_tune_file(const char *path, const std::map<std::string, int> &m)
 
 bool schedule_ok(int N, int J, int m, int G, int smem_optin)
 {
-    if (J % G != 0 || !solver_variant_exists(N, G)) return false;
+    if (G <= 0 || J % G != 0 || !solver_variant_exists(N, G)) return false;
     const size_t b = solver_smem_bytes(N, J, m, G);
     return b > 0 && b <= (size_t)smem_optin;
 }
@@ -218,7 +218,10 @@ tmr_status autotune(tmr_handle *h, int smem_optin, int *G_out)
     int cand[3], nc = 0;
     for (int G : {1, 2, 4})
         if (schedule_ok(h->N, h->J, h->opt.m, G, smem_optin)) cand[nc++] = G;
-    if (nc == 0) return fail(TMR_ERR_UNSUPPORTED, "no solver schedule fits this (N, J, m)");
+    if (nc == 0) {  // the forward model and gradient still work; tmr_retrieve will refuse
+        *G_out = 0;
+        return TMR_OK;
+    }
     if (nc == 1) {
         *G_out = cand[0];
         return TMR_OK;
@@ -245,6 +248,7 @@ tmr_status autotune(tmr_handle *h, int smem_optin, int *G_out)
     p.T_out = T;
     p.queue = h->queue;
     p.M = R;
+    p.N = h->N;
     p.J = h->J;
     p.iters = 6;
     p.m = h->opt.m;
@@ -377,7 +381,8 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     if (o.init < TMR_INIT_RANDOM || o.init > TMR_INIT_LEARNED) return fail(TMR_ERR_INVALID_ARG, "opt.init");
     if (o.power_iters < 0 || o.phase_iters < 0 || o.tol < 0) return fail(TMR_ERR_INVALID_ARG, "negative option");
     if (o.precision != TMR_PREC_FP32) return fail(TMR_ERR_UNSUPPORTED, "only TMR_PREC_FP32 is available");
-    if (!fft_supported(N)) return fail(TMR_ERR_UNSUPPORTED, "N must be a power of two in 64..4096");
+    if (!xform_supported(N))
+        return fail(TMR_ERR_UNSUPPORTED, "N must be a power of two in 64..4096 or another length in 16..4096");
     if (J > kMaxMasks) return fail(TMR_ERR_UNSUPPORTED, "J must be at most 8");
     int dev = 0;
     TMR_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
@@ -429,9 +434,9 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
             return cuda_fail(e, "copy masks");
         }
     }
-    const int twn = fft_table_len(N);
+    const int twn = xform_table(N, nullptr);
     std::vector<float2> tw(twn > 0 ? twn : 1);
-    fft_table(N, tw.data());
+    xform_table(N, tw.data());
     TRY(halloc(h, (void **)&h->tw, sizeof(float2) * tw.size(), "twiddles"));
     if (cudaMemcpy(h->tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
         tmr_destroy(h);
@@ -493,7 +498,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
             TRY(autotune(h, smem_optin, &G));
             std::lock_guard<std::mutex> lk(g_tune_mu);
             g_tune_mem[key] = G;
-            if (o.tune_cache) {
+            if (o.tune_cache && G > 0) {
                 auto fm = read_tune_file(o.tune_cache);
                 fm[key] = G;
                 write_tune_file(o.tune_cache, fm);
@@ -588,7 +593,8 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
         TMR_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
         TMR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
         if (!schedule_ok(h->N, h->J, h->opt.m, h->G, smem_optin))
-            return fail(TMR_ERR_UNSUPPORTED, "per-row state of this (N, J, m) does not fit in shared memory");
+            return fail(TMR_ERR_UNSUPPORTED,
+                        "per-row state of this (N, J, m) does not fit in shared memory: lower opt.m");
     }
     const size_t MN = (size_t)h->M * h->N, MK = MN * h->J;
     tmr_status st;
@@ -637,6 +643,7 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
     p.queue = h->queue;
     p.Nd = fit ? h->Nd : 0;
     p.M = h->M;
+    p.N = h->N;
     p.J = h->J;
     p.iters = iters;
     p.m = h->opt.m;

@@ -22,6 +22,7 @@ __host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b)
 {
     return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
 }
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __host__ __device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
 // Re(conj(a) b)
 __host__ __device__ __forceinline__ float cdotr(float2 a, float2 b) { return fmaf(a.x, b.x, a.y * b.y); }

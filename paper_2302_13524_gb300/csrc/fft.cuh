@@ -32,19 +32,22 @@ __host__ __device__ constexpr int ipowc(int b, int e) { return e == 0 ? 1 : b * 
 // above that.
 __host__ __device__ constexpr int fft_threads(int N) { return N / 8 < 32 ? 32 : N / 8; }
 
-template <int N, int E>
+// E points per thread, radix R (a power of two dividing E) in every pass but
+// the first; by default R = E (one butterfly per thread and pass).
+template <int N, int E, int R = E>
 struct FftPlan {
-    static constexpr int LN = ilog2c(N), LE = ilog2c(E);
+    static constexpr int LN = ilog2c(N), LE = ilog2c(R);
     static constexpr int P = (LN + LE - 1) / LE;  // number of passes
     static constexpr int LR0 = LN - (P - 1) * LE; // log2 of the first radix
-    __host__ __device__ static constexpr int radix(int p) { return p == 0 ? (1 << LR0) : E; }
-    __host__ __device__ static constexpr int ns(int p) { return p == 0 ? 1 : (1 << LR0) * ipowc(E, p - 1); }
+    __host__ __device__ static constexpr int radix(int p) { return p == 0 ? (1 << LR0) : R; }
+    __host__ __device__ static constexpr int ns(int p) { return p == 0 ? 1 : (1 << LR0) * ipowc(R, p - 1); }
     // offset (in float2) of pass p's twiddle block in the table
     __host__ __device__ static constexpr int tw_off(int p)
     {
         return p <= 1 ? 0 : tw_off(p - 1) + (radix(p - 1) - 1) * ns(p - 1);
     }
     static constexpr int TW_SIZE = tw_off(P);  // total table length
+    static constexpr int TW_SMALL = P >= 2 ? tw_off(P - 1) : 0;  // without the last pass
 };
 
 __host__ __device__ __forceinline__ constexpr int fft_pad(int i) { return i + (i >> 4); }
@@ -218,6 +221,43 @@ __device__ __forceinline__ void block_fft_rb(float2 (&v)[N / T], float2 *buf, co
                                              int tid)
 {
     fft_passes_rb<N, T, SIGN, 0>(v, buf, tw, wb, tid);
+}
+
+
+// ---------------------------------------------------------------------------
+// Several butterflies per thread and pass: E points per thread, radix-R passes
+// (BPT = E / R butterflies each).  The last pass takes its twiddles from
+// per-thread bases as above, one per butterfly: butterfly i of thread tid is
+// b = tid + i T, and wb[i] = exp(-2 pi i b / N).
+template <int N, int T, int R, int SIGN, int p>
+__device__ __forceinline__ void fft_passes_rbx(float2 (&v)[N / T], float2 *buf, const float2 *tw,
+                                               const float2 (&wb)[N / T / R], int tid)
+{
+    using Pl = FftPlan<N, N / T, R>;
+    if constexpr (p < Pl::P - 1) {
+        fft_pass<N, T, Pl::radix(p), Pl::ns(p), Pl::tw_off(p), SIGN, false>(v, buf, tw, tid);
+        fft_passes_rbx<N, T, R, SIGN, p + 1>(v, buf, tw, wb, tid);
+    } else if constexpr (p == Pl::P - 1) {
+        constexpr int BPT = N / T / R;
+        static_assert(Pl::radix(p) == R, "last pass must use the full radix");
+#pragma unroll
+        for (int i = 0; i < BPT; i++) {
+            float2 x[R];
+#pragma unroll
+            for (int r = 0; r < R; r++) x[r] = v[i + r * BPT];
+            if constexpr (Pl::ns(p) > 1) twiddle_powers<R, SIGN>(x, wb[i]);
+            dft_small<R, SIGN>(x);
+#pragma unroll
+            for (int q = 0; q < R; q++) v[i + q * BPT] = x[q];
+        }
+    }
+}
+
+template <int N, int T, int R, int SIGN>
+__device__ __forceinline__ void block_fft_rbx(float2 (&v)[N / T], float2 *buf, const float2 *tw,
+                                              const float2 (&wb)[N / T / R], int tid)
+{
+    fft_passes_rbx<N, T, R, SIGN, 0>(v, buf, tw, wb, tid);
 }
 
 }  // namespace tmr

@@ -15,7 +15,16 @@ void set_last_error(const char *msg);
 // FP32); returns its length in float2, writes it to out when out != NULL.
 int fft_table(int N, float2 *out);
 int fft_table_len(int N);
-bool fft_supported(int N);
+bool fft_supported(int N);  // powers of two 64..4096 (one register FFT)
+
+// Transform constants of length N (xform.cuh): the FFT table for powers of
+// two, [twiddles | half Bluestein filter | chirp] for the other lengths.
+// xform_supported: powers of two 64..4096 and every other N in 16..4096.
+bool xform_supported(int N);
+// Bluestein shape of a non-power-of-two N: FFT length L and registers per
+// thread (the instantiated variant); false when N has none.
+bool xform_blue_shape(int N, int *L, int *ne);
+int xform_table(int N, float2 *out);  // length in float2; writes when out != NULL
 
 // ---- fused forward model and gradient (kernels.cu) -------------------------
 cudaError_t launch_forward(int N, int M, int J, const float2 *T, const float2 *masks,
@@ -32,7 +41,7 @@ cudaError_t launch_apply_phase(int N, int M, const double *phi, const float2 *Ti
 // ---- persistent per-row solver (solver.cu) ---------------------------------
 struct SolverParams {
     const float2 *masks;  // [J][N]
-    const float2 *tw;     // FFT twiddle table
+    const float2 *tw;     // transform constants (xform_table)
     const float *y;       // [M][J][N]
     const float2 *T_init; // [M][N] or NULL
     float2 *T_out;        // [M][N]
@@ -43,7 +52,7 @@ struct SolverParams {
     const float2 *T_cand; // [M][N] proposed starts judged against the init, or NULL
     unsigned *cand_wins;  // rows whose proposed start was kept
     unsigned *queue;      // row work counter, zeroed before the launch
-    int Nd, M, J, iters, m, init, power_iters;
+    int N, Nd, M, J, iters, m, init, power_iters;
     unsigned long long seed;
     float clip;
     double tol;
@@ -52,6 +61,8 @@ struct SolverParams {
 bool solver_variant_exists(int N, int G);
 size_t solver_smem_bytes(int N, int J, int m, int G);
 cudaError_t launch_solver(int N, int G, const SolverParams &p, cudaStream_t s, int *clusters_out);
+// the Bluestein variants (solver_bs.cu); what == 0: shared bytes, 1: launch
+long long solver_dispatch_blue(int N, int G, int what, const SolverParams *p, cudaStream_t s, int *clusters_out);
 // Synthetic positive intensities for timing runs (autotuner).
 cudaError_t launch_fill_synthetic(float *y, size_t n, unsigned seed, cudaStream_t s);
 

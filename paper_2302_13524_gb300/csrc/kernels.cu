@@ -7,34 +7,43 @@
 // Q^H(z .* r) in registers: forward FFT, residual r = y - |z|^2 and its square
 // sum, inverse FFT of z .* r, multiply by conj(d_j), accumulate; g = -4 * acc.
 #include <cmath>
+#include <complex>
 #include <vector>
 
 #include "common.cuh"
 #include "fft.cuh"
 #include "internal.h"
+#include "xform.cuh"
 
 namespace tmr {
 
-#define TMR_DISPATCH_N(NVAR, ...)                \
-    switch (NVAR) {                              \
-    case 64: { constexpr int NN = 64; __VA_ARGS__; } break;     \
-    case 128: { constexpr int NN = 128; __VA_ARGS__; } break;   \
-    case 256: { constexpr int NN = 256; __VA_ARGS__; } break;   \
-    case 512: { constexpr int NN = 512; __VA_ARGS__; } break;   \
-    case 1024: { constexpr int NN = 1024; __VA_ARGS__; } break; \
-    case 2048: { constexpr int NN = 2048; __VA_ARGS__; } break; \
-    case 4096: { constexpr int NN = 4096; __VA_ARGS__; } break; \
-    default: return cudaErrorInvalidValue;       \
-    }
-
 bool fft_supported(int N) { return N >= 64 && N <= 4096 && (N & (N - 1)) == 0; }
 
-template <int N>
-static int fft_table_t(float2 *out)
+bool xform_blue_shape(int N, int *L, int *ne)
 {
-    using Pl = FftPlan<N, N / fft_threads(N)>;
+    if (N < 16 || N > 4096 || fft_supported(N)) return false;
+    int l = 512;
+    while (l < 2 * N - 1) l *= 2;
+    if (l > 8192) return false;
+    const int nt = l / 16;
+    const int need = (N + nt - 1) / nt;
+    *L = l;
+    *ne = l == 8192 ? need : 8;  // exact register count where it matters (largest L)
+    return need <= *ne;
+}
+
+bool xform_supported(int N)
+{
+    int L, ne;
+    return fft_supported(N) || xform_blue_shape(N, &L, &ne);
+}
+
+// Twiddles of passes 1 .. P-1 (npass = P) or 1 .. P-2 (npass = P - 1) of a plan.
+template <class Pl>
+static int plan_table(float2 *out, int npass)
+{
     if (out) {
-        for (int p = 1; p < Pl::P; p++) {
+        for (int p = 1; p < npass; p++) {
             const int R = Pl::radix(p), Ns = Pl::ns(p), off = Pl::tw_off(p);
             for (int r = 1; r < R; r++)
                 for (int j = 0; j < Ns; j++) {
@@ -43,7 +52,14 @@ static int fft_table_t(float2 *out)
                 }
         }
     }
-    return Pl::TW_SIZE;
+    return Pl::tw_off(npass);
+}
+
+template <int N>
+static int fft_table_t(float2 *out)
+{
+    using Pl = FftPlan<N, N / fft_threads(N)>;
+    return plan_table<Pl>(out, Pl::P);
 }
 
 static int fft_table_dispatch(int N, float2 *out)
@@ -63,73 +79,181 @@ static int fft_table_dispatch(int N, float2 *out)
 int fft_table(int N, float2 *out) { return fft_table_dispatch(N, out); }
 int fft_table_len(int N) { return fft_table_dispatch(N, nullptr); }
 
-// ---------------------------------------------------------------------------
-template <int N>
-__global__ void __launch_bounds__(fft_threads(N)) k_forward(const float2 *__restrict__ T,
-                                                          const float2 *__restrict__ masks,
-                                                          const float2 *__restrict__ twg,
-                                                          float *__restrict__ Y, int J)
+// In-place FP64 radix-2 DFT X_k = sum_m x_m exp(-2 pi i k m / n), n a power of two.
+static void host_fft(std::vector<std::complex<double>> &x)
 {
-    constexpr int NT = fft_threads(N), E = N / NT, TWN = FftPlan<N, E>::TW_SIZE;
-    extern __shared__ float2 smem[];
-    float2 *buf = smem, *tw = smem + fft_buf_len(N);
-    const int tid = threadIdx.x, row = blockIdx.x, j = blockIdx.y;
-    for (int i = tid; i < TWN; i += NT) tw[i] = twg[i];
-    float2 v[E];
-#pragma unroll
-    for (int e = 0; e < E; e++) {
-        const int n = tid + e * NT;
-        v[e] = cmul(T[(size_t)row * N + n], masks[(size_t)j * N + n]);
+    const size_t n = x.size();
+    for (size_t i = 1, j = 0; i < n; i++) {  // bit reversal
+        size_t bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(x[i], x[j]);
     }
-    __syncthreads();
-    block_fft<N, NT, -1>(v, buf, tw, tid);
-    float *yr = Y + ((size_t)row * J + j) * N;
-#pragma unroll
-    for (int e = 0; e < E; e++) yr[tid + e * NT] = cabs2(v[e]);
+    for (size_t len = 2; len <= n; len <<= 1) {
+        for (size_t k = 0; k < len / 2; k++) {
+            const double a = -2.0 * M_PI * (double)k / (double)len;
+            const std::complex<double> w(std::cos(a), std::sin(a));
+            for (size_t i = 0; i < n; i += len) {
+                const std::complex<double> u = x[i + k], v = x[i + k + len / 2] * w;
+                x[i + k] = u + v;
+                x[i + k + len / 2] = u - v;
+            }
+        }
+    }
 }
 
-template <int N>
-__global__ void __launch_bounds__(fft_threads(N)) k_grad(const float2 *__restrict__ T,
-                                                       const float2 *__restrict__ masks,
-                                                       const float2 *__restrict__ twg,
-                                                       const float *__restrict__ Y,
-                                                       float *__restrict__ loss,
-                                                       float2 *__restrict__ G, int J)
+template <int L, int NE>
+static int blue_table(int N, float2 *out)
 {
-    constexpr int NT = fft_threads(N), E = N / NT, TWN = FftPlan<N, E>::TW_SIZE;
+    using X = XfBlue<L, NE>;
+    const int len = X::NCONST + N;
+    if (!out) return len;
+    plan_table<typename X::Plan>(out, X::Plan::P - 1);
+    // exp(i pi s m^2 / N) with m^2 reduced mod 2N (exact)
+    auto chirp = [N](long long m, double s) {
+        const double a = s * M_PI * (double)((m * m) % (2LL * N)) / (double)N;
+        return std::complex<double>(std::cos(a), std::sin(a));
+    };
+    std::vector<std::complex<double>> b(L, 0.0);
+    for (int m = 0; m < N; m++) {
+        b[m] = chirp(m, +1.0);
+        if (m > 0) b[L - m] = b[m];
+    }
+    host_fft(b);
+    for (int k = 0; k <= L / 2; k++) {
+        const std::complex<double> v = b[k] / (double)L;
+        out[X::NCONST_TW + k] = make_float2((float)v.real(), (float)v.imag());
+    }
+    for (int n = 0; n < N; n++) {
+        const std::complex<double> c = chirp(n, -1.0);
+        out[X::NCONST + n] = make_float2((float)c.real(), (float)c.imag());
+    }
+    return len;
+}
+
+int xform_table(int N, float2 *out)
+{
+    if (fft_supported(N)) return fft_table(N, out);
+    int L, ne;
+    if (!xform_blue_shape(N, &L, &ne)) return -1;
+    switch (L) {
+    case 512: return blue_table<512, 8>(N, out);
+    case 1024: return blue_table<1024, 8>(N, out);
+    case 2048: return blue_table<2048, 8>(N, out);
+    case 4096: return blue_table<4096, 8>(N, out);
+    default: break;
+    }
+    switch (ne) {  // the constants do not depend on the register count
+    case 5: return blue_table<8192, 5>(N, out);
+    case 6: return blue_table<8192, 6>(N, out);
+    case 7: return blue_table<8192, 7>(N, out);
+    default: return blue_table<8192, 8>(N, out);
+    }
+}
+
+// Calls f(Xf{}) with the transform policy of length N.
+template <class F>
+static cudaError_t dispatch_xf(int N, F &&f)
+{
+    switch (N) {
+    case 64: return f(XfPow2<64>{});
+    case 128: return f(XfPow2<128>{});
+    case 256: return f(XfPow2<256>{});
+    case 512: return f(XfPow2<512>{});
+    case 1024: return f(XfPow2<1024>{});
+    case 2048: return f(XfPow2<2048>{});
+    case 4096: return f(XfPow2<4096>{});
+    default: break;
+    }
+    int L, ne;
+    if (!xform_blue_shape(N, &L, &ne)) return cudaErrorInvalidValue;
+    switch (L) {
+    case 512: return f(XfBlue<512, 8>{});
+    case 1024: return f(XfBlue<1024, 8>{});
+    case 2048: return f(XfBlue<2048, 8>{});
+    case 4096: return f(XfBlue<4096, 8>{});
+    default: break;
+    }
+    switch (ne) {
+    case 5: return f(XfBlue<8192, 5>{});
+    case 6: return f(XfBlue<8192, 6>{});
+    case 7: return f(XfBlue<8192, 7>{});
+    default: return f(XfBlue<8192, 8>{});
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Kernels over a transform policy Xf (xform.cuh); shared memory holds the
+// exchange buffer (Xf::LBUF) and the transform's shared constants.
+template <class Xf>
+__global__ void __launch_bounds__(Xf::NT) k_forward(int N, const float2 *__restrict__ T,
+                                                    const float2 *__restrict__ masks,
+                                                    const float2 *__restrict__ cg,
+                                                    float *__restrict__ Y, int J)
+{
+    constexpr int NT = Xf::NT, E = Xf::NE;
     extern __shared__ float2 smem[];
-    float2 *buf = smem, *tw = smem + fft_buf_len(N);
-    __shared__ float red[NT / 32], fsum[1];
+    float2 *buf = smem, *cst = smem + Xf::LBUF;
+    const int tid = threadIdx.x, row = blockIdx.x, j = blockIdx.y;
+    for (int i = tid; i < Xf::shared_consts(N); i += NT) cst[i] = cg[i];
+    Xf xf;
+    xf.setup(masks + (size_t)j * N, cg + Xf::NCONST, N, tid);
+    float2 v[E];
+#pragma unroll
+    for (int e = 0; e < E; e++)
+        v[e] = Xf::valid(e, tid, N) ? T[(size_t)row * N + tid + e * NT] : make_float2(0.f, 0.f);
+    __syncthreads();
+    xf.fwd(v, buf, cst, tid);
+    float *yr = Y + ((size_t)row * J + j) * N;
+#pragma unroll
+    for (int e = 0; e < E; e++)
+        if (Xf::valid(e, tid, N)) yr[tid + e * NT] = cabs2(v[e]);
+}
+
+template <class Xf>
+__global__ void __launch_bounds__(Xf::NT) k_grad(int N, const float2 *__restrict__ T,
+                                                 const float2 *__restrict__ masks,
+                                                 const float2 *__restrict__ cg,
+                                                 const float *__restrict__ Y,
+                                                 float *__restrict__ loss,
+                                                 float2 *__restrict__ G, int J)
+{
+    constexpr int NT = Xf::NT, E = Xf::NE;
+    extern __shared__ float2 smem[];
+    float2 *buf = smem, *cst = smem + Xf::LBUF;
+    __shared__ float red[NT / 32 > 0 ? NT / 32 : 1], fsum[1];
     const int tid = threadIdx.x, row = blockIdx.x;
-    for (int i = tid; i < TWN; i += NT) tw[i] = twg[i];
+    for (int i = tid; i < Xf::shared_consts(N); i += NT) cst[i] = cg[i];
     float2 t[E], acc[E];
 #pragma unroll
     for (int e = 0; e < E; e++) {
-        t[e] = T[(size_t)row * N + tid + e * NT];
+        t[e] = Xf::valid(e, tid, N) ? T[(size_t)row * N + tid + e * NT] : make_float2(0.f, 0.f);
         acc[e] = make_float2(0.f, 0.f);
     }
     float f = 0.f;
     __syncthreads();
     for (int j = 0; j < J; j++) {
-        const float2 *d = masks + (size_t)j * N;
+        Xf xf;
+        xf.setup(masks + (size_t)j * N, cg + Xf::NCONST, N, tid);
         const float *y = Y + ((size_t)row * J + j) * N;
         float2 v[E];
 #pragma unroll
-        for (int e = 0; e < E; e++) v[e] = cmul(t[e], d[tid + e * NT]);
-        block_fft<N, NT, -1>(v, buf, tw, tid);
+        for (int e = 0; e < E; e++) v[e] = t[e];
+        xf.fwd(v, buf, cst, tid);
 #pragma unroll
         for (int e = 0; e < E; e++) {
-            const float r = y[tid + e * NT] - cabs2(v[e]);
+            const float r = Xf::valid(e, tid, N) ? y[tid + e * NT] - cabs2(v[e]) : 0.f;
             f = fmaf(r, r, f);
             v[e] = cscale(v[e], r);
         }
-        block_fft<N, NT, +1>(v, buf, tw, tid);
+        xf.adj(v, buf, cst, tid);
 #pragma unroll
-        for (int e = 0; e < E; e++) acc[e] = cadd(acc[e], cmulc(v[e], d[tid + e * NT]));
+        for (int e = 0; e < E; e++) acc[e] = cadd(acc[e], v[e]);
     }
     if (G) {
 #pragma unroll
-        for (int e = 0; e < E; e++) G[(size_t)row * N + tid + e * NT] = cscale(acc[e], -4.f);
+        for (int e = 0; e < E; e++)
+            if (Xf::valid(e, tid, N)) G[(size_t)row * N + tid + e * NT] = cscale(acc[e], -4.f);
     }
     float fv[1] = {f};
     block_sum<1>(fv, red, fsum);
@@ -138,29 +262,29 @@ __global__ void __launch_bounds__(fft_threads(N)) k_grad(const float2 *__restric
 
 // Defocus fields: CTA (row, j) computes z_j = F(d_j .* t) and keeps the
 // entries whose pattern index j*N + k is below Nd.
-template <int N>
-__global__ void __launch_bounds__(fft_threads(N)) k_fields(const float2 *__restrict__ T,
-                                                         const float2 *__restrict__ masks,
-                                                         const float2 *__restrict__ twg,
-                                                         float2 *__restrict__ Zd, int M, int Nd)
+template <class Xf>
+__global__ void __launch_bounds__(Xf::NT) k_fields(int N, const float2 *__restrict__ T,
+                                                   const float2 *__restrict__ masks,
+                                                   const float2 *__restrict__ cg,
+                                                   float2 *__restrict__ Zd, int M, int Nd)
 {
-    constexpr int NT = fft_threads(N), E = N / NT, TWN = FftPlan<N, E>::TW_SIZE;
+    constexpr int NT = Xf::NT, E = Xf::NE;
     extern __shared__ float2 smem[];
-    float2 *buf = smem, *tw = smem + fft_buf_len(N);
+    float2 *buf = smem, *cst = smem + Xf::LBUF;
     const int tid = threadIdx.x, row = blockIdx.x, j = blockIdx.y;
-    for (int i = tid; i < TWN; i += NT) tw[i] = twg[i];
+    for (int i = tid; i < Xf::shared_consts(N); i += NT) cst[i] = cg[i];
+    Xf xf;
+    xf.setup(masks + (size_t)j * N, cg + Xf::NCONST, N, tid);
     float2 v[E];
 #pragma unroll
-    for (int e = 0; e < E; e++) {
-        const int n = tid + e * NT;
-        v[e] = cmul(T[(size_t)row * N + n], masks[(size_t)j * N + n]);
-    }
+    for (int e = 0; e < E; e++)
+        v[e] = Xf::valid(e, tid, N) ? T[(size_t)row * N + tid + e * NT] : make_float2(0.f, 0.f);
     __syncthreads();
-    block_fft<N, NT, -1>(v, buf, tw, tid);
+    xf.fwd(v, buf, cst, tid);
 #pragma unroll
     for (int e = 0; e < E; e++) {
         const int pat = j * N + tid + e * NT;
-        if (pat < Nd) Zd[(size_t)pat * M + row] = v[e];
+        if (Xf::valid(e, tid, N) && pat < Nd) Zd[(size_t)pat * M + row] = v[e];
     }
 }
 
@@ -195,31 +319,33 @@ __global__ void k_row_energy(int N, int M, const float2 *__restrict__ T, float *
 }
 
 // ---------------------------------------------------------------------------
-template <int N>
-static size_t fft_kernel_smem() { return sizeof(float2) * (fft_buf_len(N) + FftPlan<N, N / fft_threads(N)>::TW_SIZE); }
+template <class Xf>
+static size_t xf_kernel_smem(int N) { return sizeof(float2) * (Xf::LBUF + Xf::shared_consts(N)); }
 
 cudaError_t launch_forward(int N, int M, int J, const float2 *T, const float2 *masks,
                            const float2 *tw, float *Y, cudaStream_t s)
 {
     if (M == 0) return cudaSuccess;
-    TMR_DISPATCH_N(N, {
-        const size_t sm = fft_kernel_smem<NN>();
-        cudaFuncSetAttribute(k_forward<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_forward<NN><<<dim3(M, J), fft_threads(NN), sm, s>>>(T, masks, tw, Y, J);
+    return dispatch_xf(N, [&](auto xf) {
+        using XF = decltype(xf);
+        const size_t sm = xf_kernel_smem<XF>(N);
+        cudaFuncSetAttribute(k_forward<XF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_forward<XF><<<dim3(M, J), XF::NT, sm, s>>>(N, T, masks, tw, Y, J);
+        return cudaGetLastError();
     });
-    return cudaGetLastError();
 }
 
 cudaError_t launch_grad(int N, int M, int J, const float2 *T, const float2 *masks,
                         const float2 *tw, const float *Y, float *loss, float2 *G, cudaStream_t s)
 {
     if (M == 0) return cudaSuccess;
-    TMR_DISPATCH_N(N, {
-        const size_t sm = fft_kernel_smem<NN>();
-        cudaFuncSetAttribute(k_grad<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_grad<NN><<<M, fft_threads(NN), sm, s>>>(T, masks, tw, Y, loss, G, J);
+    return dispatch_xf(N, [&](auto xf) {
+        using XF = decltype(xf);
+        const size_t sm = xf_kernel_smem<XF>(N);
+        cudaFuncSetAttribute(k_grad<XF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_grad<XF><<<M, XF::NT, sm, s>>>(N, T, masks, tw, Y, loss, G, J);
+        return cudaGetLastError();
     });
-    return cudaGetLastError();
 }
 
 cudaError_t launch_fields(int N, int M, int J, int Nd, const float2 *T, const float2 *masks,
@@ -227,12 +353,13 @@ cudaError_t launch_fields(int N, int M, int J, int Nd, const float2 *T, const fl
 {
     if (M == 0 || Nd == 0) return cudaSuccess;
     const int Jn = (Nd + N - 1) / N < J ? (Nd + N - 1) / N : J;
-    TMR_DISPATCH_N(N, {
-        const size_t sm = fft_kernel_smem<NN>();
-        cudaFuncSetAttribute(k_fields<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_fields<NN><<<dim3(M, Jn), fft_threads(NN), sm, s>>>(T, masks, tw, Zd, M, Nd);
+    return dispatch_xf(N, [&](auto xf) {
+        using XF = decltype(xf);
+        const size_t sm = xf_kernel_smem<XF>(N);
+        cudaFuncSetAttribute(k_fields<XF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_fields<XF><<<dim3(M, Jn), XF::NT, sm, s>>>(N, T, masks, tw, Zd, M, Nd);
+        return cudaGetLastError();
     });
-    return cudaGetLastError();
 }
 
 cudaError_t launch_apply_phase(int N, int M, const double *phi, const float2 *Tin, float2 *Tout,

@@ -142,6 +142,7 @@ extern "C" tmr_status tmr_retrieve_rows_static(int N, int M, int J, const void *
     p.queue = queue;
     p.Nd = 0;
     p.M = M;
+    p.N = N;
     p.J = J;
     p.iters = iters;
     p.m = o.m;

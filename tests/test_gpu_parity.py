@@ -225,9 +225,10 @@ def test_zero_nan_and_ragged_rows():
 def test_invalid_arguments():
     N, M, J = 64, 4, 4
     _, d, Y = problem(N, M, J)
-    with pytest.raises(tmr.TMRError) as ei:
-        tmr.tmr_create(96, M, J, to_dev(np.ones(J * 96, np.complex64)))
-    assert ei.value.status == tmr.TMR_ERR_UNSUPPORTED
+    for bad_n in (8, 5000):  # outside 16..4096
+        with pytest.raises(tmr.TMRError) as ei:
+            tmr.tmr_create(bad_n, M, J, to_dev(np.ones(J * bad_n, np.complex64)))
+        assert ei.value.status == tmr.TMR_ERR_UNSUPPORTED
     with pytest.raises(tmr.TMRError) as ei:
         tmr.tmr_create(N, M, 9, to_dev(np.ones(9 * N, np.complex64)))
     assert ei.value.status == tmr.TMR_ERR_UNSUPPORTED
