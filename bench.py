@@ -27,6 +27,12 @@ METRIC = "TM rows/s to fidelity>=0.99 (plain vs learned-init+mixed), % of roofli
 UNIT = "rows/s"
 WORKLOAD = "plain N=2048 M=8192 (128x64) J=4 modes R=1100 Poisson 1e4"
 N_SM_NOMINAL = 152
+# measured dense bf16 burst (cuBLAS) of this GPU type, for the tensor-pipe fraction
+try:
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as _f:
+        MEASURED_BF16_TFLOPS = float(json.load(_f)["bf16_tflops"])
+except (OSError, KeyError, ValueError):
+    MEASURED_BF16_TFLOPS = 1900.0  # fallback figure
 # --workload plain (default: the headline line) or batching (uneven convergence
 # at a non-power-of-two length, Bluestein transforms, per-row early exit)
 WORKLOADS = {
@@ -35,6 +41,8 @@ WORKLOADS = {
     "batching": dict(N=2286, J=4, R=1100, ny=128, nx=64, photons=(1e3, 1e5), iters=300, tol=1e-7,
                      desc="batching N=2286 M=8192 (128x64) J=4 modes R=1100 Poisson per-row "
                           "log-uniform 1e3..1e5, early exit 1e-7, cap 300"),
+    "precision": dict(N=4096, J=4, R=2200, ny=128, nx=128, photons=1e4, iters=100, tol=0.0,
+                      desc="precision N=4096 M=16384 (128x128) J=4 modes R=2200 Poisson 1e4"),
 }
 
 
@@ -45,6 +53,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"],
+                    help="mixed: FP16 intensities, BF16 pairs, tensor-core split-BF16 DFT "
+                         "stages, last 10 iterations FP32 (N = 256 or 4096)")
     ap.add_argument("--iters", type=int, default=None, help="L-BFGS iterations (cap); default per workload")
     ap.add_argument("--power-iters", type=int, default=100)
     ap.add_argument("--phase-iters", type=int, default=100)
@@ -241,7 +252,7 @@ def main():
     Tg = torch.from_numpy(T).cuda()
     dg = torch.from_numpy(d).cuda()
     opt = dict(init="spectral", power_iters=args.power_iters, clip=2.0, m=m,
-               phase_iters=args.phase_iters, seed=seed, tol=W["tol"])
+               phase_iters=args.phase_iters, seed=seed, tol=W["tol"], precision=args.precision)
     dop = dict(ny=ny, nx=nx, n_defocus=Nd, coef=0.05)
     h = tmr.tmr_create(N, M, J, dg, dop, opt, stream=stream.cuda_stream)
     sched = tmr.tmr_schedule(h)
@@ -333,6 +344,19 @@ def main():
             "solver_ms": solver_ms, "flops_per_launch": flops}
     if clk and clk.get("sm_mhz"):
         roof["frac_at_measured_clock"] = achieved / fp32_peak_tflops(n_sm, clk["sm_mhz"])
+    if args.precision == "mixed":
+        # tensor-pipe work of the split-BF16 DFT stages: per transform, log16 N
+        # passes x N/128 groups x 12 mma.m16n8k16 (4096 flops each); the power
+        # iterations, the start and all but the last 10 iterations use them
+        passes = int(round(math.log(N, 16)))
+        per_transform = passes * (N // 128) * 12 * 4096
+        tc_iters = np.maximum(its - 10, 0) if args.iters > 10 else np.zeros_like(its)
+        n_tr = 2 * J * (M * (args.power_iters + 1) + float(np.sum(tc_iters)))
+        tc = per_transform * n_tr / (solver_ms / 1e3) / 1e12
+        roof["tensor"] = {"achieved": tc, "unit": "TFLOP/s", "peak": MEASURED_BF16_TFLOPS,
+                          "frac": tc / MEASURED_BF16_TFLOPS,
+                          "basis": "split-BF16 mma.sync flops of the DFT stages; peak = measured "
+                                   "cuBLAS bf16 burst"}
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -366,14 +390,16 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.precision == "fp32" else "mixed f16/bf16/f32 (f64 phase fit)",
                 "data": "synthetic",
                 "config": {"workload": W["desc"], "N": N, "M": M, "J": J, "grid": [ny, nx],
                            "R": R, "photons": W["photons"], "init": "spectral", "tol": W["tol"],
+                           "precision": args.precision,
                            "power_iters": args.power_iters, "iters": args.iters, "m": m,
                            "row_iters_mean": float(its.mean()), "row_iters_max": int(its.max()),
                            "n_defocus": Nd, "phase_iters": args.phase_iters,
-                           "l2": "inputs larger than L2 (y is 256 MB)",
+                           "l2": f"inputs larger than L2 (y is {M * J * N * 4 >> 20} MB)",
                            "parallelism": f"{world} independent TMs, one per GPU"},
                 "schedule": {"masks_per_cta": sched, "autotuned": True},
                 "fidelity": {"mean": float(fid.mean()), "p1": float(np.percentile(fid, 1)),

@@ -76,7 +76,19 @@ enum {
     TMR_ROW_NUMERIC = 3    /* non-finite intensity or iterate; t = 0 or last value */
 };
 
-enum { TMR_PREC_FP32 = 0 };
+/* Arithmetic of tmr_retrieve (and of tmr_forward / tmr_grad on the handle).
+ * TMR_PREC_FP32: FP32 FFTs, FP32 intensities and L-BFGS pairs.
+ * TMR_PREC_MIXED (N = 256 or 4096 only; not an arithmetic of the paper, which
+ * works in double precision): intensities stored as FP16 after dividing
+ * each row by its largest |y| (the handle packs them, M*J*N*2 bytes); L-BFGS
+ * pairs stored as BF16 (the iterate, gradient and direction stay FP32); each
+ * length-N DFT as radix-16 passes whose 16-point DFTs run on the tensor cores
+ * as split BF16 (hi + lo) GEMMs with FP32 accumulation, about 1e-5 relative
+ * error per transform; the last 10 L-BFGS iterations (when iters > 10) go
+ * back to FP32 transforms after a fresh FP32 evaluation of f and g at the
+ * current iterate, which restarts the history.  The phase-offset fit is FP64
+ * either way. */
+enum { TMR_PREC_FP32 = 0, TMR_PREC_MIXED = 1 };
 
 /* Defocus operator of the phase-offset fit (Sec. 2.3).  The defocus field
  * of pattern n is D c_n with c_n[row] = (Q t_row)[n] (the first n_defocus
@@ -99,7 +111,7 @@ typedef struct {
     double clip;            /* spectral intensity clip, <= 0: none (default 2.0)     */
     double tol;             /* early exit when |f_prev - f| / f_prev < tol; 0 = off  */
     int phase_iters;        /* L-BFGS iterations of the phase-offset fit (default 100) */
-    int precision;          /* TMR_PREC_FP32                                         */
+    int precision;          /* TMR_PREC_FP32 (default) or TMR_PREC_MIXED             */
     int use_graph;          /* replay tmr_retrieve from a captured CUDA graph (default 0) */
     size_t workspace_limit; /* max device bytes the handle may allocate; 0 = no cap  */
     int schedule;           /* masks per CTA of the solver: 1, 2 or 4 (must divide J);

@@ -20,6 +20,7 @@ TMR_ERR_CUDA, TMR_ERR_TIMEOUT, TMR_ERR_NUMERIC = 4, 5, 6
 TMR_INIT_RANDOM, TMR_INIT_BP, TMR_INIT_SPECTRAL, TMR_INIT_LEARNED = 0, 1, 2, 3
 TMR_ROW_MAXITER, TMR_ROW_CONVERGED, TMR_ROW_ZERO, TMR_ROW_NUMERIC = 0, 1, 2, 3
 TMR_PREC_FP32 = 0
+TMR_PREC_MIXED = 1
 INIT = {"random": TMR_INIT_RANDOM, "bp": TMR_INIT_BP, "spectral": TMR_INIT_SPECTRAL,
         "learned": TMR_INIT_LEARNED}
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "TIMEOUT",
@@ -140,6 +141,8 @@ def tmr_default_options(**overrides) -> tmr_options:
     for k, v in overrides.items():
         if k == "init" and isinstance(v, str):
             v = INIT[v]
+        if k == "precision" and isinstance(v, str):
+            v = {"fp32": TMR_PREC_FP32, "mixed": TMR_PREC_MIXED}[v]
         if k == "tune_cache" and isinstance(v, str):
             v = v.encode()
         setattr(o, k, v)

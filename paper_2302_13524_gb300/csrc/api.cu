@@ -92,6 +92,9 @@ struct tmr_handle {
     const int *last_status = nullptr;
     bool last_had_fit = false;
     int G = 1;  // solver schedule: masks per CTA
+    int prec = TMR_PREC_FP32;
+    void *y16 = nullptr;   // mixed precision: FP16 intensities [M][J][N]
+    float *ysc = nullptr;  // and their row scales [M]
     cudaStream_t own_stream = nullptr;  // created for graph capture when the caller gave none
     // captured retrieve graph and the arguments it was captured with
     cudaGraphExec_t gexec = nullptr;
@@ -204,10 +207,10 @@ void write_tune_file(const char *path, const std::map<std::string, int> &m)
     f << "\n}\n";
 }
 
-bool schedule_ok(int N, int J, int m, int G, int smem_optin)
+bool schedule_ok(int N, int J, int m, int G, int smem_optin, int prec = 0)
 {
-    if (G <= 0 || J % G != 0 || !solver_variant_exists(N, G)) return false;
-    const size_t b = solver_smem_bytes(N, J, m, G);
+    if (G <= 0 || J % G != 0 || !solver_variant_exists(N, G, prec)) return false;
+    const size_t b = solver_smem_bytes(N, J, m, G, prec);
     return b > 0 && b <= (size_t)smem_optin;
 }
 
@@ -217,7 +220,7 @@ tmr_status autotune(tmr_handle *h, int smem_optin, int *G_out)
 {
     int cand[3], nc = 0;
     for (int G : {1, 2, 4})
-        if (schedule_ok(h->N, h->J, h->opt.m, G, smem_optin)) cand[nc++] = G;
+        if (schedule_ok(h->N, h->J, h->opt.m, G, smem_optin, h->prec)) cand[nc++] = G;
     if (nc == 0) {  // the forward model and gradient still work; tmr_retrieve will refuse
         *G_out = 0;
         return TMR_OK;
@@ -287,12 +290,13 @@ tmr_status autotune(tmr_handle *h, int smem_optin, int *G_out)
     return st;
 }
 
-std::string tune_key(int dev, int N, int J, int m)
+std::string tune_key(int dev, int N, int J, int m, int prec)
 {
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, dev);
     char k[320];
-    snprintf(k, sizeof(k), "%s|sm%d%d|N%d|J%d|m%d", prop.name, prop.major, prop.minor, N, J, m);
+    snprintf(k, sizeof(k), "%s|sm%d%d|N%d|J%d|m%d%s", prop.name, prop.major, prop.minor, N, J, m,
+             prec ? "|mixed" : "");
     for (char *c = k; *c; c++)
         if (*c == '"' || *c == '\\') *c = '_';
     return k;
@@ -356,7 +360,7 @@ void tmr_destroy(tmr_handle *h)
     else cudaDeviceSynchronize();
     void *ptrs[] = {h->masks, h->tw, h->H, h->Zd, h->phi, h->pf_ws, h->pf_loss, h->wts, h->queue,
                     h->pf_sync, h->pf_err, h->pf_iters, h->status_scratch, h->iters_scratch,
-                    h->loss_scratch, h->Tcand, h->wins};
+                    h->loss_scratch, h->Tcand, h->wins, h->y16, h->ysc};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &b : h->stage)
@@ -380,7 +384,12 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     if (o.m < 1 || o.m > kMaxMem) return fail(TMR_ERR_INVALID_ARG, "opt.m must be in 1..6");
     if (o.init < TMR_INIT_RANDOM || o.init > TMR_INIT_LEARNED) return fail(TMR_ERR_INVALID_ARG, "opt.init");
     if (o.power_iters < 0 || o.phase_iters < 0 || o.tol < 0) return fail(TMR_ERR_INVALID_ARG, "negative option");
-    if (o.precision != TMR_PREC_FP32) return fail(TMR_ERR_UNSUPPORTED, "only TMR_PREC_FP32 is available");
+    if (o.precision != TMR_PREC_FP32 && o.precision != TMR_PREC_MIXED)
+        return fail(TMR_ERR_INVALID_ARG, "opt.precision must be TMR_PREC_FP32 or TMR_PREC_MIXED");
+    if (o.precision == TMR_PREC_MIXED && !mixed_supported(N))
+        return fail(TMR_ERR_UNSUPPORTED, "TMR_PREC_MIXED needs N = 256 or 4096 (a power of 16)");
+    if (o.precision == TMR_PREC_MIXED && o.init == TMR_INIT_LEARNED)
+        return fail(TMR_ERR_UNSUPPORTED, "TMR_PREC_MIXED does not take the learned start");
     if (!xform_supported(N))
         return fail(TMR_ERR_UNSUPPORTED, "N must be a power of two in 64..4096 or another length in 16..4096");
     if (J > kMaxMasks) return fail(TMR_ERR_UNSUPPORTED, "J must be at most 8");
@@ -397,7 +406,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
 
     int smem_optin = 0;
     TMR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
-    if (o.schedule != 0 && !schedule_ok(N, J, o.m, o.schedule, smem_optin))
+    if (o.schedule != 0 && !schedule_ok(N, J, o.m, o.schedule, smem_optin, o.precision))
         return fail(TMR_ERR_UNSUPPORTED, "opt.schedule must be 1, 2 or 4, divide J and fit the device");
 
     tmr_handle *h = new tmr_handle();
@@ -406,6 +415,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     h->J = J;
     h->opt = o;
     h->opt.tune_cache = nullptr;  // the caller's string is not kept
+    h->prec = o.precision;
     h->stream = (cudaStream_t)stream;
     if (!h->stream && o.use_graph) {
         // the legacy default stream cannot be captured: use a blocking stream
@@ -434,9 +444,9 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
             return cuda_fail(e, "copy masks");
         }
     }
-    const int twn = xform_table(N, nullptr);
+    const int twn = xform_table_prec(N, h->prec, nullptr);
     std::vector<float2> tw(twn > 0 ? twn : 1);
-    xform_table(N, tw.data());
+    xform_table_prec(N, h->prec, tw.data());
     TRY(halloc(h, (void **)&h->tw, sizeof(float2) * tw.size(), "twiddles"));
     if (cudaMemcpy(h->tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
         tmr_destroy(h);
@@ -482,7 +492,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     if (o.schedule != 0) {
         h->G = o.schedule;
     } else {
-        const std::string key = tune_key(dev, N, J, o.m);
+        const std::string key = tune_key(dev, N, J, o.m, h->prec);
         int G = 0;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -491,7 +501,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
             if (!G && o.tune_cache) {
                 auto fm = read_tune_file(o.tune_cache);
                 auto f = fm.find(key);
-                if (f != fm.end() && schedule_ok(N, J, o.m, f->second, smem_optin)) G = f->second;
+                if (f != fm.end() && schedule_ok(N, J, o.m, f->second, smem_optin, h->prec)) G = f->second;
             }
         }
         if (!G) {
@@ -521,7 +531,7 @@ tmr_status tmr_forward(tmr_handle *h, const void *T, float *Y)
     if ((st = stage(h, ST_TIN, T, sizeof(float2) * MN, true, &dT)) != TMR_OK) return st;
     if ((st = stage(h, ST_Y, Y, sizeof(float) * MK, false, &dY)) != TMR_OK) return st;
     if ((st = check_launch(launch_forward(h->N, h->M, h->J, (const float2 *)dT, h->masks, h->tw,
-                                          (float *)dY, h->stream), "forward kernel")) != TMR_OK)
+                                          (float *)dY, h->stream, h->prec), "forward kernel")) != TMR_OK)
         return st;
     bool synced = false;
     if ((st = unstage(h, Y, dY, sizeof(float) * MK, &synced)) != TMR_OK) return st;
@@ -541,7 +551,7 @@ tmr_status tmr_grad(tmr_handle *h, const void *T, const float *Y, float *loss, v
     if (loss && (st = stage(h, ST_LOSS, loss, sizeof(float) * h->M, false, &dL)) != TMR_OK) return st;
     if (G && (st = stage(h, ST_TOUT, G, sizeof(float2) * MN, false, &dG)) != TMR_OK) return st;
     if ((st = check_launch(launch_grad(h->N, h->M, h->J, (const float2 *)dT, h->masks, h->tw,
-                                       (const float *)dY, (float *)dL, (float2 *)dG, h->stream),
+                                       (const float *)dY, (float *)dL, (float2 *)dG, h->stream, h->prec),
                            "gradient kernel")) != TMR_OK)
         return st;
     bool synced = false;
@@ -592,7 +602,7 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
         int dev = 0, smem_optin = 0;
         TMR_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
         TMR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
-        if (!schedule_ok(h->N, h->J, h->opt.m, h->G, smem_optin))
+        if (!schedule_ok(h->N, h->J, h->opt.m, h->G, smem_optin, h->prec))
             return fail(TMR_ERR_UNSUPPORTED,
                         "per-row state of this (N, J, m) does not fit in shared memory: lower opt.m");
     }
@@ -652,8 +662,21 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
     p.seed = h->opt.seed;
     p.clip = (float)h->opt.clip;
     p.tol = h->opt.tol;
-    // the whole retrieve on the stream: solver, then the phase-offset fit
+    p.prec = h->prec;
+    if (h->prec == TMR_PREC_MIXED) {
+        if (!h->y16) {
+            if ((st = halloc(h, &h->y16, 2 * (MK ? MK : 1), "FP16 intensities")) != TMR_OK) return st;
+            if ((st = halloc(h, (void **)&h->ysc, sizeof(float) * (h->M ? h->M : 1), "row scales")) != TMR_OK)
+                return st;
+        }
+        p.y16 = h->y16;
+        p.ysc = h->ysc;
+    }
+    // the whole retrieve on the stream: (FP16 packing,) solver, then the phase-offset fit
     auto enqueue = [&]() -> tmr_status {
+        if (h->prec == TMR_PREC_MIXED)
+            TMR_CUDA(launch_pack_f16(h->M, (size_t)h->J * h->N, (const float *)dy, h->y16, h->ysc, h->stream),
+                     "FP16 packing");
         TMR_CUDA(cudaMemsetAsync(h->queue, 0, sizeof(unsigned) * 4, h->stream), "memset");
         TMR_CUDA(launch_solver(h->N, h->G, p, h->stream, nullptr), "solver kernel");
         if (fit) {
@@ -730,7 +753,7 @@ tmr_status tmr_defocus_forward(tmr_handle *h, const void *T, float *Y_def)
     tmr_status st;
     if ((st = stage(h, ST_TIN, T, sizeof(float2) * MN, true, &dT)) != TMR_OK) return st;
     if ((st = stage(h, ST_YDEF, Y_def, sizeof(float) * (size_t)h->Nd * h->M, false, &dY)) != TMR_OK) return st;
-    TMR_CUDA(launch_fields(h->N, h->M, h->J, h->Nd, (const float2 *)dT, h->masks, h->tw, h->Zd, h->stream),
+    TMR_CUDA(launch_fields(h->N, h->M, h->J, h->Nd, (const float2 *)dT, h->masks, h->tw, h->Zd, h->stream, h->prec),
              "fields kernel");
     TMR_CUDA(launch_defocus_forward(h->ny, h->nx, h->Nd, h->Zd, h->H, nullptr, nullptr, (float *)dY, h->stream),
              "defocus kernel");
@@ -752,7 +775,7 @@ tmr_status tmr_defocus_fit(tmr_handle *h, const void *T_est, const float *y_def,
     if ((st = stage(h, ST_YDEF, y_def, sizeof(float) * (size_t)h->Nd * h->M, true, &dY)) != TMR_OK) return st;
     if (phi && (st = stage(h, ST_PHI, phi, sizeof(double) * h->M, false, &dP)) != TMR_OK) return st;
     if (T_out && (st = stage(h, ST_TOUT, T_out, sizeof(float2) * MN, false, &dO)) != TMR_OK) return st;
-    TMR_CUDA(launch_fields(h->N, h->M, h->J, h->Nd, (const float2 *)dT, h->masks, h->tw, h->Zd, h->stream),
+    TMR_CUDA(launch_fields(h->N, h->M, h->J, h->Nd, (const float2 *)dT, h->masks, h->tw, h->Zd, h->stream, h->prec),
              "fields kernel");
     if ((st = run_phase_fit(h, (const float2 *)dT, (const float *)dY, dP ? (double *)dP : h->phi,
                             (float2 *)dO)) != TMR_OK)

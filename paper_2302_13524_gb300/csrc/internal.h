@@ -25,15 +25,23 @@ bool xform_supported(int N);
 // thread (the instantiated variant); false when N has none.
 bool xform_blue_shape(int N, int *L, int *ne);
 int xform_table(int N, float2 *out);  // length in float2; writes when out != NULL
+// Mixed precision (TMR_PREC_MIXED): N a power of 16 (256, 4096); its table is
+// [FP32 twiddles | tensor-core DFT fragments | roots W_N^k].
+bool mixed_supported(int N);
+int xform_table_prec(int N, int prec, float2 *out);
 
 // ---- fused forward model and gradient (kernels.cu) -------------------------
+// prec: TMR_PREC_FP32 (FP32 transforms) or TMR_PREC_MIXED (tensor-core transforms)
 cudaError_t launch_forward(int N, int M, int J, const float2 *T, const float2 *masks,
-                           const float2 *tw, float *Y, cudaStream_t s);
+                           const float2 *tw, float *Y, cudaStream_t s, int prec = 0);
 cudaError_t launch_grad(int N, int M, int J, const float2 *T, const float2 *masks,
-                        const float2 *tw, const float *Y, float *loss, float2 *G, cudaStream_t s);
+                        const float2 *tw, const float *Y, float *loss, float2 *G, cudaStream_t s,
+                        int prec = 0);
 // c_n[r] = (Q T[r])[n] for n < Nd, written as Zd[n][r] (the defocus fields).
 cudaError_t launch_fields(int N, int M, int J, int Nd, const float2 *T, const float2 *masks,
-                          const float2 *tw, float2 *Zd, cudaStream_t s);
+                          const float2 *tw, float2 *Zd, cudaStream_t s, int prec = 0);
+// y (float32 [M][K]) -> y16 (FP16, each row divided by its largest |y|) and the row scales
+cudaError_t launch_pack_f16(int M, size_t K, const float *y, void *y16, float *ysc, cudaStream_t s);
 // T[r] *= exp(i phi[r])
 cudaError_t launch_apply_phase(int N, int M, const double *phi, const float2 *Tin, float2 *Tout,
                                cudaStream_t s);
@@ -43,6 +51,8 @@ struct SolverParams {
     const float2 *masks;  // [J][N]
     const float2 *tw;     // transform constants (xform_table)
     const float *y;       // [M][J][N]
+    const void *y16;      // [M][J][N] FP16, row-normalised (mixed precision), else unused
+    const float *ysc;     // [M] row scales of y16
     const float2 *T_init; // [M][N] or NULL
     float2 *T_out;        // [M][N]
     int *row_status;      // [M]
@@ -53,16 +63,19 @@ struct SolverParams {
     unsigned *cand_wins;  // rows whose proposed start was kept
     unsigned *queue;      // row work counter, zeroed before the launch
     int N, Nd, M, J, iters, m, init, power_iters;
+    int prec;             // TMR_PREC_FP32 or TMR_PREC_MIXED
     unsigned long long seed;
     float clip;
     double tol;
 };
 // Variants: G masks per CTA (G in {1, 2, 4}, G divides J), cluster of J/G CTAs.
-bool solver_variant_exists(int N, int G);
-size_t solver_smem_bytes(int N, int J, int m, int G);
+bool solver_variant_exists(int N, int G, int prec = 0);
+size_t solver_smem_bytes(int N, int J, int m, int G, int prec = 0);
 cudaError_t launch_solver(int N, int G, const SolverParams &p, cudaStream_t s, int *clusters_out);
 // the Bluestein variants (solver_bs.cu); what == 0: shared bytes, 1: launch
 long long solver_dispatch_blue(int N, int G, int what, const SolverParams *p, cudaStream_t s, int *clusters_out);
+// the mixed-precision variants (solver_mx.cu)
+long long solver_dispatch_mixed(int N, int G, int what, const SolverParams *p, cudaStream_t s, int *clusters_out);
 // Synthetic positive intensities for timing runs (autotuner).
 cudaError_t launch_fill_synthetic(float *y, size_t n, unsigned seed, cudaStream_t s);
 

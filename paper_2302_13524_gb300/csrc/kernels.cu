@@ -8,7 +8,10 @@
 // sum, inverse FFT of z .* r, multiply by conj(d_j), accumulate; g = -4 * acc.
 #include <cmath>
 #include <complex>
+#include <cstring>
 #include <vector>
+
+#include <cuda_fp16.h>
 
 #include "common.cuh"
 #include "fft.cuh"
@@ -151,10 +154,79 @@ int xform_table(int N, float2 *out)
     }
 }
 
-// Calls f(Xf{}) with the transform policy of length N.
-template <class F>
-static cudaError_t dispatch_xf(int N, F &&f)
+bool mixed_supported(int N) { return N == 256 || N == 4096; }
+
+// Round to the nearest BF16 (ties to even); returns the bits.
+static uint16_t host_bf16(float v)
 {
+    uint32_t u;
+    std::memcpy(&u, &v, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+static float host_bf16_value(uint16_t b)
+{
+    const uint32_t u = (uint32_t)b << 16;
+    float v;
+    std::memcpy(&v, &u, 4);
+    return v;
+}
+
+template <int N>
+static int mixed_table(float2 *out)
+{
+    using X = XfMixed<N>;
+    if (!out) return X::NCONST;
+    std::vector<float2> full(fft_table_len(N));
+    fft_table(N, full.data());
+    for (int i = 0; i < X::OFF_FRAG; i++) out[i] = full[i];
+    // 16-point DFT blocks (row q = output, column r = input) as m16n8k16 A
+    // fragments: word w of lane (g, t) holds rows g + 8 (w & 1), columns
+    // 2t + 8 (w >> 1) + {0, 1}, the lower column in the low half
+    uint32_t *frag = reinterpret_cast<uint32_t *>(out + X::OFF_FRAG);
+    for (int tile = 0; tile < kTcTiles; tile++) {
+        const int kind = tile / 2, part = tile % 2;  // kind 0 C, 1 S, 2 -S; part 0 hi, 1 lo
+        for (int lane = 0; lane < 32; lane++) {
+            const int g = lane >> 2, t = lane & 3;
+            for (int w = 0; w < 4; w++) {
+                uint32_t word = 0;
+                for (int h = 0; h < 2; h++) {
+                    const int q = g + 8 * (w & 1), r = 2 * t + 8 * (w >> 1) + h;
+                    const double a = 2.0 * M_PI * (double)((q * r) % 16) / 16.0;
+                    const double v = kind == 0 ? std::cos(a) : (kind == 1 ? std::sin(a) : -std::sin(a));
+                    const uint16_t hi = host_bf16((float)v);
+                    const uint16_t lo = host_bf16((float)(v - (double)host_bf16_value(hi)));
+                    word |= (uint32_t)(part == 0 ? hi : lo) << (16 * h);
+                }
+                frag[(tile * 32 + lane) * 4 + w] = word;
+            }
+        }
+    }
+    for (int k = 0; k < N; k++) {
+        const double a = -2.0 * M_PI * (double)k / (double)N;
+        out[X::OFF_ROOT + k] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    return X::NCONST;
+}
+
+int xform_table_prec(int N, int prec, float2 *out)
+{
+    if (prec == 0) return xform_table(N, out);
+    if (N == 256) return mixed_table<256>(out);
+    if (N == 4096) return mixed_table<4096>(out);
+    return -1;
+}
+
+// Calls f(Xf{}) with the transform policy of length N and precision prec.
+template <class F>
+static cudaError_t dispatch_xf(int N, int prec, F &&f)
+{
+    if (prec != 0) {
+        if (N == 256) return f(XfMixed<256>{});
+        if (N == 4096) return f(XfMixed<4096>{});
+        return cudaErrorInvalidValue;
+    }
     switch (N) {
     case 64: return f(XfPow2<64>{});
     case 128: return f(XfPow2<128>{});
@@ -323,10 +395,10 @@ template <class Xf>
 static size_t xf_kernel_smem(int N) { return sizeof(float2) * (Xf::LBUF + Xf::shared_consts(N)); }
 
 cudaError_t launch_forward(int N, int M, int J, const float2 *T, const float2 *masks,
-                           const float2 *tw, float *Y, cudaStream_t s)
+                           const float2 *tw, float *Y, cudaStream_t s, int prec)
 {
     if (M == 0) return cudaSuccess;
-    return dispatch_xf(N, [&](auto xf) {
+    return dispatch_xf(N, prec, [&](auto xf) {
         using XF = decltype(xf);
         const size_t sm = xf_kernel_smem<XF>(N);
         cudaFuncSetAttribute(k_forward<XF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -336,10 +408,11 @@ cudaError_t launch_forward(int N, int M, int J, const float2 *T, const float2 *m
 }
 
 cudaError_t launch_grad(int N, int M, int J, const float2 *T, const float2 *masks,
-                        const float2 *tw, const float *Y, float *loss, float2 *G, cudaStream_t s)
+                        const float2 *tw, const float *Y, float *loss, float2 *G, cudaStream_t s,
+                        int prec)
 {
     if (M == 0) return cudaSuccess;
-    return dispatch_xf(N, [&](auto xf) {
+    return dispatch_xf(N, prec, [&](auto xf) {
         using XF = decltype(xf);
         const size_t sm = xf_kernel_smem<XF>(N);
         cudaFuncSetAttribute(k_grad<XF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -349,11 +422,11 @@ cudaError_t launch_grad(int N, int M, int J, const float2 *T, const float2 *mask
 }
 
 cudaError_t launch_fields(int N, int M, int J, int Nd, const float2 *T, const float2 *masks,
-                          const float2 *tw, float2 *Zd, cudaStream_t s)
+                          const float2 *tw, float2 *Zd, cudaStream_t s, int prec)
 {
     if (M == 0 || Nd == 0) return cudaSuccess;
     const int Jn = (Nd + N - 1) / N < J ? (Nd + N - 1) / N : J;
-    return dispatch_xf(N, [&](auto xf) {
+    return dispatch_xf(N, prec, [&](auto xf) {
         using XF = decltype(xf);
         const size_t sm = xf_kernel_smem<XF>(N);
         cudaFuncSetAttribute(k_fields<XF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -385,6 +458,45 @@ __global__ void k_fill_synthetic(float *y, size_t n, unsigned seed)
 cudaError_t launch_fill_synthetic(float *y, size_t n, unsigned seed, cudaStream_t s)
 {
     k_fill_synthetic<<<512, 256, 0, s>>>(y, n, seed);
+    return cudaGetLastError();
+}
+
+// One CTA per row: the largest |y| of the row, then y / max rounded to FP16
+// (rows of zeros keep scale 1; a non-finite value makes the scale non-finite,
+// which the solver reports as a numeric row).
+__global__ void k_pack_f16(size_t K, const float *__restrict__ y, __half *__restrict__ y16,
+                           float *__restrict__ ysc)
+{
+    const size_t row = blockIdx.x;
+    const float *yr = y + row * K;
+    float mx = 0.f;
+    for (size_t i = threadIdx.x; i < K; i += blockDim.x) {
+        const float v = fabsf(yr[i]);
+        mx = (v > mx || v != v) ? v : mx;
+    }
+    __shared__ float red[32], out[1];
+    for (int o = 16; o > 0; o >>= 1) {
+        const float v = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = (v > mx || v != v) ? v : mx;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = (red[w] > m || red[w] != red[w]) ? red[w] : m;
+        out[0] = m > 0.f ? m : (m == 0.f ? 1.f : m);
+        ysc[row] = out[0];
+    }
+    __syncthreads();
+    const float inv = 1.f / out[0];
+    __half *o16 = y16 + row * K;
+    for (size_t i = threadIdx.x; i < K; i += blockDim.x) o16[i] = __float2half_rn(yr[i] * inv);
+}
+
+cudaError_t launch_pack_f16(int M, size_t K, const float *y, void *y16, float *ysc, cudaStream_t s)
+{
+    if (M == 0) return cudaSuccess;
+    k_pack_f16<<<M, 512, 0, s>>>(K, y, (__half *)y16, ysc);
     return cudaGetLastError();
 }
 

@@ -6,9 +6,10 @@ namespace tmr {
 
 // Masks per CTA that have a kernel for length N: powers of two with
 // G * threads(N) <= 512; other lengths (Bluestein) with G = 1.
-bool solver_variant_exists(int N, int G)
+bool solver_variant_exists(int N, int G, int prec)
 {
     if (G != 1 && G != 2 && G != 4) return false;
+    if (prec != 0) return G == 1 && mixed_supported(N);
     if (fft_supported(N)) return G * fft_threads(N) <= 512;
     return G == 1 && xform_supported(N);
 }
@@ -26,6 +27,7 @@ bool solver_variant_exists(int N, int G)
 static long long solver_dispatch(int N, int G, int what, const SolverParams *p, cudaStream_t s,
                                  int *clusters_out)
 {
+    if (p->prec != 0) return solver_dispatch_mixed(N, G, what, p, s, clusters_out);
     if (!fft_supported(N)) return solver_dispatch_blue(N, G, what, p, s, clusters_out);
     TMR_SOLVER_N(64)
     TMR_SOLVER_N(128)
@@ -37,20 +39,21 @@ static long long solver_dispatch(int N, int G, int what, const SolverParams *p, 
     return what == 0 ? 0 : (long long)cudaErrorInvalidValue;
 }
 
-size_t solver_smem_bytes(int N, int J, int m, int G)
+size_t solver_smem_bytes(int N, int J, int m, int G, int prec)
 {
     SolverParams p{};
     p.N = N;
     p.J = J;
     p.m = m;
-    if (!solver_variant_exists(N, G) || J % G != 0) return 0;
+    p.prec = prec;
+    if (!solver_variant_exists(N, G, prec) || J % G != 0) return 0;
     return (size_t)solver_dispatch(N, G, 0, &p, nullptr, nullptr);
 }
 
 cudaError_t launch_solver(int N, int G, const SolverParams &p, cudaStream_t s, int *clusters_out)
 {
     if (p.M == 0) return cudaSuccess;
-    if (!solver_variant_exists(N, G) || p.J % G != 0 || p.N != N) return cudaErrorInvalidValue;
+    if (!solver_variant_exists(N, G, p.prec) || p.J % G != 0 || p.N != N) return cudaErrorInvalidValue;
     return (cudaError_t)solver_dispatch(N, G, 1, &p, s, clusters_out);
 }
 

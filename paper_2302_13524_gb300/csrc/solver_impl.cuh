@@ -43,7 +43,10 @@
 
 #include <cooperative_groups.h>
 
+#include <cuda_fp16.h>
+
 #include <cmath>
+#include <type_traits>
 
 #include "common.cuh"
 #include "fft.cuh"
@@ -247,6 +250,29 @@ __device__ __forceinline__ void warp_reduce32(float (&v)[32], int lane)
     }
 }
 
+// Storage of the L-BFGS pairs: FP32 pairs, or BF16 pairs for the mixed-precision
+// policy (the iterate, gradient and direction stay FP32).
+template <class Xf, class = void>
+struct MixedTrait : std::false_type {};
+template <class Xf>
+struct MixedTrait<Xf, std::void_t<decltype(Xf::kMixed)>> : std::integral_constant<bool, Xf::kMixed> {};
+template <class Xf>
+__host__ __device__ constexpr bool solver_mixed() { return MixedTrait<Xf>::value; }
+template <class Xf>
+using SolverHist = typename std::conditional<MixedTrait<Xf>::value, __nv_bfloat162, float2>::type;
+
+__device__ __forceinline__ float2 hist_load(float2 v) { return v; }
+__device__ __forceinline__ float2 hist_load(__nv_bfloat162 v) { return __bfloat1622float2(v); }
+template <class HT>
+__device__ __forceinline__ HT hist_store(float2 v)
+{
+    if constexpr (std::is_same<HT, float2>::value) return v;
+    else return __float22bfloat162_rn(v);
+}
+
+// FP32 iterations at the end of a mixed-precision run
+constexpr int kFinalFp32Iters = 10;
+
 // G masks per CTA (G teams of NT threads, one transform each); the cluster
 // has J/G CTAs.  Xf is the transform policy (xform.cuh).
 template <class Xf, int G>
@@ -264,8 +290,8 @@ __host__ __device__ size_t solver_smem(int N, int J, int m)
     const int JC = J / G;
     const size_t SL = (N + JC - 1) / JC;
     size_t f2 = (size_t)G * Xf::LBUF /*X (team 0's exchange) and the others' exchange*/ + Xf::shared_consts(N) +
-                (size_t)J * SL /*Y*/ + 2 * SL /*t, g*/ + 2 * (size_t)(m + 1) * SL /*pairs*/;
-    size_t bytes = f2 * sizeof(float2);
+                (size_t)J * SL /*Y*/ + 2 * SL /*t, g*/ + (solver_mixed<Xf>() ? SL : 0) /*p*/;
+    size_t bytes = f2 * sizeof(float2) + 2 * (size_t)(m + 1) * SL * sizeof(SolverHist<Xf>) /*pairs*/;
     bytes += sizeof(float) * ((size_t)kParts * C::NW + 2 * (size_t)JC * kParts);
     bytes = (bytes + 15) & ~(size_t)15;
     return bytes + sizeof(Gram);
@@ -277,6 +303,8 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
 {
     using C = SolverCfg<Xf, G>;
     constexpr int NT = C::NT, BT = C::BT, E = C::E, NW = C::NW;
+    constexpr bool kMixed = solver_mixed<Xf>();
+    using HT = SolverHist<Xf>;
     const int N = Xf::kN > 0 ? Xf::kN : P.N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cg::cluster_group cluster = cg::this_cluster();
@@ -301,8 +329,10 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
     float2 *Yr = tws + NCS;  // [J][SL]
     float2 *ts = Yr + (size_t)J * SL;
     float2 *gs = ts + SL;
-    float2 *Ss = gs + SL;  // slot a at Ss + a*SL
-    float2 *Ys = Ss + (size_t)(m + 1) * SL;
+    // mixed precision: the direction p of my slice in FP32 (the pairs are BF16)
+    float2 *Ps = gs + (kMixed ? SL : 0);
+    HT *Ss = reinterpret_cast<HT *>(gs + (kMixed ? 2 * SL : SL));  // slot a at Ss + a*SL
+    HT *Ys = Ss + (size_t)(m + 1) * SL;
     float *red = reinterpret_cast<float *>(Ys + (size_t)(m + 1) * SL);  // [kParts][NW]
     float *part = red + kParts * NW;                                      // [2][JC][kParts]
     Gram &Gm = *reinterpret_cast<Gram *>(
@@ -404,10 +434,15 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
         float2 z[E];
         {
             float pv[32] = {0.f};
+            if constexpr (kMixed) xf.tc = P.iters > kFinalFp32Iters;
             const float *yr = P.y + (size_t)row * K + (size_t)jm * N;
+            // mixed precision: row-normalised FP16 intensities times the row scale
+            const __half *yr16 = reinterpret_cast<const __half *>(P.y16) + (size_t)row * K + (size_t)jm * N;
+            const float ysc = kMixed ? P.ysc[row] : 1.f;
 #pragma unroll
             for (int e = 0; e < E; e++) {
-                yv[e] = valid(e) ? yr[ttid + e * NT] : 0.f;
+                if constexpr (kMixed) yv[e] = __half2float(yr16[ttid + e * NT]) * ysc;
+                else yv[e] = valid(e) ? yr[ttid + e * NT] : 0.f;
                 if (isfinite(yv[e])) pv[0] += yv[e];
                 else pv[1] += 1.f;
             }
@@ -519,8 +554,9 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
                 }
             }
 
-            // ---- f and gradient at t0 ----
-            {
+            // ---- f and gradient at t (the start; in a mixed-precision run also the
+            // switch to the FP32 transforms, which restarts the history) ----
+            auto eval_at_t = [&]() {
                 __syncthreads();
                 push_slice_to_X(ts);
                 cluster.sync();
@@ -557,19 +593,27 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
                     if (!Gm.stop) lbfgs_coefficients_warp(Gm, lane);
                 }
                 __syncthreads();
-            }
+            };
+            eval_at_t();
 
             // ---- L-BFGS iterations ----
             for (int it = 0; it < P.iters && !Gm.stop; it++) {
+                if constexpr (kMixed) {
+                    if (xf.tc && it == P.iters - kFinalFp32Iters) {
+                        xf.tc = false;  // the last iterations in FP32
+                        eval_at_t();
+                        if (Gm.stop) break;
+                    }
+                }
                 const int ns = Gm.slot[Gm.np];  // free slot for the new pair
-                float2 *Sn = Ss + (size_t)ns * SL;
-                float2 *Yn = Ys + (size_t)ns * SL;
+                HT *Sn = Ss + (size_t)ns * SL;
+                HT *Yn = Ys + (size_t)ns * SL;
                 // A: direction on my slice, parked in the new S slot until the step is known
                 {
                     const float gam = Gm.gamma;
                     const int np = Gm.np;
                     float c1r[kSlots], c2r[kSlots];
-                    const float2 *sp[kSlots], *yp[kSlots];
+                    const HT *sp[kSlots], *yp[kSlots];
 #pragma unroll
                     for (int k = 0; k < kSlots; k++) {
                         const int a = Gm.slot[k < np ? k : 0];
@@ -583,13 +627,14 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
 #pragma unroll
                         for (int k = 0; k < kSlots; k++) {
                             if (k < np) {
-                                const float2 sa = sp[k][i], ya = yp[k][i];
+                                const float2 sa = hist_load(sp[k][i]), ya = hist_load(yp[k][i]);
                                 acc.x = fmaf(c1r[k], sa.x, fmaf(c2r[k], ya.x, acc.x));
                                 acc.y = fmaf(c1r[k], sa.y, fmaf(c2r[k], ya.y, acc.y));
                             }
                         }
                         const float2 p = make_float2(-acc.x, -acc.y);
-                        Sn[i] = p;
+                        if constexpr (kMixed) Ps[i] = p;
+                        else Sn[i] = p;
                         for (int o = 0; o < JC; o++) cluster.map_shared_rank(X, o)[lo + i] = p;
                     }
                 }
@@ -635,8 +680,14 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
                     u[e] = cscale(z[e], r);
                 }
                 for (int i = tid; i < nmine; i += BT) {
-                    const float2 s = cscale(Sn[i], al);
-                    Sn[i] = s;
+                    float2 s;
+                    if constexpr (kMixed) {
+                        s = cscale(Ps[i], al);
+                        Sn[i] = hist_store<HT>(s);
+                    } else {
+                        s = cscale(Sn[i], al);
+                        Sn[i] = s;
+                    }
                     ts[i] = cadd(ts[i], s);
                 }
                 // F: adjoint, pushed to the slice owners
@@ -649,7 +700,7 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
                     float pv[32];
 #pragma unroll
                     for (int k = 0; k < 32; k++) pv[k] = 0.f;
-                    const float2 *sp[kSlots], *yp[kSlots];
+                    const HT *sp[kSlots], *yp[kSlots];
 #pragma unroll
                     for (int k = 0; k < kSlots; k++) {
                         const int a = Gm.slot[k <= np ? k : 0];
@@ -658,15 +709,16 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
                     }
                     for (int i = tid; i < nmine; i += BT) {
                         const float2 gn = slice_sum(i, -4.f);
-                        const float2 yn = csub(gn, gs[i]);
+                        const HT yh = hist_store<HT>(csub(gn, gs[i]));
+                        const float2 yn = hist_load(yh);  // the stored pair, as the Gram scalars see it
                         gs[i] = gn;
-                        Yn[i] = yn;
-                        const float2 sn = Sn[i];
+                        Yn[i] = yh;
+                        const float2 sn = hist_load(Sn[i]);
 #pragma unroll
                         for (int k = 0; k < kSlots; k++) {
                             if (k <= np) {  // live pairs by age, then the new one (age np)
-                                const float2 sa = sp[k][i];
-                                const float2 ya = yp[k][i];
+                                const float2 sa = hist_load(sp[k][i]);
+                                const float2 ya = hist_load(yp[k][i]);
                                 pv[4 * k + 0] += cdotr(sa, yn);
                                 pv[4 * k + 1] += cdotr(ya, yn);
                                 pv[4 * k + 2] += cdotr(sa, gn);

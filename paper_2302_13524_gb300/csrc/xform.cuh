@@ -29,6 +29,9 @@
 // memory; dc is made once per thread in registers.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <stdint.h>
+
 #include "common.cuh"
 #include "fft.cuh"
 
@@ -142,6 +145,183 @@ struct XfBlue {
         conv(v, buf, cst, tid);
 #pragma unroll
         for (int e = 0; e < NE; e++) x[e] = valid(e, tid, n) ? cconj(cmul(v[e], dc[e])) : make_float2(0.f, 0.f);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// XfMixed<N>: N = 16^P (256, 4096).  The FP32 transforms of XfPow2<N>, plus a
+// tensor-core form of the same DFT (tc = true): P radix-16 Stockham passes
+// (the butterfly, twiddle and output placement of fft_pass with R = 16), each
+// 16-point DFT of a pass evaluated as a real GEMM on the tensor cores,
+//   [Re y; Im y] = [[C, sS]; [-sS, C]] [Re x; Im x],  C = cos(2 pi q r / 16),
+//   S = sin(2 pi q r / 16), s = +1 forward, -1 inverse,
+// with mma.sync m16n8k16 (BF16 operands, FP32 accumulation) on 8 butterflies
+// per instruction group.  Operands are split hi + lo (hi = bf16(v),
+// lo = bf16(v - hi)) and each product is A_hi B_lo + A_lo B_hi + A_hi B_hi
+// (the lo*lo term dropped): about 16 significant bits per product.
+// Twiddles are FP32 roots W_N^k from a table in shared memory.
+// Constants: [FP32 small twiddles | DFT fragments (6 tiles x 32 lanes x 4
+// words: C, S, -S, each hi and lo) | roots W_N^k, k < N].
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint4 &a, uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t *>(&v); }
+
+// (lo, hi) pair of values -> hi and lo split words
+__device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t &hi, uint32_t &lo)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - __low2float(h), b - __high2float(h));
+    hi = bf16x2_bits(h);
+    lo = bf16x2_bits(l);
+}
+
+enum { kTcC = 0, kTcS = 2, kTcNS = 4, kTcTiles = 6 };  // tile index: base + 0 (hi) or + 1 (lo)
+
+template <int N_>
+struct XfMixed {
+    static constexpr bool kBlue = false;
+    static constexpr bool kMixed = true;
+    static constexpr int kN = N_;
+    using F32 = XfPow2<N_>;
+    static constexpr int NT = F32::NT, NE = F32::NE;
+    static constexpr int LBUF = F32::LBUF;
+    static constexpr int NB = N_ / 16;  // butterflies per pass
+    static constexpr int P = ilog2c(N_) / 4;
+    static_assert(ipowc(16, P) == N_, "N must be a power of 16");
+    static constexpr int NWT = NT / 32;       // warps per team
+    static constexpr int GPW = NB / 8 / NWT;  // 8-butterfly groups per warp and pass
+    static_assert(GPW * 8 * NWT == NB && GPW >= 1, "group split");
+    static constexpr int OFF_FRAG = F32::NCONST;
+    static constexpr int FRAG_F2 = kTcTiles * 32 * 4 / 2;  // in float2 units
+    static constexpr int OFF_ROOT = OFF_FRAG + FRAG_F2;
+    static constexpr int NCONST = OFF_ROOT + N_;
+    __host__ __device__ static constexpr int shared_consts(int n) { return NCONST; }
+
+    F32 f32;
+    bool tc;
+
+    __device__ __forceinline__ static bool valid(int e, int tid, int n) { return true; }
+
+    __device__ __forceinline__ void setup(const float2 *__restrict__ mask, const float2 *__restrict__ chirp,
+                                          int n, int tid)
+    {
+        f32.setup(mask, chirp, n, tid);
+        tc = true;
+    }
+
+    template <int SIGN, int p>
+    __device__ __forceinline__ void tc_pass(float2 *buf, const float2 *cst, int tid) const
+    {
+        constexpr int Ns = ipowc(16, p);
+        const int lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
+        const uint4 *frag = reinterpret_cast<const uint4 *>(cst + OFF_FRAG);
+        const float2 *root = cst + OFF_ROOT;
+        const uint4 Ch = frag[(kTcC + 0) * 32 + lane], Cl = frag[(kTcC + 1) * 32 + lane];
+        // forward: Re y = C Re x + S Im x, Im y = C Im x - S Re x; inverse: S -> -S
+        const uint4 Ph = frag[((SIGN < 0 ? kTcS : kTcNS) + 0) * 32 + lane];
+        const uint4 Pl = frag[((SIGN < 0 ? kTcS : kTcNS) + 1) * 32 + lane];
+        const uint4 Qh = frag[((SIGN < 0 ? kTcNS : kTcS) + 0) * 32 + lane];
+        const uint4 Ql = frag[((SIGN < 0 ? kTcNS : kTcS) + 1) * 32 + lane];
+        float2 out[GPW][4];
+#pragma unroll
+        for (int gi = 0; gi < GPW; gi++) {
+            const int grp = warp * GPW + gi;
+            const int b = grp * 8 + g;
+            const int j = b & (Ns - 1);
+            float2 xin[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int r = 2 * t + (u & 1) + 8 * (u >> 1);
+                float2 v = buf[fft_pad(b + r * NB)];
+                if constexpr (Ns > 1) {
+                    float2 w = root[(r * j) * (N_ / (16 * Ns))];
+                    if constexpr (SIGN > 0) w.y = -w.y;
+                    v = cmul(v, w);
+                }
+                xin[u] = v;
+            }
+            uint32_t reh0, rel0, reh1, rel1, imh0, iml0, imh1, iml1;
+            split_bf16x2(xin[0].x, xin[1].x, reh0, rel0);
+            split_bf16x2(xin[2].x, xin[3].x, reh1, rel1);
+            split_bf16x2(xin[0].y, xin[1].y, imh0, iml0);
+            split_bf16x2(xin[2].y, xin[3].y, imh1, iml1);
+            float cre[4] = {0.f, 0.f, 0.f, 0.f}, cim[4] = {0.f, 0.f, 0.f, 0.f};
+            // small terms first, then the hi x hi products
+            mma_bf16_16816(cre, Ch, rel0, rel1);
+            mma_bf16_16816(cre, Cl, reh0, reh1);
+            mma_bf16_16816(cre, Ph, iml0, iml1);
+            mma_bf16_16816(cre, Pl, imh0, imh1);
+            mma_bf16_16816(cim, Ch, iml0, iml1);
+            mma_bf16_16816(cim, Cl, imh0, imh1);
+            mma_bf16_16816(cim, Qh, rel0, rel1);
+            mma_bf16_16816(cim, Ql, reh0, reh1);
+            mma_bf16_16816(cre, Ch, reh0, reh1);
+            mma_bf16_16816(cre, Ph, imh0, imh1);
+            mma_bf16_16816(cim, Ch, imh0, imh1);
+            mma_bf16_16816(cim, Qh, reh0, reh1);
+#pragma unroll
+            for (int u = 0; u < 4; u++) out[gi][u] = make_float2(cre[u], cim[u]);
+        }
+        __syncthreads();  // every input of the pass is read
+#pragma unroll
+        for (int gi = 0; gi < GPW; gi++) {
+            const int grp = warp * GPW + gi;
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int bb = grp * 8 + 2 * t + (u & 1);
+                const int q = g + 8 * (u >> 1);
+                const int jj = bb & (Ns - 1);
+                buf[fft_pad((bb - jj) * 16 + jj + q * Ns)] = out[gi][u];
+            }
+        }
+        __syncthreads();
+    }
+    template <int SIGN, int p>
+    __device__ __forceinline__ void tc_passes(float2 *buf, const float2 *cst, int tid) const
+    {
+        if constexpr (p < P) {
+            tc_pass<SIGN, p>(buf, cst, tid);
+            tc_passes<SIGN, p + 1>(buf, cst, tid);
+        }
+    }
+    // x (thread-strided) <- DFT_N^SIGN x through the tensor-core passes
+    template <int SIGN>
+    __device__ __forceinline__ void tc_transform(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid) const
+    {
+#pragma unroll
+        for (int e = 0; e < NE; e++) buf[fft_pad(tid + e * NT)] = x[e];
+        __syncthreads();
+        tc_passes<SIGN, 0>(buf, cst, tid);
+#pragma unroll
+        for (int e = 0; e < NE; e++) x[e] = buf[fft_pad(tid + e * NT)];
+        __syncthreads();
+    }
+    __device__ __forceinline__ void fwd(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid) const
+    {
+        if (!tc) {
+            f32.fwd(x, buf, cst, tid);
+            return;
+        }
+#pragma unroll
+        for (int e = 0; e < NE; e++) x[e] = cmul(x[e], f32.dm[e]);
+        tc_transform<-1>(x, buf, cst, tid);
+    }
+    __device__ __forceinline__ void adj(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid) const
+    {
+        if (!tc) {
+            f32.adj(x, buf, cst, tid);
+            return;
+        }
+        tc_transform<+1>(x, buf, cst, tid);
+#pragma unroll
+        for (int e = 0; e < NE; e++) x[e] = cmulc(x[e], f32.dm[e]);
     }
 };
 
