@@ -103,7 +103,8 @@ __device__ __forceinline__ void dft_small(float2 (&x)[R])
 }
 
 // One Stockham pass (see file comment).  buf: shared, fft_buf_len(N) float2.
-template <int N, int T, int R, int NS, int TWOFF, int SIGN, bool LAST>
+// TRAIL = false drops the barrier after the read-back (ping-pong buffers, below).
+template <int N, int T, int R, int NS, int TWOFF, int SIGN, bool LAST, bool TRAIL = true>
 __device__ __forceinline__ void fft_pass(float2 (&v)[N / T], float2 *buf, const float2 *tw, int tid)
 {
     constexpr int E = N / T, BPT = E / R;
@@ -137,7 +138,7 @@ __device__ __forceinline__ void fft_pass(float2 (&v)[N / T], float2 *buf, const 
         __syncthreads();
 #pragma unroll
         for (int e = 0; e < E; e++) v[e] = buf[fft_pad(tid + e * T)];
-        __syncthreads();
+        if constexpr (TRAIL) __syncthreads();
     }
 }
 
@@ -258,6 +259,42 @@ __device__ __forceinline__ void block_fft_rbx(float2 (&v)[N / T], float2 *buf, c
                                               const float2 (&wb)[N / T / R], int tid)
 {
     fft_passes_rbx<N, T, R, SIGN, 0>(v, buf, tw, wb, tid);
+}
+
+
+// ---------------------------------------------------------------------------
+// Ping-pong exchange: exchange k of a transform (k = 0 .. P-2) goes through
+// buffer (ph + k) & 1 of a pair, and the barrier after each read-back is
+// dropped: the next exchange writes the other buffer, and its own barrier
+// orders every read of this one before any later write to it.  ph carries the
+// alternation from one transform to the next (it flips when a transform has
+// an odd number of exchanges), so a transform's first write never lands in the
+// buffer that the previous transform read last.  Every thread of the block
+// must run the same sequence of transforms.  Last pass and twiddle bases as
+// in fft_passes_rbx.
+template <int N, int T, int R, int SIGN, int p>
+__device__ __forceinline__ void fft_passes_pp(float2 (&v)[N / T], float2 *b0, float2 *b1, const float2 *tw,
+                                              const float2 (&wb)[N / T / R], int tid)
+{
+    using Pl = FftPlan<N, N / T, R>;
+    if constexpr (p < Pl::P - 1) {
+        fft_pass<N, T, Pl::radix(p), Pl::ns(p), Pl::tw_off(p), SIGN, false, false>(v, (p & 1) ? b1 : b0, tw,
+                                                                                 tid);
+        fft_passes_pp<N, T, R, SIGN, p + 1>(v, b0, b1, tw, wb, tid);
+    } else if constexpr (p == Pl::P - 1) {
+        fft_passes_rbx<N, T, R, SIGN, p>(v, b0, tw, wb, tid);
+    }
+}
+
+// buf: two fft_buf_len(N) buffers back to back; ph: the pair's parity (0 or 1)
+template <int N, int T, int R, int SIGN>
+__device__ __forceinline__ void block_fft_pp(float2 (&v)[N / T], float2 *buf, const float2 *tw,
+                                             const float2 (&wb)[N / T / R], int tid, int &ph)
+{
+    using Pl = FftPlan<N, N / T, R>;
+    float2 *b0 = buf + (ph ? fft_buf_len(N) : 0), *b1 = buf + (ph ? 0 : fft_buf_len(N));
+    fft_passes_pp<N, T, R, SIGN, 0>(v, b0, b1, tw, wb, tid);
+    ph ^= (Pl::P - 1) & 1;
 }
 
 }  // namespace tmr

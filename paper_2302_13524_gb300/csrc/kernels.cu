@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(Xf::NT) k_forward(int N, const float2 *__restr
 {
     constexpr int NT = Xf::NT, E = Xf::NE;
     extern __shared__ float2 smem[];
-    float2 *buf = smem, *cst = smem + Xf::LBUF;
+    float2 *buf = smem, *cst = smem + Xf::BUFS * Xf::LBUF;
     const int tid = threadIdx.x, row = blockIdx.x, j = blockIdx.y;
     for (int i = tid; i < Xf::shared_consts(N); i += NT) cst[i] = cg[i];
     Xf xf;
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(Xf::NT) k_grad(int N, const float2 *__restrict
 {
     constexpr int NT = Xf::NT, E = Xf::NE;
     extern __shared__ float2 smem[];
-    float2 *buf = smem, *cst = smem + Xf::LBUF;
+    float2 *buf = smem, *cst = smem + Xf::BUFS * Xf::LBUF;
     __shared__ float red[NT / 32 > 0 ? NT / 32 : 1], fsum[1];
     const int tid = threadIdx.x, row = blockIdx.x;
     for (int i = tid; i < Xf::shared_consts(N); i += NT) cst[i] = cg[i];
@@ -307,6 +307,7 @@ __global__ void __launch_bounds__(Xf::NT) k_grad(int N, const float2 *__restrict
     for (int j = 0; j < J; j++) {
         Xf xf;
         xf.setup(masks + (size_t)j * N, cg + Xf::NCONST, N, tid);
+        __syncthreads();  // a fresh policy restarts the exchange-buffer alternation
         const float *y = Y + ((size_t)row * J + j) * N;
         float2 v[E];
 #pragma unroll
@@ -342,7 +343,7 @@ __global__ void __launch_bounds__(Xf::NT) k_fields(int N, const float2 *__restri
 {
     constexpr int NT = Xf::NT, E = Xf::NE;
     extern __shared__ float2 smem[];
-    float2 *buf = smem, *cst = smem + Xf::LBUF;
+    float2 *buf = smem, *cst = smem + Xf::BUFS * Xf::LBUF;
     const int tid = threadIdx.x, row = blockIdx.x, j = blockIdx.y;
     for (int i = tid; i < Xf::shared_consts(N); i += NT) cst[i] = cg[i];
     Xf xf;
@@ -392,7 +393,7 @@ __global__ void k_row_energy(int N, int M, const float2 *__restrict__ T, float *
 
 // ---------------------------------------------------------------------------
 template <class Xf>
-static size_t xf_kernel_smem(int N) { return sizeof(float2) * (Xf::LBUF + Xf::shared_consts(N)); }
+static size_t xf_kernel_smem(int N) { return sizeof(float2) * (Xf::BUFS * Xf::LBUF + Xf::shared_consts(N)); }
 
 cudaError_t launch_forward(int N, int M, int J, const float2 *T, const float2 *masks,
                            const float2 *tw, float *Y, cudaStream_t s, int prec)

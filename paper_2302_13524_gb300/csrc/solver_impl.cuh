@@ -95,7 +95,7 @@ struct Gram {
 // needed root is bracketed (expanding outwards from a point of known sign)
 // and found by Newton steps kept inside the bracket.  Ties go to the smallest
 // positive root.  c4 == 0 means w == 0: no step.
-static __device__ float quartic_argmin(const float *c)
+static __device__ float quartic_argmin_safe(const float *c)
 {
     const float c1 = c[1], c2 = c[2], c3 = c[3], c4 = c[4];
     if (!(c4 > 0.f)) {
@@ -180,6 +180,63 @@ static __device__ float quartic_argmin(const float *c)
         const float v = phi(cand[k]);
         if (v < bestv || (v == bestv && cand[k] > 0.f && (best <= 0.f || cand[k] < best))) {
             best = cand[k];
+            bestv = v;
+        }
+    }
+    return best;
+}
+
+// The same minimiser from the closed-form roots of the cubic phi'(a) = 0
+// (Cardano's formula for one real root, the trigonometric form for three),
+// each polished by Newton steps on phi' in FP32; among the real roots the one
+// with the smallest phi wins (ties: the smallest positive root).  Falls back
+// to the bracketing search when c4 <= 0 or a root comes out non-finite.
+static __device__ float quartic_argmin(const float *c)
+{
+    const float c1 = c[1], c2 = c[2], c3 = c[3], c4 = c[4];
+    if (!(c4 > 0.f)) return quartic_argmin_safe(c);
+    auto g = [&](float a) { return fmaf(fmaf(fmaf(4.f * c4, a, 3.f * c3), a, 2.f * c2), a, c1); };
+    auto dg = [&](float a) { return fmaf(fmaf(12.f * c4, a, 6.f * c3), a, 2.f * c2); };
+    auto phi = [&](float a) { return a * fmaf(fmaf(fmaf(c4, a, c3), a, c2), a, c1); };
+    // phi'(a) / (4 c4) = a^3 + B a^2 + C a + D; a = x - B/3 gives x^3 + p x + q
+    const float inv = 1.f / c4;
+    const float B3 = 0.25f * c3 * inv;  // B / 3
+    const float C = 0.5f * c2 * inv, D = 0.25f * c1 * inv;
+    const float p = fmaf(-3.f * B3, B3, C);
+    const float q = fmaf(B3, fmaf(2.f * B3, B3, -C), D);
+    const float hp = p * (1.f / 3.f), hq = 0.5f * q;
+    const float disc = fmaf(hq, hq, hp * hp * hp);
+    float cand[3];
+    int nc;
+    if (disc > 0.f) {
+        const float u = cbrtf(-hq - copysignf(sqrtf(disc), hq));
+        cand[0] = (u != 0.f ? u - hp / u : 0.f) - B3;
+        nc = 1;
+    } else {
+        const float r = sqrtf(fmaxf(-hp, 0.f));
+        const float r3 = r * r * r;
+        const float arg = r3 > 0.f ? fminf(fmaxf(-hq / r3, -1.f), 1.f) : 0.f;
+        const float th = acosf(arg) * (1.f / 3.f);
+        const float tr = 2.0943951023931955f;  // 2 pi / 3
+        cand[0] = 2.f * r * cosf(th) - B3;
+        cand[1] = 2.f * r * cosf(th - tr) - B3;
+        cand[2] = 2.f * r * cosf(th + tr) - B3;
+        nc = 3;
+    }
+    float best = 0.f, bestv = 0.f;
+    for (int k = 0; k < nc; k++) {
+        float a = cand[k];
+        for (int it = 0; it < 4; it++) {
+            const float d = dg(a);
+            if (!(d != 0.f)) break;
+            const float na = a - g(a) / d;
+            if (!isfinite(na) || na == a) break;
+            a = na;
+        }
+        if (!isfinite(a)) return quartic_argmin_safe(c);
+        const float v = phi(a);
+        if (k == 0 || v < bestv || (v == bestv && a > 0.f && (best <= 0.f || a < best))) {
+            best = a;
             bestv = v;
         }
     }
@@ -289,7 +346,8 @@ __host__ __device__ size_t solver_smem(int N, int J, int m)
     using C = SolverCfg<Xf, G>;
     const int JC = J / G;
     const size_t SL = (N + JC - 1) / JC;
-    size_t f2 = (size_t)G * Xf::LBUF /*X (team 0's exchange) and the others' exchange*/ + Xf::shared_consts(N) +
+    size_t f2 = (size_t)G * Xf::BUFS * Xf::LBUF /*X (team 0's first buffer) and the exchange buffers*/ +
+                Xf::shared_consts(N) +
                 (size_t)J * SL /*Y*/ + 2 * SL /*t, g*/ + (solver_mixed<Xf>() ? SL : 0) /*p*/;
     size_t bytes = f2 * sizeof(float2) + 2 * (size_t)(m + 1) * SL * sizeof(SolverHist<Xf>) /*pairs*/;
     bytes += sizeof(float) * ((size_t)kParts * C::NW + 2 * (size_t)JC * kParts);
@@ -323,8 +381,8 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
     // ---- shared memory ----
     float2 *X = reinterpret_cast<float2 *>(smem_raw);
     // exchange buffer of this team's FFTs: team 0 reuses X (free once gathered)
-    float2 *buf = X + (size_t)team * Xf::LBUF;
-    float2 *tws = X + (size_t)G * Xf::LBUF;
+    float2 *buf = X + (size_t)team * Xf::BUFS * Xf::LBUF;
+    float2 *tws = X + (size_t)G * Xf::BUFS * Xf::LBUF;
     const int NCS = Xf::shared_consts(N);
     float2 *Yr = tws + NCS;  // [J][SL]
     float2 *ts = Yr + (size_t)J * SL;

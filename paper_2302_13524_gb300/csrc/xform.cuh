@@ -43,12 +43,16 @@ struct XfPow2 {
     static constexpr int kN = N_;              // length fixed at compile time
     static constexpr int NT = fft_threads(N_);  // threads per team
     static constexpr int NE = N_ / NT;          // registers per length-N vector
-    static constexpr int LBUF = fft_buf_len(N_);  // exchange buffer per team (float2)
+    static constexpr int LBUF = fft_buf_len(N_);  // one exchange buffer (float2)
+    // exchange buffers per team: two (ping-pong, one barrier per exchange)
+    // where shared memory allows, else one (two barriers per exchange)
+    static constexpr int BUFS = N_ <= 2048 ? 2 : 1;
     static constexpr int NCONST = FftSmall<N_, NT>::TW_SMALL;  // constants before the chirp (float2)
     __host__ __device__ static constexpr int shared_consts(int n) { return NCONST; }
 
     float2 dm[NE];
-    float2 wb;
+    float2 wb[1];
+    int ph;  // ping-pong parity
 
     __device__ __forceinline__ static bool valid(int e, int tid, int n) { return true; }
 
@@ -59,17 +63,25 @@ struct XfPow2 {
         for (int e = 0; e < NE; e++) dm[e] = mask[tid + e * NT];
         double s, c;
         sincospi(-2.0 * (double)tid / (double)N_, &s, &c);
-        wb = make_float2((float)c, (float)s);
+        wb[0] = make_float2((float)c, (float)s);
+        ph = 0;
     }
-    __device__ __forceinline__ void fwd(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid) const
+    template <int SIGN>
+    __device__ __forceinline__ void fft(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid)
+    {
+        if constexpr (BUFS == 2) block_fft_pp<N_, NT, NE, SIGN>(x, buf, cst, wb, tid, ph);
+        else block_fft_rb<N_, NT, SIGN>(x, buf, cst, wb[0], tid);
+    }
+    // buf: BUFS * LBUF float2 of this team
+    __device__ __forceinline__ void fwd(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid)
     {
 #pragma unroll
         for (int e = 0; e < NE; e++) x[e] = cmul(x[e], dm[e]);
-        block_fft_rb<N_, NT, -1>(x, buf, cst, wb, tid);
+        fft<-1>(x, buf, cst, tid);
     }
-    __device__ __forceinline__ void adj(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid) const
+    __device__ __forceinline__ void adj(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid)
     {
-        block_fft_rb<N_, NT, +1>(x, buf, cst, wb, tid);
+        fft<+1>(x, buf, cst, tid);
 #pragma unroll
         for (int e = 0; e < NE; e++) x[e] = cmulc(x[e], dm[e]);
     }
@@ -85,6 +97,7 @@ struct XfBlue {
     static_assert(NE <= EL / 2, "N <= L / 2");
     using Plan = FftPlan<L_, EL, R>;
     static constexpr int LBUF = fft_buf_len(L_);
+    static constexpr int BUFS = 1;
     static constexpr int NCONST_TW = Plan::TW_SMALL;
     static constexpr int NCONST = NCONST_TW + L_ / 2 + 1;
     __host__ __device__ static constexpr int shared_consts(int n) { return NCONST + n; }
@@ -123,7 +136,7 @@ struct XfBlue {
         }
         block_fft_rbx<L_, NT, R, +1>(v, buf, cst, wb, tid);
     }
-    __device__ __forceinline__ void fwd(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid) const
+    __device__ __forceinline__ void fwd(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid)
     {
         float2 v[EL];
 #pragma unroll
@@ -134,7 +147,7 @@ struct XfBlue {
 #pragma unroll
         for (int e = 0; e < NE; e++) x[e] = valid(e, tid, n) ? cmul(v[e], c[tid + e * NT]) : make_float2(0.f, 0.f);
     }
-    __device__ __forceinline__ void adj(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid) const
+    __device__ __forceinline__ void adj(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid)
     {
         float2 v[EL];
         const float2 *c = cst + NCONST;
@@ -192,6 +205,7 @@ struct XfMixed {
     using F32 = XfPow2<N_>;
     static constexpr int NT = F32::NT, NE = F32::NE;
     static constexpr int LBUF = F32::LBUF;
+    static constexpr int BUFS = F32::BUFS;
     static constexpr int NB = N_ / 16;  // butterflies per pass
     static constexpr int P = ilog2c(N_) / 4;
     static_assert(ipowc(16, P) == N_, "N must be a power of 16");
@@ -292,9 +306,12 @@ struct XfMixed {
         }
     }
     // x (thread-strided) <- DFT_N^SIGN x through the tensor-core passes
+    // works in the buffer the FP32 transforms would write next (every pass
+    // ends with a barrier, so the ping-pong parity stays as it is)
     template <int SIGN>
-    __device__ __forceinline__ void tc_transform(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid) const
+    __device__ __forceinline__ void tc_transform(float2 (&x)[NE], float2 *buf0, const float2 *cst, int tid) const
     {
+        float2 *buf = buf0 + (BUFS == 2 && f32.ph ? LBUF : 0);
 #pragma unroll
         for (int e = 0; e < NE; e++) buf[fft_pad(tid + e * NT)] = x[e];
         __syncthreads();
@@ -303,7 +320,7 @@ struct XfMixed {
         for (int e = 0; e < NE; e++) x[e] = buf[fft_pad(tid + e * NT)];
         __syncthreads();
     }
-    __device__ __forceinline__ void fwd(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid) const
+    __device__ __forceinline__ void fwd(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid)
     {
         if (!tc) {
             f32.fwd(x, buf, cst, tid);
@@ -313,7 +330,7 @@ struct XfMixed {
         for (int e = 0; e < NE; e++) x[e] = cmul(x[e], f32.dm[e]);
         tc_transform<-1>(x, buf, cst, tid);
     }
-    __device__ __forceinline__ void adj(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid) const
+    __device__ __forceinline__ void adj(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid)
     {
         if (!tc) {
             f32.adj(x, buf, cst, tid);
