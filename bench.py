@@ -338,8 +338,15 @@ def main():
     flops = solver_flops(N, J, m, its, args.power_iters)
     achieved = flops / (solver_ms / 1e3) / 1e12
     peak_max = fp32_peak_tflops(n_sm, 2070.0)
+    # DRAM bytes of one solver launch from an ncu capture of the plain workload
+    # at 4096 rows (138.8 MB read + 43.4 MB written), scaled by the rows
+    traffic = None
+    if args.workload == "plain" and args.precision == "fp32":
+        traffic = (138.755072e6 + 43.423232e6) * M / 4096
     roof = {"bound": "alu", "kernel": f"k_solver (N={N})", "achieved": achieved, "peak": peak_max,
-            "unit": "TFLOP/s", "frac": achieved / peak_max, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved / peak_max, "traffic": traffic,
+            "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 4096-row "
+                             "launch of this kernel, scaled to M rows" if traffic else None,
             "peak_basis": f"FP32 FFMA {n_sm} SMs x 128 lanes x 2 x 2070 MHz (max clock)",
             "solver_ms": solver_ms, "flops_per_launch": flops}
     if clk and clk.get("sm_mhz"):
