@@ -508,8 +508,12 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
             TRY(autotune(h, smem_optin, &G));
             std::lock_guard<std::mutex> lk(g_tune_mu);
             g_tune_mem[key] = G;
-            if (o.tune_cache && G > 0) {
-                auto fm = read_tune_file(o.tune_cache);
+        }
+        if (o.tune_cache && G > 0) {  // the file records the choice, also one made earlier in this process
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto fm = read_tune_file(o.tune_cache);
+            auto f = fm.find(key);
+            if (f == fm.end() || f->second != G) {
                 fm[key] = G;
                 write_tune_file(o.tune_cache, fm);
             }

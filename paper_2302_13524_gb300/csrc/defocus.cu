@@ -61,12 +61,13 @@ __device__ void make_tw(float2 *tw, int n)
 
 __device__ void fft2_inplace(float2 *g, int ny, int nx, int sign, const float2 *twy, const float2 *twx)
 {
+    // ny, nx powers of two: every index below is a shift or a mask
     const int pitch = nx + 1;
     const int lx = __ffs(nx) - 1, ly = __ffs(ny) - 1;
     const int tid = threadIdx.x, nt = blockDim.x;
     // rows: bit reversal
     for (int i = tid; i < ny * nx; i += nt) {
-        const int a = i / nx, b = i % nx;
+        const int a = i >> lx, b = i & (nx - 1);
         const int rb = (int)bitrev((unsigned)b, lx);
         if (rb > b) {
             const float2 t = g[a * pitch + b];
@@ -75,13 +76,13 @@ __device__ void fft2_inplace(float2 *g, int ny, int nx, int sign, const float2 *
         }
     }
     __syncthreads();
-    for (int half = 1; half < nx; half <<= 1) {
-        const int step = nx / (2 * half);
+    for (int lh = 0; lh < lx; lh++) {
+        const int half = 1 << lh;
         for (int i = tid; i < ny * (nx / 2); i += nt) {
-            const int a = i / (nx / 2), q = i % (nx / 2);
-            const int grp = q / half, k = q % half;
-            const int b0 = grp * 2 * half + k, b1 = b0 + half;
-            float2 w = twx[k * step];
+            const int a = i >> (lx - 1), q = i & (nx / 2 - 1);
+            const int k = q & (half - 1);
+            const int b0 = ((q >> lh) << (lh + 1)) + k, b1 = b0 + half;
+            float2 w = twx[k << (lx - 1 - lh)];
             if (sign > 0) w.y = -w.y;
             const float2 x0 = g[a * pitch + b0], x1 = cmul(g[a * pitch + b1], w);
             g[a * pitch + b0] = cadd(x0, x1);
@@ -91,7 +92,7 @@ __device__ void fft2_inplace(float2 *g, int ny, int nx, int sign, const float2 *
     }
     // columns
     for (int i = tid; i < ny * nx; i += nt) {
-        const int a = i / nx, b = i % nx;
+        const int a = i >> lx, b = i & (nx - 1);
         const int ra = (int)bitrev((unsigned)a, ly);
         if (ra > a) {
             const float2 t = g[a * pitch + b];
@@ -100,13 +101,13 @@ __device__ void fft2_inplace(float2 *g, int ny, int nx, int sign, const float2 *
         }
     }
     __syncthreads();
-    for (int half = 1; half < ny; half <<= 1) {
-        const int step = ny / (2 * half);
+    for (int lh = 0; lh < ly; lh++) {
+        const int half = 1 << lh;
         for (int i = tid; i < (ny / 2) * nx; i += nt) {
-            const int q = i / nx, b = i % nx;
-            const int grp = q / half, k = q % half;
-            const int a0 = grp * 2 * half + k, a1 = a0 + half;
-            float2 w = twy[k * step];
+            const int q = i >> lx, b = i & (nx - 1);
+            const int k = q & (half - 1);
+            const int a0 = ((q >> lh) << (lh + 1)) + k, a1 = a0 + half;
+            float2 w = twy[k << (ly - 1 - lh)];
             if (sign > 0) w.y = -w.y;
             const float2 x0 = g[a0 * pitch + b], x1 = cmul(g[a1 * pitch + b], w);
             g[a0 * pitch + b] = cadd(x0, x1);
@@ -120,11 +121,11 @@ __device__ void fft2_inplace(float2 *g, int ny, int nx, int sign, const float2 *
 __device__ void defocus_apply_smem(float2 *g, int ny, int nx, const float2 *__restrict__ H,
                                    bool adjoint, const float2 *twy, const float2 *twx)
 {
-    const int pitch = nx + 1, P = ny * nx;
+    const int pitch = nx + 1, P = ny * nx, lx = __ffs(nx) - 1;
     fft2_inplace(g, ny, nx, -1, twy, twx);
     const float inv = 1.0f / (float)P;
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        const int a = i / nx, b = i % nx;
+        const int a = i >> lx, b = i & (nx - 1);
         float2 h = H[i];
         if (adjoint) h.y = -h.y;
         g[a * pitch + b] = cscale(cmul(g[a * pitch + b], h), inv);
@@ -189,14 +190,16 @@ __device__ bool grid_sync(unsigned *bar, int *err)
             __threadfence();
             atomicAdd(bar + 1, 1u);
         } else {
+            // poll tightly at first (the other CTAs usually arrive within
+            // microseconds), then back off; give up after about a second
             long long spins = 0;
             while (*vgen == gen) {
                 if (*verr) break;
-                if (++spins > (1LL << 24)) {  // ~1 s at 64 ns a poll, then give up
+                if (++spins > (1LL << 24)) {
                     atomicExch(err, 1);
                     break;
                 }
-                __nanosleep(64);
+                if (spins > 4096) __nanosleep(64);
             }
         }
         __threadfence();
@@ -303,7 +306,8 @@ __device__ void pf_coefficients(PFGram &G)
 __device__ void pf_eval(const PhaseFitParams &Pp, const PFWork &W, float2 *g, const float2 *twy,
                         const float2 *twx, double *red, double *out)
 {
-    const int ny = Pp.ny, nx = Pp.nx, P = ny * nx, pitch = nx + 1;
+    const int ny = Pp.ny, nx = Pp.nx, P = ny * nx, pitch = nx + 1, lx = __ffs(nx) - 1;
+    auto at = [&](int k) { return (k >> lx) * pitch + (k & (nx - 1)); };
     float *part = W.part + (size_t)blockIdx.x * P;
     for (int k = threadIdx.x; k < P; k += blockDim.x) part[k] = 0.f;
     double fl = 0.0;
@@ -311,12 +315,12 @@ __device__ void pf_eval(const PhaseFitParams &Pp, const PFWork &W, float2 *g, co
         const float2 *cn = Pp.Zd + (size_t)n * P;
         const float *In = Pp.Ydef + (size_t)n * P;
         for (int k = threadIdx.x; k < P; k += blockDim.x)
-            g[(k / nx) * pitch + k % nx] = cmul(cn[k], __ldcg(W.u + k));
+            g[at(k)] = cmul(cn[k], __ldcg(W.u + k));
         __syncthreads();
         defocus_apply_smem(g, ny, nx, Pp.H, false, twy, twx);
         float fpl = 0.f;
         for (int k = threadIdx.x; k < P; k += blockDim.x) {
-            const int gi = (k / nx) * pitch + k % nx;
+            const int gi = at(k);
             const float2 w = g[gi];
             const float Gv = In[k] - cabs2(w);
             fpl = fmaf(Gv, Gv, fpl);
@@ -326,7 +330,7 @@ __device__ void pf_eval(const PhaseFitParams &Pp, const PFWork &W, float2 *g, co
         __syncthreads();
         defocus_apply_smem(g, ny, nx, Pp.H, true, twy, twx);
         for (int k = threadIdx.x; k < P; k += blockDim.x) {
-            const float2 v = cmulc(g[(k / nx) * pitch + k % nx], cn[k]);  // conj(c_n) D^H(w G)
+            const float2 v = cmulc(g[at(k)], cn[k]);  // conj(c_n) D^H(w G)
             const float2 cu = __ldcg(W.u + k);
             part[k] += -4.f * fmaf(cu.x, v.y, -cu.y * v.x);  // -4 Im(conj(u) v)
         }
