@@ -352,11 +352,14 @@ def main():
     if clk and clk.get("sm_mhz"):
         roof["frac_at_measured_clock"] = achieved / fp32_peak_tflops(n_sm, clk["sm_mhz"])
     if args.precision == "mixed":
-        # tensor-pipe work of the split-BF16 DFT stages: per transform, log16 N
-        # passes x N/128 groups x 12 mma.m16n8k16 (4096 flops each); the power
-        # iterations, the start and all but the last 10 iterations use them
-        passes = int(round(math.log(N, 16)))
-        per_transform = passes * (N // 128) * 12 * 4096
+        # tensor-pipe work of the split-BF16 DFT stages: per transform, A
+        # radix-16 passes of N/128 groups x 12 mma.m16n8k16 and B radix-8 passes
+        # of N/64 groups x 3 (4096 flops each), N = 16^A 8^B with A largest; the
+        # power iterations, the start and all but the last 10 iterations use them
+        lg = int(round(math.log2(N)))
+        a16 = (3 if lg >= 12 else 0) if lg % 3 == 0 else (1 if lg % 3 == 1 else 2)
+        b8 = (lg - 4 * a16) // 3
+        per_transform = (a16 * (N // 128) * 12 + b8 * (N // 64) * 3) * 4096
         tc_iters = np.maximum(its - 10, 0) if args.iters > 10 else np.zeros_like(its)
         n_tr = 2 * J * (M * (args.power_iters + 1) + float(np.sum(tc_iters)))
         tc = per_transform * n_tr / (solver_ms / 1e3) / 1e12

@@ -78,13 +78,13 @@ enum {
 
 /* Arithmetic of tmr_retrieve (and of tmr_forward / tmr_grad on the handle).
  * TMR_PREC_FP32: FP32 FFTs, FP32 intensities and L-BFGS pairs.
- * TMR_PREC_MIXED (N = 256 or 4096 only; not an arithmetic of the paper, which
- * works in double precision): intensities stored as FP16 after dividing
- * each row by its largest |y| (the handle packs them, M*J*N*2 bytes); L-BFGS
- * pairs stored as BF16 (the iterate, gradient and direction stay FP32); each
- * length-N DFT as radix-16 passes whose 16-point DFTs run on the tensor cores
- * as split BF16 (hi + lo) GEMMs with FP32 accumulation, about 1e-5 relative
- * error per transform; the last 10 L-BFGS iterations (when iters > 10) go
+ * TMR_PREC_MIXED (N = 256, 1024, 2048 or 4096; not an arithmetic of the
+ * paper, which works in double precision): intensities stored as FP16 after
+ * dividing each row by its largest |y| (the handle packs them, M*J*N*2
+ * bytes); L-BFGS pairs stored as BF16 (the iterate, gradient and direction
+ * stay FP32); each length-N DFT as radix-16 and radix-8 passes whose small
+ * DFTs run on the tensor cores as split BF16 (hi + lo) GEMMs with FP32
+ * accumulation, about 1e-5 relative error per transform; the last 10 L-BFGS iterations (when iters > 10) go
  * back to FP32 transforms after a fresh FP32 evaluation of f and g at the
  * current iterate, which restarts the history.  The phase-offset fit is FP64
  * either way. */

@@ -387,9 +387,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     if (o.precision != TMR_PREC_FP32 && o.precision != TMR_PREC_MIXED)
         return fail(TMR_ERR_INVALID_ARG, "opt.precision must be TMR_PREC_FP32 or TMR_PREC_MIXED");
     if (o.precision == TMR_PREC_MIXED && !mixed_supported(N))
-        return fail(TMR_ERR_UNSUPPORTED, "TMR_PREC_MIXED needs N = 256 or 4096 (a power of 16)");
-    if (o.precision == TMR_PREC_MIXED && o.init == TMR_INIT_LEARNED)
-        return fail(TMR_ERR_UNSUPPORTED, "TMR_PREC_MIXED does not take the learned start");
+        return fail(TMR_ERR_UNSUPPORTED, "TMR_PREC_MIXED needs N = 256, 1024, 2048 or 4096");
     if (!xform_supported(N))
         return fail(TMR_ERR_UNSUPPORTED, "N must be a power of two in 64..4096 or another length in 16..4096");
     if (J > kMaxMasks) return fail(TMR_ERR_UNSUPPORTED, "J must be at most 8");

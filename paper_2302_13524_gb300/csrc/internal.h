@@ -25,8 +25,8 @@ bool xform_supported(int N);
 // thread (the instantiated variant); false when N has none.
 bool xform_blue_shape(int N, int *L, int *ne);
 int xform_table(int N, float2 *out);  // length in float2; writes when out != NULL
-// Mixed precision (TMR_PREC_MIXED): N a power of 16 (256, 4096); its table is
-// [FP32 twiddles | tensor-core DFT fragments | roots W_N^k].
+// Mixed precision (TMR_PREC_MIXED): N = 256, 1024, 2048 or 4096; its table is
+// [FP32 twiddles | tensor-core DFT fragments (radix 16, radix 8) | roots W_N^k].
 bool mixed_supported(int N);
 int xform_table_prec(int N, int prec, float2 *out);
 

@@ -154,7 +154,7 @@ int xform_table(int N, float2 *out)
     }
 }
 
-bool mixed_supported(int N) { return N == 256 || N == 4096; }
+bool mixed_supported(int N) { return N == 256 || N == 1024 || N == 2048 || N == 4096; }
 
 // Round to the nearest BF16 (ties to even); returns the bits.
 static uint16_t host_bf16(float v)
@@ -173,6 +173,27 @@ static float host_bf16_value(uint16_t b)
     return v;
 }
 
+// m16n8k16 A fragments of a 16 x 16 tile given element by element: word w of
+// lane (g, t) holds rows g + 8 (w & 1), columns 2t + 8 (w >> 1) + {0, 1}, the
+// lower column in the low half; part 0 = hi, 1 = lo of the BF16 split.
+template <class F>
+static void write_frag(uint32_t *dst, int part, F &&elem)
+{
+    for (int lane = 0; lane < 32; lane++) {
+        const int g = lane >> 2, t = lane & 3;
+        for (int w = 0; w < 4; w++) {
+            uint32_t word = 0;
+            for (int h = 0; h < 2; h++) {
+                const double v = elem(g + 8 * (w & 1), 2 * t + 8 * (w >> 1) + h);
+                const uint16_t hi = host_bf16((float)v);
+                const uint16_t lo = host_bf16((float)(v - (double)host_bf16_value(hi)));
+                word |= (uint32_t)(part == 0 ? hi : lo) << (16 * h);
+            }
+            dst[lane * 4 + w] = word;
+        }
+    }
+}
+
 template <int N>
 static int mixed_table(float2 *out)
 {
@@ -180,28 +201,30 @@ static int mixed_table(float2 *out)
     if (!out) return X::NCONST;
     std::vector<float2> full(fft_table_len(N));
     fft_table(N, full.data());
-    for (int i = 0; i < X::OFF_FRAG; i++) out[i] = full[i];
-    // 16-point DFT blocks (row q = output, column r = input) as m16n8k16 A
-    // fragments: word w of lane (g, t) holds rows g + 8 (w & 1), columns
-    // 2t + 8 (w >> 1) + {0, 1}, the lower column in the low half
-    uint32_t *frag = reinterpret_cast<uint32_t *>(out + X::OFF_FRAG);
-    for (int tile = 0; tile < kTcTiles; tile++) {
-        const int kind = tile / 2, part = tile % 2;  // kind 0 C, 1 S, 2 -S; part 0 hi, 1 lo
-        for (int lane = 0; lane < 32; lane++) {
-            const int g = lane >> 2, t = lane & 3;
-            for (int w = 0; w < 4; w++) {
-                uint32_t word = 0;
-                for (int h = 0; h < 2; h++) {
-                    const int q = g + 8 * (w & 1), r = 2 * t + 8 * (w >> 1) + h;
-                    const double a = 2.0 * M_PI * (double)((q * r) % 16) / 16.0;
-                    const double v = kind == 0 ? std::cos(a) : (kind == 1 ? std::sin(a) : -std::sin(a));
-                    const uint16_t hi = host_bf16((float)v);
-                    const uint16_t lo = host_bf16((float)(v - (double)host_bf16_value(hi)));
-                    word |= (uint32_t)(part == 0 ? hi : lo) << (16 * h);
-                }
-                frag[(tile * 32 + lane) * 4 + w] = word;
-            }
-        }
+    for (int i = 0; i < X::OFF_FRAG16; i++) out[i] = full[i];
+    auto cs = [](int q, int r, int R, bool sine) {
+        const double a = 2.0 * M_PI * (double)((q * r) % R) / (double)R;
+        return sine ? std::sin(a) : std::cos(a);
+    };
+    // radix 16: blocks C, S, -S of the 16-point DFT (row q = output, column r = input)
+    uint32_t *f16 = reinterpret_cast<uint32_t *>(out + X::OFF_FRAG16);
+    for (int tile = 0; tile < kTcTiles16; tile++) {
+        const int kind = tile / 2;  // 0 C, 1 S, 2 -S
+        write_frag(f16 + tile * 128, tile % 2, [&](int q, int r) {
+            return kind == 0 ? cs(q, r, 16, false) : (kind == 1 ? cs(q, r, 16, true) : -cs(q, r, 16, true));
+        });
+    }
+    // radix 8: the whole real form [[C, sS], [-sS, C]] (s = +1 forward, -1 inverse),
+    // rows 0-7 Re y_q, 8-15 Im y_q; columns 0-7 Re x_r, 8-15 Im x_r
+    uint32_t *f8 = reinterpret_cast<uint32_t *>(out + X::OFF_FRAG8);
+    for (int tile = 0; tile < kTcTiles8; tile++) {
+        const double sgn = tile / 2 == 0 ? 1.0 : -1.0;
+        write_frag(f8 + tile * 128, tile % 2, [&](int row, int col) {
+            const int q = row & 7, r = col & 7;
+            const bool re_out = row < 8, re_in = col < 8;
+            if (re_out == re_in) return cs(q, r, 8, false);
+            return (re_out ? sgn : -sgn) * cs(q, r, 8, true);
+        });
     }
     for (int k = 0; k < N; k++) {
         const double a = -2.0 * M_PI * (double)k / (double)N;
@@ -213,9 +236,13 @@ static int mixed_table(float2 *out)
 int xform_table_prec(int N, int prec, float2 *out)
 {
     if (prec == 0) return xform_table(N, out);
-    if (N == 256) return mixed_table<256>(out);
-    if (N == 4096) return mixed_table<4096>(out);
-    return -1;
+    switch (N) {
+    case 256: return mixed_table<256>(out);
+    case 1024: return mixed_table<1024>(out);
+    case 2048: return mixed_table<2048>(out);
+    case 4096: return mixed_table<4096>(out);
+    default: return -1;
+    }
 }
 
 // Calls f(Xf{}) with the transform policy of length N and precision prec.
@@ -223,9 +250,13 @@ template <class F>
 static cudaError_t dispatch_xf(int N, int prec, F &&f)
 {
     if (prec != 0) {
-        if (N == 256) return f(XfMixed<256>{});
-        if (N == 4096) return f(XfMixed<4096>{});
-        return cudaErrorInvalidValue;
+        switch (N) {
+        case 256: return f(XfMixed<256>{});
+        case 1024: return f(XfMixed<1024>{});
+        case 2048: return f(XfMixed<2048>{});
+        case 4096: return f(XfMixed<4096>{});
+        default: return cudaErrorInvalidValue;
+        }
     }
     switch (N) {
     case 64: return f(XfPow2<64>{});

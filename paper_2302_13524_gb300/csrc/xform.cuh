@@ -162,19 +162,22 @@ struct XfBlue {
 };
 
 // ---------------------------------------------------------------------------
-// XfMixed<N>: N = 16^P (256, 4096).  The FP32 transforms of XfPow2<N>, plus a
-// tensor-core form of the same DFT (tc = true): P radix-16 Stockham passes
-// (the butterfly, twiddle and output placement of fft_pass with R = 16), each
-// 16-point DFT of a pass evaluated as a real GEMM on the tensor cores,
-//   [Re y; Im y] = [[C, sS]; [-sS, C]] [Re x; Im x],  C = cos(2 pi q r / 16),
-//   S = sin(2 pi q r / 16), s = +1 forward, -1 inverse,
+// XfMixed<N>: N a power of two, 64 <= N <= 4096, written N = 16^A 8^B with A
+// as large as possible.  The FP32 transforms of XfPow2<N>, plus a tensor-core
+// form of the same DFT (tc = true): A radix-16 then B radix-8 Stockham passes
+// (the butterfly, twiddle and output placement of fft_pass), each R-point DFT
+// of a pass evaluated as a real GEMM on the tensor cores,
+//   [Re y; Im y] = [[C, sS]; [-sS, C]] [Re x; Im x],  C = cos(2 pi q r / R),
+//   S = sin(2 pi q r / R), s = +1 forward, -1 inverse,
 // with mma.sync m16n8k16 (BF16 operands, FP32 accumulation) on 8 butterflies
-// per instruction group.  Operands are split hi + lo (hi = bf16(v),
+// per instruction group: for R = 16 the 32 x 32 block takes 2 x 2 tiles
+// (12 instructions with the split below), for R = 8 the 16 x 16 block is one
+// tile (3 instructions).  Operands are split hi + lo (hi = bf16(v),
 // lo = bf16(v - hi)) and each product is A_hi B_lo + A_lo B_hi + A_hi B_hi
 // (the lo*lo term dropped): about 16 significant bits per product.
 // Twiddles are FP32 roots W_N^k from a table in shared memory.
-// Constants: [FP32 small twiddles | DFT fragments (6 tiles x 32 lanes x 4
-// words: C, S, -S, each hi and lo) | roots W_N^k, k < N].
+// Constants: [FP32 small twiddles | radix-16 fragments (C, S, -S; hi, lo) |
+// radix-8 fragments (forward and inverse blocks; hi, lo) | roots W_N^k].
 __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint4 &a, uint32_t b0, uint32_t b1)
 {
     asm volatile(
@@ -195,7 +198,12 @@ __device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t &hi, uin
     lo = bf16x2_bits(l);
 }
 
-enum { kTcC = 0, kTcS = 2, kTcNS = 4, kTcTiles = 6 };  // tile index: base + 0 (hi) or + 1 (lo)
+// fragment tiles: radix 16: C, S, -S (hi at even, lo at odd index); radix 8:
+// forward block then inverse block (hi, lo)
+enum { kTcC = 0, kTcS = 2, kTcNS = 4, kTcTiles16 = 6, kTc8Fwd = 0, kTc8Inv = 2, kTcTiles8 = 4 };
+
+// radix-16 passes of N = 2^lg written 16^A 8^B with A largest
+__host__ __device__ constexpr int mixed_a16(int lg) { return lg % 3 == 0 ? (lg >= 12 ? 3 : 0) : (lg % 3 == 1 ? 1 : 2); }
 
 template <int N_>
 struct XfMixed {
@@ -206,17 +214,19 @@ struct XfMixed {
     static constexpr int NT = F32::NT, NE = F32::NE;
     static constexpr int LBUF = F32::LBUF;
     static constexpr int BUFS = F32::BUFS;
-    static constexpr int NB = N_ / 16;  // butterflies per pass
-    static constexpr int P = ilog2c(N_) / 4;
-    static_assert(ipowc(16, P) == N_, "N must be a power of 16");
-    static constexpr int NWT = NT / 32;       // warps per team
-    static constexpr int GPW = NB / 8 / NWT;  // 8-butterfly groups per warp and pass
-    static_assert(GPW * 8 * NWT == NB && GPW >= 1, "group split");
-    static constexpr int OFF_FRAG = F32::NCONST;
-    static constexpr int FRAG_F2 = kTcTiles * 32 * 4 / 2;  // in float2 units
-    static constexpr int OFF_ROOT = OFF_FRAG + FRAG_F2;
+    static constexpr int LG = ilog2c(N_);
+    static constexpr int A16 = mixed_a16(LG);     // radix-16 passes
+    static constexpr int B8 = (LG - 4 * A16) / 3;  // radix-8 passes
+    static_assert(4 * A16 + 3 * B8 == LG && A16 >= 0 && B8 >= 0, "N = 16^A 8^B");
+    static constexpr int P = A16 + B8;
+    static constexpr int NWT = NT / 32;  // warps per team
+    static constexpr int OFF_FRAG16 = F32::NCONST;
+    static constexpr int OFF_FRAG8 = OFF_FRAG16 + kTcTiles16 * 32 * 4 / 2;  // in float2 units
+    static constexpr int OFF_ROOT = OFF_FRAG8 + kTcTiles8 * 32 * 4 / 2;
     static constexpr int NCONST = OFF_ROOT + N_;
     __host__ __device__ static constexpr int shared_consts(int n) { return NCONST; }
+    __host__ __device__ static constexpr int radix(int p) { return p < A16 ? 16 : 8; }
+    __host__ __device__ static constexpr int ns(int p) { return p <= 0 ? 1 : ns(p - 1) * radix(p - 1); }
 
     F32 f32;
     bool tc;
@@ -230,12 +240,16 @@ struct XfMixed {
         tc = true;
     }
 
+    // one radix-16 pass: 8-butterfly groups, lane (g, t) loads inputs
+    // r = 2t, 2t+1, 2t+8, 2t+9 of butterfly g and ends with outputs
+    // q = g, g+8 of butterflies 2t, 2t+1
     template <int SIGN, int p>
-    __device__ __forceinline__ void tc_pass(float2 *buf, const float2 *cst, int tid) const
+    __device__ __forceinline__ void tc_pass16(float2 *buf, const float2 *cst, int tid) const
     {
-        constexpr int Ns = ipowc(16, p);
+        constexpr int Ns = ns(p), NB = N_ / 16, GPW = NB / 8 / NWT;
+        static_assert(GPW * 8 * NWT == NB && GPW >= 1, "group split");
         const int lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
-        const uint4 *frag = reinterpret_cast<const uint4 *>(cst + OFF_FRAG);
+        const uint4 *frag = reinterpret_cast<const uint4 *>(cst + OFF_FRAG16);
         const float2 *root = cst + OFF_ROOT;
         const uint4 Ch = frag[(kTcC + 0) * 32 + lane], Cl = frag[(kTcC + 1) * 32 + lane];
         // forward: Re y = C Re x + S Im x, Im y = C Im x - S Re x; inverse: S -> -S
@@ -297,17 +311,72 @@ struct XfMixed {
         }
         __syncthreads();
     }
+    // one radix-8 pass: lane (g, t) loads inputs r = 2t, 2t+1 of butterfly g
+    // and ends with output q = g of butterflies 2t, 2t+1
+    template <int SIGN, int p>
+    __device__ __forceinline__ void tc_pass8(float2 *buf, const float2 *cst, int tid) const
+    {
+        constexpr int Ns = ns(p), NB = N_ / 8, GPW = NB / 8 / NWT;
+        static_assert(GPW * 8 * NWT == NB && GPW >= 1, "group split");
+        const int lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
+        const uint4 *frag = reinterpret_cast<const uint4 *>(cst + OFF_FRAG8);
+        const float2 *root = cst + OFF_ROOT;
+        constexpr int base = SIGN < 0 ? kTc8Fwd : kTc8Inv;
+        const uint4 Ah = frag[(base + 0) * 32 + lane], Al = frag[(base + 1) * 32 + lane];
+        float2 out[GPW][2];
+#pragma unroll
+        for (int gi = 0; gi < GPW; gi++) {
+            const int grp = warp * GPW + gi;
+            const int b = grp * 8 + g;
+            const int j = b & (Ns - 1);
+            float2 xin[2];
+#pragma unroll
+            for (int u = 0; u < 2; u++) {
+                const int r = 2 * t + u;
+                float2 v = buf[fft_pad(b + r * NB)];
+                if constexpr (Ns > 1) {
+                    float2 w = root[(r * j) * (N_ / (8 * Ns))];
+                    if constexpr (SIGN > 0) w.y = -w.y;
+                    v = cmul(v, w);
+                }
+                xin[u] = v;
+            }
+            uint32_t reh, rel, imh, iml;
+            split_bf16x2(xin[0].x, xin[1].x, reh, rel);  // rows 2t, 2t+1: Re of inputs 2t, 2t+1
+            split_bf16x2(xin[0].y, xin[1].y, imh, iml);  // rows 2t+8, 2t+9: their Im
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+            mma_bf16_16816(d, Ah, rel, iml);
+            mma_bf16_16816(d, Al, reh, imh);
+            mma_bf16_16816(d, Ah, reh, imh);
+            // rows g (Re y_g) and g + 8 (Im y_g), columns 2t, 2t+1
+            out[gi][0] = make_float2(d[0], d[2]);
+            out[gi][1] = make_float2(d[1], d[3]);
+        }
+        __syncthreads();  // every input of the pass is read
+#pragma unroll
+        for (int gi = 0; gi < GPW; gi++) {
+            const int grp = warp * GPW + gi;
+#pragma unroll
+            for (int u = 0; u < 2; u++) {
+                const int bb = grp * 8 + 2 * t + u;
+                const int jj = bb & (Ns - 1);
+                buf[fft_pad((bb - jj) * 8 + jj + g * Ns)] = out[gi][u];
+            }
+        }
+        __syncthreads();
+    }
     template <int SIGN, int p>
     __device__ __forceinline__ void tc_passes(float2 *buf, const float2 *cst, int tid) const
     {
         if constexpr (p < P) {
-            tc_pass<SIGN, p>(buf, cst, tid);
+            if constexpr (radix(p) == 16) tc_pass16<SIGN, p>(buf, cst, tid);
+            else tc_pass8<SIGN, p>(buf, cst, tid);
             tc_passes<SIGN, p + 1>(buf, cst, tid);
         }
     }
-    // x (thread-strided) <- DFT_N^SIGN x through the tensor-core passes
-    // works in the buffer the FP32 transforms would write next (every pass
-    // ends with a barrier, so the ping-pong parity stays as it is)
+    // x (thread-strided) <- DFT_N^SIGN x through the tensor-core passes; works
+    // in the buffer the FP32 transforms would write next (every pass ends with
+    // a barrier, so the ping-pong parity stays as it is)
     template <int SIGN>
     __device__ __forceinline__ void tc_transform(float2 (&x)[NE], float2 *buf0, const float2 *cst, int tid) const
     {
