@@ -85,9 +85,31 @@ def train(model: tmr.MLP, X: torch.Tensor, Tt: torch.Tensor, epochs: int, batch:
     return hist
 
 
+ARMS = (("random", "fp32"), ("spectral", "fp32"), ("learned", "fp32"), ("spectral", "mixed"),
+        ("learned", "mixed"))
+
+
+def to_099(res, budgets, ref_frac, rows):
+    """Per arm: the smallest budget whose mean fidelity is >= 0.99 and whose
+    fraction of rows >= 0.99 is within 0.5 % of ref_frac, with its rows/s."""
+    out = {}
+    for init, prec in ARMS:
+        key = f"{init}+{prec}"
+        for it in budgets:
+            r = res[f"{key}/{it}"]
+            if r["mean"] >= 0.99 and r["frac_ge_0_99"] >= ref_frac - 0.005:
+                out[key] = dict(iters=it, rows_per_s=rows / (r["ms_per_fiber"] / 1e3), mean=r["mean"],
+                                frac_ge_0_99=r["frac_ge_0_99"])
+                break
+        else:
+            out[key] = None
+    return out
+
+
 def evaluate(model, tm_fn, fibers, N, M, J, masks, photons, budgets, power_iters, seed=1):
-    """For every start (random, spectral, learned) and iteration budget: mean
-    fidelity, fraction >= 0.99 and retrieve time on held-out fibers."""
+    """For every start (random, spectral, learned), arithmetic (FP32, mixed)
+    and iteration budget: mean fidelity, fraction >= 0.99 and retrieve time on
+    held-out fibers."""
     dg = torch.from_numpy(np.ascontiguousarray(masks, dtype=np.complex64)).cuda()
     gen = torch.Generator(device="cuda")
     gen.manual_seed(seed)
@@ -96,8 +118,8 @@ def evaluate(model, tm_fn, fibers, N, M, J, masks, photons, budgets, power_iters
         for f in fibers:
             data.append(fiber_data(h0, tm_fn(f), photons, gen))
     out = {}
-    for init in ("random", "spectral", "learned"):
-        opt = dict(init=init, power_iters=power_iters if init != "random" else 0)
+    for init, prec in ARMS:
+        opt = dict(init=init, power_iters=power_iters if init != "random" else 0, precision=prec)
         with tmr.tmr_create(N, M, J, dg, None, opt) as h:
             if init == "learned":
                 tmr.tmr_set_init_model(h, model)
@@ -115,7 +137,7 @@ def evaluate(model, tm_fn, fibers, N, M, J, masks, photons, budgets, power_iters
                     if init == "learned":
                         kept += tmr.tmr_learned_rows(h)
                 fi = np.concatenate(fids)
-                out[f"{init}/{it}"] = dict(mean=float(fi.mean()), frac_ge_0_99=float(np.mean(fi >= 0.99)),
+                out[f"{init}+{prec}/{it}"] = dict(mean=float(fi.mean()), frac_ge_0_99=float(np.mean(fi >= 0.99)),
                                             ms_per_fiber=ms / len(data),
                                             rows_kept=(kept / fi.size) if init == "learned" else None)
     return out
@@ -166,10 +188,12 @@ def main(argv=None):
         budgets = [int(b) for b in a.budgets.split(",")]
         res = evaluate(model, tm_fn, cfg["test_fibers"][:a.test_fibers], N, M, J, d, cfg["photons"],
                        budgets, a.power_iters)
+    ref = res[f"spectral+fp32/{max(budgets)}"]["frac_ge_0_99"]
     rep = {"config": dict(N=N, J=J, R=R, rows_per_fiber=M, train_fibers=a.train_fibers,
                           test_fibers=a.test_fibers, widths=[J * N, h1, h2, 2 * N], epochs=a.epochs,
                           batch=a.batch, lr=a.lr, power_iters=a.power_iters),
-           "train_loss": hist, "seconds": dict(data=t_data, train=t_train), "held_out": res}
+           "train_loss": hist, "seconds": dict(data=t_data, train=t_train), "held_out": res,
+           "to_fidelity_0_99": to_099(res, budgets, ref, M)}
     line = json.dumps(rep)
     if a.out:
         with open(a.out, "w") as fh:
