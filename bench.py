@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--rows", type=int, default=None, help="override M (grid kept 128 wide)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the short-budget sweep to the 0.99 bar")
     args = ap.parse_args()
     if args.iters is None:
         args.iters = WORKLOADS[args.workload]["iters"]
@@ -368,6 +369,30 @@ def main():
                           "basis": "split-BF16 mma.sync flops of the DFT stages; peak = measured "
                                    "cuBLAS bf16 burst"}
 
+    # ---- smallest budget that meets the 0.99 bar (the whole retrieve, phase
+    # fit included): mean fidelity >= 0.99 and the fraction of rows >= 0.99
+    # within 0.5 % of the configured budget's ----
+    to099 = None
+    if not args.no_sweep and args.iters > 10:
+        ref_frac = float(np.mean(fid >= 0.99))
+        for it in (10, 20, 30, 50, 75):
+            if it >= args.iters:
+                break
+            tmr.tmr_retrieve(h, y, y_def, it, T_out, status)  # warm (graph, staging)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tmr.tmr_retrieve(h, y, y_def, it, T_out, status)
+            e1.record(stream)
+            e1.synchronize()
+            f_it = fidelity(T_out, Tg).float().cpu().numpy()
+            if f_it.mean() >= 0.99 and np.mean(f_it >= 0.99) >= ref_frac - 0.005:
+                t_it = e0.elapsed_time(e1)
+                to099 = {"iters": it, "value": world * M / (t_it / 1e3), "unit": UNIT, "ms_per_step": t_it,
+                         "mean": float(f_it.mean()), "frac_ge_0.99": float(np.mean(f_it >= 0.99)),
+                         "criterion": "mean >= 0.99 and rows >= 0.99 within 0.5 % of the configured budget's"}
+                break
+
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
     if not args.no_e2e:
@@ -416,6 +441,7 @@ def main():
                              "frac_ge_0.99": float(np.mean(fid >= 0.99)),
                              "matrix_after_phase_fit": mfid},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "to_fidelity_0.99": to099,
                 "gpu_launches": 4 * args.steps}
         print(json.dumps(line))
     if world > 1:
