@@ -69,6 +69,22 @@ def parse():
     return args
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest x over all ranks (the slowest rank's time); x itself at world 1."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rows_per_s(rows_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job throughput: every rank's rows over the slowest rank's time."""
+    return world * rows_per_rank / seconds
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -305,13 +321,8 @@ def main():
     barrier()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * M / (ms / 1e3)
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world)
+    value = job_rows_per_s(M, world, ms / 1e3)
 
     # ---- quality of the result (after timing) ----
     def fidelity(A, B):
@@ -404,13 +415,8 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.steps):
             tmr.tmr_retrieve(h, y_h, yd_h, args.iters, T_h)
-        dt = (time.perf_counter() - t0) / args.steps
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * M / dt, "unit": UNIT,
+        dt = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
+        e2e = {"value": job_rows_per_s(M, world, dt), "unit": UNIT,
                "h2d_bytes_per_step": int(y_h.numel() * 4 + yd_h.numel() * 4),
                "d2h_bytes_per_step": int(T_h.numel() * 8), "ms_per_step": dt * 1e3}
 
