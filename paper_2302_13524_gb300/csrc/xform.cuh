@@ -205,6 +205,18 @@ enum { kTcC = 0, kTcS = 2, kTcNS = 4, kTcTiles16 = 6, kTc8Fwd = 0, kTc8Inv = 2, 
 // radix-16 passes of N = 2^lg written 16^A 8^B with A largest
 __host__ __device__ constexpr int mixed_a16(int lg) { return lg % 3 == 0 ? (lg >= 12 ? 3 : 0) : (lg % 3 == 1 ? 1 : 2); }
 
+// Element i of a tensor-core transform's buffer lives at tc_addr(i): bits 2-3
+// of i are XORed with a hash of bits 4, 6, 8 and 10, a bijection inside each
+// 16-element block.  The passes read a butterfly's inputs at strides of N/16
+// (N/8) and write outputs at strides of 16 or 256; with a plain (or per-16
+// padded) layout those land on the same banks, and the swizzle spreads them
+// (for N = 2048 the 64-bit accesses of a transform take 1.29 times the
+// minimum number of shared-memory wavefronts instead of 3.0).
+__device__ __forceinline__ int tc_addr(int i)
+{
+    return i ^ ((((i >> 4) ^ (i >> 6) ^ (i >> 8) ^ (i >> 10)) & 3) << 2);
+}
+
 template <int N_>
 struct XfMixed {
     static constexpr bool kBlue = false;
@@ -267,7 +279,7 @@ struct XfMixed {
 #pragma unroll
             for (int u = 0; u < 4; u++) {
                 const int r = 2 * t + (u & 1) + 8 * (u >> 1);
-                float2 v = buf[fft_pad(b + r * NB)];
+                float2 v = buf[tc_addr(b + r * NB)];
                 if constexpr (Ns > 1) {
                     float2 w = root[(r * j) * (N_ / (16 * Ns))];
                     if constexpr (SIGN > 0) w.y = -w.y;
@@ -306,7 +318,7 @@ struct XfMixed {
                 const int bb = grp * 8 + 2 * t + (u & 1);
                 const int q = g + 8 * (u >> 1);
                 const int jj = bb & (Ns - 1);
-                buf[fft_pad((bb - jj) * 16 + jj + q * Ns)] = out[gi][u];
+                buf[tc_addr((bb - jj) * 16 + jj + q * Ns)] = out[gi][u];
             }
         }
         __syncthreads();
@@ -333,7 +345,7 @@ struct XfMixed {
 #pragma unroll
             for (int u = 0; u < 2; u++) {
                 const int r = 2 * t + u;
-                float2 v = buf[fft_pad(b + r * NB)];
+                float2 v = buf[tc_addr(b + r * NB)];
                 if constexpr (Ns > 1) {
                     float2 w = root[(r * j) * (N_ / (8 * Ns))];
                     if constexpr (SIGN > 0) w.y = -w.y;
@@ -360,7 +372,7 @@ struct XfMixed {
             for (int u = 0; u < 2; u++) {
                 const int bb = grp * 8 + 2 * t + u;
                 const int jj = bb & (Ns - 1);
-                buf[fft_pad((bb - jj) * 8 + jj + g * Ns)] = out[gi][u];
+                buf[tc_addr((bb - jj) * 8 + jj + g * Ns)] = out[gi][u];
             }
         }
         __syncthreads();
@@ -382,11 +394,11 @@ struct XfMixed {
     {
         float2 *buf = buf0 + (BUFS == 2 && f32.ph ? LBUF : 0);
 #pragma unroll
-        for (int e = 0; e < NE; e++) buf[fft_pad(tid + e * NT)] = x[e];
+        for (int e = 0; e < NE; e++) buf[tc_addr(tid + e * NT)] = x[e];
         __syncthreads();
         tc_passes<SIGN, 0>(buf, cst, tid);
 #pragma unroll
-        for (int e = 0; e < NE; e++) x[e] = buf[fft_pad(tid + e * NT)];
+        for (int e = 0; e < NE; e++) x[e] = buf[tc_addr(tid + e * NT)];
         __syncthreads();
     }
     __device__ __forceinline__ void fwd(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid)
