@@ -671,21 +671,20 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
                     const float gam = Gm.gamma;
                     const int np = Gm.np;
                     float c1r[kSlots], c2r[kSlots];
-                    const HT *sp[kSlots], *yp[kSlots];
+                    int so[kSlots];  // slot offsets (same for the S and Y halves)
 #pragma unroll
                     for (int k = 0; k < kSlots; k++) {
                         const int a = Gm.slot[k < np ? k : 0];
                         c1r[k] = k < np ? Gm.c1[k] : 0.f;
                         c2r[k] = k < np ? Gm.c2[k] : 0.f;
-                        sp[k] = Ss + (size_t)a * SL;
-                        yp[k] = Ys + (size_t)a * SL;
+                        so[k] = a * SL;
                     }
                     for (int i = tid; i < nmine; i += BT) {
                         float2 acc = cscale(gs[i], gam);
 #pragma unroll
                         for (int k = 0; k < kSlots; k++) {
                             if (k < np) {
-                                const float2 sa = hist_load(sp[k][i]), ya = hist_load(yp[k][i]);
+                                const float2 sa = hist_load(Ss[so[k] + i]), ya = hist_load(Ys[so[k] + i]);
                                 acc.x = fmaf(c1r[k], sa.x, fmaf(c2r[k], ya.x, acc.x));
                                 acc.y = fmaf(c1r[k], sa.y, fmaf(c2r[k], ya.y, acc.y));
                             }
@@ -758,13 +757,9 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
                     float pv[32];
 #pragma unroll
                     for (int k = 0; k < 32; k++) pv[k] = 0.f;
-                    const HT *sp[kSlots], *yp[kSlots];
+                    int so[kSlots];  // slot offsets (same for the S and Y halves)
 #pragma unroll
-                    for (int k = 0; k < kSlots; k++) {
-                        const int a = Gm.slot[k <= np ? k : 0];
-                        sp[k] = Ss + (size_t)a * SL;
-                        yp[k] = Ys + (size_t)a * SL;
-                    }
+                    for (int k = 0; k < kSlots; k++) so[k] = Gm.slot[k <= np ? k : 0] * SL;
                     for (int i = tid; i < nmine; i += BT) {
                         const float2 gn = slice_sum(i, -4.f);
                         const HT yh = hist_store<HT>(csub(gn, gs[i]));
@@ -775,8 +770,8 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
 #pragma unroll
                         for (int k = 0; k < kSlots; k++) {
                             if (k <= np) {  // live pairs by age, then the new one (age np)
-                                const float2 sa = hist_load(sp[k][i]);
-                                const float2 ya = hist_load(yp[k][i]);
+                                const float2 sa = hist_load(Ss[so[k] + i]);
+                                const float2 ya = hist_load(Ys[so[k] + i]);
                                 pv[4 * k + 0] += cdotr(sa, yn);
                                 pv[4 * k + 1] += cdotr(ya, yn);
                                 pv[4 * k + 2] += cdotr(sa, gn);
