@@ -182,9 +182,11 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- reference arm
-def cpu_oracle_sample(W, M, iters, power_iters, rows_n, seed=0):
+def cpu_oracle_sample(W, M, iters, power_iters, rows_n, seed=0, keep=None):
     """Time the FP64 oracle on rows_n sampled rows of workload W.  Returns
-    (rows/s, seconds, threads, description)."""
+    (rows/s, seconds, threads, description); when keep is a dict it receives
+    the sample (intensities rounded to float32, the masks, the true rows and
+    the oracle's rows) for a comparison with the GPU on the same inputs."""
     import oracle
     import synth
     N, J, R = W["N"], W["J"], W["R"]
@@ -197,11 +199,14 @@ def cpu_oracle_sample(W, M, iters, power_iters, rows_n, seed=0):
     Y = oracle.forward(T, d)
     ph = synth.row_photons(dict(photons=W["photons"]), M, seed=seed)[rows]
     Y = synth.shot_noise(Y, synth.photon_scale(Y.mean(), ph), seed=seed, row_ids=rows)
+    Y = Y.astype(np.float32)  # the values a float32 caller would pass
     t0 = time.perf_counter()
     Tr, _, _, _ = oracle.retrieve_rows(Y, d, iters, init="spectral", power_iters=power_iters,
-                                       clip=2.0, tol=W["tol"], row_ids=rows)
+                                       clip=2.0, tol=W["tol"], seed=seed)
     dt = time.perf_counter() - t0
     fid = oracle.fidelity_rows(Tr, T)
+    if keep is not None:
+        keep.update(Y=Y, d=d, T=T, Tr=Tr, fid=fid)
     desc = (f"{len(rows)} sampled rows of the workload, Algorithm 1 only ({power_iters} power + "
             f"{iters} L-BFGS iterations, naive O(N^2) DFT, FP64, OpenMP over rows); the global "
             f"phase-offset fit is not in the sample; mean fidelity {fid.mean():.4f}")
@@ -422,10 +427,31 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        keep = {}
         v, dt, cores, desc = cpu_oracle_sample(W, M, args.iters, args.power_iters,
-                                               rows_n=max(1, min(16, os.cpu_count() or 8)))
+                                               rows_n=max(1, min(16, os.cpu_count() or 8)), seed=seed,
+                                               keep=keep)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
                "seconds": dt}
+        # the same sampled rows (oracle-made intensities) through the library with
+        # this run's options: the error of this arithmetic against the FP64 oracle
+        import oracle
+        ns = keep["Y"].shape[0]
+        Ts = torch.empty((ns, N), dtype=torch.complex64, device="cuda")
+        with tmr.tmr_create(N, ns, J, torch.from_numpy(keep["d"].astype(np.complex64)).cuda(), None,
+                            opt) as hs:
+            tmr.tmr_retrieve(hs, torch.from_numpy(keep["Y"]).cuda(), None, args.iters, Ts)
+            torch.cuda.synchronize()
+        Tg = Ts.cpu().numpy()
+        fg = oracle.fidelity_rows(Tg, keep["T"])
+        agree = oracle.fidelity_rows(Tg, keep["Tr"])
+        dfid = np.abs(fg - keep["fid"])
+        cpu["oracle_parity"] = {"rows": int(ns), "precision": args.precision,
+                                "mean_abs_fidelity_diff": float(dfid.mean()),
+                                "max_abs_fidelity_diff": float(dfid.max()),
+                                "frac_within_1e-3": float(np.mean(dfid <= 1e-3)),
+                                "gpu_vs_oracle_row_fidelity_mean": float(agree.mean()),
+                                "gpu_vs_oracle_row_fidelity_min": float(agree.min())}
 
     h.close()
     if rank == 0:
