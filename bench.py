@@ -356,10 +356,10 @@ def main():
     achieved = flops / (solver_ms / 1e3) / 1e12
     peak_max = fp32_peak_tflops(n_sm, 2070.0)
     # DRAM bytes of one solver launch from an ncu capture of the plain workload
-    # at 4096 rows (138.8 MB read + 43.4 MB written), scaled by the rows
+    # at 4096 rows (138.0 MB read + 42.7 MB written), scaled by the rows
     traffic = None
     if args.workload == "plain" and args.precision == "fp32":
-        traffic = (138.755072e6 + 43.423232e6) * M / 4096
+        traffic = (138.029056e6 + 42.719488e6) * M / 4096
     roof = {"bound": "alu", "kernel": f"k_solver (N={N})", "achieved": achieved, "peak": peak_max,
             "unit": "TFLOP/s", "frac": achieved / peak_max, "traffic": traffic,
             "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 4096-row "
