@@ -21,7 +21,8 @@ bool fft_supported(int N);  // powers of two 64..4096 (one register FFT)
 // two, [twiddles | half Bluestein filter | chirp] for the other lengths.
 // xform_supported: powers of two 64..4096 and every other N in 16..4096.
 bool xform_supported(int N);
-// Bluestein shape of a non-power-of-two N: FFT length L and registers per
+// Bluestein shape of a non-power-of-two N: FFT length L (4096 with split
+// outputs for N in (2048, 2731]) and registers per
 // thread (the instantiated variant); false when N has none.
 bool xform_blue_shape(int N, int *L, int *ne);
 int xform_table(int N, float2 *out);  // length in float2; writes when out != NULL

@@ -25,6 +25,11 @@ bool fft_supported(int N) { return N >= 64 && N <= 4096 && (N & (N - 1)) == 0; }
 bool xform_blue_shape(int N, int *L, int *ne)
 {
     if (N < 16 || N > 4096 || fft_supported(N)) return false;
+    if (N > 2048 && N <= kBlueSplitMaxN) {  // split outputs at L = 4096 (XfBlueSplit)
+        *L = 4096;
+        *ne = (N + 511) / 512;
+        return true;
+    }
     int l = 512;
     while (l < 2 * N - 1) l *= 2;
     if (l > 8192) return false;
@@ -134,11 +139,47 @@ static int blue_table(int N, float2 *out)
     return len;
 }
 
+// [twiddles | B_1 | B_2 | chirp] of the split-output transform (XfBlueSplit)
+template <int NE>
+static int blue_split_table(int N, float2 *out)
+{
+    using X = XfBlueSplit<NE>;
+    constexpr int L = X::L;
+    const int len = X::NCONST + N;
+    if (!out) return len;
+    std::vector<float2> full(fft_table_len(L));
+    fft_table(L, full.data());
+    for (int i = 0; i < X::NCONST_TW; i++) out[i] = full[i];
+    auto chirp = [N](long long m, double sgn) {
+        const long long q = (m * m) % (2LL * N);
+        const double a = sgn * M_PI * (double)q / (double)N;
+        return std::complex<double>(std::cos(a), std::sin(a));
+    };
+    const int H = (N + 1) / 2;
+    for (int half = 0; half < 2; half++) {
+        // b_m = exp(i pi m^2 / N) on the half's range of k - n
+        const int m0 = half == 0 ? -(N - 1) : H - (N - 1), m1 = half == 0 ? H - 1 : N - 1;
+        std::vector<std::complex<double>> b(L, 0.0);
+        for (int m = m0; m <= m1; m++) b[((m % L) + L) % L] = chirp(m < 0 ? -m : m, +1.0);
+        host_fft(b);
+        for (int k = 0; k < L; k++) {
+            const std::complex<double> v = b[k] / (double)L;
+            out[X::NCONST_TW + half * L + k] = make_float2((float)v.real(), (float)v.imag());
+        }
+    }
+    for (int n = 0; n < N; n++) {
+        const std::complex<double> c = chirp(n, -1.0);
+        out[X::NCONST + n] = make_float2((float)c.real(), (float)c.imag());
+    }
+    return len;
+}
+
 int xform_table(int N, float2 *out)
 {
     if (fft_supported(N)) return fft_table(N, out);
     int L, ne;
     if (!xform_blue_shape(N, &L, &ne)) return -1;
+    if (N > 2048 && L == 4096) return ne == 5 ? blue_split_table<5>(N, out) : blue_split_table<6>(N, out);
     switch (L) {
     case 512: return blue_table<512, 8>(N, out);
     case 1024: return blue_table<1024, 8>(N, out);
@@ -147,7 +188,6 @@ int xform_table(int N, float2 *out)
     default: break;
     }
     switch (ne) {  // the constants do not depend on the register count
-    case 5: return blue_table<8192, 5>(N, out);
     case 6: return blue_table<8192, 6>(N, out);
     case 7: return blue_table<8192, 7>(N, out);
     default: return blue_table<8192, 8>(N, out);
@@ -270,6 +310,7 @@ static cudaError_t dispatch_xf(int N, int prec, F &&f)
     }
     int L, ne;
     if (!xform_blue_shape(N, &L, &ne)) return cudaErrorInvalidValue;
+    if (N > 2048 && L == 4096) return ne == 5 ? f(XfBlueSplit<5>{}) : f(XfBlueSplit<6>{});
     switch (L) {
     case 512: return f(XfBlue<512, 8>{});
     case 1024: return f(XfBlue<1024, 8>{});
@@ -277,8 +318,7 @@ static cudaError_t dispatch_xf(int N, int prec, F &&f)
     case 4096: return f(XfBlue<4096, 8>{});
     default: break;
     }
-    switch (ne) {
-    case 5: return f(XfBlue<8192, 5>{});
+    switch (ne) {  // L = 8192: N in (2731, 4096], 6..8 registers
     case 6: return f(XfBlue<8192, 6>{});
     case 7: return f(XfBlue<8192, 7>{});
     default: return f(XfBlue<8192, 8>{});

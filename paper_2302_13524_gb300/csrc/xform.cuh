@@ -161,6 +161,101 @@ struct XfBlue {
     }
 };
 
+// XfBlueSplit<NE>: N in (2048, 2731] by Bluestein at L = 4096 < 2N - 1, with
+// the outputs split in two halves [0, H) and [H, N), H = ceil(N / 2).  Output
+// k needs b_{k-n} for n < N only; for the first half the indices run over
+// [-(N-1), H-1], for the second over [H-(N-1), N-1], each of length at most
+// N + H - 1 <= L, so each half is an exact cyclic convolution with its own
+// filter b~_h (b_m placed at m mod L on the half's range, zero elsewhere):
+//   F x = c .* F_L^{+}( A .* B_h ) on half h,   A = F_L^{-}(x .* d .* c),
+//   B_h = F_L(b~_h) / L.
+// One forward and two inverse length-4096 FFTs per transform (three, against
+// two of length 8192 above), 8 points per thread; the filters are not even,
+// so both are stored whole.
+// Constants: [ FFT twiddles | B_1 (L) | B_2 (L) | chirp c (N) ].
+constexpr int kBlueSplitMaxN = 2731;  // N + ceil(N / 2) - 1 <= 4096
+
+template <int NE_>
+struct XfBlueSplit {
+    static constexpr bool kBlue = true;
+    static constexpr int kN = 0;
+    static constexpr int L = 4096;
+    static constexpr int NT = L / 8, EL = 8;
+    static constexpr int NE = NE_;
+    static_assert(NE * NT <= 2 * L, "registers");
+    static constexpr int LBUF = fft_buf_len(L);
+    static constexpr int BUFS = 1;
+    static constexpr int NCONST_TW = FftSmall<L, NT>::TW_SMALL;
+    static constexpr int NCONST = NCONST_TW + 2 * L;
+    __host__ __device__ static constexpr int shared_consts(int n) { return NCONST + n; }
+
+    float2 dc[NE];
+    float2 wb;
+    int n, h;
+
+    __device__ __forceinline__ static bool valid(int e, int tid, int n) { return tid + e * NT < n; }
+
+    __device__ __forceinline__ void setup(const float2 *__restrict__ mask, const float2 *__restrict__ chirp,
+                                          int n_, int tid)
+    {
+        n = n_;
+        h = (n_ + 1) / 2;
+#pragma unroll
+        for (int e = 0; e < NE; e++) {
+            const int i = tid + e * NT;
+            dc[e] = i < n ? cmul(mask[i], chirp[i]) : make_float2(0.f, 0.f);
+        }
+        double s, co;
+        sincospi(-2.0 * (double)tid / (double)L, &s, &co);
+        wb = make_float2((float)co, (float)s);
+    }
+    // out[e] (index k = tid + e NT < n) <- (c .* conv_h(a))_k, a given in v
+    __device__ __forceinline__ void conv2(float2 (&v)[EL], float2 (&out)[NE], float2 *buf, const float2 *cst,
+                                          int tid, bool conj_out) const
+    {
+        block_fft_rb<L, NT, -1>(v, buf, cst, wb, tid);
+        const float2 *c = cst + NCONST;
+#pragma unroll
+        for (int half = 0; half < 2; half++) {
+            const float2 *B = cst + NCONST_TW + half * L;
+            float2 w[EL];
+#pragma unroll
+            for (int e = 0; e < EL; e++) w[e] = cmul(v[e], B[tid + e * NT]);
+            block_fft_rb<L, NT, +1>(w, buf, cst, wb, tid);
+#pragma unroll
+            for (int e = 0; e < NE; e++) {
+                const int k = tid + e * NT;
+                const bool mine = half == 0 ? k < h : (k >= h && k < n);
+                if (mine) out[e] = conj_out ? w[e] : cmul(w[e], c[k]);
+            }
+        }
+    }
+    __device__ __forceinline__ void fwd(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid)
+    {
+        float2 v[EL];
+#pragma unroll
+        for (int e = 0; e < EL; e++)
+            v[e] = (e < NE && valid(e, tid, n)) ? cmul(x[e < NE ? e : 0], dc[e < NE ? e : 0]) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int e = 0; e < NE; e++) x[e] = make_float2(0.f, 0.f);
+        conv2(v, x, buf, cst, tid, false);
+    }
+    __device__ __forceinline__ void adj(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid)
+    {
+        const float2 *c = cst + NCONST;
+        float2 v[EL];
+#pragma unroll
+        for (int e = 0; e < EL; e++)
+            v[e] = (e < NE && valid(e, tid, n)) ? cmul(cconj(x[e < NE ? e : 0]), c[tid + e * NT])
+                                                : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int e = 0; e < NE; e++) x[e] = make_float2(0.f, 0.f);
+        conv2(v, x, buf, cst, tid, true);  // x <- conv(a) on [0, n), unmultiplied
+#pragma unroll
+        for (int e = 0; e < NE; e++) x[e] = valid(e, tid, n) ? cconj(cmul(x[e], dc[e])) : make_float2(0.f, 0.f);
+    }
+};
+
 // ---------------------------------------------------------------------------
 // XfMixed<N>: N a power of two, 64 <= N <= 4096, written N = 16^A 8^B with A
 // as large as possible.  The FP32 transforms of XfPow2<N>, plus a tensor-core

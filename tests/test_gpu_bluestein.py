@@ -20,9 +20,10 @@ if not torch.cuda.is_available():
 
 import paper_2302_13524_gb300 as tmr  # noqa: E402
 
-# one length per Bluestein shape: L = 512 .. 4096 and L = 8192 with 5..8
-# registers per thread (2286 is the uneven-convergence workload's length)
-BLUE_N = [17, 100, 300, 1000, 1500, 2286, 3000, 3500, 4095]
+# one length per Bluestein shape: L = 512 .. 4096; the split-output form at
+# L = 4096 with 5 and 6 registers per thread (2286 is the uneven-convergence
+# workload's length, 2731 the largest split length); L = 8192 with 6..8
+BLUE_N = [17, 100, 300, 1000, 1500, 2286, 2600, 2731, 2732, 3000, 3500, 4095]
 
 
 def handle(N, M, J, d, dop=None, **opt):
