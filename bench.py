@@ -474,9 +474,9 @@ def main():
                              "matrix_after_phase_fit": mfid},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "to_fidelity_0.99": to099,
-                # kernels per timed step: k_solver, k_row_energy, k_phase_fit,
-                # k_apply_phase (+ k_pack_f16 in mixed precision)
-                "gpu_launches": (5 if args.precision == "mixed" else 4) * args.steps}
+                # kernels per timed step: k_solver, k_fields, k_row_energy,
+                # k_phase_fit, k_apply_phase (+ k_pack_f16 in mixed precision)
+                "gpu_launches": (6 if args.precision == "mixed" else 5) * args.steps}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

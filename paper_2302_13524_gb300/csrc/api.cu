@@ -651,9 +651,9 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
     p.row_status = (int *)dS;
     p.row_iters = (int *)dI;
     p.row_loss = (float *)dL;
-    p.Zd = fit ? h->Zd : nullptr;
+    p.Zd = nullptr;  // the fit's fields are made from the final T (below)
     p.queue = h->queue;
-    p.Nd = fit ? h->Nd : 0;
+    p.Nd = 0;
     p.M = h->M;
     p.N = h->N;
     p.J = h->J;
@@ -682,6 +682,9 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
         TMR_CUDA(cudaMemsetAsync(h->queue, 0, sizeof(unsigned) * 4, h->stream), "memset");
         TMR_CUDA(launch_solver(h->N, h->G, p, h->stream, nullptr), "solver kernel");
         if (fit) {
+            TMR_CUDA(launch_fields(h->N, h->M, h->J, h->Nd, (const float2 *)dT, h->masks, h->tw, h->Zd,
+                                   h->stream, h->prec),
+                     "fields kernel");
             tmr_status s2 = run_phase_fit(h, (const float2 *)dT, (const float *)dYd, h->phi, (float2 *)dT);
             if (s2 != TMR_OK) return s2;
         }
