@@ -351,7 +351,7 @@ struct XfMixed {
     // r = 2t, 2t+1, 2t+8, 2t+9 of butterfly g and ends with outputs
     // q = g, g+8 of butterflies 2t, 2t+1
     template <int SIGN, int p>
-    __device__ __forceinline__ void tc_pass16(float2 *buf, const float2 *cst, int tid) const
+    __device__ __forceinline__ void tc_pass16(const float2 *src, float2 *dst, const float2 *cst, int tid) const
     {
         constexpr int Ns = ns(p), NB = N_ / 16, GPW = NB / 8 / NWT;
         static_assert(GPW * 8 * NWT == NB && GPW >= 1, "group split");
@@ -374,7 +374,7 @@ struct XfMixed {
 #pragma unroll
             for (int u = 0; u < 4; u++) {
                 const int r = 2 * t + (u & 1) + 8 * (u >> 1);
-                float2 v = buf[tc_addr(b + r * NB)];
+                float2 v = src[tc_addr(b + r * NB)];
                 if constexpr (Ns > 1) {
                     float2 w = root[(r * j) * (N_ / (16 * Ns))];
                     if constexpr (SIGN > 0) w.y = -w.y;
@@ -404,7 +404,7 @@ struct XfMixed {
 #pragma unroll
             for (int u = 0; u < 4; u++) out[gi][u] = make_float2(cre[u], cim[u]);
         }
-        __syncthreads();  // every input of the pass is read
+        if (src == dst) __syncthreads();  // in place: every input is read before any write
 #pragma unroll
         for (int gi = 0; gi < GPW; gi++) {
             const int grp = warp * GPW + gi;
@@ -413,7 +413,7 @@ struct XfMixed {
                 const int bb = grp * 8 + 2 * t + (u & 1);
                 const int q = g + 8 * (u >> 1);
                 const int jj = bb & (Ns - 1);
-                buf[tc_addr((bb - jj) * 16 + jj + q * Ns)] = out[gi][u];
+                dst[tc_addr((bb - jj) * 16 + jj + q * Ns)] = out[gi][u];
             }
         }
         __syncthreads();
@@ -421,7 +421,7 @@ struct XfMixed {
     // one radix-8 pass: lane (g, t) loads inputs r = 2t, 2t+1 of butterfly g
     // and ends with output q = g of butterflies 2t, 2t+1
     template <int SIGN, int p>
-    __device__ __forceinline__ void tc_pass8(float2 *buf, const float2 *cst, int tid) const
+    __device__ __forceinline__ void tc_pass8(const float2 *src, float2 *dst, const float2 *cst, int tid) const
     {
         constexpr int Ns = ns(p), NB = N_ / 8, GPW = NB / 8 / NWT;
         static_assert(GPW * 8 * NWT == NB && GPW >= 1, "group split");
@@ -440,7 +440,7 @@ struct XfMixed {
 #pragma unroll
             for (int u = 0; u < 2; u++) {
                 const int r = 2 * t + u;
-                float2 v = buf[tc_addr(b + r * NB)];
+                float2 v = src[tc_addr(b + r * NB)];
                 if constexpr (Ns > 1) {
                     float2 w = root[(r * j) * (N_ / (8 * Ns))];
                     if constexpr (SIGN > 0) w.y = -w.y;
@@ -459,7 +459,7 @@ struct XfMixed {
             out[gi][0] = make_float2(d[0], d[2]);
             out[gi][1] = make_float2(d[1], d[3]);
         }
-        __syncthreads();  // every input of the pass is read
+        if (src == dst) __syncthreads();  // in place: every input is read before any write
 #pragma unroll
         for (int gi = 0; gi < GPW; gi++) {
             const int grp = warp * GPW + gi;
@@ -467,34 +467,44 @@ struct XfMixed {
             for (int u = 0; u < 2; u++) {
                 const int bb = grp * 8 + 2 * t + u;
                 const int jj = bb & (Ns - 1);
-                buf[tc_addr((bb - jj) * 8 + jj + g * Ns)] = out[gi][u];
+                dst[tc_addr((bb - jj) * 8 + jj + g * Ns)] = out[gi][u];
             }
         }
         __syncthreads();
     }
     template <int SIGN, int p>
-    __device__ __forceinline__ void tc_passes(float2 *buf, const float2 *cst, int tid) const
+    // pass p reads b0 (p even) or b1 (p odd) and writes the other one; with a
+    // single buffer (b0 == b1) the passes work in place
+    __device__ __forceinline__ void tc_passes(float2 *b0, float2 *b1, const float2 *cst, int tid) const
     {
         if constexpr (p < P) {
-            if constexpr (radix(p) == 16) tc_pass16<SIGN, p>(buf, cst, tid);
-            else tc_pass8<SIGN, p>(buf, cst, tid);
-            tc_passes<SIGN, p + 1>(buf, cst, tid);
+            const float2 *src = (p & 1) ? b1 : b0;
+            float2 *dst = (p & 1) ? b0 : b1;
+            if constexpr (radix(p) == 16) tc_pass16<SIGN, p>(src, dst, cst, tid);
+            else tc_pass8<SIGN, p>(src, dst, cst, tid);
+            tc_passes<SIGN, p + 1>(b0, b1, cst, tid);
         }
     }
-    // x (thread-strided) <- DFT_N^SIGN x through the tensor-core passes; works
-    // in the buffer the FP32 transforms would write next (every pass ends with
-    // a barrier, so the ping-pong parity stays as it is)
+    // x (thread-strided) <- DFT_N^SIGN x through the tensor-core passes.  With
+    // two buffers the passes alternate between them (one barrier per pass),
+    // starting in the buffer the FP32 transforms would write next, and the
+    // ping-pong parity is left pointing at the buffer not read last, so the
+    // next transform's first write cannot race the final read-back; with one
+    // buffer every pass works in place and the transform ends with a barrier.
     template <int SIGN>
-    __device__ __forceinline__ void tc_transform(float2 (&x)[NE], float2 *buf0, const float2 *cst, int tid) const
+    __device__ __forceinline__ void tc_transform(float2 (&x)[NE], float2 *buf0, const float2 *cst, int tid)
     {
-        float2 *buf = buf0 + (BUFS == 2 && f32.ph ? LBUF : 0);
+        float2 *cur = buf0 + (BUFS == 2 && f32.ph ? LBUF : 0);
+        float2 *oth = BUFS == 2 ? buf0 + (f32.ph ? 0 : LBUF) : cur;
 #pragma unroll
-        for (int e = 0; e < NE; e++) buf[tc_addr(tid + e * NT)] = x[e];
+        for (int e = 0; e < NE; e++) cur[tc_addr(tid + e * NT)] = x[e];
         __syncthreads();
-        tc_passes<SIGN, 0>(buf, cst, tid);
+        tc_passes<SIGN, 0>(cur, oth, cst, tid);
+        const float2 *last = (P & 1) ? oth : cur;
 #pragma unroll
-        for (int e = 0; e < NE; e++) x[e] = buf[tc_addr(tid + e * NT)];
-        __syncthreads();
+        for (int e = 0; e < NE; e++) x[e] = last[tc_addr(tid + e * NT)];
+        if constexpr (BUFS == 2) f32.ph ^= (P & 1) ? 0 : 1;
+        else __syncthreads();
     }
     __device__ __forceinline__ void fwd(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid)
     {
