@@ -60,7 +60,7 @@ struct SolverParams {
     int *row_iters;       // [M]
     float *row_loss;      // [M]
     float2 *Zd;           // [Nd][M] defocus fields of the final iterate, or NULL
-    const float2 *T_cand; // [M][N] proposed starts judged against the init, or NULL
+    const float2 *T_cand; // [M][N] proposed starts compared per row with the init, or NULL
     unsigned *cand_wins;  // rows whose proposed start was kept
     unsigned *queue;      // row work counter, zeroed before the launch
     int N, Nd, M, J, iters, m, init, power_iters;

@@ -585,7 +585,7 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
                 for (int i = tid; i < nmine; i += BT) ts[i] = cscale(ts[i], sc);
             }
 
-            // ---- judge a proposed start (learned initialiser) against this one ----
+            // ---- per-row selection: a proposed start (learned initialiser) against this one ----
             if (P.T_cand) {
                 for (int i = tid; i < nmine; i += BT) gs[i] = P.T_cand[(size_t)row * N + lo + i];
                 float fv[2];

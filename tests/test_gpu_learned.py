@@ -1,6 +1,6 @@
 """The learned initialiser through the C ABI: the network's forward pass and
 gradient against the FP64 oracle network (BF16 products, FP32 accumulation),
-training on the GPU, and the per-row judge inside tmr_retrieve."""
+training on the GPU, and the per-row selection inside tmr_retrieve."""
 import numpy as np
 import pytest
 
@@ -62,8 +62,8 @@ def test_mlp_training_learns_a_smooth_target():
     assert last < 0.1 * first
 
 
-def test_learned_start_is_judged_per_row():
-    """The judge keeps a proposal only where its loss beats the spectral start:
+def test_learned_start_is_selected_per_row():
+    """The per-row selection keeps a proposal only where its loss beats the spectral start:
     every other row must come out exactly as in the plain spectral run, and the
     number of rows that differ is the number the handle reports as kept."""
     N, M, J, iters = 256, 24, 4, 20
@@ -93,7 +93,7 @@ def test_learned_gain_measured_on_held_out_fibers():
     """What the trained network gains, measured: a small fiber family (N = 256,
     shared input basis, 6 training and 2 held-out fibers), the network trained
     by the library's kernels on rows the plain solver retrieved, then every
-    start and arithmetic run on the held-out fibers.  The per-row judge bounds
+    start and arithmetic run on the held-out fibers.  The per-row selection bounds
     the effect: rows whose proposal it rejects come out exactly as with the
     spectral start, so the mean fidelities differ by at most the fraction of
     rows kept; the measured gain is printed."""

@@ -75,9 +75,9 @@ def test_mixed_rejects_other_lengths():
     assert ei.value.status == tmr.TMR_ERR_INVALID_ARG
 
 
-def test_mixed_learned_start_is_judged_per_row():
-    """The learned start with mixed precision: the judge (in tensor-core
-    arithmetic) keeps a proposal only where its loss beats the spectral start,
+def test_mixed_learned_start_is_selected_per_row():
+    """The learned start with mixed precision: the per-row selection (in
+    tensor-core arithmetic) keeps a proposal only where its loss beats the spectral start,
     so the rows it does not keep come out exactly as in the mixed spectral run."""
     N, M, J, iters = 256, 24, 4, 20
     T, d, Y = problem(N, M, J, seed=9)
