@@ -137,7 +137,8 @@ void tmr_default_options(tmr_options *opt);
  * Supported on the GPU: 1 <= J <= 8 and N a power of two with
  * 64 <= N <= 4096 (one register FFT of length N), or any other N with
  * 16 <= N <= 4096 (Bluestein's chirp-z form of the same DFT through FFTs of
- * a power-of-two length L >= 2N - 1, one mask per CTA).  When no solver
+ * a power-of-two length L >= 2N - 1, or, for 2048 < N <= 2731, through
+ * 4096-point FFTs with the outputs split in two halves; one mask per CTA).  When no solver
  * schedule fits the per-row state of (N, J, opt->m) in shared memory the
  * handle is still made (tmr_forward, tmr_grad and tmr_defocus_forward work),
  * tmr_schedule reports 0 and tmr_retrieve returns UNSUPPORTED.
