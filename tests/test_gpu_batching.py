@@ -132,3 +132,34 @@ def test_early_exit_uneven_rows_one_launch():
     fid_g = oracle.fidelity_rows(to_np(To), T)
     assert np.mean(fid_g) >= 0.97
     assert abs(np.mean(st_g == 1) - np.mean(st_o == 1)) <= 0.15
+
+
+@pytest.mark.parametrize("N,prec,tol", [(300, "fp32", 1e-7), (2286, "fp32", 1e-7), (256, "mixed", 0.0)])
+def test_graph_replay_other_transforms(N, prec, tol):
+    """Graph replay with the Bluestein transforms (L = 1024 and the split form
+    at N = 2286, per-row early exit on) and with mixed precision (the FP16
+    packing kernel inside the captured region): the replayed retrieve matches
+    direct launches bit for bit, twice in a row."""
+    M, J, Nd, grid = 64, 4, 24, (8, 8)
+    T, d, Y = problem(N, M, J, seed=N)
+    C = oracle.defocus_fields(T.astype(np.complex128), d.astype(np.complex128), Nd)
+    Yd = f32(oracle.defocus_forward(C, grid, coef=0.05))
+    dop = dict(ny=grid[0], nx=grid[1], n_defocus=Nd, coef=0.05)
+    res = {}
+    for graph in (0, 1):
+        outs = []
+        with tmr.tmr_create(N, M, J, to_dev(d), dop, dict(use_graph=graph, init="spectral", power_iters=20,
+                                                            precision=prec, tol=tol)) as h:
+            yg, ydg = to_dev(Y), to_dev(Yd)
+            To = torch.empty((M, N), dtype=torch.complex64, device="cuda")
+            st = torch.empty(M, dtype=torch.int32, device="cuda")
+            its = torch.empty(M, dtype=torch.int32, device="cuda")
+            for _ in range(2):  # with a graph: capture, then replay
+                To.zero_()
+                tmr.tmr_retrieve(h, yg, ydg, 40, To, st, its)
+                tmr.tmr_sync(h, 60.0)
+                outs.append((to_np(To), to_np(st), to_np(its)))
+        res[graph] = outs
+    for k in range(2):
+        for a, b in zip(res[1][k], res[0][k]):
+            np.testing.assert_array_equal(a, b)
