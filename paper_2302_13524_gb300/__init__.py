@@ -14,3 +14,4 @@ from ._lib import (  # noqa: F401
     tmr_learned_rows, tmr_mlp_create, tmr_mlp_destroy, tmr_mlp_forward, tmr_mlp_get_params,
     tmr_mlp_grad, tmr_mlp_set_params, tmr_mlp_train_step, tmr_retrieve_from, tmr_retrieve_rows_static,
     tmr_schedule, tmr_set_init_model, tmr_sync, tmr_workspace_bytes)
+from .retriever import Retriever  # noqa: F401,E402

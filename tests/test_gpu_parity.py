@@ -278,3 +278,45 @@ def test_plain_full_size_sampled_rows():
     assert np.mean(np.abs(fid_g - fid_o) <= 1e-3) >= 7 / 8, (fid_g, fid_o)
     fid_all = oracle.fidelity_rows(Tg, T)
     assert np.mean(fid_all) >= 0.98
+
+
+# ------------------------------------------------------------ torch wrapper
+def test_retriever_matches_the_functions():
+    """The Retriever class is marshalling only: its outputs equal those of the
+    C-ABI functions bit for bit, and it refuses tensors of the wrong dtype,
+    shape, device or layout."""
+    N, M, J, Nd, grid = 256, 16, 4, 20, (4, 4)
+    T, d, Y = problem(N, M, J, seed=31)
+    C = oracle.defocus_fields(T.astype(np.complex128), d.astype(np.complex128), Nd)
+    Yd = f32(oracle.defocus_forward(C, grid, coef=0.05))
+    dop = dict(ny=grid[0], nx=grid[1], n_defocus=Nd, coef=0.05)
+    opt = dict(init=tmr.TMR_INIT_SPECTRAL, power_iters=30)
+    Tg, Yg, Ydg, dg = to_dev(T), to_dev(Y), to_dev(Yd), to_dev(d)
+    with tmr.Retriever(dg, M, dop, **opt) as r:
+        Yr = r.forward(Tg)
+        lr, Gr = r.grad(Tg, Yg)
+        out = r.retrieve(Yg, Ydg, 25)
+        Ydr = r.defocus_forward(Tg)
+        with pytest.raises(TypeError):
+            r.forward(Tg.to(torch.complex128))
+        with pytest.raises(ValueError):
+            r.forward(Tg[:, :N // 2])
+        with pytest.raises(ValueError):
+            r.forward(Tg.cpu())
+        with pytest.raises(ValueError):
+            r.retrieve(to_dev(np.ascontiguousarray(Y.transpose(0, 2, 1))).transpose(1, 2), None, 5)
+        torch.cuda.synchronize()
+    with handle(N, M, J, d, dop, **opt) as h:
+        Yf = torch.empty_like(Yr)
+        tmr.tmr_forward(h, Tg, Yf)
+        lf = torch.empty_like(lr)
+        Gf = torch.empty_like(Gr)
+        tmr.tmr_grad(h, Tg, Yg, lf, Gf)
+        Tf = torch.empty_like(out["T"])
+        sf = torch.empty_like(out["status"])
+        tmr.tmr_retrieve(h, Yg, Ydg, 25, Tf, sf)
+        Ydf = torch.empty_like(Ydr)
+        tmr.tmr_defocus_forward(h, Tg, Ydf)
+        torch.cuda.synchronize()
+    for a, b in ((Yr, Yf), (lr, lf), (Gr, Gf), (out["T"], Tf), (out["status"], sf), (Ydr, Ydf)):
+        np.testing.assert_array_equal(to_np(a), to_np(b))
