@@ -59,12 +59,33 @@ __device__ void make_tw(float2 *tw, int n)
     }
 }
 
+// Two consecutive radix-2 DIT stages (halves h and 2h) fused on the group
+// {b0, b0 + h, b0 + 2h, b0 + 3h}: stage one pairs (0, 1) and (2, 3) with
+// W_{2h}^k, stage two pairs (0, 2) with W_{4h}^k and (1, 3) with W_{4h}^{k+h}.
+__device__ __forceinline__ void dit2x2(float2 &x0, float2 &x1, float2 &x2, float2 &x3, float2 w1, float2 w2,
+                                       float2 w3)
+{
+    const float2 t1 = cmul(x1, w1), t3 = cmul(x3, w1);
+    const float2 a0 = cadd(x0, t1), a1 = csub(x0, t1), a2 = cadd(x2, t3), a3 = csub(x2, t3);
+    const float2 u2 = cmul(a2, w2), u3 = cmul(a3, w3);
+    x0 = cadd(a0, u2);
+    x2 = csub(a0, u2);
+    x1 = cadd(a1, u3);
+    x3 = csub(a1, u3);
+}
+
 __device__ void fft2_inplace(float2 *g, int ny, int nx, int sign, const float2 *twy, const float2 *twx)
 {
-    // ny, nx powers of two: every index below is a shift or a mask
+    // ny, nx powers of two: every index below is a shift or a mask; stages are
+    // fused two at a time (one barrier per pair), an odd last stage alone
     const int pitch = nx + 1;
     const int lx = __ffs(nx) - 1, ly = __ffs(ny) - 1;
     const int tid = threadIdx.x, nt = blockDim.x;
+    auto tw = [sign](const float2 *t, int i) {
+        float2 w = t[i];
+        if (sign > 0) w.y = -w.y;
+        return w;
+    };
     // rows: bit reversal
     for (int i = tid; i < ny * nx; i += nt) {
         const int a = i >> lx, b = i & (nx - 1);
@@ -76,14 +97,31 @@ __device__ void fft2_inplace(float2 *g, int ny, int nx, int sign, const float2 *
         }
     }
     __syncthreads();
-    for (int lh = 0; lh < lx; lh++) {
+    int lh = 0;
+    for (; lh + 1 < lx; lh += 2) {
+        const int h = 1 << lh;
+        for (int i = tid; i < ny * (nx / 4); i += nt) {
+            const int a = i >> (lx - 2), q = i & (nx / 4 - 1);
+            const int k = q & (h - 1);
+            const int b0 = ((q >> lh) << (lh + 2)) + k;
+            float2 *r = g + a * pitch + b0;
+            float2 x0 = r[0], x1 = r[h], x2 = r[2 * h], x3 = r[3 * h];
+            dit2x2(x0, x1, x2, x3, tw(twx, k << (lx - 1 - lh)), tw(twx, k << (lx - 2 - lh)),
+                   tw(twx, (k + h) << (lx - 2 - lh)));
+            r[0] = x0;
+            r[h] = x1;
+            r[2 * h] = x2;
+            r[3 * h] = x3;
+        }
+        __syncthreads();
+    }
+    if (lh < lx) {
         const int half = 1 << lh;
         for (int i = tid; i < ny * (nx / 2); i += nt) {
             const int a = i >> (lx - 1), q = i & (nx / 2 - 1);
             const int k = q & (half - 1);
             const int b0 = ((q >> lh) << (lh + 1)) + k, b1 = b0 + half;
-            float2 w = twx[k << (lx - 1 - lh)];
-            if (sign > 0) w.y = -w.y;
+            const float2 w = tw(twx, k << (lx - 1 - lh));
             const float2 x0 = g[a * pitch + b0], x1 = cmul(g[a * pitch + b1], w);
             g[a * pitch + b0] = cadd(x0, x1);
             g[a * pitch + b1] = csub(x0, x1);
@@ -101,14 +139,31 @@ __device__ void fft2_inplace(float2 *g, int ny, int nx, int sign, const float2 *
         }
     }
     __syncthreads();
-    for (int lh = 0; lh < ly; lh++) {
+    lh = 0;
+    for (; lh + 1 < ly; lh += 2) {
+        const int h = 1 << lh;
+        for (int i = tid; i < (ny / 4) * nx; i += nt) {
+            const int q = i >> lx, b = i & (nx - 1);
+            const int k = q & (h - 1);
+            const int a0 = ((q >> lh) << (lh + 2)) + k;
+            float2 *c = g + a0 * pitch + b;
+            float2 x0 = c[0], x1 = c[h * pitch], x2 = c[2 * h * pitch], x3 = c[3 * h * pitch];
+            dit2x2(x0, x1, x2, x3, tw(twy, k << (ly - 1 - lh)), tw(twy, k << (ly - 2 - lh)),
+                   tw(twy, (k + h) << (ly - 2 - lh)));
+            c[0] = x0;
+            c[h * pitch] = x1;
+            c[2 * h * pitch] = x2;
+            c[3 * h * pitch] = x3;
+        }
+        __syncthreads();
+    }
+    if (lh < ly) {
         const int half = 1 << lh;
         for (int i = tid; i < (ny / 2) * nx; i += nt) {
             const int q = i >> lx, b = i & (nx - 1);
             const int k = q & (half - 1);
             const int a0 = ((q >> lh) << (lh + 1)) + k, a1 = a0 + half;
-            float2 w = twy[k << (ly - 1 - lh)];
-            if (sign > 0) w.y = -w.y;
+            const float2 w = tw(twy, k << (ly - 1 - lh));
             const float2 x0 = g[a0 * pitch + b], x1 = cmul(g[a1 * pitch + b], w);
             g[a0 * pitch + b] = cadd(x0, x1);
             g[a1 * pitch + b] = csub(x0, x1);
