@@ -216,8 +216,9 @@ bool schedule_ok(int N, int J, int m, int G, int smem_optin, int prec = 0)
 
 // Time every valid schedule on synthetic rows (spectral start, a few power
 // and L-BFGS iterations) and return the fastest.
-tmr_status autotune(tmr_handle *h, int smem_optin, int *G_out)
+tmr_status autotune(tmr_handle *h, int smem_optin, int *G_out, bool *timed)
 {
+    *timed = false;
     int cand[3], nc = 0;
     for (int G : {1, 2, 4})
         if (schedule_ok(h->N, h->J, h->opt.m, G, smem_optin, h->prec)) cand[nc++] = G;
@@ -225,12 +226,21 @@ tmr_status autotune(tmr_handle *h, int smem_optin, int *G_out)
         *G_out = 0;
         return TMR_OK;
     }
-    if (nc == 1) {
+    if (nc == 1) {  // the only schedule: final without timing
         *G_out = cand[0];
+        *timed = true;
         return TMR_OK;
     }
     const int R = 608;
     const size_t K = (size_t)h->J * h->N;
+    // the timing rows are temporary device memory of the handle: under a
+    // workspace_limit they must fit in what is left, else the first
+    // candidate is taken untimed
+    const size_t tune_bytes = sizeof(float) * R * K + sizeof(float2) * R * h->N;
+    if (h->opt.workspace_limit && h->held + tune_bytes > h->opt.workspace_limit) {
+        *G_out = cand[0];  // not timed: not cached either
+        return TMR_OK;
+    }
     float *y = nullptr;
     float2 *T = nullptr;
     if (cudaMalloc(&y, sizeof(float) * R * K) != cudaSuccess ||
@@ -287,6 +297,7 @@ tmr_status autotune(tmr_handle *h, int smem_optin, int *G_out)
     cudaFree(y);
     cudaFree(T);
     *G_out = bestG;
+    *timed = st == TMR_OK;
     return st;
 }
 
@@ -502,12 +513,15 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
                 if (f != fm.end() && schedule_ok(N, J, o.m, f->second, smem_optin, h->prec)) G = f->second;
             }
         }
+        bool timed = true;  // a cached choice was timed when it was made
         if (!G) {
-            TRY(autotune(h, smem_optin, &G));
-            std::lock_guard<std::mutex> lk(g_tune_mu);
-            g_tune_mem[key] = G;
+            TRY(autotune(h, smem_optin, &G, &timed));
+            if (timed) {
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                g_tune_mem[key] = G;
+            }
         }
-        if (o.tune_cache && G > 0) {  // the file records the choice, also one made earlier in this process
+        if (o.tune_cache && G > 0 && timed) {  // the file records the choice, also one made earlier in this process
             std::lock_guard<std::mutex> lk(g_tune_mu);
             auto fm = read_tune_file(o.tune_cache);
             auto f = fm.find(key);

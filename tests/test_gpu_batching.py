@@ -163,3 +163,20 @@ def test_graph_replay_other_transforms(N, prec, tol):
     for k in range(2):
         for a, b in zip(res[1][k], res[0][k]):
             np.testing.assert_array_equal(a, b)
+
+
+def test_autotuner_respects_the_workspace_limit():
+    """Under a workspace limit too small for the autotuner's timing rows the
+    handle takes a schedule untimed, stays within the limit, and does not
+    cache that choice for handles without a limit."""
+    N, M, J = 1024, 8, 4
+    _, d, Y = problem(N, M, J, seed=44)
+    with tmr.tmr_create(N, M, J, to_dev(d), None, dict(m=3)) as h:
+        need = tmr.tmr_workspace_bytes(h)
+    limit = need + 4 * 1024 * 1024  # room for the retrieve buffers, not for 608 timing rows
+    with tmr.tmr_create(N, M, J, to_dev(d), None, dict(m=4, workspace_limit=limit)) as h:
+        assert tmr.tmr_schedule(h) in (1, 2, 4)
+        To = torch.empty((M, N), dtype=torch.complex64, device="cuda")
+        tmr.tmr_retrieve(h, to_dev(Y), None, 5, To)
+        torch.cuda.synchronize()
+        assert tmr.tmr_workspace_bytes(h) <= limit
