@@ -663,13 +663,14 @@ int orc_lbfgs_step(const double *y, const double *masks, int N, int J, const dou
                    const double *S, const double *Yh, int np, double *p_out, double *coef_out,
                    double *alpha_out, double *t_out, double *loss_out, double *g_out)
 {
+    if (N <= 0 || J <= 0 || np < 0) return -1;
     const cplx *d = (const cplx *)masks;
     cplx *tw = make_twiddles(N);
     size_t K = (size_t)J * N;
     int n2 = 2 * N;
     cplx *z = malloc(sizeof(cplx) * K), *w = malloc(sizeof(cplx) * K), *rz = malloc(sizeof(cplx) * K);
     cplx *sc = malloc(sizeof(cplx) * N), *g = malloc(sizeof(cplx) * N), *p = (cplx *)p_out;
-    double *r = malloc(sizeof(double) * K), *alpha = malloc(sizeof(double) * (np > 0 ? np : 1));
+    double *r = calloc(K, sizeof(double)), *alpha = malloc(sizeof(double) * (np > 0 ? np : 1));
     loss_grad_row((const cplx *)t, y, d, N, J, tw, g, z, rz, sc);
     two_loop(n2, (const double *)g, S, Yh, np, (double *)p, alpha);
     if (rdot(p, g, N) >= 0)
