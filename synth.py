@@ -18,18 +18,20 @@ the paper's workloads:
   as the rows of a multimode fiber's TM do;
 * ``mask_phases`` -- the J random phase vectors psi_j of Eq. probingmatrix,
   uniform in [0, 2 pi), and d_j = exp(i psi_j);
-* ``shot_noise`` -- Poisson counts at a photon scale, divided back.
+* ``shot_noise`` -- Poisson counts at a photon scale, divided back;
+* ``fiber_disc`` / ``camera_frames`` -- the fiber core on a pixel grid, and
+  camera-count speckle images of it (the raw input of the preprocessing).
 
 Seeds: each draw uses ``numpy.random.default_rng([seed, stream, ...])`` with a
 fixed stream number per kind (0 = TM, 1 = masks, 2 = noise, 3 = row photon
-levels), so one part can be regenerated without the others, and noise for a
+levels, 4 = camera frames), so one part can be regenerated without the others, and noise for a
 single row depends only on (seed, row).
 """
 from __future__ import annotations
 
 import numpy as np
 
-STREAM_TM, STREAM_MASK, STREAM_NOISE, STREAM_PHOTONS = 0, 1, 2, 3
+STREAM_TM, STREAM_MASK, STREAM_NOISE, STREAM_PHOTONS, STREAM_CAMERA = 0, 1, 2, 3, 4
 
 # Workloads.  N input modes, M output pixels on an ny x nx grid (row = a*nx + b),
 # J masks, K = J*N intensities per row.
@@ -131,6 +133,29 @@ def photon_scale(Y_mean: float, photons) -> np.ndarray:
     """Photons per unit intensity so that a row of mean intensity Y_mean
     collects `photons` per pixel on average."""
     return np.asarray(photons, dtype=np.float64) / Y_mean
+
+
+def fiber_disc(ny: int, nx: int, radius: float = 0.45) -> np.ndarray:
+    """Pixels of an ny x nx grid (p = a*nx + b) inside the fiber core, a disc
+    centred on the grid of radius `radius` times the smaller side: bool [ny*nx]."""
+    a, b = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    r = radius * min(ny, nx)
+    return (((a - (ny - 1) / 2) ** 2 + (b - (nx - 1) / 2) ** 2) <= r * r).ravel()
+
+
+def camera_frames(K: int, H: int, W: int, photons: float = 2000.0, dark: float = 2.0,
+                  radius: float = 0.45, seed: int = 0, dtype=np.uint16) -> np.ndarray:
+    """K speckle images [K, H, W] of a fiber's distal end as a camera records
+    them: exponential speckle of mean `photons` counts inside a centred disc,
+    Poisson counts plus a Poisson dark level outside.  uint16 frames are
+    clipped at 65535; float32 frames keep the counts as floats."""
+    rng = np.random.default_rng([seed, STREAM_CAMERA])
+    core = fiber_disc(H, W, radius).reshape(H, W)
+    lam = rng.exponential(photons, size=(K, H, W)) * core + dark
+    counts = rng.poisson(lam)
+    if np.dtype(dtype) == np.uint16:
+        return np.minimum(counts, 65535).astype(np.uint16)
+    return counts.astype(dtype)
 
 
 def sample_rows(M: int, n: int, seed: int = 0) -> np.ndarray:
