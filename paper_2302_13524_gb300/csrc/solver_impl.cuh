@@ -513,18 +513,30 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
                 Gm.stop = 0;
                 Gm.early = 0;
                 Gm.sumy = Gm.red[0];
-                if (Gm.red[1] > 0.0) { Gm.status = ROW_NUMERIC; Gm.stop = 1; Gm.early = 1; }
+                if (Gm.red[1] > 0.0 || !isfinite(Gm.red[0])) { Gm.status = ROW_NUMERIC; Gm.stop = 1; Gm.early = 1; }
                 else if (Gm.red[0] == 0.0) { Gm.status = ROW_ZERO; Gm.stop = 1; Gm.early = 1; }
             }
             __syncthreads();
         }
-        const float sumy = Gm.sumy;
+        // The row is solved in units of its mean intensity ybar: y / ybar and
+        // t / sqrt(ybar), scaled back on output.  The minimiser is the same up
+        // to rounding, and the quartic line-search coefficients, which grow as
+        // the fourth power of the intensity scale, stay inside FP32 range for
+        // raw camera counts too.
+        const float ybar = Gm.sumy / (float)K;
+        const bool scaled = ybar > 0.f && isfinite(ybar);
+        const float yinv = scaled ? 1.f / ybar : 1.f;
+        const float tsc = scaled ? sqrtf(ybar) : 1.f;  // t = tsc * (normalised t)
+        const float tinv = 1.f / tsc;
+#pragma unroll
+        for (int e = 0; e < E; e++) yv[e] *= yinv;
+        const float sumy = Gm.sumy * yinv;
         const float JN = (float)J * N;
 
         if (!Gm.stop) {
             // ---- initialisation ----
             if (P.T_init) {
-                for (int i = tid; i < nmine; i += BT) ts[i] = P.T_init[(size_t)row * N + lo + i];
+                for (int i = tid; i < nmine; i += BT) ts[i] = cscale(P.T_init[(size_t)row * N + lo + i], tinv);
             } else if (P.init == INIT_BP) {
                 float2 u[E];
 #pragma unroll
@@ -587,7 +599,7 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
 
             // ---- per-row selection: a proposed start (learned initialiser) against this one ----
             if (P.T_cand) {
-                for (int i = tid; i < nmine; i += BT) gs[i] = P.T_cand[(size_t)row * N + lo + i];
+                for (int i = tid; i < nmine; i += BT) gs[i] = cscale(P.T_cand[(size_t)row * N + lo + i], tinv);
                 float fv[2];
                 for (int c = 0; c < 2; c++) {  // f at the start above, then at the proposal
                     __syncthreads();
@@ -854,18 +866,21 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
         // ---- outputs (rows decided before initialisation come back as zero) ----
         const bool early = Gm.early != 0;
         for (int i = tid; i < nmine; i += BT)
-            P.T_out[(size_t)row * N + lo + i] = early ? make_float2(0.f, 0.f) : ts[i];
+            P.T_out[(size_t)row * N + lo + i] = early ? make_float2(0.f, 0.f) : cscale(ts[i], tsc);
         if (jr == 0 && tid == 0) {
             if (P.row_status) P.row_status[row] = Gm.status;
             if (P.row_iters) P.row_iters[row] = Gm.done;
-            if (P.row_loss)
-                P.row_loss[row] = early ? (Gm.status == ROW_ZERO ? 0.f : __int_as_float(0x7fc00000)) : (float)Gm.f;
+            if (P.row_loss) {
+                const double f2 = scaled ? (double)ybar * (double)ybar : 1.0;  // f scales as y^2
+                P.row_loss[row] = early ? (Gm.status == ROW_ZERO ? 0.f : __int_as_float(0x7fc00000))
+                                        : (float)((double)Gm.f * f2);
+            }
         }
         if (P.Zd) {
 #pragma unroll
             for (int e = 0; e < E; e++) {
                 const int pat = jm * N + ttid + e * NT;
-                if (valid(e) && pat < P.Nd) P.Zd[(size_t)pat * M + row] = early ? make_float2(0.f, 0.f) : z[e];
+                if (valid(e) && pat < P.Nd) P.Zd[(size_t)pat * M + row] = early ? make_float2(0.f, 0.f) : cscale(z[e], tsc);
             }
         }
         __syncthreads();

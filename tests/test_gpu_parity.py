@@ -320,3 +320,35 @@ def test_retriever_matches_the_functions():
         torch.cuda.synchronize()
     for a, b in ((Yr, Yf), (lr, lf), (Gr, Gf), (out["T"], Tf), (out["status"], sf), (Ydr, Ydf)):
         np.testing.assert_array_equal(to_np(a), to_np(b))
+
+
+def test_intensity_scale_invariance():
+    """f(c t') with y' = c^2 y is c^4 f(t'), so the minimiser scales by sqrt(c)
+    (Eq. optTMsmall2).  A power-of-two scale passes through the row
+    normalisation exactly: T(4096 y) = 64 T(y) and the loss 2^24 times, bit for
+    bit.  Photon-count scale (y ~ 1e4 per pixel, where the quartic's c4 would
+    leave FP32 range without the normalisation) gives the same fidelities."""
+    N, M, J, iters = 1024, 6, 4, 60
+    T, d, Y = problem(N, M, J, seed=61, tm="modes", R=300)
+    opt = dict(init=tmr.TMR_INIT_SPECTRAL, power_iters=50)
+
+    def run(Yin):
+        To = torch.empty((M, N), dtype=torch.complex64, device="cuda")
+        st = torch.empty(M, dtype=torch.int32, device="cuda")
+        it = torch.empty(M, dtype=torch.int32, device="cuda")
+        lo = torch.empty(M, dtype=torch.float32, device="cuda")
+        with handle(N, M, J, d, **opt) as h:
+            tmr.tmr_retrieve(h, to_dev(f32(Yin)), None, iters, To, st, it, lo)
+            torch.cuda.synchronize()
+        return to_np(To), to_np(st), to_np(it), to_np(lo)
+
+    T1, s1, i1, l1 = run(Y)
+    T2, s2, i2, l2 = run(Y * np.float32(4096.0))
+    assert np.array_equal(T2, T1 * np.float32(64.0))
+    assert np.array_equal(l2, l1 * np.float32(2.0 ** 24))
+    assert np.array_equal(s1, s2) and np.array_equal(i1, i2)
+    T3, s3, i3, _ = run(Y * np.float32(1e4 / Y.mean()))
+    f1 = oracle.fidelity_rows(T1, T)
+    f3 = oracle.fidelity_rows(T3, T)
+    assert (i3 > 5).all() and np.median(f1) > 0.99  # no row stopped at the start
+    np.testing.assert_allclose(f3, f1, atol=1e-3)
