@@ -274,6 +274,63 @@ tmr_status tmr_retrieve_rows_static(int N, int M, int J, const void *masks, cons
                                     int *row_status, int *row_iters, float *row_loss,
                                     void *stream);
 
+/* ---- Camera preprocessing (Sec. 2.2, the procedure after Algorithm 1) ----
+ *
+ * Before the per-row solves the paper shrinks the problem in two steps:
+ * half-sampling keeps every other pixel of each intensity image in both
+ * directions (the kept grid samples the transmitted field at twice the camera
+ * pixel size, still enough for the fiber's NA), and a binary fiber mask on
+ * the half grid, whose one-region holds 99.9 % of the total intensity,
+ * decides which rows are solved; the others are zero.
+ *
+ * Half grid.  Rows and columns offset, offset + 2, ... of an H x W frame are
+ * kept (offset 0 reads the paper's "odd indexes" counted from one; 1 keeps
+ * the other phase): ny = (H - offset + 1) / 2, nx = (W - offset + 1) / 2,
+ * M = ny * nx, and grid pixel p = a * nx + b is camera pixel
+ * (2a + offset, 2b + offset).  This p is the row index of T and y.
+ *
+ * Energy and mask.  E[p] = sum over the K frames of frame_i(p): exact in
+ * 64-bit integers for uint16 frames, FP64 for float32 frames, summed in a
+ * fixed order (repeated calls agree bitwise).  With the pixels sorted by E
+ * descending, c is the smallest count whose leading energies sum to at least
+ * energy_frac * sum(E) (compared in FP64), tau is the c-th largest energy and
+ * mask[p] = (E[p] >= tau): ties with the last pixel taken are included.
+ * All-dark frames (sum(E) = 0) give an empty mask. */
+enum { TMR_PIX_U16 = 0, TMR_PIX_F32 = 1 }; /* frame pixel types */
+
+/* Device scratch tmr_preprocess needs for K frames of H x W at this offset,
+ * about 8 * M * (ceil(K / 256) + 1) + M bytes; 0 for invalid sizes. */
+size_t tmr_preprocess_workspace_bytes(int K, int H, int W, int offset);
+
+/* Camera frames -> the rows of the retrieval problem.
+ *   frames     device, [K][H][W] uint16 (TMR_PIX_U16) or float32 (TMR_PIX_F32),
+ *              frame i = probe pattern i = j * N + k (mask-major, as in y);
+ *              float32 frames must be non-negative and finite
+ *   y          device float32 [M][K] (the layout [M][J][N] of tmr_retrieve):
+ *              y[p][i] = frame i at grid pixel p, zero where mask[p] == 0
+ *   mask       device uint8 [M] or NULL: 1 inside the fiber mask
+ *   energy     device float64 [M] or NULL: E[p]
+ *   n_inside   device int32 [1] or NULL: pixels inside the mask; -1 when a
+ *              float32 frame set gave a negative or non-finite energy (the
+ *              mask is then empty and y all zero)
+ *   workspace  device scratch of at least tmr_preprocess_workspace_bytes
+ *   stream     cudaStream_t, NULL for the legacy default stream
+ * All arrays are the caller's and must be device memory.  Argument errors
+ * (sizes, offset not 0/1, energy_frac outside (0, 1], pixel_type, NULL or
+ * host pointers, a short workspace, K above 65535 * 256) return
+ * TMR_ERR_INVALID_ARG synchronously; otherwise the call is asynchronous on
+ * `stream` and allocates nothing. */
+tmr_status tmr_preprocess(const void *frames, int pixel_type, int K, int H, int W, int offset,
+                          double energy_frac, float *y, unsigned char *mask, double *energy,
+                          int *n_inside, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Half-sampling alone: out[i][p] = frame i at grid pixel p, for n frames
+ * [n][H][W] (uint16 or float32, device) into device float32 [n][M].  Used for
+ * the defocus images, whose layout [n_defocus][M] is already y_def's.  Same
+ * argument rules as tmr_preprocess; asynchronous on `stream`. */
+tmr_status tmr_half_sample(const void *frames, int pixel_type, int n, int H, int W, int offset,
+                           float *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,6 +21,7 @@ TMR_INIT_RANDOM, TMR_INIT_BP, TMR_INIT_SPECTRAL, TMR_INIT_LEARNED = 0, 1, 2, 3
 TMR_ROW_MAXITER, TMR_ROW_CONVERGED, TMR_ROW_ZERO, TMR_ROW_NUMERIC = 0, 1, 2, 3
 TMR_PREC_FP32 = 0
 TMR_PREC_MIXED = 1
+TMR_PIX_U16, TMR_PIX_F32 = 0, 1
 INIT = {"random": TMR_INIT_RANDOM, "bp": TMR_INIT_BP, "spectral": TMR_INIT_SPECTRAL,
         "learned": TMR_INIT_LEARNED}
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "TIMEOUT",
@@ -79,6 +80,10 @@ def _load():
         "tmr_destroy": ([H], None),
         "tmr_retrieve_rows_static": ([ip, ip, ip, vp, fp, ip, ctypes.POINTER(tmr_options), vp, vp,
                                       vp, fp, vp], ctypes.c_int),
+        "tmr_preprocess_workspace_bytes": ([ip, ip, ip, ip], ctypes.c_size_t),
+        "tmr_preprocess": ([vp, ip, ip, ip, ip, ip, ctypes.c_double, fp, vp, dp, vp, vp, ctypes.c_size_t,
+                            vp], ctypes.c_int),
+        "tmr_half_sample": ([vp, ip, ip, ip, ip, ip, fp, vp], ctypes.c_int),
     }
     for name, (args, res) in sigs.items():
         f = getattr(L, name)
@@ -111,7 +116,7 @@ def _ptr(x, dtype=None, count=None, name="array"):
         import torch
         if dtype is not None:
             want = {"c64": torch.complex64, "f32": torch.float32, "i32": torch.int32,
-                    "f64": torch.float64}[dtype]
+                    "f64": torch.float64, "u8": torch.uint8}[dtype]
             if x.dtype != want:
                 raise TypeError(f"{name}: dtype {x.dtype}, expected {want}")
         if not x.is_contiguous():
@@ -122,7 +127,8 @@ def _ptr(x, dtype=None, count=None, name="array"):
     import numpy as np
     if isinstance(x, np.ndarray):
         if dtype is not None:
-            want = {"c64": np.complex64, "f32": np.float32, "i32": np.int32, "f64": np.float64}[dtype]
+            want = {"c64": np.complex64, "f32": np.float32, "i32": np.int32, "f64": np.float64,
+                    "u8": np.uint8}[dtype]
             if x.dtype != want:
                 raise TypeError(f"{name}: dtype {x.dtype}, expected {want}")
         if not x.flags["C_CONTIGUOUS"]:
@@ -340,3 +346,66 @@ def tmr_retrieve_rows_static(N, M, J, masks, y, iters, opt, T_out, row_status=No
         _ptr(T_out, "c64", M * N, "T_out"), _ptr(row_status, "i32", M, "row_status"),
         _ptr(row_iters, "i32", M, "row_iters"), _ptr(row_loss, "f32", M, "row_loss"),
         ctypes.c_void_p(stream) if stream else None))
+
+
+# ---- camera preprocessing ----------------------------------------------------
+def half_grid(H: int, W: int, offset: int = 0) -> tuple[int, int]:
+    """(ny, nx) of the half-sampled grid of an H x W frame."""
+    return (int(H) - offset + 1) // 2, (int(W) - offset + 1) // 2
+
+
+def _frames(frames, count):
+    """(pointer, pixel type) of a frame stack: uint16 (or int16 holding the same
+    bits) -> TMR_PIX_U16, float32 -> TMR_PIX_F32."""
+    mod = type(frames).__module__
+    if mod.startswith("torch"):
+        import torch
+        names = {torch.int16: TMR_PIX_U16, torch.float32: TMR_PIX_F32}
+        if hasattr(torch, "uint16"):
+            names[torch.uint16] = TMR_PIX_U16
+        kind = names.get(frames.dtype)
+        ok_contig = frames.is_contiguous()
+        n = frames.numel()
+        ptr = frames.data_ptr()
+    else:
+        import numpy as np
+        frames = np.asarray(frames)
+        kind = {np.dtype(np.uint16): TMR_PIX_U16, np.dtype(np.int16): TMR_PIX_U16,
+                np.dtype(np.float32): TMR_PIX_F32}.get(frames.dtype)
+        ok_contig = frames.flags["C_CONTIGUOUS"]
+        n = frames.size
+        ptr = frames.ctypes.data
+    if kind is None:
+        raise TypeError(f"frames: dtype {frames.dtype}, expected uint16 (or int16 bits) or float32")
+    if not ok_contig:
+        raise ValueError("frames: not contiguous")
+    if n != count:
+        raise ValueError(f"frames: {n} elements, expected {count}")
+    return ctypes.c_void_p(ptr), kind
+
+
+def tmr_preprocess_workspace_bytes(K: int, H: int, W: int, offset: int = 0) -> int:
+    return int(lib.tmr_preprocess_workspace_bytes(int(K), int(H), int(W), int(offset)))
+
+
+def tmr_preprocess(frames, K, H, W, offset, energy_frac, y, mask=None, energy=None, n_inside=None,
+                   workspace=None, workspace_bytes=0, stream=None):
+    """Camera frames [K][H][W] -> rows y [M][K], fiber mask, energies, count (device arrays)."""
+    ny, nx = half_grid(H, W, offset)
+    M = max(ny, 0) * max(nx, 0)
+    fp_, kind = _frames(frames, int(K) * int(H) * int(W))
+    _check(lib.tmr_preprocess(
+        fp_, kind, int(K), int(H), int(W), int(offset), float(energy_frac),
+        _ptr(y, "f32", M * int(K), "y"), _ptr(mask, "u8", M, "mask"), _ptr(energy, "f64", M, "energy"),
+        _ptr(n_inside, "i32", 1, "n_inside"), _ptr(workspace, None, None, "workspace"),
+        int(workspace_bytes), ctypes.c_void_p(stream) if stream else None))
+
+
+def tmr_half_sample(frames, n, H, W, offset, out, stream=None):
+    """Half-sampled frames: out [n][M] float32 (device arrays)."""
+    ny, nx = half_grid(H, W, offset)
+    M = max(ny, 0) * max(nx, 0)
+    fp_, kind = _frames(frames, int(n) * int(H) * int(W))
+    _check(lib.tmr_half_sample(fp_, kind, int(n), int(H), int(W), int(offset),
+                               _ptr(out, "f32", int(n) * M, "out"),
+                               ctypes.c_void_p(stream) if stream else None))

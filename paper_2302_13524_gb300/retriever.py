@@ -113,3 +113,30 @@ class Retriever:
 
     def __exit__(self, *a):
         self.close()
+
+
+def preprocess(frames: torch.Tensor, H: int | None = None, W: int | None = None, offset: int = 0,
+               energy_frac: float = 0.999, stream: torch.cuda.Stream | None = None) -> dict:
+    """Camera frames [K, H, W] (CUDA uint16, int16 holding uint16 bits, or float32)
+    -> dict(y [M, K] float32, mask [M] uint8, energy [M] float64, n_inside [1] int32),
+    the half-sampled, fiber-masked rows of Sec. 2.2 (tmr_preprocess).  y viewed as
+    [M, J, N] is the input of Retriever.retrieve."""
+    if not isinstance(frames, torch.Tensor) or not frames.is_cuda:
+        raise TypeError("frames: a CUDA tensor is expected")
+    if frames.dim() != 3:
+        raise ValueError("frames: shape [K, H, W] expected")
+    K, H, W = frames.shape
+    ny, nx = _lib.half_grid(H, W, offset)
+    M = ny * nx
+    dev = frames.device
+    out = dict(y=torch.empty((M, K), dtype=torch.float32, device=dev),
+               mask=torch.empty((M,), dtype=torch.uint8, device=dev),
+               energy=torch.empty((M,), dtype=torch.float64, device=dev),
+               n_inside=torch.empty((1,), dtype=torch.int32, device=dev))
+    wb = _lib.tmr_preprocess_workspace_bytes(K, H, W, offset)
+    ws = torch.empty((max(wb, 1),), dtype=torch.uint8, device=dev)
+    _lib.tmr_preprocess(frames.contiguous(), K, H, W, offset, energy_frac, out["y"], out["mask"],
+                        out["energy"], out["n_inside"], ws, wb,
+                        stream=stream.cuda_stream if stream is not None else None)
+    out["workspace"] = ws  # kept alive until the asynchronous call has run
+    return out

@@ -151,11 +151,13 @@ def camera_frames(K: int, H: int, W: int, photons: float = 2000.0, dark: float =
     clipped at 65535; float32 frames keep the counts as floats."""
     rng = np.random.default_rng([seed, STREAM_CAMERA])
     core = fiber_disc(H, W, radius).reshape(H, W)
-    lam = rng.exponential(photons, size=(K, H, W)) * core + dark
-    counts = rng.poisson(lam)
-    if np.dtype(dtype) == np.uint16:
-        return np.minimum(counts, 65535).astype(np.uint16)
-    return counts.astype(dtype)
+    out = np.empty((K, H, W), dtype=dtype)
+    for k0 in range(0, K, 256):  # frame blocks bound the temporaries
+        k1 = min(K, k0 + 256)
+        lam = rng.exponential(photons, size=(k1 - k0, H, W)) * core + dark
+        counts = rng.poisson(lam)
+        out[k0:k1] = np.minimum(counts, 65535) if np.dtype(dtype) == np.uint16 else counts
+    return out
 
 
 def sample_rows(M: int, n: int, seed: int = 0) -> np.ndarray:
