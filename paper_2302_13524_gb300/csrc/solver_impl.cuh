@@ -81,6 +81,7 @@ struct Gram {
     float Sg[kSlots], Yg[kSlots];
     float c1[kSlots], c2[kSlots];  // direction coefficients by age (c2 includes gamma)
     float gamma, gg, f, sumy, alpha;
+    float yscale, tsc;  // the row's intensity scale 4^-j and its t scale 2^j
     float red[kParts];  // the last cluster-wide sums
     int slot[kSlots];
     int np;
@@ -250,6 +251,19 @@ static __device__ float quartic_argmin(const float *c)
 // broadcasting the new unknown with a shuffle.  Falls back to p = -g (and
 // clears the history) when there is no pair or the result is not a descent
 // direction.
+// Exponent j of a row's intensity scale: with the mean intensity ybar in
+// [2^(e-1), 2^e), j = floor(e / 2), so y 4^-j has a mean in [1/2, 2), rows
+// whose mean is already there keep j = 0, and scaling y by 4^k moves j by
+// exactly k; 0 for a non-positive or non-finite mean.
+static __device__ __forceinline__ int row_scale_exp(float sumy, int K)
+{
+    const float yb = sumy / (float)K;
+    if (!(yb > 0.f) || !isfinite(yb)) return 0;
+    int e;
+    frexpf(yb, &e);
+    return e >> 1;  // floor(e / 2) for either sign
+}
+
 static __device__ void lbfgs_coefficients_warp(Gram &G, int lane)
 {
     const int np = G.np;
@@ -513,29 +527,34 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
                 Gm.stop = 0;
                 Gm.early = 0;
                 Gm.sumy = Gm.red[0];
+                const int js = row_scale_exp(Gm.red[0], K);
+                Gm.yscale = ldexpf(1.f, -2 * js);
+                Gm.tsc = ldexpf(1.f, js);
                 if (Gm.red[1] > 0.0 || !isfinite(Gm.red[0])) { Gm.status = ROW_NUMERIC; Gm.stop = 1; Gm.early = 1; }
                 else if (Gm.red[0] == 0.0) { Gm.status = ROW_ZERO; Gm.stop = 1; Gm.early = 1; }
             }
             __syncthreads();
         }
-        // The row is solved in units of its mean intensity ybar: y / ybar and
-        // t / sqrt(ybar), scaled back on output.  The minimiser is the same up
-        // to rounding, and the quartic line-search coefficients, which grow as
-        // the fourth power of the intensity scale, stay inside FP32 range for
-        // raw camera counts too.
-        const float ybar = Gm.sumy / (float)K;
-        const bool scaled = ybar > 0.f && isfinite(ybar);
-        const float yinv = scaled ? 1.f / ybar : 1.f;
-        const float tsc = scaled ? sqrtf(ybar) : 1.f;  // t = tsc * (normalised t)
-        const float tinv = 1.f / tsc;
+        // The row is solved with y 4^-j and t 2^-j, scaled back on output,
+        // where 4^j is a power of four near its mean intensity (j = 0 for a
+        // mean in [1/2, 2)).  Eq. optTMsmall2 is homogeneous, and a scale by
+        // a power of two is exact, so every row takes the same steps as the
+        // unscaled problem would in exact-range arithmetic; the quartic
+        // line-search coefficients, which grow as the fourth power of the
+        // intensity scale, stay inside FP32 range for raw camera counts.  (The
+        // scales live in shared memory, not in registers through the loop.)
+        {
+            const float ysc = Gm.yscale;
 #pragma unroll
-        for (int e = 0; e < E; e++) yv[e] *= yinv;
-        const float sumy = Gm.sumy * yinv;
+            for (int e = 0; e < E; e++) yv[e] *= ysc;
+        }
+        const float sumy = Gm.sumy * Gm.yscale;
         const float JN = (float)J * N;
 
         if (!Gm.stop) {
             // ---- initialisation ----
             if (P.T_init) {
+                const float tinv = 1.f / Gm.tsc;  // t = 2^j (normalised t)
                 for (int i = tid; i < nmine; i += BT) ts[i] = cscale(P.T_init[(size_t)row * N + lo + i], tinv);
             } else if (P.init == INIT_BP) {
                 float2 u[E];
@@ -599,6 +618,7 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
 
             // ---- per-row selection: a proposed start (learned initialiser) against this one ----
             if (P.T_cand) {
+                const float tinv = 1.f / Gm.tsc;
                 for (int i = tid; i < nmine; i += BT) gs[i] = cscale(P.T_cand[(size_t)row * N + lo + i], tinv);
                 float fv[2];
                 for (int c = 0; c < 2; c++) {  // f at the start above, then at the proposal
@@ -865,13 +885,14 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
 
         // ---- outputs (rows decided before initialisation come back as zero) ----
         const bool early = Gm.early != 0;
+        const float tsc = Gm.tsc;
         for (int i = tid; i < nmine; i += BT)
             P.T_out[(size_t)row * N + lo + i] = early ? make_float2(0.f, 0.f) : cscale(ts[i], tsc);
         if (jr == 0 && tid == 0) {
             if (P.row_status) P.row_status[row] = Gm.status;
             if (P.row_iters) P.row_iters[row] = Gm.done;
             if (P.row_loss) {
-                const double f2 = scaled ? (double)ybar * (double)ybar : 1.0;  // f scales as y^2
+                const double f2 = (double)tsc * tsc * tsc * tsc;  // f scales as y^2 = t^4
                 P.row_loss[row] = early ? (Gm.status == ROW_ZERO ? 0.f : __int_as_float(0x7fc00000))
                                         : (float)((double)Gm.f * f2);
             }
