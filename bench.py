@@ -474,28 +474,48 @@ def main():
     # ---- smallest budget that meets the 0.99 bar (the whole retrieve, phase
     # fit included): mean fidelity >= 0.99 and the fraction of rows >= 0.99
     # within 0.5 % of the configured budget's ----
+    # The budget has two parts, the power iterations of the spectral start and
+    # the L-BFGS iterations; for each start length the smallest L-BFGS budget
+    # that passes is timed, and the fastest passing pair is reported.
     to099 = None
     if not args.no_sweep and args.iters > 10:
         ref_frac = float(np.mean(fid >= 0.99))
-        for it in (10, 20, 30, 50, 75):
-            if it >= args.iters:
-                break
-            tmr.tmr_retrieve(h, y, y_def, it, T_out, status)  # warm (graph, staging)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            tmr.tmr_retrieve(h, y, y_def, it, T_out, status)
-            e1.record(stream)
-            e1.synchronize()
-            f_it = fidelity(T_out, Tg).float().cpu().numpy()
-            if cam:
-                f_it = f_it[disc]
-            if f_it.mean() >= 0.99 and np.mean(f_it >= 0.99) >= ref_frac - 0.005:
-                t_it = e0.elapsed_time(e1)
-                to099 = {"iters": it, "value": world * M / (t_it / 1e3), "unit": UNIT, "ms_per_step": t_it,
-                         "mean": float(f_it.mean()), "frac_ge_0.99": float(np.mean(f_it >= 0.99)),
-                         "criterion": "mean >= 0.99 and rows >= 0.99 within 0.5 % of the configured budget's"}
-                break
+        tried = []
+        for pits in sorted({args.power_iters, 50, 30}, reverse=True):
+            if pits > args.power_iters:
+                continue
+            hp = h if pits == args.power_iters else tmr.tmr_create(
+                N, M, J, dg, dop, dict(opt, power_iters=pits), stream=stream.cuda_stream)
+            for it in (10, 20, 30, 50, 75):
+                if it >= args.iters:
+                    break
+                if cam:
+                    preprocess()
+                tmr.tmr_retrieve(hp, y, y_def, it, T_out, status)  # warm (graph, staging)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if cam:
+                    preprocess()
+                tmr.tmr_retrieve(hp, y, y_def, it, T_out, status)
+                e1.record(stream)
+                e1.synchronize()
+                f_it = fidelity(T_out, Tg).float().cpu().numpy()
+                if cam:
+                    f_it = f_it[disc]
+                if f_it.mean() >= 0.99 and np.mean(f_it >= 0.99) >= ref_frac - 0.005:
+                    t_it = e0.elapsed_time(e1)
+                    tried.append({"power_iters": pits, "iters": it, "value": world * M / (t_it / 1e3),
+                                  "unit": UNIT, "ms_per_step": t_it, "mean": float(f_it.mean()),
+                                  "frac_ge_0.99": float(np.mean(f_it >= 0.99))})
+                    break
+            if hp is not h:
+                hp.close()
+        if tried:
+            to099 = dict(max(tried, key=lambda r: r["value"]))
+            to099["criterion"] = ("mean >= 0.99 and rows >= 0.99 within 0.5 % of the configured budget's; "
+                                  "fastest passing (power, L-BFGS) pair")
+            to099["passing"] = [{k: r[k] for k in ("power_iters", "iters", "value")} for r in tried]
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None  # (the camera step's preprocessing takes device frames only)
