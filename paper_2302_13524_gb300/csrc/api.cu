@@ -33,6 +33,17 @@ void tmr::set_last_error(const char *msg)
     snprintf(g_last_error_buf, sizeof(g_last_error_buf), "%s", msg);
 }
 
+bool tmr::is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 namespace {
 
 tmr_status fail(tmr_status st, const std::string &msg)
@@ -52,17 +63,6 @@ tmr_status cuda_fail(cudaError_t e, const char *what)
         cudaError_t e__ = (call);                 \
         if (e__ != cudaSuccess) return cuda_fail(e__, what); \
     } while (0)
-
-bool is_device_ptr(const void *p)
-{
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
 
 }  // namespace
 

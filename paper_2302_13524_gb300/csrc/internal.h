@@ -11,6 +11,10 @@ namespace tmr {
 // Message returned by tmr_last_error() on this thread (fixed buffer, no heap).
 void set_last_error(const char *msg);
 
+// True when p is device (or managed) memory; false for NULL, host memory and
+// pointers the runtime does not know (the lookup error is cleared).
+bool is_device_ptr(const void *p);
+
 // Twiddle table of the block FFT for length N (FP64 on the host, rounded to
 // FP32); returns its length in float2, writes it to out when out != NULL.
 int fft_table(int N, float2 *out);

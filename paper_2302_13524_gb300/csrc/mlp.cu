@@ -255,16 +255,7 @@ tmr_status mfail(tmr_status st, const char *msg)
     return st;
 }
 
-bool dev_ptr(const void *p)
-{
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+bool dev_ptr(const void *p) { return tmr::is_device_ptr(p); }
 
 int ew_blocks(size_t n)
 {

@@ -64,15 +64,7 @@ cudaError_t fill_twiddles(int N, float2 *tw, cudaStream_t s)
     return cudaGetLastError();
 }
 
-bool device_ptr(const void *p)
-{
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+bool device_ptr(const void *p) { return tmr::is_device_ptr(p); }
 
 }  // namespace
 

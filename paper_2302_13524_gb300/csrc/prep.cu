@@ -34,15 +34,7 @@ tmr_status fail(tmr_status st, const char *msg)
     return st;
 }
 
-bool device_ptr(const void *p)
-{
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+bool device_ptr(const void *p) { return tmr::is_device_ptr(p); }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
