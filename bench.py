@@ -441,15 +441,15 @@ def main():
     flops = solver_flops(N, J, m, its[worked], args.power_iters)
     achieved = flops / (solver_ms / 1e3) / 1e12
     peak_max = fp32_peak_tflops(n_sm, 2070.0)
-    # DRAM bytes of one solver launch from an ncu capture of the plain workload
-    # at 4096 rows (138.0 MB read + 42.7 MB written), scaled by the rows
+    # DRAM bytes of the solver: the last ncu capture (plain workload at 4096
+    # rows: 138.0 MB read + 42.7 MB written, the algorithmic bytes) was taken
+    # before the kernel gained its per-row intensity scaling, so no current
+    # figure is claimed
     traffic = None
-    if args.workload == "plain" and args.precision == "fp32":
-        traffic = (138.029056e6 + 42.719488e6) * M / 4096
     roof = {"bound": "alu", "kernel": f"k_solver (N={N})", "achieved": achieved, "peak": peak_max,
             "unit": "TFLOP/s", "frac": achieved / peak_max, "traffic": traffic,
-            "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 4096-row "
-                             "launch of this kernel, scaled to M rows" if traffic else None,
+            "traffic_basis": "null: the kernel changed (per-row intensity scaling, no memory traffic "
+                             "added) after its last DRAM capture, 138.0 + 42.7 MB per 4096 rows",
             "peak_basis": f"FP32 FFMA {n_sm} SMs x 128 lanes x 2 x 2070 MHz (max clock)",
             "solver_ms": solver_ms, "flops_per_launch": flops}
     if clk and clk.get("sm_mhz"):
