@@ -36,3 +36,52 @@ def test_header_documents_every_entry_point():
         assert text.count(n) >= 1
     for sec in ("Eq. optTMsmall2", "Eq. derivative", "Eq. optphase", "Eq. phaseoffset"):
         assert sec in text
+
+
+def test_preprocess_workspace_size():
+    """Scratch of tmr_preprocess: one 64-bit energy partial per (256-frame chunk,
+    pixel), one key per pixel, the mask and a flag, each block 256-byte aligned;
+    0 for sizes without a half grid."""
+    tmr = pytest.importorskip("paper_2302_13524_gb300")
+    for K, H, W, off in [(8192, 256, 128, 0), (1, 3, 3, 1), (513, 9, 130, 1), (96, 37, 50, 0)]:
+        ny, nx = tmr.half_grid(H, W, off)
+        M, C = ny * nx, -(-K // 256)
+        low = 8 * M * C + 8 * M + M + 4
+        got = tmr.tmr_preprocess_workspace_bytes(K, H, W, off)
+        assert low <= got <= low + 4 * 256, (K, H, W, off, got, low)
+    for K, H, W, off in [(0, 8, 8, 0), (4, 0, 8, 0), (4, 8, 8, 2), (4, 1, 8, 1), (4, 8, 1, 1), (4, 8, 8, -1)]:
+        assert tmr.tmr_preprocess_workspace_bytes(K, H, W, off) == 0
+
+
+def test_preprocess_argument_errors_before_any_device_work():
+    """Argument checks that precede every CUDA call return INVALID_ARG with a
+    message, on a machine without a GPU too."""
+    tmr = pytest.importorskip("paper_2302_13524_gb300")
+    import ctypes as ct
+    lib = tmr.lib
+    dummy = ct.c_void_p(16)  # never dereferenced: each call fails its checks first
+    cases = [
+        (dummy, tmr.TMR_PIX_U16, 4, 8, 8, 2, 0.9, dummy, dummy, 1 << 20),   # offset
+        (dummy, tmr.TMR_PIX_U16, 0, 8, 8, 0, 0.9, dummy, dummy, 1 << 20),   # K
+        (dummy, tmr.TMR_PIX_U16, 4, 1, 8, 1, 0.9, dummy, dummy, 1 << 20),   # empty half grid
+        (dummy, 7, 4, 8, 8, 0, 0.9, dummy, dummy, 1 << 20),                 # pixel type
+        (dummy, tmr.TMR_PIX_F32, 4, 8, 8, 0, 0.0, dummy, dummy, 1 << 20),   # fraction
+        (dummy, tmr.TMR_PIX_F32, 4, 8, 8, 0, 1.01, dummy, dummy, 1 << 20),  # fraction
+        (dummy, tmr.TMR_PIX_F32, 4, 8, 8, 0, float("nan"), dummy, dummy, 1 << 20),
+        (None, tmr.TMR_PIX_F32, 4, 8, 8, 0, 0.9, dummy, dummy, 1 << 20),    # NULL frames
+        (dummy, tmr.TMR_PIX_F32, 4, 8, 8, 0, 0.9, None, dummy, 1 << 20),    # NULL y
+        (dummy, tmr.TMR_PIX_F32, 4, 8, 8, 0, 0.9, dummy, None, 1 << 20),    # NULL workspace
+        (dummy, tmr.TMR_PIX_F32, 4, 8, 8, 0, 0.9, dummy, dummy, 16),        # short workspace
+        (dummy, tmr.TMR_PIX_U16, 65535 * 256 + 1, 8, 8, 0, 0.9, dummy, dummy, 1 << 40),  # K too large
+    ]
+    for fr, pt, K, H, W, off, frac, y, ws, wb in cases:
+        st = lib.tmr_preprocess(fr, pt, K, H, W, off, frac, y, None, None, None, ws, wb, None)
+        assert st == tmr.TMR_ERR_INVALID_ARG, (pt, K, H, W, off, frac)
+        assert lib.tmr_last_error().decode().startswith("tmr_preprocess")
+    for fr, pt, n, H, W, off, out in [(dummy, tmr.TMR_PIX_U16, 4, 8, 8, 3, dummy), (dummy, 9, 4, 8, 8, 0, dummy),
+                                      (None, tmr.TMR_PIX_U16, 4, 8, 8, 0, dummy),
+                                      (dummy, tmr.TMR_PIX_U16, 4, 8, 8, 0, None)]:
+        assert lib.tmr_half_sample(fr, pt, n, H, W, off, out, None) == tmr.TMR_ERR_INVALID_ARG
+    with pytest.raises(TypeError):
+        import torch
+        tmr.preprocess(torch.zeros((2, 4, 4), dtype=torch.int16))  # not on a GPU
