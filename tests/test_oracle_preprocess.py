@@ -121,3 +121,19 @@ def test_camera_rows_are_the_kept_pixels_pixel_major(offset):
             for i in range(K):
                 assert y[p, i] == (fr[i, r, c] if mask[p] else 0)
     assert mask.any() and not mask.all()
+
+
+def test_camera_frames_generator():
+    """Seeded, shaped and structured as stated: the same seed gives the same
+    frames, the disc is bright and the outside holds only the dark level."""
+    import synth
+    a = synth.camera_frames(300, 20, 30, seed=9)
+    b = synth.camera_frames(300, 20, 30, seed=9)
+    c = synth.camera_frames(300, 20, 30, seed=10)
+    assert a.dtype == np.uint16 and a.shape == (300, 20, 30)
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    core = synth.fiber_disc(20, 30, 0.45).reshape(20, 30)
+    assert core.sum() > 0 and (~core).sum() > 0
+    assert a[:, core].mean() > 1000 and a[:, ~core].mean() < 5
+    f = synth.camera_frames(8, 6, 6, seed=1, dtype=np.float32)
+    assert f.dtype == np.float32 and (f >= 0).all() and np.array_equal(f, np.round(f))
