@@ -118,6 +118,14 @@ typedef struct {
                                0 = chosen by the autotuner (default)                 */
     const char *tune_cache; /* JSON file caching autotuned schedules per device, N, J,
                                m; NULL = this process only                           */
+    long long wait_spins;   /* bound on each device-side wait of the phase-offset fit's
+                               grid barrier, in polls (default 1 << 24, about one
+                               second); when a wait runs out the fit stops, every CTA
+                               returns, phi keeps its last value and tmr_sync
+                               returns TMR_ERR_TIMEOUT                               */
+    int withhold_release;   /* test hook, 0 in normal use: 1 = the fit's grid barrier
+                               is never released, so every wait runs out after
+                               wait_spins polls (exercises the bounded wait)         */
 } tmr_options;
 
 /* Fill *opt with the defaults above. */
@@ -191,8 +199,10 @@ tmr_status tmr_defocus_fit(tmr_handle *h, const void *T_est, const float *y_def,
                            void *T_out);
 
 /* Wait for the handle's stream, at most timeout_s seconds (<= 0: no limit),
- * polling.  Returns TMR_ERR_TIMEOUT when the work is still running,
- * TMR_ERR_NUMERIC when a row of the last retrieve reported non-finite values. */
+ * polling.  Returns TMR_ERR_TIMEOUT when the work is still running or when a
+ * grid-barrier wait of the last phase-offset fit (tmr_retrieve with y_def, or
+ * tmr_defocus_fit) ran out (opt.wait_spins), TMR_ERR_NUMERIC when a row of
+ * the last retrieve reported non-finite values. */
 tmr_status tmr_sync(tmr_handle *h, double timeout_s);
 
 /* Message describing the calling thread's last error ("" if none). */
@@ -250,12 +260,14 @@ void tmr_destroy(tmr_handle *h);
  * the whole device memory budget, loops that cannot afford the device-wide
  * synchronisation a first cudaMalloc may cause, or hosts that forbid device
  * allocation after start-up.  It runs the same persistent solver as
- * tmr_retrieve (initialisation, `iters` L-BFGS iterations of Algorithm 1;
+ * tmr_retrieve (initialisation, then `iters` of the same L-BFGS iterations;
  * no phase-offset fit) with the caller's arrays, all of which must be device
- * memory: masks complex64 [J][N], y float32 [M][J][N], T_out complex64 [M][N],
- * row_status / row_iters int32 [M] and row_loss float32 [M] (each may be NULL).
+ * memory of the current device: masks complex64 [J][N], y float32 [M][J][N],
+ * T_out complex64 [M][N], row_status / row_iters int32 [M] and row_loss
+ * float32 [M] (each may be NULL).
  * opt: NULL for the defaults; workspace_limit, use_graph, schedule and tune_cache
- * are ignored (one mask per CTA).
+ * are ignored (one mask per CTA); opt->precision must be TMR_PREC_FP32
+ * (TMR_ERR_UNSUPPORTED otherwise).
  * stream: cudaStream_t, NULL for the legacy default stream.
  *
  * Its only scratch (a row work counter and the FFT twiddle table) lives in
@@ -264,7 +276,9 @@ void tmr_destroy(tmr_handle *h);
  * 1 <= opt->m <= 6; larger sizes return TMR_ERR_UNSUPPORTED with a message.
  * It calls no cudaMalloc, cudaFree or other allocating routine.  The first
  * call on a device looks up the array's device address (once per device, with
- * that device current); make that first call before any stream capture.
+ * that device current) and keeps it until the process exits; make that first
+ * call before any stream capture, and do not use the entry point on a device
+ * after a cudaDeviceReset of that device (the array may have moved).
  * Every call on a device shares the array and rewrites it (the counter is
  * cleared, the table refilled), so calls whose work overlaps on the GPU -- on
  * different streams, or from different threads -- race and must be ordered

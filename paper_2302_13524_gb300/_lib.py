@@ -39,7 +39,8 @@ class tmr_options(ctypes.Structure):
                 ("power_iters", ctypes.c_int), ("clip", ctypes.c_double), ("tol", ctypes.c_double),
                 ("phase_iters", ctypes.c_int), ("precision", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("workspace_limit", ctypes.c_size_t),
-                ("schedule", ctypes.c_int), ("tune_cache", ctypes.c_char_p)]
+                ("schedule", ctypes.c_int), ("tune_cache", ctypes.c_char_p),
+                ("wait_spins", ctypes.c_longlong), ("withhold_release", ctypes.c_int)]
 
 
 class tmr_defocus_op(ctypes.Structure):

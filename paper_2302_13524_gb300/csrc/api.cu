@@ -33,16 +33,25 @@ void tmr::set_last_error(const char *msg)
     snprintf(g_last_error_buf, sizeof(g_last_error_buf), "%s", msg);
 }
 
-bool tmr::is_device_ptr(const void *p)
+int tmr::pointer_class(const void *p)
 {
-    if (!p) return false;
+    if (!p) return PTR_HOST;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return PTR_HOST;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return PTR_DEVICE;
+    if (a.type != cudaMemoryTypeDevice) return PTR_HOST;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return PTR_OTHER_DEVICE;
+    }
+    return a.device == dev ? PTR_DEVICE : PTR_OTHER_DEVICE;
 }
+
+bool tmr::is_device_ptr(const void *p) { return pointer_class(p) == PTR_DEVICE; }
 
 namespace {
 
@@ -135,10 +144,13 @@ void hfree(tmr_handle *h, void *p, size_t bytes)
 // otherwise a staging buffer (copied in when `in`).
 tmr_status stage(tmr_handle *h, int slot, const void *src, size_t bytes, bool in, void **dev)
 {
-    if (is_device_ptr(src)) {
+    const int pc = pointer_class(src);
+    if (pc == PTR_DEVICE) {
         *dev = const_cast<void *>(src);
         return TMR_OK;
     }
+    if (pc == PTR_OTHER_DEVICE)
+        return fail(TMR_ERR_INVALID_ARG, "array lives on another device than the current one");
     DevBuf &b = h->stage[slot];
     if (b.bytes < bytes) {
         hfree(h, b.p, b.bytes);
@@ -333,6 +345,8 @@ void tmr_default_options(tmr_options *o)
     o->workspace_limit = 0;
     o->schedule = 0;
     o->tune_cache = nullptr;
+    o->wait_spins = 1LL << 24;
+    o->withhold_release = 0;
 }
 
 int tmr_schedule(const tmr_handle *h) { return h ? h->G : 0; }
@@ -395,6 +409,8 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     if (o.m < 1 || o.m > kMaxMem) return fail(TMR_ERR_INVALID_ARG, "opt.m must be in 1..6");
     if (o.init < TMR_INIT_RANDOM || o.init > TMR_INIT_LEARNED) return fail(TMR_ERR_INVALID_ARG, "opt.init");
     if (o.power_iters < 0 || o.phase_iters < 0 || o.tol < 0) return fail(TMR_ERR_INVALID_ARG, "negative option");
+    if (o.wait_spins < 1 || o.wait_spins > (1LL << 40))
+        return fail(TMR_ERR_INVALID_ARG, "opt.wait_spins must be in 1..2^40");
     if (o.precision != TMR_PREC_FP32 && o.precision != TMR_PREC_MIXED)
         return fail(TMR_ERR_INVALID_ARG, "opt.precision must be TMR_PREC_FP32 or TMR_PREC_MIXED");
     if (o.precision == TMR_PREC_MIXED && !mixed_supported(N))
@@ -600,6 +616,8 @@ static tmr_status run_phase_fit(tmr_handle *h, const float2 *Tin, const float *d
     p.err = h->pf_err;
     p.iters_done = h->pf_iters;
     p.loss_out = h->pf_loss;
+    p.wait_spins = h->opt.wait_spins;
+    p.withhold_release = h->opt.withhold_release != 0;
     TMR_CUDA(launch_phase_fit(p, h->stream), "phase-fit kernel");
     if (Tout) TMR_CUDA(launch_apply_phase(h->N, h->M, dphi, Tin, Tout, h->stream), "apply phase");
     return TMR_OK;
@@ -799,6 +817,8 @@ tmr_status tmr_defocus_fit(tmr_handle *h, const void *T_est, const float *y_def,
     if ((st = run_phase_fit(h, (const float2 *)dT, (const float *)dY, dP ? (double *)dP : h->phi,
                             (float2 *)dO)) != TMR_OK)
         return st;
+    h->last_status = nullptr;  // no rows were solved: tmr_sync checks the fit's flag only
+    h->last_had_fit = true;
     bool synced = false;
     if (phi && (st = unstage(h, phi, dP, sizeof(double) * h->M, &synced)) != TMR_OK) return st;
     if (T_out && (st = unstage(h, T_out, dO, sizeof(float2) * MN, &synced)) != TMR_OK) return st;

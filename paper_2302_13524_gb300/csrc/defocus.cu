@@ -230,8 +230,12 @@ cudaError_t launch_defocus_forward(int ny, int nx, int Nd, const float2 *Zd, con
 // ---------------------------------------------------------------------------
 // Phase-offset fit.
 
-// bounded grid barrier; bar[0] arrival count, bar[1] generation
-__device__ bool grid_sync(unsigned *bar, int *err)
+// bounded grid barrier; bar[0] arrival count, bar[1] generation.  A wait gives
+// up after `limit` polls (about 64 ns each after the first 4096), raises *err
+// and returns false; so does every CTA that sees *err raised.  `withhold`
+// (a test hook) keeps the last CTA from releasing the others, so that every
+// wait runs out.
+__device__ bool grid_sync(unsigned *bar, int *err, long long limit, bool withhold)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -240,7 +244,7 @@ __device__ bool grid_sync(unsigned *bar, int *err)
         const unsigned gen = *vgen;
         __threadfence();
         const unsigned arrived = atomicAdd(bar, 1u) + 1u;
-        if (arrived == gridDim.x) {
+        if (arrived == gridDim.x && !withhold) {
             atomicExch(bar, 0u);
             __threadfence();
             atomicAdd(bar + 1, 1u);
@@ -250,7 +254,7 @@ __device__ bool grid_sync(unsigned *bar, int *err)
             long long spins = 0;
             while (*vgen == gen) {
                 if (*verr) break;
-                if (++spins > (1LL << 24)) {
+                if (++spins > limit) {
                     atomicExch(err, 1);
                     break;
                 }
@@ -436,7 +440,7 @@ __global__ void __launch_bounds__(512) k_phase_fit(PhaseFitParams Pp)
             }
             W.pdot[(size_t)blockIdx.x * kPfDots + tid] = val;
         }
-        if (!grid_sync(Pp.sync, Pp.err)) return false;
+        if (!grid_sync(Pp.sync, Pp.err, Pp.wait_spins, Pp.withhold_release)) return false;
         if (tid < kPfDots) {
             double acc = 0.0;
             for (int b = 0; b < nb; b++) {
@@ -457,15 +461,27 @@ __global__ void __launch_bounds__(512) k_phase_fit(PhaseFitParams Pp)
         }
     };
 
+    // a wait ran out (or another CTA's did): phi keeps its last accepted value
+    // on my chunk, without the constant-phase normalisation, and the CTA returns
+    auto bail = [&]() {
+        for (int k = k0 + tid; k < k1; k += nt) Pp.phi[k] = W.phi[k];
+    };
+
     // ---- phi = 0: loss and gradient ----
     for (int k = k0 + tid; k < k1; k += nt) {
         W.phi[k] = 0.0;
         W.phit[k] = 0.0;
     }
     write_u(W.phit);
-    if (!grid_sync(Pp.sync, Pp.err)) return;
+    if (!grid_sync(Pp.sync, Pp.err, Pp.wait_spins, Pp.withhold_release)) {
+        bail();
+        return;
+    }
     pf_eval(Pp, W, g, twy, twx, red, out);
-    if (!grid_sync(Pp.sync, Pp.err)) return;
+    if (!grid_sync(Pp.sync, Pp.err, Pp.wait_spins, Pp.withhold_release)) {
+        bail();
+        return;
+    }
     {
         double v[kPfDots] = {0.0};
         double vmax = 0.0;
@@ -476,7 +492,10 @@ __global__ void __launch_bounds__(512) k_phase_fit(PhaseFitParams Pp)
             v[4 * kPfSlots + 1] += s * s;
             vmax = fmax(vmax, fabs(s));
         }
-        if (!grid_dots(v, vmax)) return;
+        if (!grid_dots(v, vmax)) {
+            bail();
+            return;
+        }
     }
     if (tid == 0) {
         double f = 0.0;
@@ -518,9 +537,15 @@ __global__ void __launch_bounds__(512) k_phase_fit(PhaseFitParams Pp)
         for (int h = 0; h <= 30; h++) {
             for (int k = k0 + tid; k < k1; k += nt) W.phit[k] = W.phi[k] + a * W.p[k];
             write_u(W.phit);
-            if (!grid_sync(Pp.sync, Pp.err)) return;
+            if (!grid_sync(Pp.sync, Pp.err, Pp.wait_spins, Pp.withhold_release)) {
+        bail();
+        return;
+    }
             pf_eval(Pp, W, g, twy, twx, red, out);
-            if (!grid_sync(Pp.sync, Pp.err)) return;
+            if (!grid_sync(Pp.sync, Pp.err, Pp.wait_spins, Pp.withhold_release)) {
+        bail();
+        return;
+    }
             ft = 0.0;
             for (int b = 0; b < nb; b++) ft += __ldcg(W.fpart + b);
             if (ft <= f0 + 1e-4 * a * gp) {
@@ -555,7 +580,10 @@ __global__ void __launch_bounds__(512) k_phase_fit(PhaseFitParams Pp)
                 v[4 * kPfSlots + 1] += gn * gn;
                 vmax = fmax(vmax, fabs(gn));
             }
-            if (!grid_dots(v, vmax)) return;
+            if (!grid_dots(v, vmax)) {
+            bail();
+            return;
+        }
             if (tid == 0) {
                 const double *t = G.red;
                 for (int i = 0; i <= np; i++) {
@@ -604,7 +632,10 @@ __global__ void __launch_bounds__(512) k_phase_fit(PhaseFitParams Pp)
             v[0] += wk * c;
             v[1] += wk * s;
         }
-        if (!grid_dots(v, 0.0)) return;
+        if (!grid_dots(v, 0.0)) {
+            bail();
+            return;
+        }
         const double shift = atan2(G.red[1], G.red[0]);
         for (int k = k0 + tid; k < k1; k += nt) Pp.phi[k] = W.phi[k] - shift;
         if (blockIdx.x == 0 && tid == 0) {

@@ -17,8 +17,10 @@
 //
 // Twiddles come from a table with one block per pass p >= 1:
 // tw_p[(r-1) Ns + j] = exp(-2 pi i r j / (Ns R)), r = 1..R-1, j = 0..Ns-1,
-// computed in FP64 on the host and rounded to FP32 (no device trig).  A
-// thread reads its row j contiguously across the warp.
+// computed in FP64 and rounded to FP32: on the host for a handle
+// (tmr::fft_table), on the device for the allocation-free entry point
+// (noalloc.cu; the two agree to 1 ulp of FP32).  A thread reads its row j
+// contiguously across the warp.
 #pragma once
 
 #include "common.cuh"

@@ -11,8 +11,14 @@ namespace tmr {
 // Message returned by tmr_last_error() on this thread (fixed buffer, no heap).
 void set_last_error(const char *msg);
 
-// True when p is device (or managed) memory; false for NULL, host memory and
-// pointers the runtime does not know (the lookup error is cleared).
+// Where a caller array lives: PTR_DEVICE for memory of the current device (or
+// managed memory), PTR_OTHER_DEVICE for device memory of another GPU (which a
+// kernel of this device must not touch: without peer access it faults),
+// PTR_HOST for NULL, host memory and pointers the runtime does not know (the
+// lookup error is cleared).
+enum { PTR_HOST = 0, PTR_DEVICE = 1, PTR_OTHER_DEVICE = 2 };
+int pointer_class(const void *p);
+// pointer_class(p) == PTR_DEVICE
 bool is_device_ptr(const void *p);
 
 // Twiddle table of the block FFT for length N (FP64 on the host, rounded to
@@ -107,6 +113,8 @@ struct PhaseFitParams {
     int *err;            // error flag, zeroed before the launch
     int *iters_done;     // [1]
     double *loss_out;    // [1]
+    long long wait_spins;   // polls before a grid-barrier wait gives up
+    bool withhold_release;  // test hook: the barrier is never released
 };
 size_t phase_fit_workspace_doubles(int P, int Nd, int m, int grid);
 int phase_fit_grid(int ny, int nx, int Nd);

@@ -7,7 +7,18 @@
 // loads the library holds until the process exits.  Host code never passes
 // the symbol itself to a kernel (in host code it is only a stand-in): the
 // device address comes from cudaGetSymbolAddress, fetched once per device
-// with that device current, on the first call made on that device.
+// with that device current, on the first call made on that device, and kept
+// for the life of the process: after cudaDeviceReset the module is loaded
+// again and the array may move, so the entry point must not be used on a
+// device that was reset after its first call there.
+//
+// The twiddle table is filled on the device (k_fill_twiddles, sincospi in
+// FP64 rounded to FP32): the host table of the handle path would have to be
+// copied from pageable host memory, a copy that blocks the calling thread
+// until the stream reaches it.  Both tables round the same FP64
+// angles; an FP64 result one ulp off can move the FP32 rounding by one ulp,
+// so the table agrees with the host table to 1 ulp of FP32 (6e-8 absolute)
+// and the retrieved rows agree with tmr_retrieve's to FP32 rounding.
 #include <cstdio>
 #include <mutex>
 
@@ -78,18 +89,22 @@ extern "C" tmr_status tmr_retrieve_rows_static(int N, int M, int J, const void *
     tmr_default_options(&o);
     if (opt) o = *opt;
     if (N <= 0 || M < 0 || J <= 0 || iters < 0) return fail(TMR_ERR_INVALID_ARG, "bad size or iters");
+    if (M == 0) return TMR_OK;  // no rows: nothing is launched, the arrays are not read
     if (!masks || !y || !T_out) return fail(TMR_ERR_INVALID_ARG, "NULL array");
     if (!tmr::fft_supported(N)) return fail(TMR_ERR_UNSUPPORTED, "N must be a power of two in 64..4096");
     if (J > tmr::kMaxMasks) return fail(TMR_ERR_UNSUPPORTED, "J must be at most 8");
     if (o.m < 1 || o.m > tmr::kMaxMem) return fail(TMR_ERR_INVALID_ARG, "opt.m must be in 1..6");
     if (o.init < TMR_INIT_RANDOM || o.init > TMR_INIT_SPECTRAL || o.power_iters < 0 || o.tol < 0)
         return fail(TMR_ERR_INVALID_ARG, "bad option");
+    if (o.precision != TMR_PREC_FP32)
+        return fail(TMR_ERR_UNSUPPORTED, "the static entry point runs the FP32 solver only (opt.precision)");
     const int twn = tmr::fft_table_len(N);
     if ((size_t)twn * sizeof(float2) + kCounterBytes > kStaticScratchBytes)
         return fail(TMR_ERR_UNSUPPORTED, "twiddle table larger than the static scratch");
     const void *arrays[] = {masks, y, T_out, row_status, row_iters, row_loss};
     for (const void *a : arrays)
-        if (a && !device_ptr(a)) return fail(TMR_ERR_INVALID_ARG, "every array must be device memory");
+        if (a && !device_ptr(a))
+            return fail(TMR_ERR_INVALID_ARG, "every array must be device memory of the current device");
 
     int dev = 0, smem_optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)

@@ -15,6 +15,25 @@ def rel_l2_rows(a, b):
     return float(np.max(np.where(den > 0, num / np.where(den > 0, den, 1), num)))
 
 
+def max_rel_elem_rows(a, b):
+    """max over rows r and entries i of |a_ri - b_ri| / max_i |b_ri| (complex
+    modulus; rows of b that are zero: absolute).  Unlike rel_l2_rows, one
+    wrong entry (a bad bin of one mask, a wrong twiddle at one index) shows at
+    its full size instead of being diluted by the row's norm."""
+    a = np.asarray(a).reshape(a.shape[0], -1)
+    b = np.asarray(b).reshape(b.shape[0], -1)
+    num = np.max(np.abs(a - b), axis=1)
+    den = np.max(np.abs(b), axis=1)
+    return float(np.max(np.where(den > 0, num / np.where(den > 0, den, 1), num)))
+
+
+def assert_rows_close(a, b, tol):
+    """Both measures at the same bar: per-row relative L2 and per-entry error
+    relative to the row's largest entry."""
+    e2, em = rel_l2_rows(a, b), max_rel_elem_rows(a, b)
+    assert e2 <= tol and em <= tol, f"rel L2 {e2:.3e}, max entry {em:.3e}, bar {tol:.1e}"
+
+
 def c64(x):
     return np.ascontiguousarray(x, dtype=np.complex64)
 

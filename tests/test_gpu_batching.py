@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import c64, f32, problem, rel_l2_rows, to_dev, to_np
+from helpers import c64, f32, problem, assert_rows_close, rel_l2_rows, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -39,7 +39,7 @@ def test_schedules_match_oracle(N, J, G):
         torch.cuda.synchronize()
     Tr, _, it_ref, _ = oracle.retrieve_rows(Y, d.astype(np.complex128), iters, T_init=T_init)
     assert np.all(to_np(its) == it_ref)
-    assert rel_l2_rows(to_np(Tn), Tr) <= 1e-4 * iters
+    assert_rows_close(to_np(Tn), Tr, 1e-4 * iters)
 
 
 def test_schedules_agree_on_a_full_spectral_run():

@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import c64, f32, problem, rel_l2_rows, to_dev, to_np
+from helpers import c64, f32, problem, assert_rows_close, rel_l2_rows, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -40,7 +40,7 @@ def test_forward_parity(N, J):
     with handle(N, M, J, d) as h:
         tmr.tmr_forward(h, to_dev(T), Y)
         torch.cuda.synchronize()
-    assert rel_l2_rows(to_np(Y), Y_ref) <= 1e-5
+    assert_rows_close(to_np(Y), Y_ref, 1e-5)
 
 
 @pytest.mark.parametrize("N", BLUE_N)
@@ -56,7 +56,7 @@ def test_grad_parity(N):
         tmr.tmr_grad(h, to_dev(T), to_dev(Y), loss, G)
         torch.cuda.synchronize()
     assert np.max(np.abs(to_np(loss) - loss_ref) / loss_ref) <= 1e-5
-    assert rel_l2_rows(to_np(G), G_ref) <= 1e-5
+    assert_rows_close(to_np(G), G_ref, 1e-5)
 
 
 @pytest.mark.parametrize("N,J", [(100, 4), (2286, 4), (1500, 3)])
@@ -70,7 +70,7 @@ def test_init_parity(N, J, init, pits, tol):
     with handle(N, M, J, d, init=tmr.INIT[init], seed=42, power_iters=pits, clip=2.0) as h:
         tmr.tmr_retrieve(h, to_dev(Y), None, 0, T0)
         torch.cuda.synchronize()
-    assert rel_l2_rows(to_np(T0), T0_ref) <= tol
+    assert_rows_close(to_np(T0), T0_ref, tol)
 
 
 def _perturbed(T, N, seed):
@@ -91,7 +91,7 @@ def test_first_step_parity(N, J):
     for r in range(M):
         ref = oracle.lbfgs_step(Y[r].astype(np.float64), d.astype(np.complex128),
                                 T_init[r].astype(np.complex128))
-        assert rel_l2_rows(to_np(Tn)[r:r + 1], ref["t"][None]) <= 1e-5
+        assert_rows_close(to_np(Tn)[r:r + 1], ref["t"][None], 1e-5)
         assert abs(to_np(loss)[r] - ref["loss"]) <= 1e-4 * ref["loss"] + 1e-6 * np.sum(Y[r] ** 2)
 
 
@@ -107,7 +107,7 @@ def test_few_steps_parity(iters):
         torch.cuda.synchronize()
     Tr, _, it_ref, _ = oracle.retrieve_rows(Y, d.astype(np.complex128), iters, T_init=T_init)
     assert np.all(to_np(its) == it_ref)
-    assert rel_l2_rows(to_np(Tn), Tr) <= 1e-4 * iters
+    assert_rows_close(to_np(Tn), Tr, 1e-4 * iters)
 
 
 def test_small_whole_retrieval_parity():
@@ -188,7 +188,7 @@ def test_batching_full_size_sampled_rows():
         torch.cuda.synchronize()
         Y_clean = to_np(Yg)
         Y_or = oracle.forward(T[rows].astype(np.complex128), d.astype(np.complex128))
-        assert rel_l2_rows(Y_clean[rows], Y_or) <= 1e-5
+        assert_rows_close(Y_clean[rows], Y_or, 1e-5)
         ph = synth.row_photons(cfg, M, seed=0)
         scale = synth.photon_scale(float(Y_clean.mean()), ph)
         Yn = f32(synth.shot_noise(Y_clean, scale, seed=0))
@@ -233,4 +233,4 @@ def test_large_length_needs_a_short_history():
         tmr.tmr_retrieve_from(h, to_dev(T_init), to_dev(Y), None, iters, Tn)
         torch.cuda.synchronize()
     Tr, _, _, _ = oracle.retrieve_rows(Y, d.astype(np.complex128), iters, m=1, T_init=T_init)
-    assert rel_l2_rows(to_np(Tn), Tr) <= 1e-4 * iters
+    assert_rows_close(to_np(Tn), Tr, 1e-4 * iters)

@@ -45,6 +45,40 @@ def test_mlp_forward_and_gradient_match_oracle(dims, B):
     assert np.dot(g, Go) / (np.linalg.norm(g) * np.linalg.norm(Go)) >= 0.999
 
 
+def test_mlp_train_step_is_adam_on_its_gradient():
+    """tmr_mlp_train_step against the oracle's Adam (FP64) parameter by
+    parameter over 5 steps: at each step the gradient the library computes
+    (tmr_mlp_grad, the same kernels the train step runs, deterministic) is fed
+    to oracle.mlp.adam_step with the oracle's own moments, and the library's
+    updated FP32 parameters must match the oracle's to FP32 rounding of the
+    update."""
+    rng = np.random.default_rng(7)
+    dims, B, lr = (24, 16, 12, 10), 9, 3e-3
+    with tmr.tmr_mlp_create(*dims, seed=2) as m:
+        n = m.n_params
+        theta = np.empty(n, np.float32)
+        tmr.tmr_mlp_get_params(m, theta)
+        th_o = theta.astype(np.float64)
+        mo, vo = np.zeros(n), np.zeros(n)
+        G = torch.empty(n, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        for t in range(1, 6):
+            X = to_dev(rng.standard_normal((B, dims[0])).astype(np.float32))
+            T = to_dev(rng.standard_normal((B, dims[3])).astype(np.float32))
+            tmr.tmr_mlp_grad(m, X, T, B, loss, G)
+            G2 = torch.empty_like(G)
+            tmr.tmr_mlp_grad(m, X, T, B, loss, G2)
+            torch.cuda.synchronize()
+            g = to_np(G).astype(np.float64)
+            np.testing.assert_array_equal(to_np(G2), to_np(G))  # deterministic
+            tmr.tmr_mlp_train_step(m, X, T, B, lr, loss)
+            tmr.tmr_mlp_get_params(m, theta)
+            th_o, mo, vo = omlp.adam_step(th_o, g, mo, vo, t, lr=lr)
+            err = np.abs(theta.astype(np.float64) - th_o)
+            assert np.all(err <= 1e-6 * np.abs(th_o) + 1e-4 * lr), (t, float(err.max()))
+            th_o = theta.astype(np.float64)  # continue from the library's FP32 parameters
+
+
 def test_mlp_training_learns_a_smooth_target():
     rng = np.random.default_rng(0)
     dims, B = (64, 128, 128, 16), 128

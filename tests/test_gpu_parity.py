@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import c64, f32, problem, rel_l2_rows, to_dev, to_np
+from helpers import c64, f32, problem, assert_rows_close, rel_l2_rows, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -34,7 +34,7 @@ def test_forward_parity(N, J):
     with handle(N, M, J, d) as h:
         tmr.tmr_forward(h, to_dev(T), Y)
         torch.cuda.synchronize()
-    assert rel_l2_rows(to_np(Y), Y_ref) <= 1e-5
+    assert_rows_close(to_np(Y), Y_ref, 1e-5)
 
 
 @pytest.mark.parametrize("N", ALL_N)
@@ -51,7 +51,7 @@ def test_grad_parity(N):
         tmr.tmr_grad(h, to_dev(T), to_dev(Y), loss, G)
         torch.cuda.synchronize()
     assert np.max(np.abs(to_np(loss) - loss_ref) / loss_ref) <= 1e-5
-    assert rel_l2_rows(to_np(G), G_ref) <= 1e-5
+    assert_rows_close(to_np(G), G_ref, 1e-5)
 
 
 def test_grad_host_buffers_match_device():
@@ -82,7 +82,7 @@ def test_init_parity(N, J, init, pits, tol):
     with handle(N, M, J, d, init=tmr.INIT[init], seed=42, power_iters=pits, clip=2.0) as h:
         tmr.tmr_retrieve(h, to_dev(Y), None, 0, T0)
         torch.cuda.synchronize()
-    assert rel_l2_rows(to_np(T0), T0_ref) <= tol
+    assert_rows_close(to_np(T0), T0_ref, tol)
 
 
 # ------------------------------------------------------------ L-BFGS steps
@@ -100,7 +100,7 @@ def test_first_step_parity(N, J):
     for r in range(M):
         ref = oracle.lbfgs_step(Y[r].astype(np.float64), d.astype(np.complex128),
                                 T_init[r].astype(np.complex128))
-        assert rel_l2_rows(to_np(Tn)[r:r + 1], ref["t"][None]) <= 1e-5
+        assert_rows_close(to_np(Tn)[r:r + 1], ref["t"][None], 1e-5)
         assert abs(to_np(loss)[r] - ref["loss"]) <= 1e-4 * ref["loss"] + 1e-6 * np.sum(Y[r] ** 2)
 
 
@@ -117,7 +117,7 @@ def test_few_steps_parity(iters):
         torch.cuda.synchronize()
     Tr, _, it_ref, _ = oracle.retrieve_rows(Y, d.astype(np.complex128), iters, T_init=T_init)
     assert np.all(to_np(its) == it_ref)
-    assert rel_l2_rows(to_np(Tn), Tr) <= 1e-4 * iters
+    assert_rows_close(to_np(Tn), Tr, 1e-4 * iters)
 
 
 # ------------------------------------------------------------ whole path, tiny
@@ -149,10 +149,16 @@ def test_tiny_whole_path_parity(init):
     fid_g = oracle.fidelity_rows(Tg, T)
     fid_o = oracle.fidelity_rows(ref["T"], T)
     close = np.abs(fid_g - fid_o) <= 1e-3
-    # rows whose FP32 and FP64 trajectories part at a bifurcation of the
-    # non-convex landscape may settle differently; allow 2 % of rows
-    assert close.mean() >= 0.98, (fid_g, fid_o)
-    assert abs(np.mean(fid_g >= 0.99) - np.mean(fid_o >= 0.99)) <= 0.02
+    # per-row fidelity within 1e-3 of the oracle's and equal failure counts,
+    # each to within 1 % of the rows (1 of 128): a row whose FP32 and FP64
+    # trajectories part at a bifurcation of the non-convex landscape may settle
+    # differently.  (The oracle itself moves no row under relative changes of
+    # 6e-8 to y, so the bar is not looser than its own spread.)
+    n_off = int(np.sum(~close))
+    n_fail_g, n_fail_o = int(np.sum(fid_g < 0.99)), int(np.sum(fid_o < 0.99))
+    print(f"{init}: rows off by > 1e-3: {n_off}; failures gpu {n_fail_g} oracle {n_fail_o}")
+    assert n_off <= int(0.01 * M), (fid_g, fid_o)
+    assert abs(n_fail_g - n_fail_o) <= int(0.01 * M)
     if init == "spectral":
         assert np.mean(fid_g) >= 0.97
         # the phase fit ties the rows together: one global phase is left
@@ -171,7 +177,7 @@ def test_defocus_forward_parity():
     with handle(N, M, J, d, dict(ny=ny, nx=nx, n_defocus=Nd, coef=0.05)) as h:
         tmr.tmr_defocus_forward(h, to_dev(T), out)
         torch.cuda.synchronize()
-    assert rel_l2_rows(to_np(out), Yd) <= 1e-5
+    assert_rows_close(to_np(out), Yd, 1e-5)
 
 
 @pytest.mark.parametrize("grid,Nd", [((16, 8), 24), ((32, 32), 50)])
@@ -248,8 +254,9 @@ def test_invalid_arguments():
 # ------------------------------------------------------------ full size, sampled rows
 def test_plain_full_size_sampled_rows():
     """The plain workload (N=2048, M=8192, J=4, mode model, Poisson 1e4) in the
-    launch configuration the benchmark times; the oracle recomputes 8 sampled
-    rows one by one."""
+    launch configuration the benchmark times; the oracle recomputes 32 sampled
+    rows one by one, and every one of them must end within 1e-3 of the
+    oracle's fidelity."""
     cfg = synth.CONFIGS["plain"]
     N, M, J = cfg["N"], cfg["M"], cfg["J"]
     T = c64(synth.tm_modes(M, N, cfg["R"], seed=0))
@@ -257,13 +264,13 @@ def test_plain_full_size_sampled_rows():
     d = c64(d)
     Yg = torch.empty((M, J, N), dtype=torch.float32, device="cuda")
     iters, pits = 30, 100
-    rows = synth.sample_rows(M, 8, seed=0)
+    rows = synth.sample_rows(M, 32, seed=0)
     with handle(N, M, J, d, init=tmr.TMR_INIT_SPECTRAL, power_iters=pits, clip=2.0) as h:
         tmr.tmr_forward(h, to_dev(T), Yg)
         torch.cuda.synchronize()
         Y_clean = to_np(Yg)
         Y_or = oracle.forward(T[rows].astype(np.complex128), d.astype(np.complex128))
-        assert rel_l2_rows(Y_clean[rows], Y_or) <= 1e-5
+        assert_rows_close(Y_clean[rows], Y_or, 1e-5)
         scale = synth.photon_scale(float(Y_clean.mean()), cfg["photons"])
         Yn = f32(synth.shot_noise(Y_clean, scale, seed=0))
         To = torch.empty((M, N), dtype=torch.complex64, device="cuda")
@@ -275,7 +282,8 @@ def test_plain_full_size_sampled_rows():
                                        power_iters=pits, clip=2.0, row_ids=rows)
     fid_g = oracle.fidelity_rows(Tg[rows], T[rows])
     fid_o = oracle.fidelity_rows(Tr, T[rows])
-    assert np.mean(np.abs(fid_g - fid_o) <= 1e-3) >= 7 / 8, (fid_g, fid_o)
+    assert np.all(np.abs(fid_g - fid_o) <= 1e-3), (fid_g, fid_o)
+    assert np.sum(fid_g < 0.99) == np.sum(fid_o < 0.99)
     fid_all = oracle.fidelity_rows(Tg, T)
     assert np.mean(fid_all) >= 0.98
 
@@ -352,3 +360,54 @@ def test_intensity_scale_invariance():
     f3 = oracle.fidelity_rows(T3, T)
     assert (i3 > 5).all() and np.median(f1) > 0.99  # no row stopped at the start
     np.testing.assert_allclose(f3, f1, atol=1e-3)
+
+
+# ------------------------------------------------------------ bounded waits
+def test_phase_fit_wait_runs_out_and_reports_timeout():
+    """The fit's grid barrier is held shut (test hook): every CTA's wait runs
+    out after wait_spins polls, the kernel returns, phi is left at its last
+    value (zero, the start) and tmr_sync reports TIMEOUT; the context stays
+    usable and a handle without the hook fits normally afterwards."""
+    ny, nx, Nd = 16, 8, 24
+    M, N, J = ny * nx, 64, 4
+    T, d, _ = problem(N, M, J, seed=71)
+    C = oracle.defocus_fields(T.astype(np.complex128), d.astype(np.complex128), Nd)
+    Yd = f32(oracle.defocus_forward(C, (ny, nx)))
+    dop = dict(ny=ny, nx=nx, n_defocus=Nd, coef=0.05)
+    phi = torch.full((M,), float("nan"), dtype=torch.float64, device="cuda")
+    To = torch.empty((M, N), dtype=torch.complex64, device="cuda")
+    with handle(N, M, J, d, dop, withhold_release=1, wait_spins=1 << 14) as h:
+        tmr.tmr_defocus_fit(h, to_dev(T), to_dev(Yd), phi, To)
+        with pytest.raises(tmr.TMRError) as ei:
+            tmr.tmr_sync(h, 60.0)
+        assert ei.value.status == tmr.TMR_ERR_TIMEOUT
+        assert "grid barrier" in str(ei.value)
+    torch.cuda.synchronize()
+    assert np.all(to_np(phi) == 0.0)
+    np.testing.assert_array_equal(to_np(To), T)  # diag(e^{i 0}) T
+    with handle(N, M, J, d, dop, phase_iters=20) as h:
+        tmr.tmr_defocus_fit(h, to_dev(T), to_dev(Yd), phi, To)
+        tmr.tmr_sync(h, 60.0)
+    assert np.all(np.isfinite(to_np(phi)))
+    with pytest.raises(tmr.TMRError) as ei:
+        handle(N, M, J, d, dop, wait_spins=0)
+    assert ei.value.status == tmr.TMR_ERR_INVALID_ARG
+
+
+def test_sync_wall_clock_limit_on_a_long_launch():
+    """tmr_sync gives up after its wall-clock limit while the retrieve still
+    runs (TIMEOUT), and a later tmr_sync with a longer limit returns OK once
+    the work is done."""
+    N, M, J = 2048, 4096, 4
+    _, d, _ = problem(N, 2, J, seed=72)
+    rng = np.random.default_rng(72)
+    Y = torch.from_numpy(rng.exponential(1.0, (M, J, N)).astype(np.float32)).cuda()
+    To = torch.empty((M, N), dtype=torch.complex64, device="cuda")
+    with handle(N, M, J, d, power_iters=100, schedule=2) as h:
+        torch.cuda.synchronize()
+        tmr.tmr_retrieve(h, Y, None, 300, To)
+        with pytest.raises(tmr.TMRError) as ei:
+            tmr.tmr_sync(h, 1e-3)
+        assert ei.value.status == tmr.TMR_ERR_TIMEOUT
+        tmr.tmr_sync(h, 120.0)
+    assert np.all(np.isfinite(to_np(To)))

@@ -416,6 +416,33 @@ def test_mlp_gradient_finite_differences():
     assert np.max(abs(fd - g)) < 1e-8 * max(1.0, np.max(abs(g)))
 
 
+def test_adam_constant_gradient_closed_form():
+    """Under a constant gradient g the bias-corrected moments are exactly
+    m_hat = g and v_hat = g^2 at every step t (m_t = (1 - b1^t) g,
+    v_t = (1 - b2^t) g^2), so after k steps theta = -k lr g / (|g| + eps).
+    A missing or stale bias correction (t held at 1, or none) breaks this
+    for every t > 1."""
+    from oracle import mlp
+    g = np.array([0.3, -2.0, 1e-3, 5.0])
+    th, m, v = np.zeros(4), np.zeros(4), np.zeros(4)
+    for t in range(1, 8):
+        th, m, v = mlp.adam_step(th, g, m, v, t, lr=0.01)
+        np.testing.assert_allclose(th, -t * 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-15)
+
+
+def test_adam_two_steps_by_hand():
+    """g1 = 1, g2 = -2, lr = 1: m2 = -0.11, v2 = 0.004999, m_hat = -0.11 / 0.19,
+    v_hat = 0.004999 / 0.001999, theta2 = -1/(1 + 1e-8) - m_hat / (sqrt(v_hat) + 1e-8)
+    (worked out by hand from the definition of Adam, Kingma & Ba 2015)."""
+    from oracle import mlp
+    th, m, v = mlp.adam_step(np.zeros(1), np.array([1.0]), np.zeros(1), np.zeros(1), 1, lr=1.0)
+    th, m, v = mlp.adam_step(th, np.array([-2.0]), m, v, 2, lr=1.0)
+    assert abs(m[0] + 0.11) < 1e-15 and abs(v[0] - 0.004999) < 1e-15
+    mh, vh = -0.11 / 0.19, 0.004999 / 0.001999
+    assert abs(th[0] - (-1.0 / (1.0 + 1e-8) - mh / (np.sqrt(vh) + 1e-8))) < 1e-13
+    assert abs(th[0] - (-1.0 + 0.366101)) < 1e-5  # 0.578947 / 1.581376
+
+
 def test_adam_first_step_is_signed_lr():
     from oracle import mlp
     g = np.array([0.3, -2.0, 1e-3, 0.0])
