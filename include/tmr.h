@@ -114,7 +114,12 @@ typedef struct {
     int precision;          /* TMR_PREC_FP32 (default) or TMR_PREC_MIXED             */
     int use_graph;          /* replay tmr_retrieve from a captured CUDA graph (default 0) */
     size_t workspace_limit; /* max device bytes the handle may allocate; 0 = no cap  */
-    int schedule;           /* masks per CTA of the solver: 1, 2 or 4 (must divide J);
+    int schedule;           /* solver layout: 1, 2 or 4 = masks per CTA (must divide J),
+                               a cluster of J/G CTAs per row, 8 points per thread;
+                               16 = one CTA per row (FP32, N = 512..2048 with
+                               J N / 16 <= 512 threads, 16 points per thread, L-BFGS
+                               pairs in a global-memory workspace of 2 (m+1) N
+                               complex64 per resident CTA);
                                0 = chosen by the autotuner (default)                 */
     const char *tune_cache; /* JSON file caching autotuned schedules per device, N, J,
                                m; NULL = this process only                           */
@@ -133,9 +138,10 @@ void tmr_default_options(tmr_options *opt);
 
 /* Create a handle for M rows of length N probed with J masks.  With
  * opt->schedule == 0 the first handle for a (device, N, J, m) times every
- * solver schedule (G masks per CTA, a cluster of J/G CTAs per row) on
- * synthetic rows and keeps the fastest; the choice is cached in memory and,
- * when opt->tune_cache names a file, in that JSON file.
+ * solver schedule that fits (G masks per CTA with a cluster of J/G CTAs per
+ * row, and one CTA per row) on synthetic rows and keeps the fastest; the
+ * choice is cached in memory and, when opt->tune_cache names a file, in that
+ * JSON file.
  *   masks      complex64 [J][N], |d| = 1 (not checked), copied.
  *   defocus_op NULL: no phase-offset fit; else copied (H copied).
  *   opt        NULL: defaults.
@@ -246,8 +252,9 @@ tmr_status tmr_set_init_model(tmr_handle *h, tmr_mlp *model);
  * kept (synchronises the handle's stream), or -1. */
 long long tmr_learned_rows(tmr_handle *h);
 
-/* Masks per CTA of the solver schedule the handle uses (after autotuning),
- * or 0 for a NULL handle or when no schedule fits (see tmr_create). */
+/* The solver schedule the handle uses (after autotuning): 1, 2 or 4 masks per
+ * CTA, or 16 for one CTA per row; 0 for a NULL handle or when no schedule
+ * fits (see tmr_create). */
 int tmr_schedule(const tmr_handle *h);
 
 /* Release the handle and everything it allocated.  NULL is allowed. */

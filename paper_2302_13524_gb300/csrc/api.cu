@@ -95,6 +95,9 @@ struct tmr_handle {
     int *pf_err = nullptr, *pf_iters = nullptr;
     int *status_scratch = nullptr, *iters_scratch = nullptr;
     float *loss_scratch = nullptr;
+    // L-BFGS pair workspace of the one-CTA-per-row schedule (pair_ctas regions)
+    float2 *pairs = nullptr;
+    int pair_ctas = 0;
     // staging buffers for host arrays, keyed by slot
     DevBuf stage[8];
     // last retrieve, for tmr_sync's numeric check
@@ -221,7 +224,7 @@ void write_tune_file(const char *path, const std::map<std::string, int> &m)
 
 bool schedule_ok(int N, int J, int m, int G, int smem_optin, int prec = 0)
 {
-    if (G <= 0 || J % G != 0 || !solver_variant_exists(N, G, prec)) return false;
+    if (G <= 0 || !solver_schedule_valid(N, J, G, prec)) return false;
     const size_t b = solver_smem_bytes(N, J, m, G, prec);
     return b > 0 && b <= (size_t)smem_optin;
 }
@@ -231,9 +234,10 @@ bool schedule_ok(int N, int J, int m, int G, int smem_optin, int prec = 0)
 tmr_status autotune(tmr_handle *h, int smem_optin, int *G_out, bool *timed)
 {
     *timed = false;
-    int cand[3], nc = 0;
-    for (int G : {1, 2, 4})
-        if (schedule_ok(h->N, h->J, h->opt.m, G, smem_optin, h->prec)) cand[nc++] = G;
+    int cand[4], nc = 0;
+    for (int G : {1, 2, 4, kRowSchedule})
+        if (schedule_ok(h->N, h->J, h->opt.m, G, smem_optin, h->prec) && (G != kRowSchedule || h->pairs))
+            cand[nc++] = G;
     if (nc == 0) {  // the forward model and gradient still work; tmr_retrieve will refuse
         *G_out = 0;
         return TMR_OK;
@@ -272,6 +276,8 @@ tmr_status autotune(tmr_handle *h, int smem_optin, int *G_out, bool *timed)
     p.y = y;
     p.T_out = T;
     p.queue = h->queue;
+    p.pairs = h->pairs;
+    p.pair_ctas = h->pair_ctas;
     p.M = R;
     p.N = h->N;
     p.J = h->J;
@@ -385,7 +391,7 @@ void tmr_destroy(tmr_handle *h)
     else cudaDeviceSynchronize();
     void *ptrs[] = {h->masks, h->tw, h->H, h->Zd, h->phi, h->pf_ws, h->pf_loss, h->wts, h->queue,
                     h->pf_sync, h->pf_err, h->pf_iters, h->status_scratch, h->iters_scratch,
-                    h->loss_scratch, h->Tcand, h->wins, h->y16, h->ysc};
+                    h->loss_scratch, h->Tcand, h->wins, h->y16, h->ysc, h->pairs};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &b : h->stage)
@@ -432,7 +438,8 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     int smem_optin = 0;
     TMR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
     if (o.schedule != 0 && !schedule_ok(N, J, o.m, o.schedule, smem_optin, o.precision))
-        return fail(TMR_ERR_UNSUPPORTED, "opt.schedule must be 1, 2 or 4, divide J and fit the device");
+        return fail(TMR_ERR_UNSUPPORTED,
+                    "opt.schedule must be 1, 2 or 4 (dividing J) or 16 (one CTA per row), and fit the device");
 
     tmr_handle *h = new tmr_handle();
     h->N = N;
@@ -513,6 +520,21 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
         TRY(halloc(h, (void **)&h->pf_loss, sizeof(double) * 4, "phase loss"));
         cudaMemset(h->pf_err, 0, sizeof(int) * 4);
     }
+    // the one-CTA-per-row schedule keeps its L-BFGS pairs in global memory: one
+    // region per resident CTA, allocated when that schedule can run (and is
+    // asked for or a candidate of the autotuner); under a workspace_limit that
+    // it would exceed, the schedule is left out
+    if ((o.schedule == 0 || o.schedule == kRowSchedule) && schedule_ok(N, J, o.m, kRowSchedule, smem_optin, h->prec)) {
+        const int ctas = solver_row_max_ctas(N, J, o.m);
+        const size_t bytes = sizeof(float2) * solver_row_pair_stride(N, o.m) * (size_t)(ctas > 0 ? ctas : 0);
+        if (ctas > 0 && (!o.workspace_limit || h->held + bytes <= o.workspace_limit)) {
+            TRY(halloc(h, (void **)&h->pairs, bytes, "L-BFGS pair workspace"));
+            h->pair_ctas = ctas;
+        } else if (o.schedule == kRowSchedule) {
+            tmr_destroy(h);
+            return fail(TMR_ERR_OOM, "L-BFGS pair workspace of schedule 16 exceeds workspace_limit");
+        }
+    }
     // solver schedule: given, cached, or autotuned
     if (o.schedule != 0) {
         h->G = o.schedule;
@@ -528,6 +550,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
                 auto f = fm.find(key);
                 if (f != fm.end() && schedule_ok(N, J, o.m, f->second, smem_optin, h->prec)) G = f->second;
             }
+            if (G == kRowSchedule && !h->pairs) G = 0;  // no pair workspace here: tune again
         }
         bool timed = true;  // a cached choice was timed when it was made
         if (!G) {
@@ -685,6 +708,8 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
     p.row_loss = (float *)dL;
     p.Zd = nullptr;  // the fit's fields are made from the final T (below)
     p.queue = h->queue;
+    p.pairs = h->pairs;
+    p.pair_ctas = h->pair_ctas;
     p.Nd = 0;
     p.M = h->M;
     p.N = h->N;

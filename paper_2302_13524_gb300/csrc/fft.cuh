@@ -19,7 +19,8 @@
 // tw_p[(r-1) Ns + j] = exp(-2 pi i r j / (Ns R)), r = 1..R-1, j = 0..Ns-1,
 // computed in FP64 and rounded to FP32: on the host for a handle
 // (tmr::fft_table), on the device for the allocation-free entry point
-// (noalloc.cu; the two agree to 1 ulp of FP32).  A thread reads its row j
+// (noalloc.cu; the two agree to 1 ulp of FP32) and, for its radix-16 plans,
+// by the one-CTA-per-row solver (solver_row.cuh).  A thread reads its row j
 // contiguously across the warp.
 #pragma once
 
@@ -99,8 +100,41 @@ __device__ __forceinline__ void dft_small(float2 (&x)[R])
         x[6] = csub(e[2], o2);
         x[3] = cadd(e[3], o3);
         x[7] = csub(e[3], o3);
+    } else if constexpr (R == 16) {
+        // 16 = 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2;
+        // X[k1 + 4 k2] = sum_n2 W4^(n2 k2) W16^(n2 k1) sum_n1 x[4 n1 + n2] W4^(n1 k1)
+        float2 a[4][4];  // a[n2][k1]
+#pragma unroll
+        for (int n2 = 0; n2 < 4; n2++) {
+            float2 c[4] = {x[n2], x[4 + n2], x[8 + n2], x[12 + n2]};
+            dft_small<4, SIGN>(c);
+#pragma unroll
+            for (int k1 = 0; k1 < 4; k1++) a[n2][k1] = c[k1];
+        }
+        // W16^k = exp(SIGN i pi k / 8) for the products n2 k1 in {1, 2, 3, 4, 6, 9}
+        constexpr float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f;
+        constexpr float h = 0.70710678118654752440f;
+        constexpr float sg = SIGN < 0 ? -1.f : 1.f;
+        const float2 w1 = make_float2(c1, sg * s1), w2 = make_float2(h, sg * h), w3 = make_float2(s1, sg * c1);
+        const float2 w6 = make_float2(-h, sg * h), w9 = make_float2(-c1, -sg * s1);
+        a[1][1] = cmul(a[1][1], w1);
+        a[1][2] = cmul(a[1][2], w2);
+        a[1][3] = cmul(a[1][3], w3);
+        a[2][1] = cmul(a[2][1], w2);
+        a[2][2] = rot4<SIGN>(a[2][2]);
+        a[2][3] = cmul(a[2][3], w6);
+        a[3][1] = cmul(a[3][1], w3);
+        a[3][2] = cmul(a[3][2], w6);
+        a[3][3] = cmul(a[3][3], w9);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; k1++) {
+            float2 c[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+            dft_small<4, SIGN>(c);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; k2++) x[k1 + 4 * k2] = c[k2];
+        }
     } else {
-        static_assert(R == 1 || R == 2 || R == 4 || R == 8, "unsupported radix");
+        static_assert(R == 1 || R == 2 || R == 4 || R == 8 || R == 16, "unsupported radix");
     }
 }
 
@@ -193,6 +227,18 @@ __device__ __forceinline__ void twiddle_powers(float2 (&x)[R], float2 wb)
             x[5] = cmul(x[5], cmul(w4, wb));
             x[6] = cmul(x[6], cmul(w4, w2));
             x[7] = cmul(x[7], cmul(w4, w3));
+            if constexpr (R >= 16) {
+                const float2 w8 = cmul(w4, w4);
+                x[8] = cmul(x[8], w8);
+                x[9] = cmul(x[9], cmul(w8, wb));
+                x[10] = cmul(x[10], cmul(w8, w2));
+                x[11] = cmul(x[11], cmul(w8, w3));
+                const float2 w12 = cmul(w8, w4);
+                x[12] = cmul(x[12], w12);
+                x[13] = cmul(x[13], cmul(w12, wb));
+                x[14] = cmul(x[14], cmul(w12, w2));
+                x[15] = cmul(x[15], cmul(w12, w3));
+            }
         }
     }
 }

@@ -73,18 +73,31 @@ struct SolverParams {
     const float2 *T_cand; // [M][N] proposed starts compared per row with the init, or NULL
     unsigned *cand_wins;  // rows whose proposed start was kept
     unsigned *queue;      // row work counter, zeroed before the launch
+    float2 *pairs;        // one-CTA-per-row schedule: L-BFGS pairs, pair_ctas regions of
+    int pair_ctas;        //   2 (m + 1) N float2 each (global memory), else unused
     int N, Nd, M, J, iters, m, init, power_iters;
     int prec;             // TMR_PREC_FP32 or TMR_PREC_MIXED
     unsigned long long seed;
     float clip;
     double tol;
 };
-// Variants: G masks per CTA (G in {1, 2, 4}, G divides J), cluster of J/G CTAs.
+// Variants: G masks per CTA (G in {1, 2, 4}, G divides J), cluster of J/G CTAs;
+// or G = kRowSchedule (16): one CTA per row holding all J masks at 16 points
+// per thread, FP32, N = 512 .. 2048 with J N / 16 <= 512, L-BFGS pairs in the
+// global workspace p.pairs (solver_row.cuh).
+constexpr int kRowSchedule = 16;
 bool solver_variant_exists(int N, int G, int prec = 0);
+// schedule G usable for (N, J): variant exists, J % G == 0 for cluster schedules
+bool solver_schedule_valid(int N, int J, int G, int prec = 0);
+// one-CTA-per-row schedule: CTAs resident at once (the pair regions a launch needs)
+int solver_row_max_ctas(int N, int J, int m);
+size_t solver_row_pair_stride(int N, int m);  // float2 per CTA region
 size_t solver_smem_bytes(int N, int J, int m, int G, int prec = 0);
 cudaError_t launch_solver(int N, int G, const SolverParams &p, cudaStream_t s, int *clusters_out);
 // the Bluestein variants (solver_bs.cu); what == 0: shared bytes, 1: launch
 long long solver_dispatch_blue(int N, int G, int what, const SolverParams *p, cudaStream_t s, int *clusters_out);
+// the one-CTA-per-row variants (solver_row.cu)
+long long solver_dispatch_row(int N, int what, const SolverParams *p, cudaStream_t s, int *ctas_out);
 // the mixed-precision variants (solver_mx.cu)
 long long solver_dispatch_mixed(int N, int G, int what, const SolverParams *p, cudaStream_t s, int *clusters_out);
 // Synthetic positive intensities for timing runs (autotuner).

@@ -8,6 +8,7 @@ namespace tmr {
 // G * threads(N) <= 512; other lengths (Bluestein) with G = 1.
 bool solver_variant_exists(int N, int G, int prec)
 {
+    if (G == kRowSchedule) return prec == 0 && (N == 512 || N == 1024 || N == 2048);
     if (G != 1 && G != 2 && G != 4) return false;
     if (prec != 0) return G == 1 && mixed_supported(N);
     if (fft_supported(N)) return G * fft_threads(N) <= 512;
@@ -27,6 +28,7 @@ bool solver_variant_exists(int N, int G, int prec)
 static long long solver_dispatch(int N, int G, int what, const SolverParams *p, cudaStream_t s,
                                  int *clusters_out)
 {
+    if (G == kRowSchedule) return solver_dispatch_row(N, what, p, s, clusters_out);
     if (p->prec != 0) return solver_dispatch_mixed(N, G, what, p, s, clusters_out);
     if (!fft_supported(N)) return solver_dispatch_blue(N, G, what, p, s, clusters_out);
     TMR_SOLVER_N(64)
@@ -46,14 +48,21 @@ size_t solver_smem_bytes(int N, int J, int m, int G, int prec)
     p.J = J;
     p.m = m;
     p.prec = prec;
-    if (!solver_variant_exists(N, G, prec) || J % G != 0) return 0;
+    if (!solver_schedule_valid(N, J, G, prec)) return 0;
     return (size_t)solver_dispatch(N, G, 0, &p, nullptr, nullptr);
+}
+
+bool solver_schedule_valid(int N, int J, int G, int prec)
+{
+    if (!solver_variant_exists(N, G, prec) || J < 1) return false;
+    if (G == kRowSchedule) return J * (N / 16) <= 512;
+    return J % G == 0;
 }
 
 cudaError_t launch_solver(int N, int G, const SolverParams &p, cudaStream_t s, int *clusters_out)
 {
     if (p.M == 0) return cudaSuccess;
-    if (!solver_variant_exists(N, G, p.prec) || p.J % G != 0 || p.N != N) return cudaErrorInvalidValue;
+    if (!solver_schedule_valid(N, p.J, G, p.prec) || p.N != N) return cudaErrorInvalidValue;
     return (cudaError_t)solver_dispatch(N, G, 1, &p, s, clusters_out);
 }
 

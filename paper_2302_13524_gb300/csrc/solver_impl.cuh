@@ -244,6 +244,69 @@ static __device__ float quartic_argmin(const float *c)
     return best;
 }
 
+// quartic_argmin with the up to three Newton polishings on lanes 0..2 of a
+// warp (every lane of the warp calls it and gets the same result): the same
+// candidates, steps and selection, in the same order, as the one-thread form.
+static __device__ float quartic_argmin_warp(const float *c, int lane)
+{
+    const float c1 = c[1], c2 = c[2], c3 = c[3], c4 = c[4];
+    if (!(c4 > 0.f)) return quartic_argmin_safe(c);
+    auto g = [&](float a) { return fmaf(fmaf(fmaf(4.f * c4, a, 3.f * c3), a, 2.f * c2), a, c1); };
+    auto dg = [&](float a) { return fmaf(fmaf(12.f * c4, a, 6.f * c3), a, 2.f * c2); };
+    auto phi = [&](float a) { return a * fmaf(fmaf(fmaf(c4, a, c3), a, c2), a, c1); };
+    const float inv = 1.f / c4;
+    const float B3 = 0.25f * c3 * inv;
+    const float C = 0.5f * c2 * inv, D = 0.25f * c1 * inv;
+    const float p = fmaf(-3.f * B3, B3, C);
+    const float q = fmaf(B3, fmaf(2.f * B3, B3, -C), D);
+    const float hp = p * (1.f / 3.f), hq = 0.5f * q;
+    const float disc = fmaf(hq, hq, hp * hp * hp);
+    float a = 0.f;
+    int nc;
+    if (disc > 0.f) {
+        nc = 1;
+        if (lane == 0) {
+            const float u = cbrtf(-hq - copysignf(sqrtf(disc), hq));
+            a = (u != 0.f ? u - hp / u : 0.f) - B3;
+        }
+    } else {
+        nc = 3;
+        if (lane < 3) {
+            const float r = sqrtf(fmaxf(-hp, 0.f));
+            const float r3 = r * r * r;
+            const float arg = r3 > 0.f ? fminf(fmaxf(-hq / r3, -1.f), 1.f) : 0.f;
+            const float th = acosf(arg) * (1.f / 3.f);
+            const float tr = 2.0943951023931955f;  // 2 pi / 3
+            a = 2.f * r * cosf(lane == 0 ? th : (lane == 1 ? th - tr : th + tr)) - B3;
+        }
+    }
+    if (lane < nc) {
+        for (int it = 0; it < 4; it++) {
+            const float d = dg(a);
+            if (!(d != 0.f)) break;
+            const float na = a - g(a) / d;
+            if (!isfinite(na) || na == a) break;
+            a = na;
+        }
+    }
+    const float v = phi(a);
+    float best = 0.f, bestv = 0.f;
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const float ak = __shfl_sync(0xffffffffu, a, k), vk = __shfl_sync(0xffffffffu, v, k);
+        if (k < nc) {
+            bad = bad || !isfinite(ak);
+            if (k == 0 || vk < bestv || (vk == bestv && ak > 0.f && (best <= 0.f || ak < best))) {
+                best = ak;
+                bestv = vk;
+            }
+        }
+    }
+    if (bad) return quartic_argmin_safe(c);
+    return best;
+}
+
 // Compact-form coefficients, run by one warp (lane i owns age i):
 // p = -(gamma g + sum_i c1_i s_i + sum_i c2_i y_i), c2 already scaled by gamma.
 // R c2 = -S^T g is solved by back substitution and R^T c1 =
@@ -303,6 +366,77 @@ static __device__ void lbfgs_coefficients_warp(Gram &G, int lane)
         if (!ok) G.np = 0;
     }
     __syncwarp();
+}
+
+// Gram bookkeeping after the batched dot products of an iteration, run by one
+// warp (lane i owns age i): the new column of S^T Y and Y^T Y and the new
+// S^T g, Y^T g from Gm.red, the pair test s^T y > 1e-10 |s| |y|, the shift
+// that drops the oldest pair once m are held (its slot becomes the free one),
+// the loss and the stopping tests, then the next direction's coefficients.
+static __device__ void lbfgs_gram_update(Gram &Gm, int lane, int m, int it, int iters, double tol)
+{
+    const int np = Gm.np;
+    const float *tot = Gm.red;
+    if (lane <= np) {
+        Gm.SY[lane][np] = tot[4 * lane + 0];
+        Gm.YY[lane][np] = tot[4 * lane + 1];
+        Gm.Sg[lane] = tot[4 * lane + 2];
+        Gm.Yg[lane] = tot[4 * lane + 3];
+    }
+    const float sy = tot[4 * np + 0], yy = tot[4 * np + 1];
+    const float fnew = tot[kIdxF];
+    const bool accept = sy > 1e-10f * sqrtf(tot[kIdxSS]) * sqrtf(yy) && sy > 0.f;
+    int np2 = np + (accept ? 1 : 0);
+    __syncwarp();
+    if (accept && lane == 0) Gm.rD[np] = 1.f / sy;
+    __syncwarp();
+    if (np2 > m) {
+        // drop the oldest pair: age i + 1 becomes age i
+        float sy_r[kSlots], yy_r[kSlots], sg = 0.f, yg = 0.f, rd = 0.f;
+        int sl = 0;
+        const bool mine = lane < np2 - 1;
+        const int src = lane + 1;
+#pragma unroll
+        for (int j = 0; j < kSlots; j++) {
+            sy_r[j] = (mine && j + 1 < kSlots) ? Gm.SY[src][j + 1 < kSlots ? j + 1 : 0] : 0.f;
+            yy_r[j] = (mine && j + 1 < kSlots) ? Gm.YY[src][j + 1 < kSlots ? j + 1 : 0] : 0.f;
+        }
+        if (mine) {
+            sg = Gm.Sg[src];
+            yg = Gm.Yg[src];
+            rd = Gm.rD[src];
+        }
+        // the m + 1 allocated slots rotate: the oldest pair's slot
+        // becomes the free one at position m
+        const int sl_old0 = Gm.slot[0];
+        if (lane < m) sl = Gm.slot[lane + 1];
+        __syncwarp();
+        if (mine) {
+#pragma unroll
+            for (int j = 0; j < kSlots; j++) {
+                Gm.SY[lane][j] = sy_r[j];
+                Gm.YY[lane][j] = yy_r[j];
+            }
+            Gm.Sg[lane] = sg;
+            Gm.Yg[lane] = yg;
+            Gm.rD[lane] = rd;
+        }
+        if (lane < m) Gm.slot[lane] = sl;
+        if (lane == m) Gm.slot[lane] = sl_old0;
+        np2 = m;
+    }
+    if (lane == 0) {
+        Gm.np = np2;
+        Gm.gg = tot[kIdxGG];
+        const float rel = fabsf(Gm.f - fnew) / fmaxf(Gm.f, 1e-30f);
+        Gm.f = fnew;
+        Gm.done = it + 1;
+        if (!isfinite(fnew) || !isfinite(Gm.gg)) { Gm.status = ROW_NUMERIC; Gm.stop = 1; }
+        else if (tol > 0.0 && rel < (float)tol) { Gm.status = ROW_CONVERGED; Gm.stop = 1; }
+        else if (it + 1 < iters && (fnew == 0.f || Gm.gg == 0.f)) { Gm.status = ROW_CONVERGED; Gm.stop = 1; }
+    }
+    __syncwarp();
+    if (!Gm.stop && it + 1 < iters) lbfgs_coefficients_warp(Gm, lane);
 }
 
 // Sum of up to 32 values over a warp by recursive halving: after the call,
@@ -748,11 +882,13 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
                         pv[4] = fmaf(b, b, pv[4]);
                     }
                     cluster_sum(pv, 5);  // B2
-                    if (tid == 0) {
-                        const float al = quartic_argmin(Gm.red);
-                        Gm.alpha = al;
-                        if (!isfinite(al)) { Gm.status = ROW_NUMERIC; Gm.stop = 1; }
-                        else if (al == 0.f) { Gm.status = ROW_CONVERGED; Gm.stop = 1; }
+                    if (warp == 0) {
+                        const float al = quartic_argmin_warp(Gm.red, lane);
+                        if (lane == 0) {
+                            Gm.alpha = al;
+                            if (!isfinite(al)) { Gm.status = ROW_NUMERIC; Gm.stop = 1; }
+                            else if (al == 0.f) { Gm.status = ROW_CONVERGED; Gm.stop = 1; }
+                        }
                     }
                     __syncthreads();
                 }
@@ -815,69 +951,7 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
                     }
                     pv[kIdxF] = fpart;
                     cluster_sum(pv, kParts);  // B4
-                    if (warp == 0) {
-                        const float *tot = Gm.red;
-                        if (lane <= np) {
-                            Gm.SY[lane][np] = tot[4 * lane + 0];
-                            Gm.YY[lane][np] = tot[4 * lane + 1];
-                            Gm.Sg[lane] = tot[4 * lane + 2];
-                            Gm.Yg[lane] = tot[4 * lane + 3];
-                        }
-                        const float sy = tot[4 * np + 0], yy = tot[4 * np + 1];
-                        const float fnew = tot[kIdxF];
-                        const bool accept = sy > 1e-10f * sqrtf(tot[kIdxSS]) * sqrtf(yy) && sy > 0.f;
-                        int np2 = np + (accept ? 1 : 0);
-                        __syncwarp();
-                        if (accept && lane == 0) Gm.rD[np] = 1.f / sy;
-                        __syncwarp();
-                        if (np2 > m) {
-                            // drop the oldest pair: age i + 1 becomes age i
-                            float sy_r[kSlots], yy_r[kSlots], sg = 0.f, yg = 0.f, rd = 0.f;
-                            int sl = 0;
-                            const bool mine = lane < np2 - 1;
-                            const int src = lane + 1;
-#pragma unroll
-                            for (int j = 0; j < kSlots; j++) {
-                                sy_r[j] = (mine && j + 1 < kSlots) ? Gm.SY[src][j + 1 < kSlots ? j + 1 : 0] : 0.f;
-                                yy_r[j] = (mine && j + 1 < kSlots) ? Gm.YY[src][j + 1 < kSlots ? j + 1 : 0] : 0.f;
-                            }
-                            if (mine) {
-                                sg = Gm.Sg[src];
-                                yg = Gm.Yg[src];
-                                rd = Gm.rD[src];
-                            }
-                            // the m + 1 allocated slots rotate: the oldest pair's slot
-                            // becomes the free one at position m
-                            const int sl_old0 = Gm.slot[0];
-                            if (lane < m) sl = Gm.slot[lane + 1];
-                            __syncwarp();
-                            if (mine) {
-#pragma unroll
-                                for (int j = 0; j < kSlots; j++) {
-                                    Gm.SY[lane][j] = sy_r[j];
-                                    Gm.YY[lane][j] = yy_r[j];
-                                }
-                                Gm.Sg[lane] = sg;
-                                Gm.Yg[lane] = yg;
-                                Gm.rD[lane] = rd;
-                            }
-                            if (lane < m) Gm.slot[lane] = sl;
-                            if (lane == m) Gm.slot[lane] = sl_old0;
-                            np2 = m;
-                        }
-                        if (lane == 0) {
-                            Gm.np = np2;
-                            Gm.gg = tot[kIdxGG];
-                            const float rel = fabsf(Gm.f - fnew) / fmaxf(Gm.f, 1e-30f);
-                            Gm.f = fnew;
-                            Gm.done = it + 1;
-                            if (!isfinite(fnew) || !isfinite(Gm.gg)) { Gm.status = ROW_NUMERIC; Gm.stop = 1; }
-                            else if (P.tol > 0.0 && rel < (float)P.tol) { Gm.status = ROW_CONVERGED; Gm.stop = 1; }
-                            else if (it + 1 < P.iters && (fnew == 0.f || Gm.gg == 0.f)) { Gm.status = ROW_CONVERGED; Gm.stop = 1; }
-                        }
-                        __syncwarp();
-                        if (!Gm.stop && it + 1 < P.iters) lbfgs_coefficients_warp(Gm, lane);
-                    }
+                    if (warp == 0) lbfgs_gram_update(Gm, lane, m, it, P.iters, P.tol);
                     __syncthreads();
                 }
             }

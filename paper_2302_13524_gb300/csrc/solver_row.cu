@@ -1,0 +1,54 @@
+// solver_row.cu -- instantiations of the one-CTA-per-row solver (solver_row.cuh).
+#include "solver_row.cuh"
+
+namespace tmr {
+
+#define TMR_ROW_N(NN)                                                      \
+    case NN:                                                               \
+        if (what == 0) return (long long)row_smem<NN>(p->J, p->m);         \
+        return (long long)launch_solver_row_t<NN>(*p, s, ctas_out);
+
+// what == 0: shared-memory bytes; what == 1: launch.
+long long solver_dispatch_row(int N, int what, const SolverParams *p, cudaStream_t s, int *ctas_out)
+{
+    if (!row_variant_fits(N, p->J)) return what == 0 ? 0 : (long long)cudaErrorInvalidValue;
+    switch (N) {
+        TMR_ROW_N(512)
+        TMR_ROW_N(1024)
+        TMR_ROW_N(2048)
+    default: return what == 0 ? 0 : (long long)cudaErrorInvalidValue;
+    }
+}
+
+template <int N>
+static int row_max_ctas_t(int J, int m)
+{
+    const size_t sm = row_smem<N>(J, m);
+    if (cudaFuncSetAttribute(k_solver_row<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int dev = 0, nsm = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solver_row<N>, J * RowCfg<N>::NT, sm) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return occ * nsm;
+}
+
+int solver_row_max_ctas(int N, int J, int m)
+{
+    if (!row_variant_fits(N, J)) return 0;
+    switch (N) {
+    case 512: return row_max_ctas_t<512>(J, m);
+    case 1024: return row_max_ctas_t<1024>(J, m);
+    case 2048: return row_max_ctas_t<2048>(J, m);
+    default: return 0;
+    }
+}
+
+size_t solver_row_pair_stride(int N, int m) { return row_pair_stride(N, m); }
+
+}  // namespace tmr

@@ -26,7 +26,8 @@ def _perturbed(T, N, seed, scale=0.3):
 
 
 @pytest.mark.parametrize("N,J,G", [(256, 4, 1), (256, 4, 2), (256, 4, 4), (1024, 4, 2), (1024, 4, 4),
-                                   (2048, 4, 2), (512, 2, 2), (128, 3, 1)])
+                                   (2048, 4, 2), (512, 2, 2), (128, 3, 1),
+                                   (2048, 4, 16), (1024, 8, 16), (512, 3, 16), (512, 4, 16)])
 def test_schedules_match_oracle(N, J, G):
     M, iters = 9, 5
     T, d, Y = problem(N, M, J, seed=N + G)
@@ -46,13 +47,13 @@ def test_schedules_agree_on_a_full_spectral_run():
     N, M, J, iters = 1024, 40, 4, 30
     T, d, Y = problem(N, M, J, seed=5)
     out = {}
-    for G in (1, 2, 4):
+    for G in (1, 2, 4, 16):
         To = torch.empty((M, N), dtype=torch.complex64, device="cuda")
         with tmr.tmr_create(N, M, J, to_dev(d), None, dict(schedule=G, power_iters=40)) as h:
             tmr.tmr_retrieve(h, to_dev(Y), None, iters, To)
             torch.cuda.synchronize()
         out[G] = oracle.fidelity_rows(to_np(To), T)
-    for G in (2, 4):
+    for G in (2, 4, 16):
         assert np.mean(np.abs(out[G] - out[1]) <= 1e-3) >= 0.95
 
 
@@ -64,6 +65,12 @@ def test_invalid_schedule_rejected():
     assert ei.value.status == tmr.TMR_ERR_UNSUPPORTED
     with pytest.raises(tmr.TMRError):
         tmr.tmr_create(4096, M, J, to_dev(np.ones((J, 4096), np.complex64)), None, dict(schedule=4))
+    with pytest.raises(tmr.TMRError) as ei:  # one CTA per row: N <= 2048 and J N / 16 <= 512
+        tmr.tmr_create(4096, M, J, to_dev(np.ones((J, 4096), np.complex64)), None, dict(schedule=16))
+    assert ei.value.status == tmr.TMR_ERR_UNSUPPORTED
+    with pytest.raises(tmr.TMRError) as ei:
+        tmr.tmr_create(2048, M, 8, to_dev(np.ones((8, 2048), np.complex64)), None, dict(schedule=16))
+    assert ei.value.status == tmr.TMR_ERR_UNSUPPORTED
 
 
 def test_autotuner_picks_and_caches(tmp_path):
@@ -72,7 +79,7 @@ def test_autotuner_picks_and_caches(tmp_path):
     cache = str(tmp_path / "tune.json")
     with tmr.tmr_create(N, M, J, to_dev(d), None, dict(schedule=0, tune_cache=cache)) as h:
         G = tmr.tmr_schedule(h)
-    assert G in (1, 2, 4)
+    assert G in (1, 2, 4, 16)
     entries = json.load(open(cache))
     key = [k for k in entries if "|N512|J4|m5" in k]
     assert len(key) == 1 and entries[key[0]] == G
