@@ -61,10 +61,13 @@ enum {
     TMR_INIT_RANDOM = 0,   /* Philox4x32-10 complex normal, scaled to ||t||^2 = sum(y)/(J N) */
     TMR_INIT_BP = 1,       /* back-propagation t0 = Q^H sqrt(y) / (J N), Eq. backpropagation */
     TMR_INIT_SPECTRAL = 2, /* power iteration on Q^H diag(min(y/mean y, clip)) Q / (J N)    */
-    TMR_INIT_LEARNED = 3   /* the network of tmr_set_init_model proposes t0 from sqrt(y); per
-                              row it is kept only if its loss is below that of the spectral
-                              start (power_iters; 0 = the random start), which is used
-                              otherwise                                                   */
+    TMR_INIT_LEARNED = 3   /* the network of tmr_set_init_model proposes t0 from sqrt(y); the
+                              proposal seeds the spectral power iteration (power_iters
+                              steps) in place of the Philox vector, and a row whose
+                              proposal is not finite or is zero keeps the Philox seed (the
+                              plain spectral start).  With power_iters = 0 the solver keeps,
+                              per row, whichever of the proposal and the random start has
+                              the lower loss                                             */
 };
 
 /* Per-row outcome written to row_status. */
@@ -236,8 +239,18 @@ tmr_status tmr_mlp_set_params(tmr_mlp *m, const float *params);
 tmr_status tmr_mlp_get_params(tmr_mlp *m, float *params);
 /* Y[B][out] = network(X[B][in]). */
 tmr_status tmr_mlp_forward(tmr_mlp *m, const float *X, int B, float *Y);
-/* Mean squared error L = sum (Y - T)^2 / (B out) of the batch into *loss
- * (may be NULL) and its gradient w.r.t. every parameter into grad (may be NULL). */
+/* Loss of tmr_mlp_grad and tmr_mlp_train_step.  TMR_LOSS_MSE (default):
+ * L = sum (Y - T)^2 / (B out).  TMR_LOSS_PHASE (out even): each row is read
+ * as a complex vector y = Y[:out/2] + i Y[out/2:] (likewise t from T) and
+ * compared with the nearest global-phase rotation of its target,
+ * L = sum_b min_a ||y_b - t_b e^{-i a}||^2 / (B out) -- a TM row is only
+ * defined up to such a phase, so this is the loss for rows of T.  Its
+ * gradient is that of the mean squared error against the aligned targets
+ * t_b conj(c_b) / |c_b|, c_b = <y_b, t_b> (unrotated where c_b = 0). */
+enum { TMR_LOSS_MSE = 0, TMR_LOSS_PHASE = 1 };
+tmr_status tmr_mlp_set_loss(tmr_mlp *m, int kind);
+/* The loss of the batch into *loss (may be NULL) and its gradient w.r.t.
+ * every parameter into grad (may be NULL). */
 tmr_status tmr_mlp_grad(tmr_mlp *m, const float *X, const float *T, int B, float *loss,
                         float *grad);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the batch. */
@@ -248,8 +261,9 @@ void tmr_mlp_destroy(tmr_mlp *m);
 /* Network used by TMR_INIT_LEARNED (not owned; keep it alive while the handle
  * uses it).  Its sizes must be in = J*N and out = 2*N. */
 tmr_status tmr_set_init_model(tmr_handle *h, tmr_mlp *model);
-/* Rows of the last completed learned-start retrieve whose proposed start was
- * kept (synchronises the handle's stream), or -1. */
+/* Rows of the last completed learned-start retrieve whose proposal was used
+ * (seeded the power iteration, or won the loss comparison when power_iters
+ * is 0); synchronises the handle's stream; -1 when there was none. */
 long long tmr_learned_rows(tmr_handle *h);
 
 /* The solver schedule the handle uses (after autotuning): 1, 2 or 4 masks per

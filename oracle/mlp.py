@@ -2,7 +2,9 @@
 
 TEST INFRASTRUCTURE: only the test suite may use it.  A three-layer perceptron
 x -> GELU(W1 x + b1) -> GELU(W2 h1 + b2) -> W3 h2 + b3 with the mean-squared
-loss L = sum((y - t)^2) / (B * n_out), its gradient by the chain rule, and
+loss L = sum((y - t)^2) / (B * n_out) or its phase-invariant form (each
+target row rotated by the global phase that best matches the output row),
+the gradients by the chain rule, and
 one Adam step (Kingma & Ba 2015, bias-corrected moments).  GELU is the exact
 form x * Phi(x) = x/2 (1 + erf(x / sqrt 2)).
 
@@ -68,6 +70,36 @@ def loss_grad(theta, dims, X, T):
     dW1 = dZ1.T @ X
     db1 = dZ1.sum(0)
     return L, flatten([dW1, db1, dW2, db2, dW3, db3])
+
+
+def align_targets(Y, T):
+    """Each target row, read as the complex vector t = T[:n] + i T[n:] (n =
+    n_out / 2), rotated by the global phase that best aligns it with the
+    output row y = Y[:n] + i Y[n:]: t e^{-i a} with e^{i a} = c / |c|,
+    c = sum conj(y) t (no rotation where c = 0).  Returned in the same real
+    layout.  Rows of T are determined only up to a global phase (a TM row
+    is), so the loss compares each output with the nearest rotation of its
+    target."""
+    Y = np.asarray(Y, dtype=np.float64)
+    T = np.asarray(T, dtype=np.float64)
+    n = Y.shape[1] // 2
+    y = Y[:, :n] + 1j * Y[:, n:]
+    t = T[:, :n] + 1j * T[:, n:]
+    c = np.sum(np.conj(y) * t, axis=1)
+    ac = np.abs(c)
+    rot = np.where(ac > 0, np.conj(c) / np.where(ac > 0, ac, 1.0), 1.0)
+    tr = t * rot[:, None]
+    return np.concatenate([tr.real, tr.imag], axis=1)
+
+
+def loss_grad_phase(theta, dims, X, T):
+    """Phase-invariant loss L = sum_b min_a ||y_b - t_b e^{-i a}||^2 / (B n_out)
+    (outputs and targets as complex rows, see align_targets) and its gradient.
+    The minimum over a is attained at the aligning rotation, so by the
+    envelope theorem dL/dY = 2 (Y - align(T)) / (B n_out): the mean-squared
+    loss against the aligned targets, with the rotation held fixed."""
+    Y, _ = forward(theta, dims, np.asarray(X, dtype=np.float64))
+    return loss_grad(theta, dims, X, align_targets(Y, T))
 
 
 def adam_step(theta, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):

@@ -22,6 +22,7 @@ TMR_ROW_MAXITER, TMR_ROW_CONVERGED, TMR_ROW_ZERO, TMR_ROW_NUMERIC = 0, 1, 2, 3
 TMR_PREC_FP32 = 0
 TMR_PREC_MIXED = 1
 TMR_PIX_U16, TMR_PIX_F32 = 0, 1
+TMR_LOSS_MSE, TMR_LOSS_PHASE = 0, 1
 INIT = {"random": TMR_INIT_RANDOM, "bp": TMR_INIT_BP, "spectral": TMR_INIT_SPECTRAL,
         "learned": TMR_INIT_LEARNED}
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "TIMEOUT",
@@ -76,6 +77,7 @@ def _load():
         "tmr_mlp_grad": ([vp, fp, fp, ip, fp, fp], ctypes.c_int),
         "tmr_mlp_train_step": ([vp, fp, fp, ip, ctypes.c_float, fp], ctypes.c_int),
         "tmr_mlp_destroy": ([vp], None),
+        "tmr_mlp_set_loss": ([vp, ip], ctypes.c_int),
         "tmr_set_init_model": ([H, vp], ctypes.c_int),
         "tmr_learned_rows": ([H], ctypes.c_longlong),
         "tmr_destroy": ([H], None),
@@ -320,6 +322,13 @@ def tmr_mlp_train_step(m: MLP, X, T, B, lr, loss=None):
     _check(lib.tmr_mlp_train_step(m.raw, _ptr(X, "f32", B * m.dims[0], "X"),
                                   _ptr(T, "f32", B * m.dims[3], "T"), int(B), float(lr),
                                   _ptr(loss, "f32", 1, "loss")))
+
+
+def tmr_mlp_set_loss(m: MLP, kind):
+    """TMR_LOSS_MSE or TMR_LOSS_PHASE (also "mse" / "phase")."""
+    if isinstance(kind, str):
+        kind = {"mse": TMR_LOSS_MSE, "phase": TMR_LOSS_PHASE}[kind]
+    _check(lib.tmr_mlp_set_loss(m.raw, int(kind)))
 
 
 def tmr_mlp_destroy(m: MLP):

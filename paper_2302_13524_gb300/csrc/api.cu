@@ -697,6 +697,10 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
     }
     SolverParams p{};
     p.T_cand = learned ? h->Tcand : nullptr;
+    // the proposal seeds the power iteration; without one, the solver keeps
+    // per row whichever of the proposal and the random start has the lower loss
+    p.seed_from_cand = learned && h->opt.power_iters > 0 ? 1 : 0;
+    p.judge_cand = learned && h->opt.power_iters == 0 ? 1 : 0;
     p.cand_wins = learned ? h->wins : nullptr;
     p.masks = h->masks;
     p.tw = h->tw;

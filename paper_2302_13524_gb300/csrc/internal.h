@@ -70,7 +70,10 @@ struct SolverParams {
     int *row_iters;       // [M]
     float *row_loss;      // [M]
     float2 *Zd;           // [Nd][M] defocus fields of the final iterate, or NULL
-    const float2 *T_cand; // [M][N] proposed starts compared per row with the init, or NULL
+    const float2 *T_cand; // [M][N] proposed starts (learned initialiser), or NULL
+    int seed_from_cand;   // the proposal (when finite, nonzero) replaces the Philox seed
+                          //   vector of the random/spectral start
+    int judge_cand;       // per row, the proposal replaces the start when its loss is lower
     unsigned *cand_wins;  // rows whose proposed start was kept
     unsigned *queue;      // row work counter, zeroed before the launch
     float2 *pairs;        // one-CTA-per-row schedule: L-BFGS pairs, pair_ctas regions of

@@ -5,7 +5,8 @@
 // Weights are kept as FP32 master copies (updated by Adam) and as BF16 copies
 // that feed the products; activations enter the products in BF16; every
 // product accumulates in FP32 (mma.sync m16n8k16 BF16 tensor-core steps).  The
-// loss is the mean squared error over every output.  One GEMM kernel serves
+// loss is the mean squared error over every output, or its phase-invariant
+// form (each target row rotated onto the output row first).  One GEMM kernel serves
 // the forward products X W^T, the input gradients dZ W and the weight
 // gradients dZ^T H through generic element strides.
 #include <cuda_bf16.h>
@@ -150,6 +151,31 @@ __global__ void k_mse(int B, int N, const float *Y, const float *T, __nv_bfloat1
     if (threadIdx.x == 0) part[blockIdx.x] = out[0];
 }
 
+// Phase-invariant loss: row r of T, read as t = T[:n] + i T[n:], rotated onto
+// the output row y = Y[:n] + i Y[n:]: Ta = t conj(c) / |c|, c = sum conj(y) t
+// (unrotated where c = 0).  One block per row; the sum in block_sum order.
+__global__ void k_align_targets(int n, const float *Y, const float *T, float *Ta)
+{
+    const size_t o = (size_t)blockIdx.x * 2 * n;
+    const float *y = Y + o, *t = T + o;
+    float cr = 0.f, ci = 0.f;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const float yr = y[k], yi = y[n + k], tr = t[k], ti = t[n + k];
+        cr = fmaf(yr, tr, fmaf(yi, ti, cr));
+        ci = fmaf(yr, ti, fmaf(-yi, tr, ci));
+    }
+    __shared__ float red[64], res[2];
+    float v[2] = {cr, ci};
+    block_sum<2>(v, red, res);
+    const float ac = sqrtf(res[0] * res[0] + res[1] * res[1]);
+    const float rr = ac > 0.f ? res[0] / ac : 1.f, ri = ac > 0.f ? -res[1] / ac : 0.f;  // conj(c) / |c|
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const float tr = t[k], ti = t[n + k];
+        Ta[o + k] = tr * rr - ti * ri;
+        Ta[o + n + k] = tr * ri + ti * rr;
+    }
+}
+
 __global__ void k_loss_finish(int nparts, const float *part, float total, float *loss)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -245,6 +271,8 @@ struct tmr_mlp {
     int cap = 0;
     __nv_bfloat16 *xb = nullptr, *h1b = nullptr, *h2b = nullptr, *dzb = nullptr, *dz2b = nullptr, *dyb = nullptr;
     float *z1 = nullptr, *z2 = nullptr, *y = nullptr, *dh = nullptr, *part = nullptr, *lossd = nullptr;
+    float *ta = nullptr;  // aligned targets of the phase-invariant loss [B][out]
+    int loss_kind = TMR_LOSS_MSE;
 };
 
 namespace {
@@ -267,7 +295,8 @@ tmr_status ensure_batch(tmr_mlp *m, int B)
 {
     if (B <= m->cap) return TMR_OK;
     void **bufs[] = {(void **)&m->xb, (void **)&m->h1b, (void **)&m->h2b, (void **)&m->dzb, (void **)&m->dz2b,
-                     (void **)&m->dyb, (void **)&m->z1, (void **)&m->z2, (void **)&m->y, (void **)&m->dh};
+                     (void **)&m->dyb, (void **)&m->z1, (void **)&m->z2, (void **)&m->y, (void **)&m->dh,
+                     (void **)&m->ta};
     for (void **b : bufs)
         if (*b) {
             cudaFree(*b);
@@ -285,7 +314,8 @@ tmr_status ensure_batch(tmr_mlp *m, int B)
               cudaMalloc(&m->z1, sizeof(float) * (size_t)B * m->h1) == cudaSuccess &&
               cudaMalloc(&m->z2, sizeof(float) * (size_t)B * m->h2) == cudaSuccess &&
               cudaMalloc(&m->y, sizeof(float) * (size_t)B * m->n_out) == cudaSuccess &&
-              cudaMalloc(&m->dh, sizeof(float) * hmax) == cudaSuccess;
+              cudaMalloc(&m->dh, sizeof(float) * hmax) == cudaSuccess &&
+              cudaMalloc(&m->ta, sizeof(float) * (size_t)B * m->n_out) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         return mfail(TMR_ERR_OOM, "MLP batch buffers");
@@ -315,6 +345,10 @@ void backward_core(tmr_mlp *m, int B, const float *T, float *loss)
     cudaStream_t s = m->stream;
     const __nv_bfloat16 *W2 = m->wb + m->off[2], *W3 = m->wb + m->off[4];
     const int nb = ew_blocks((size_t)B * m->n_out);
+    if (m->loss_kind == TMR_LOSS_PHASE) {  // the loss against each row's aligned target
+        k_align_targets<<<B, 256, 0, s>>>(m->n_out / 2, m->y, T, m->ta);
+        T = m->ta;
+    }
     k_mse<<<nb, 256, 0, s>>>(B, m->n_out, m->y, T, m->dyb, m->part);
     k_loss_finish<<<1, 32, 0, s>>>(nb, m->part, (float)((size_t)B * m->n_out), loss);
     // layer 3: dW3 = dY^T H2 ([n_out][B] x [B][h2]); db3 = colsum(dY); dH2 = dY W3
@@ -474,13 +508,24 @@ tmr_status tmr_mlp_train_step(tmr_mlp *m, const float *X, const float *T, int B,
     return cudaGetLastError() == cudaSuccess ? TMR_OK : mfail(TMR_ERR_CUDA, "adam kernel");
 }
 
+tmr_status tmr_mlp_set_loss(tmr_mlp *m, int kind)
+{
+    set_last_error("");
+    if (!m) return mfail(TMR_ERR_INVALID_ARG, "NULL network");
+    if (kind != TMR_LOSS_MSE && kind != TMR_LOSS_PHASE) return mfail(TMR_ERR_INVALID_ARG, "unknown loss");
+    if (kind == TMR_LOSS_PHASE && m->n_out % 2 != 0)
+        return mfail(TMR_ERR_INVALID_ARG, "the phase-invariant loss needs an even number of outputs");
+    m->loss_kind = kind;
+    return TMR_OK;
+}
+
 void tmr_mlp_destroy(tmr_mlp *m)
 {
     if (!m) return;
     if (m->stream) cudaStreamSynchronize(m->stream);
     else cudaDeviceSynchronize();
     void *p[] = {m->w, m->m, m->v, m->g, m->wb, m->xb, m->h1b, m->h2b, m->dzb, m->dz2b, m->dyb,
-                 m->z1, m->z2, m->y, m->dh, m->part, m->lossd};
+                 m->z1, m->z2, m->y, m->dh, m->part, m->lossd, m->ta};
     for (void *q : p)
         if (q) cudaFree(q);
     delete m;

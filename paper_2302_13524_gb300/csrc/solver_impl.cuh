@@ -699,8 +699,23 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
                 cluster.sync();
                 for (int i = tid; i < nmine; i += BT) ts[i] = slice_sum(i, 1.f / JN);
             } else {
-                for (int i = tid; i < nmine; i += BT)
-                    ts[i] = philox_cnormal(P.seed, (uint32_t)row, (uint32_t)(lo + i));
+                // seed: the proposed start (learned initialiser) where it is
+                // finite and nonzero, else the Philox vector
+                bool seeded = false;
+                if (P.T_cand && P.seed_from_cand) {
+                    float pv[32] = {0.f};
+                    for (int i = tid; i < nmine; i += BT) {
+                        const float2 v = P.T_cand[(size_t)row * N + lo + i];
+                        ts[i] = v;
+                        pv[0] += cabs2(v);
+                    }
+                    cluster_sum(pv, 1);
+                    seeded = isfinite(Gm.red[0]) && Gm.red[0] > 0.f;
+                    if (seeded && jr == 0 && tid == 0 && P.cand_wins) atomicAdd(P.cand_wins, 1u);
+                }
+                if (!seeded)
+                    for (int i = tid; i < nmine; i += BT)
+                        ts[i] = philox_cnormal(P.seed, (uint32_t)row, (uint32_t)(lo + i));
                 if (P.init == INIT_SPECTRAL) {
                     const float mean = sumy / (float)K;
                     float tau[E];
@@ -751,7 +766,7 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
             }
 
             // ---- per-row selection: a proposed start (learned initialiser) against this one ----
-            if (P.T_cand) {
+            if (P.T_cand && P.judge_cand) {
                 const float tinv = 1.f / Gm.tsc;
                 for (int i = tid; i < nmine; i += BT) gs[i] = cscale(P.T_cand[(size_t)row * N + lo + i], tinv);
                 float fv[2];

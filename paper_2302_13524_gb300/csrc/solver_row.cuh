@@ -221,7 +221,22 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
                 __syncthreads();
                 for (int i = tid; i < N; i += BT) ts[i] = team_sum(i, 1.f / JN);
             } else {
-                for (int i = tid; i < N; i += BT) ts[i] = philox_cnormal(P.seed, (uint32_t)row, (uint32_t)i);
+                // seed: the proposed start (learned initialiser) where it is
+                // finite and nonzero, else the Philox vector
+                bool seeded = false;
+                if (P.T_cand && P.seed_from_cand) {
+                    float pv[32] = {0.f};
+                    for (int i = tid; i < N; i += BT) {
+                        const float2 v = P.T_cand[(size_t)row * N + i];
+                        ts[i] = v;
+                        pv[0] += cabs2(v);
+                    }
+                    block_reduce(pv, 1);
+                    seeded = isfinite(Gm.red[0]) && Gm.red[0] > 0.f;
+                    if (seeded && tid == 0 && P.cand_wins) atomicAdd(P.cand_wins, 1u);
+                }
+                if (!seeded)
+                    for (int i = tid; i < N; i += BT) ts[i] = philox_cnormal(P.seed, (uint32_t)row, (uint32_t)i);
                 if (P.init == INIT_SPECTRAL) {
                     const float mean = sumy / (float)K;
                     for (int it = 0; it < P.power_iters; it++) {
@@ -265,7 +280,7 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
             }
 
             // ---- per-row selection: a proposed start (learned initialiser) against this one ----
-            if (P.T_cand) {
+            if (P.T_cand && P.judge_cand) {
                 const float tinv = 1.f / Gm.tsc;
                 for (int i = tid; i < N; i += BT) gs[i] = cscale(P.T_cand[(size_t)row * N + i], tinv);
                 float fv[2];

@@ -96,41 +96,57 @@ def test_mlp_training_learns_a_smooth_target():
     assert last < 0.1 * first
 
 
-def test_learned_start_is_selected_per_row():
-    """The per-row selection keeps a proposal only where its loss beats the spectral start:
-    every other row must come out exactly as in the plain spectral run, and the
-    number of rows that differ is the number the handle reports as kept."""
+def test_learned_start_seeds_and_falls_back():
+    """TMR_INIT_LEARNED with power iterations: the network's proposal seeds the
+    power iteration.  A network whose proposals are all zero (zero weights)
+    leaves every row on the Philox seed: the retrieve equals the plain
+    spectral one bit for bit and no row counts as seeded.  A network with
+    nonzero proposals seeds every row.  Without power iterations the solver
+    keeps, per row, the proposal or the random start, whichever has the lower
+    loss: rows that kept the random start equal the plain random-start run."""
     N, M, J, iters = 256, 24, 4, 20
     T, d, Y = problem(N, M, J, seed=8)
-    outs, kept = {}, None
-    for init in ("spectral", "learned"):
+
+    def run(init, pits, model=None):
         To = torch.empty((M, N), dtype=torch.complex64, device="cuda")
-        with tmr.tmr_create(N, M, J, to_dev(d), None, dict(init=init, power_iters=40, schedule=1)) as h:
+        with tmr.tmr_create(N, M, J, to_dev(d), None, dict(init=init, power_iters=pits, schedule=1)) as h:
             if init == "learned":
                 with pytest.raises(tmr.TMRError):
                     tmr.tmr_retrieve(h, to_dev(Y), None, iters, To)  # no network yet
-                m = tmr.tmr_mlp_create(J * N, 64, 64, 2 * N, seed=5)
-                tmr.tmr_set_init_model(h, m)
+                tmr.tmr_set_init_model(h, model)
             tmr.tmr_retrieve(h, to_dev(Y), None, iters, To)
             torch.cuda.synchronize()
-            if init == "learned":
-                kept = tmr.tmr_learned_rows(h)
-                m.close()
-        outs[init] = to_np(To)
-    differ = np.any(outs["learned"] != outs["spectral"], axis=1)
-    assert 0 <= kept < M
-    assert int(differ.sum()) == kept
-    assert np.mean(oracle.fidelity_rows(outs["learned"], T)) > 0.9
+            kept = tmr.tmr_learned_rows(h) if init == "learned" else None
+        return to_np(To), kept
+
+    with tmr.tmr_mlp_create(J * N, 64, 64, 2 * N, seed=5) as zero_net, \
+            tmr.tmr_mlp_create(J * N, 64, 64, 2 * N, seed=5) as net:
+        tmr.tmr_mlp_set_params(zero_net, np.zeros(zero_net.n_params, np.float32))
+        plain, _ = run("spectral", 40)
+        z, kept_z = run("learned", 40, zero_net)
+        assert kept_z == 0
+        np.testing.assert_array_equal(z, plain)
+        seeded, kept_s = run("learned", 40, net)
+        assert kept_s == M
+        assert np.mean(np.any(seeded != plain, axis=1)) > 0.9
+        assert np.mean(oracle.fidelity_rows(seeded, T)) > 0.9
+        rnd, _ = run("random", 0)
+        judged, kept_j = run("learned", 0, net)
+        differ = np.any(judged != rnd, axis=1)
+        assert 0 <= kept_j <= M and int(differ.sum()) == kept_j
 
 
 def test_learned_gain_measured_on_held_out_fibers():
-    """What the trained network gains, measured: a small fiber family (N = 256,
-    shared input basis, 6 training and 2 held-out fibers), the network trained
-    by the library's kernels on rows the plain solver retrieved, then every
-    start and arithmetic run on the held-out fibers.  The per-row selection bounds
-    the effect: rows whose proposal it rejects come out exactly as with the
-    spectral start, so the mean fidelities differ by at most the fraction of
-    rows kept; the measured gain is printed."""
+    """What the trained network gains, measured on held-out fibers of a small
+    family (N = 256, J = 4, shared input basis of R = 140 modes, 512 rows per
+    fiber; 60 training fibers, 2 held-out fibers): the network is trained by
+    the library's kernels (phase-invariant loss) on rows the plain solver
+    retrieved, then the plain spectral start and the learned start (the
+    proposal seeding the same power iteration) run with the same budgets.
+    The learned start must give a higher mean fidelity at every budget of
+    the grid, reach mean fidelity 0.98 with fewer operator products (power
+    plus L-BFGS iterations; each applies Q and Q^H once), and beat the
+    random start when no power iteration runs."""
     from paper_2302_13524_gb300 import learned_init as li
     import synth
     N, M, J, R = 256, 512, 4, 140
@@ -139,16 +155,27 @@ def test_learned_gain_measured_on_held_out_fibers():
     def tm_fn(f):
         return synth.tm_family(M, N, R, fiber_seed=f, basis_seed=0)
 
-    X, Tt = li.build_dataset(tm_fn, [1, 2, 3, 4, 5, 6], N, M, J, d, 1e4, 60, 60)
+    X, Tt = li.build_dataset(tm_fn, list(range(1, 61)), N, M, J, d, 1e4, 60, 60)
+    P, I = (0, 10, 20, 30, 40, 50, 60, 80), (10, 20, 30, 40)
+    budgets = [(p, i) for p in P for i in I]
     with tmr.tmr_mlp_create(J * N, 256, 256, 2 * N, seed=0) as model:
-        hist = li.train(model, X, Tt, 4, 128, 3e-4)
-        res = li.evaluate(model, tm_fn, [101, 102], N, M, J, d, 1e4, [10, 40], 60)
-    assert all(np.isfinite(hist))
-    for prec in ("fp32", "mixed"):
-        for it in (10, 40):
-            sp, le = res[f"spectral+{prec}/{it}"], res[f"learned+{prec}/{it}"]
-            gain = le["mean"] - sp["mean"]
-            print(f"learned vs spectral ({prec}, {it} iterations): mean fidelity gain {gain:+.4f}, "
-                  f"rows kept {le['rows_kept']:.3f}")
-            assert abs(gain) <= le["rows_kept"] + 1e-6
-    assert res["spectral+fp32/40"]["mean"] > 0.9
+        hist = li.train(model, X, Tt, 30, 128, 3e-4)
+        res = li.evaluate(model, tm_fn, [101, 102], N, M, J, d, 1e4, budgets,
+                          arms=(("random", "fp32"), ("spectral", "fp32"), ("learned", "fp32")))
+    assert all(np.isfinite(hist)) and hist[-1] < hist[0] - 0.01, hist  # the loss falls
+    mean = {(arm, p, i): res[f"{arm}+fp32/{p}/{i}"]["mean"] for arm in ("spectral", "learned")
+            for p in P for i in I}
+    for p in (10, 20, 30, 40):
+        for i in I:
+            print(f"P={p} I={i}: spectral {mean['spectral', p, i]:.4f} learned {mean['learned', p, i]:.4f}")
+            assert mean["learned", p, i] > mean["spectral", p, i], (p, i)
+
+    def products(arm, bar):
+        ok = [p + i for p in P for i in I if mean[arm, p, i] >= bar]
+        return min(ok) if ok else 10 ** 9
+
+    sp, le = products("spectral", 0.98), products("learned", 0.98)
+    print(f"operator products to mean fidelity 0.98: spectral {sp}, learned {le}")
+    assert le < sp
+    for i in I:
+        assert mean["learned", 0, i] > res[f"random+fp32/0/{i}"]["mean"] + 0.03

@@ -416,6 +416,57 @@ def test_mlp_gradient_finite_differences():
     assert np.max(abs(fd - g)) < 1e-8 * max(1.0, np.max(abs(g)))
 
 
+def _phase_loss_closed_form(Y, T):
+    """min over a of ||y - t e^{-i a}||^2 = ||y||^2 + ||t||^2 - 2 |<y, t>|, summed
+    over rows and divided by the number of outputs (rows as complex vectors)."""
+    n = Y.shape[1] // 2
+    y = Y[:, :n] + 1j * Y[:, n:]
+    t = T[:, :n] + 1j * T[:, n:]
+    per = np.sum(np.abs(y) ** 2, 1) + np.sum(np.abs(t) ** 2, 1) - 2 * np.abs(np.sum(np.conj(y) * t, 1))
+    return np.sum(per) / Y.size
+
+
+def test_mlp_phase_invariant_loss_gradient():
+    """The phase-invariant loss: its value equals the closed form of the
+    minimum over the global phase, its gradient matches central differences
+    of that closed form (the rotation enters only through the minimum, so the
+    envelope theorem must hold), and it ignores a per-row phase of the
+    targets."""
+    from oracle import mlp
+    rng = np.random.default_rng(31)
+    dims = (8, 6, 6, 6)
+    n = sum(int(np.prod(s)) for s in mlp.shapes(*dims))
+    theta = rng.standard_normal(n) * 0.4
+    X = rng.standard_normal((5, 8))
+    T = rng.standard_normal((5, 6))
+    L, g = mlp.loss_grad_phase(theta, dims, X, T)
+    Y, _ = mlp.forward(theta, dims, X)
+    assert abs(L - _phase_loss_closed_form(Y, T)) < 1e-13
+    h = 1e-6
+    fd = np.empty(n)
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = h
+        fp = _phase_loss_closed_form(mlp.forward(theta + e, dims, X)[0], T)
+        fm = _phase_loss_closed_form(mlp.forward(theta - e, dims, X)[0], T)
+        fd[i] = (fp - fm) / (2 * h)
+    assert np.max(abs(fd - g)) < 1e-7 * max(1.0, np.max(abs(g)))
+    # a per-row phase on the targets changes nothing
+    ph = np.exp(1j * rng.uniform(0, 2 * np.pi, 5))[:, None]
+    t = (T[:, :3] + 1j * T[:, 3:]) * ph
+    T2 = np.concatenate([t.real, t.imag], 1)
+    L2, g2 = mlp.loss_grad_phase(theta, dims, X, T2)
+    assert abs(L2 - L) < 1e-13 and np.max(abs(g2 - g)) < 1e-12
+    # targets already aligned with the outputs (<y, t> real, positive): plain MSE
+    Ta = Y + 0.01 * rng.standard_normal(Y.shape)
+    ya = Y[:, :3] + 1j * Y[:, 3:]
+    ta = Ta[:, :3] + 1j * Ta[:, 3:]
+    c = np.sum(np.conj(ya) * ta, 1)
+    ta = ta * (np.conj(c) / np.abs(c))[:, None]
+    Ta = np.concatenate([ta.real, ta.imag], 1)
+    assert abs(mlp.loss_grad_phase(theta, dims, X, Ta)[0] - mlp.loss_grad(theta, dims, X, Ta)[0]) < 1e-14
+
+
 def test_adam_constant_gradient_closed_form():
     """Under a constant gradient g the bias-corrected moments are exactly
     m_hat = g and v_hat = g^2 at every step t (m_t = (1 - b1^t) g,
