@@ -258,6 +258,17 @@ tmr_status tmr_mlp_train_step(tmr_mlp *m, const float *X, const float *T, int B,
                               float *loss);
 void tmr_mlp_destroy(tmr_mlp *m);
 
+/* The network's BF16 product on the tensor cores (tcgen05.mma, FP32
+ * accumulation in tensor memory, TMA-fed): C[M][N] = A B^T with A [M][K] and
+ * B [N][K] BF16 (bit patterns in uint16 storage), rows K-contiguous with
+ * strides lda, ldb elements; C float32 with row stride ldc >= N.  Device
+ * arrays of the current device.  Needs M, N >= 128, K >= 64, K, lda and ldb
+ * multiples of 8 and 16-byte aligned A and B (UNSUPPORTED otherwise; the
+ * network falls back to its mma.sync kernel there).  Synchronises `stream`;
+ * TMR_ERR_TIMEOUT if a barrier wait of the kernel ran out. */
+tmr_status tmr_gemm_bf16(int M, int N, int K, const void *A, int lda, const void *B, int ldb, float *C, int ldc,
+                         void *stream);
+
 /* Network used by TMR_INIT_LEARNED (not owned; keep it alive while the handle
  * uses it).  Its sizes must be in = J*N and out = 2*N. */
 tmr_status tmr_set_init_model(tmr_handle *h, tmr_mlp *model);

@@ -78,6 +78,7 @@ def _load():
         "tmr_mlp_train_step": ([vp, fp, fp, ip, ctypes.c_float, fp], ctypes.c_int),
         "tmr_mlp_destroy": ([vp], None),
         "tmr_mlp_set_loss": ([vp, ip], ctypes.c_int),
+        "tmr_gemm_bf16": ([ip, ip, ip, vp, ip, vp, ip, fp, ip, vp], ctypes.c_int),
         "tmr_set_init_model": ([H, vp], ctypes.c_int),
         "tmr_learned_rows": ([H], ctypes.c_longlong),
         "tmr_destroy": ([H], None),
@@ -329,6 +330,22 @@ def tmr_mlp_set_loss(m: MLP, kind):
     if isinstance(kind, str):
         kind = {"mse": TMR_LOSS_MSE, "phase": TMR_LOSS_PHASE}[kind]
     _check(lib.tmr_mlp_set_loss(m.raw, int(kind)))
+
+
+def tmr_gemm_bf16(A, B, C, stream=None):
+    """C = A B^T on the tensor cores; A [M][K], B [N][K] BF16 torch tensors (rows
+    contiguous), C float32 [M][N]."""
+    import torch
+    for name, x, dt in (("A", A, torch.bfloat16), ("B", B, torch.bfloat16), ("C", C, torch.float32)):
+        if x.dtype != dt or x.dim() != 2 or x.stride(1) != 1:
+            raise TypeError(f"{name}: expected a 2-D {dt} tensor with contiguous rows")
+    M, K = A.shape
+    N = B.shape[0]
+    if B.shape[1] != K or tuple(C.shape) != (M, N):
+        raise ValueError("shapes: A [M][K], B [N][K], C [M][N]")
+    _check(lib.tmr_gemm_bf16(M, N, K, ctypes.c_void_p(A.data_ptr()), A.stride(0), ctypes.c_void_p(B.data_ptr()),
+                             B.stride(0), ctypes.c_void_p(C.data_ptr()), C.stride(0),
+                             ctypes.c_void_p(stream) if stream else None))
 
 
 def tmr_mlp_destroy(m: MLP):

@@ -1,6 +1,7 @@
 // internal.h -- launchers shared between the C-ABI layer and the kernels.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 
@@ -105,6 +106,14 @@ long long solver_dispatch_row(int N, int what, const SolverParams *p, cudaStream
 long long solver_dispatch_mixed(int N, int G, int what, const SolverParams *p, cudaStream_t s, int *clusters_out);
 // Synthetic positive intensities for timing runs (autotuner).
 cudaError_t launch_fill_synthetic(float *y, size_t n, unsigned seed, cudaStream_t s);
+
+// ---- BF16 tensor-core GEMM (gemm_tc.cu) ---------------------------------------
+// C[M][N] (FP32, row stride ldc) = A B^T with A [M][K], B [N][K] BF16, K-contiguous
+// rows of stride lda, ldb.  Needs M, N >= 128, K >= 64, K, lda, ldb multiples of 8
+// and 16-byte aligned A, B; *err (device) is raised when a barrier wait ran out.
+bool gemm_tc_supported(int M, int N, int K, const void *A, int lda, const void *B, int ldb);
+cudaError_t gemm_tc(int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb,
+                    float *C, int ldc, int *err, cudaStream_t s);
 
 // ---- learned initialiser (mlp.cu) --------------------------------------------
 // rows of y (B of them) -> features -> network -> starts T scaled to the

@@ -110,11 +110,36 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const __
         }
 }
 
-static void gemm(int M, int N, int K, const __nv_bfloat16 *A, long long sam, long long sak,
-                 const __nv_bfloat16 *B, long long sbk, long long sbn, float *C, cudaStream_t s)
+static void gemm_sync(int M, int N, int K, const __nv_bfloat16 *A, long long sam, long long sak,
+                      const __nv_bfloat16 *B, long long sbk, long long sbn, float *C, cudaStream_t s)
 {
     dim3 grid((N + GB_N - 1) / GB_N, (M + GB_M - 1) / GB_M);
     k_gemm_bf16<<<grid, 128, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, N);
+}
+
+// out[c][r] = in[r][c] for an rows x cols BF16 matrix (row strides ldi, ldo);
+// 32 x 32 tiles through shared memory, block (32, 8)
+__global__ void k_transpose_bf16(int rows, int cols, const __nv_bfloat16 *__restrict__ in, long long ldi,
+                                 __nv_bfloat16 *__restrict__ out, long long ldo)
+{
+    __shared__ __nv_bfloat16 t[32][34];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += 8) {
+        const int r = r0 + j, c = c0 + threadIdx.x;
+        t[j][threadIdx.x] = (r < rows && c < cols) ? in[(size_t)r * ldi + c] : __float2bfloat16(0.f);
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += 8) {
+        const int c = c0 + j, r = r0 + threadIdx.x;
+        if (c < cols && r < rows) out[(size_t)c * ldo + r] = t[threadIdx.x][j];
+    }
+}
+
+static void transpose_bf16(int rows, int cols, const __nv_bfloat16 *in, long long ldi, __nv_bfloat16 *out,
+                           cudaStream_t s)
+{
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+    k_transpose_bf16<<<grid, dim3(32, 8), 0, s>>>(rows, cols, in, ldi, out, rows);
 }
 
 __device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
@@ -273,6 +298,10 @@ struct tmr_mlp {
     float *z1 = nullptr, *z2 = nullptr, *y = nullptr, *dh = nullptr, *part = nullptr, *lossd = nullptr;
     float *ta = nullptr;  // aligned targets of the phase-invariant loss [B][out]
     int loss_kind = TMR_LOSS_MSE;
+    // tensor-core GEMM: transposed-operand scratch and the barrier-timeout flag
+    __nv_bfloat16 *tsa = nullptr, *tsb = nullptr;
+    size_t tsa_cap = 0, tsb_cap = 0;
+    int *tc_err = nullptr;
 };
 
 namespace {
@@ -285,6 +314,42 @@ tmr_status mfail(tmr_status st, const char *msg)
 
 bool dev_ptr(const void *p) { return tmr::is_device_ptr(p); }
 
+// C[M][N] = sum_k A(m, k) B(k, n), A(m, k) = A[m sam + k sak], B(k, n) = B[k sbk + n sbn]:
+// on the tcgen05 tensor cores (gemm_tc.cu) when the shape allows, each operand
+// first made K-contiguous (a transpose into the network's scratch when it is
+// stored M- or N-contiguous); otherwise the mma.sync tile kernel above.
+void gemm(tmr_mlp *m, int M, int N, int K, const __nv_bfloat16 *A, long long sam, long long sak,
+          const __nv_bfloat16 *B, long long sbk, long long sbn, float *C)
+{
+    cudaStream_t s = m->stream;
+    if (M >= 128 && N >= 128 && K >= 64 && K % 8 == 0 && m->tc_err) {
+        const __nv_bfloat16 *At = A, *Bt = B;
+        long long lda = sam, ldb = sbn;
+        bool ok = true;
+        if (sak != 1) {  // stored [K][M] (sam == 1): transpose to [M][K]
+            ok = sam == 1 && (size_t)M * K <= m->tsa_cap;
+            if (ok) {
+                transpose_bf16(K, M, A, sak, m->tsa, s);
+                At = m->tsa;
+                lda = K;
+            }
+        }
+        if (ok && sbk != 1) {  // stored [K][N] (sbn == 1): transpose to [N][K]
+            ok = sbn == 1 && (size_t)N * K <= m->tsb_cap;
+            if (ok) {
+                transpose_bf16(K, N, B, sbk, m->tsb, s);
+                Bt = m->tsb;
+                ldb = K;
+            }
+        }
+        if (ok && lda <= 0x7fffffff && ldb <= 0x7fffffff && gemm_tc_supported(M, N, K, At, (int)lda, Bt, (int)ldb) &&
+            gemm_tc(M, N, K, At, (int)lda, Bt, (int)ldb, C, N, m->tc_err, s) == cudaSuccess)
+            return;
+        cudaGetLastError();
+    }
+    gemm_sync(M, N, K, A, sam, sak, B, sbk, sbn, C, s);
+}
+
 int ew_blocks(size_t n)
 {
     size_t b = (n + 255) / 256;
@@ -296,7 +361,7 @@ tmr_status ensure_batch(tmr_mlp *m, int B)
     if (B <= m->cap) return TMR_OK;
     void **bufs[] = {(void **)&m->xb, (void **)&m->h1b, (void **)&m->h2b, (void **)&m->dzb, (void **)&m->dz2b,
                      (void **)&m->dyb, (void **)&m->z1, (void **)&m->z2, (void **)&m->y, (void **)&m->dh,
-                     (void **)&m->ta};
+                     (void **)&m->ta, (void **)&m->tsa, (void **)&m->tsb};
     for (void **b : bufs)
         if (*b) {
             cudaFree(*b);
@@ -316,6 +381,18 @@ tmr_status ensure_batch(tmr_mlp *m, int B)
               cudaMalloc(&m->y, sizeof(float) * (size_t)B * m->n_out) == cudaSuccess &&
               cudaMalloc(&m->dh, sizeof(float) * hmax) == cudaSuccess &&
               cudaMalloc(&m->ta, sizeof(float) * (size_t)B * m->n_out) == cudaSuccess;
+    // transposed operands of the tensor-core GEMM: A sides [max(out, h1, h2)][B],
+    // B sides W3^T, W2^T and [max(in, h1, h2)][B]
+    const size_t hmx = (size_t)(m->h1 > m->h2 ? m->h1 : m->h2);
+    const size_t amax = (size_t)B * ((size_t)m->n_out > hmx ? (size_t)m->n_out : hmx);
+    size_t bmax = (size_t)m->h2 * m->n_out;
+    if ((size_t)m->h1 * m->h2 > bmax) bmax = (size_t)m->h1 * m->h2;
+    const size_t bb = (size_t)B * ((size_t)m->n_in > hmx ? (size_t)m->n_in : hmx);
+    if (bb > bmax) bmax = bb;
+    ok = ok && cudaMalloc(&m->tsa, sizeof(__nv_bfloat16) * amax) == cudaSuccess &&
+         cudaMalloc(&m->tsb, sizeof(__nv_bfloat16) * bmax) == cudaSuccess;
+    m->tsa_cap = ok ? amax : 0;
+    m->tsb_cap = ok ? bmax : 0;
     if (!ok) {
         cudaGetLastError();
         return mfail(TMR_ERR_OOM, "MLP batch buffers");
@@ -331,11 +408,11 @@ void forward_core(tmr_mlp *m, int B)
     const __nv_bfloat16 *W1 = m->wb + m->off[0], *W2 = m->wb + m->off[2], *W3 = m->wb + m->off[4];
     const float *b1 = m->w + m->off[1], *b2 = m->w + m->off[3], *b3 = m->w + m->off[5];
     // Z1 = X W1^T: A = X [B][n_in], B(k, n) = W1[n][k]
-    gemm(B, m->h1, m->n_in, m->xb, m->n_in, 1, W1, 1, m->n_in, m->z1, s);
+    gemm(m, B, m->h1, m->n_in, m->xb, m->n_in, 1, W1, 1, m->n_in, m->z1);
     k_bias_act<<<ew_blocks((size_t)B * m->h1), 256, 0, s>>>(B, m->h1, m->z1, b1, m->h1b, 1);
-    gemm(B, m->h2, m->h1, m->h1b, m->h1, 1, W2, 1, m->h1, m->z2, s);
+    gemm(m, B, m->h2, m->h1, m->h1b, m->h1, 1, W2, 1, m->h1, m->z2);
     k_bias_act<<<ew_blocks((size_t)B * m->h2), 256, 0, s>>>(B, m->h2, m->z2, b2, m->h2b, 1);
-    gemm(B, m->n_out, m->h2, m->h2b, m->h2, 1, W3, 1, m->h2, m->y, s);
+    gemm(m, B, m->n_out, m->h2, m->h2b, m->h2, 1, W3, 1, m->h2, m->y);
     k_bias_act<<<ew_blocks((size_t)B * m->n_out), 256, 0, s>>>(B, m->n_out, m->y, b3, nullptr, 0);
 }
 
@@ -352,17 +429,17 @@ void backward_core(tmr_mlp *m, int B, const float *T, float *loss)
     k_mse<<<nb, 256, 0, s>>>(B, m->n_out, m->y, T, m->dyb, m->part);
     k_loss_finish<<<1, 32, 0, s>>>(nb, m->part, (float)((size_t)B * m->n_out), loss);
     // layer 3: dW3 = dY^T H2 ([n_out][B] x [B][h2]); db3 = colsum(dY); dH2 = dY W3
-    gemm(m->n_out, m->h2, B, m->dyb, 1, m->n_out, m->h2b, m->h2, 1, m->g + m->off[4], s);
+    gemm(m, m->n_out, m->h2, B, m->dyb, 1, m->n_out, m->h2b, m->h2, 1, m->g + m->off[4]);
     k_colsum<<<(m->n_out + 255) / 256, 256, 0, s>>>(B, m->n_out, m->dyb, m->g + m->off[5]);
-    gemm(B, m->h2, m->n_out, m->dyb, m->n_out, 1, W3, m->h2, 1, m->dh, s);
+    gemm(m, B, m->h2, m->n_out, m->dyb, m->n_out, 1, W3, m->h2, 1, m->dh);
     k_gelu_back<<<ew_blocks((size_t)B * m->h2), 256, 0, s>>>((size_t)B * m->h2, m->dh, m->z2, m->dz2b);
     // layer 2
-    gemm(m->h2, m->h1, B, m->dz2b, 1, m->h2, m->h1b, m->h1, 1, m->g + m->off[2], s);
+    gemm(m, m->h2, m->h1, B, m->dz2b, 1, m->h2, m->h1b, m->h1, 1, m->g + m->off[2]);
     k_colsum<<<(m->h2 + 255) / 256, 256, 0, s>>>(B, m->h2, m->dz2b, m->g + m->off[3]);
-    gemm(B, m->h1, m->h2, m->dz2b, m->h2, 1, W2, m->h1, 1, m->dh, s);
+    gemm(m, B, m->h1, m->h2, m->dz2b, m->h2, 1, W2, m->h1, 1, m->dh);
     k_gelu_back<<<ew_blocks((size_t)B * m->h1), 256, 0, s>>>((size_t)B * m->h1, m->dh, m->z1, m->dzb);
     // layer 1
-    gemm(m->h1, m->n_in, B, m->dzb, 1, m->h1, m->xb, m->n_in, 1, m->g + m->off[0], s);
+    gemm(m, m->h1, m->n_in, B, m->dzb, 1, m->h1, m->xb, m->n_in, 1, m->g + m->off[0]);
     k_colsum<<<(m->h1 + 255) / 256, 256, 0, s>>>(B, m->h1, m->dzb, m->g + m->off[1]);
 }
 
@@ -413,7 +490,9 @@ tmr_status tmr_mlp_create(tmr_mlp **out, int n_in, int n_h1, int n_h2, int n_out
                     cudaMalloc(&m->g, sizeof(float) * o) == cudaSuccess &&
                     cudaMalloc(&m->wb, sizeof(__nv_bfloat16) * o) == cudaSuccess &&
                     cudaMalloc(&m->part, sizeof(float) * 152 * 8) == cudaSuccess &&
-                    cudaMalloc(&m->lossd, sizeof(float) * 4) == cudaSuccess;
+                    cudaMalloc(&m->lossd, sizeof(float) * 4) == cudaSuccess &&
+                    cudaMalloc(&m->tc_err, sizeof(int)) == cudaSuccess &&
+                    cudaMemset(m->tc_err, 0, sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         tmr_mlp_destroy(m);
@@ -461,9 +540,12 @@ tmr_status tmr_mlp_get_params(tmr_mlp *m, float *params)
 {
     set_last_error("");
     if (!m || !params) return mfail(TMR_ERR_INVALID_ARG, "NULL argument");
+    int tc_err = 0;
     if (cudaMemcpyAsync(params, m->w, sizeof(float) * m->np, cudaMemcpyDefault, m->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&tc_err, m->tc_err, sizeof(int), cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
         cudaStreamSynchronize(m->stream) != cudaSuccess)
         return mfail(TMR_ERR_CUDA, "get params");
+    if (tc_err) return mfail(TMR_ERR_TIMEOUT, "a tensor-core GEMM barrier wait ran out");
     return TMR_OK;
 }
 
@@ -525,7 +607,7 @@ void tmr_mlp_destroy(tmr_mlp *m)
     if (m->stream) cudaStreamSynchronize(m->stream);
     else cudaDeviceSynchronize();
     void *p[] = {m->w, m->m, m->v, m->g, m->wb, m->xb, m->h1b, m->h2b, m->dzb, m->dz2b, m->dyb,
-                 m->z1, m->z2, m->y, m->dh, m->part, m->lossd, m->ta};
+                 m->z1, m->z2, m->y, m->dh, m->part, m->lossd, m->ta, m->tsa, m->tsb, m->tc_err};
     for (void *q : p)
         if (q) cudaFree(q);
     delete m;

@@ -21,8 +21,12 @@ def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
-@pytest.mark.parametrize("dims,B", [((8, 6, 6, 4), 5), ((70, 40, 33, 20), 37), ((256, 96, 64, 130), 64)])
+@pytest.mark.parametrize("dims,B", [((8, 6, 6, 4), 5), ((70, 40, 33, 20), 37), ((256, 96, 64, 130), 64),
+                                    ((512, 264, 200, 136), 296)])
 def test_mlp_forward_and_gradient_match_oracle(dims, B):
+    """The last shape runs every product on the tcgen05 tensor cores (sizes of
+    at least 128 x 128 x 64 with rows a multiple of 8), with tails in every
+    dimension; the others run the mma.sync tile kernel."""
     rng = np.random.default_rng(sum(dims))
     with tmr.tmr_mlp_create(*dims, seed=3) as m:
         theta = (rng.standard_normal(m.n_params) * 0.3).astype(np.float32)
@@ -43,6 +47,40 @@ def test_mlp_forward_and_gradient_match_oracle(dims, B):
     g = to_np(G)
     assert _rel(g, Go) <= 3e-2
     assert np.dot(g, Go) / (np.linalg.norm(g) * np.linalg.norm(Go)) >= 0.999
+
+
+@pytest.mark.parametrize("dims,B", [((8, 6, 6, 4), 5), ((256, 96, 64, 130), 64)])
+def test_mlp_phase_invariant_loss_matches_oracle(dims, B):
+    """TMR_LOSS_PHASE against oracle.mlp.loss_grad_phase: the same targets give
+    the same loss and gradient (BF16 products), and turning every target row
+    by its own global phase changes neither the library's loss nor its
+    gradient beyond BF16 rounding."""
+    rng = np.random.default_rng(sum(dims) + 1)
+    n = dims[3] // 2
+    with tmr.tmr_mlp_create(*dims, seed=4) as m:
+        theta = (rng.standard_normal(m.n_params) * 0.3).astype(np.float32)
+        tmr.tmr_mlp_set_params(m, theta)
+        tmr.tmr_mlp_set_loss(m, "phase")
+        X = rng.standard_normal((B, dims[0])).astype(np.float32)
+        T = rng.standard_normal((B, dims[3])).astype(np.float32)
+        t = (T[:, :n] + 1j * T[:, n:]) * np.exp(1j * rng.uniform(0, 2 * np.pi, B))[:, None]
+        T2 = np.concatenate([t.real, t.imag], 1).astype(np.float32)
+        out = {}
+        for key, TT in (("T", T), ("T2", T2)):
+            loss = torch.empty(1, dtype=torch.float32, device="cuda")
+            G = torch.empty(m.n_params, dtype=torch.float32, device="cuda")
+            tmr.tmr_mlp_grad(m, to_dev(X), to_dev(TT), B, loss, G)
+            torch.cuda.synchronize()
+            out[key] = (float(to_np(loss)[0]), to_np(G))
+        with pytest.raises(tmr.TMRError):
+            tmr.tmr_mlp_set_loss(m, 7)
+    Lo, Go = omlp.loss_grad_phase(theta.astype(np.float64), dims, X, T)
+    L, g = out["T"]
+    assert abs(L - Lo) <= 2e-2 * Lo
+    assert _rel(g, Go) <= 3e-2
+    assert np.dot(g, Go) / (np.linalg.norm(g) * np.linalg.norm(Go)) >= 0.999
+    L2, g2 = out["T2"]
+    assert abs(L2 - L) <= 1e-3 * L and _rel(g2, g) <= 1e-2
 
 
 def test_mlp_train_step_is_adam_on_its_gradient():
