@@ -24,10 +24,14 @@ import torch
 from . import _lib as tmr
 
 
-def fiber_data(h, T: np.ndarray, photons: float, gen: torch.Generator):
-    """(T on device, noisy intensities y) for one fiber through tmr_forward."""
+def fiber_data(h, T, photons: float, gen: torch.Generator):
+    """(T on device, noisy intensities y) for one fiber (a numpy array or a
+    complex64 device tensor) through tmr_forward."""
     M, N = T.shape
-    Tg = torch.from_numpy(np.ascontiguousarray(T, dtype=np.complex64)).cuda()
+    if isinstance(T, torch.Tensor):
+        Tg = T.to(device="cuda", dtype=torch.complex64).contiguous()
+    else:
+        Tg = torch.from_numpy(np.ascontiguousarray(T, dtype=np.complex64)).cuda()
     y = torch.empty((M, h.J, N), dtype=torch.float32, device="cuda")
     tmr.tmr_forward(h, Tg, y)
     s = photons / float(y.mean())

@@ -95,6 +95,35 @@ def tm_family(M: int, N: int, R: int, fiber_seed: int, basis_seed: int = 0,
     return (T * np.sqrt(M / R)).astype(dtype)
 
 
+def tm_family_device(M: int, N: int, R: int, fiber_seed: int, basis_seed: int = 0, device: str = "cuda"):
+    """The fiber family of tm_family drawn on a GPU with torch's seeded
+    generator (the same distribution -- shared input basis V per basis_seed,
+    coupling U and phases theta per fiber_seed, E||row||^2 = 1 -- but not the
+    same numbers as the numpy version).  For workloads too large to draw on
+    the host in reasonable time (25 training fibers of 8192 x 2048); returns
+    a complex64 torch tensor on `device`."""
+    import torch
+
+    def gen(seed, stream, sub):
+        g = torch.Generator(device=device)
+        g.manual_seed(int(seed) * 1_000_003 + stream * 1009 + sub)
+        return g
+
+    R = min(R, M, N)
+
+    def cgauss(g, rows, cols):
+        re = torch.randn((rows, cols), generator=g, device=device, dtype=torch.float64)
+        im = torch.randn((rows, cols), generator=g, device=device, dtype=torch.float64)
+        return torch.complex(re, im)
+
+    V = torch.linalg.qr(cgauss(gen(basis_seed, STREAM_TM, 1), N, R))[0].conj().T
+    gf = gen(fiber_seed, STREAM_TM, 2)
+    U = torch.linalg.qr(cgauss(gf, M, R))[0]
+    theta = torch.rand(R, generator=gf, device=device, dtype=torch.float64) * (2.0 * np.pi)
+    T = (U * torch.exp(1j * theta)) @ V
+    return (T * np.sqrt(M / R)).to(torch.complex64)
+
+
 def make_tm(cfg: dict, seed: int = 0, M: int | None = None) -> np.ndarray:
     M = cfg["M"] if M is None else M
     if cfg["tm"] == "iid":
