@@ -123,6 +123,9 @@ typedef struct {
                                J N / 16 <= 512 threads, 16 points per thread, L-BFGS
                                pairs in a global-memory workspace of 2 (m+1) N
                                complex64 per resident CTA);
+                               32 = for 2048 < N <= 2731, one mask per CTA with the
+                               full-length Bluestein plan (FFTs of L = 8192) instead
+                               of the split outputs at L = 4096 of schedule 1;
                                0 = chosen by the autotuner (default)                 */
     const char *tune_cache; /* JSON file caching autotuned schedules per device, N, J,
                                m; NULL = this process only                           */
@@ -278,9 +281,14 @@ tmr_status tmr_set_init_model(tmr_handle *h, tmr_mlp *model);
 long long tmr_learned_rows(tmr_handle *h);
 
 /* The solver schedule the handle uses (after autotuning): 1, 2 or 4 masks per
- * CTA, or 16 for one CTA per row; 0 for a NULL handle or when no schedule
- * fits (see tmr_create). */
+ * CTA, 16 for one CTA per row, 32 for the full-length Bluestein plan; 0 for a
+ * NULL handle or when no schedule fits (see tmr_create). */
 int tmr_schedule(const tmr_handle *h);
+/* The schedules the autotuner timed when this handle was made, and the mean
+ * time of their timed runs in milliseconds (each: 4 power and 6 L-BFGS
+ * iterations on 608 synthetic rows): writes up to cap entries, returns their
+ * number (0 when the schedule was given, cached, or the only one). */
+int tmr_autotune_report(const tmr_handle *h, int *codes, float *ms, int cap);
 
 /* Release the handle and everything it allocated.  NULL is allowed. */
 void tmr_destroy(tmr_handle *h);

@@ -13,6 +13,6 @@ from ._lib import (  # noqa: F401
     tmr_defocus_forward, tmr_destroy, tmr_forward, tmr_grad, tmr_last_error, tmr_retrieve,
     tmr_learned_rows, tmr_mlp_create, tmr_mlp_destroy, tmr_mlp_forward, tmr_mlp_get_params,
     tmr_gemm_bf16, tmr_mlp_grad, tmr_mlp_set_loss, tmr_mlp_set_params, tmr_mlp_train_step, tmr_retrieve_from, tmr_retrieve_rows_static,
-    tmr_schedule, tmr_set_init_model, tmr_sync, tmr_workspace_bytes, half_grid, tmr_half_sample,
+    tmr_autotune_report, tmr_schedule, tmr_set_init_model, tmr_sync, tmr_workspace_bytes, half_grid, tmr_half_sample,
     tmr_preprocess, tmr_preprocess_workspace_bytes)
 from .retriever import Retriever, preprocess  # noqa: F401,E402

@@ -79,6 +79,7 @@ def _load():
         "tmr_mlp_destroy": ([vp], None),
         "tmr_mlp_set_loss": ([vp, ip], ctypes.c_int),
         "tmr_gemm_bf16": ([ip, ip, ip, vp, ip, vp, ip, fp, ip, vp], ctypes.c_int),
+        "tmr_autotune_report": ([H, vp, vp, ip], ctypes.c_int),
         "tmr_set_init_model": ([H, vp], ctypes.c_int),
         "tmr_learned_rows": ([H], ctypes.c_longlong),
         "tmr_destroy": ([H], None),
@@ -258,6 +259,15 @@ def tmr_last_error() -> str:
 
 def tmr_workspace_bytes(h: Handle) -> int:
     return int(lib.tmr_workspace_bytes(h.raw))
+
+
+def tmr_autotune_report(h: Handle) -> dict:
+    """{schedule code: mean ms of its timed runs} for the schedules the
+    autotuner timed when the handle was made ({} when none were timed)."""
+    codes = (ctypes.c_int * 8)()
+    ms = (ctypes.c_float * 8)()
+    n = lib.tmr_autotune_report(h.raw, codes, ms, 8)
+    return {int(codes[i]): float(ms[i]) for i in range(min(n, 8))}
 
 
 def tmr_schedule(h: Handle) -> int:

@@ -98,6 +98,12 @@ struct tmr_handle {
     // L-BFGS pair workspace of the one-CTA-per-row schedule (pair_ctas regions)
     float2 *pairs = nullptr;
     int pair_ctas = 0;
+    // transform table of the full-length Bluestein schedule (2048 < N <= 2731)
+    float2 *tw_alt = nullptr;
+    // what the autotuner timed when this handle was made (none: given or cached)
+    int tune_n = 0;
+    int tune_codes[8] = {};
+    float tune_ms[8] = {};
     // staging buffers for host arrays, keyed by slot
     DevBuf stage[8];
     // last retrieve, for tmr_sync's numeric check
@@ -234,9 +240,10 @@ bool schedule_ok(int N, int J, int m, int G, int smem_optin, int prec = 0)
 tmr_status autotune(tmr_handle *h, int smem_optin, int *G_out, bool *timed)
 {
     *timed = false;
-    int cand[4], nc = 0;
-    for (int G : {1, 2, 4, kRowSchedule})
-        if (schedule_ok(h->N, h->J, h->opt.m, G, smem_optin, h->prec) && (G != kRowSchedule || h->pairs))
+    int cand[5], nc = 0;
+    for (int G : {1, 2, 4, kRowSchedule, kBlueFullSchedule})
+        if (schedule_ok(h->N, h->J, h->opt.m, G, smem_optin, h->prec) && (G != kRowSchedule || h->pairs) &&
+            (G != kBlueFullSchedule || h->tw_alt))
             cand[nc++] = G;
     if (nc == 0) {  // the forward model and gradient still work; tmr_retrieve will refuse
         *G_out = 0;
@@ -291,6 +298,7 @@ tmr_status autotune(tmr_handle *h, int smem_optin, int *G_out, bool *timed)
     tmr_status st = TMR_OK;
     for (int c = 0; c < nc && st == TMR_OK; c++) {
         float ms = 0.f;
+        p.tw = cand[c] == kBlueFullSchedule ? h->tw_alt : h->tw;
         for (int rep = 0; rep < 3; rep++) {
             cudaMemsetAsync(h->queue, 0, sizeof(unsigned) * 4, s);
             cudaEventRecord(e0, s);
@@ -304,6 +312,11 @@ tmr_status autotune(tmr_handle *h, int smem_optin, int *G_out, bool *timed)
             float t = 0.f;
             cudaEventElapsedTime(&t, e0, e1);
             if (rep > 0) ms += t;  // the first run warms up
+        }
+        if (st == TMR_OK) {
+            h->tune_codes[h->tune_n] = cand[c];
+            h->tune_ms[h->tune_n] = ms / 2.f;
+            h->tune_n++;
         }
         if (st == TMR_OK && ms < best) {
             best = ms;
@@ -357,6 +370,16 @@ void tmr_default_options(tmr_options *o)
 
 int tmr_schedule(const tmr_handle *h) { return h ? h->G : 0; }
 
+int tmr_autotune_report(const tmr_handle *h, int *codes, float *ms, int cap)
+{
+    if (!h) return 0;
+    for (int i = 0; i < h->tune_n && i < cap; i++) {
+        if (codes) codes[i] = h->tune_codes[i];
+        if (ms) ms[i] = h->tune_ms[i];
+    }
+    return h->tune_n;
+}
+
 tmr_status tmr_set_init_model(tmr_handle *h, tmr_mlp *model)
 {
     tmr::set_last_error("");
@@ -391,7 +414,7 @@ void tmr_destroy(tmr_handle *h)
     else cudaDeviceSynchronize();
     void *ptrs[] = {h->masks, h->tw, h->H, h->Zd, h->phi, h->pf_ws, h->pf_loss, h->wts, h->queue,
                     h->pf_sync, h->pf_err, h->pf_iters, h->status_scratch, h->iters_scratch,
-                    h->loss_scratch, h->Tcand, h->wins, h->y16, h->ysc, h->pairs};
+                    h->loss_scratch, h->Tcand, h->wins, h->y16, h->ysc, h->pairs, h->tw_alt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &b : h->stage)
@@ -439,7 +462,8 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     TMR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
     if (o.schedule != 0 && !schedule_ok(N, J, o.m, o.schedule, smem_optin, o.precision))
         return fail(TMR_ERR_UNSUPPORTED,
-                    "opt.schedule must be 1, 2 or 4 (dividing J) or 16 (one CTA per row), and fit the device");
+                    "opt.schedule must be 1, 2 or 4 (dividing J), 16 (one CTA per row) or 32 (full-length "
+                    "Bluestein), and fit the device");
 
     tmr_handle *h = new tmr_handle();
     h->N = N;
@@ -535,6 +559,18 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
             return fail(TMR_ERR_OOM, "L-BFGS pair workspace of schedule 16 exceeds workspace_limit");
         }
     }
+    // the other Bluestein plan's table, when that schedule can run
+    if ((o.schedule == 0 || o.schedule == kBlueFullSchedule) &&
+        schedule_ok(N, J, o.m, kBlueFullSchedule, smem_optin, h->prec)) {
+        const int n = xform_table_blue_full(N, nullptr);
+        std::vector<float2> t2(n > 0 ? n : 1);
+        xform_table_blue_full(N, t2.data());
+        TRY(halloc(h, (void **)&h->tw_alt, sizeof(float2) * t2.size(), "full Bluestein table"));
+        if (cudaMemcpy(h->tw_alt, t2.data(), sizeof(float2) * t2.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            tmr_destroy(h);
+            return fail(TMR_ERR_CUDA, "copy full Bluestein table");
+        }
+    }
     // solver schedule: given, cached, or autotuned
     if (o.schedule != 0) {
         h->G = o.schedule;
@@ -551,6 +587,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
                 if (f != fm.end() && schedule_ok(N, J, o.m, f->second, smem_optin, h->prec)) G = f->second;
             }
             if (G == kRowSchedule && !h->pairs) G = 0;  // no pair workspace here: tune again
+            if (G == kBlueFullSchedule && !h->tw_alt) G = 0;
         }
         bool timed = true;  // a cached choice was timed when it was made
         if (!G) {
@@ -703,7 +740,7 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
     p.judge_cand = learned && h->opt.power_iters == 0 ? 1 : 0;
     p.cand_wins = learned ? h->wins : nullptr;
     p.masks = h->masks;
-    p.tw = h->tw;
+    p.tw = h->G == kBlueFullSchedule ? h->tw_alt : h->tw;
     p.y = (const float *)dy;
     p.T_init = (const float2 *)dTin;
     p.T_out = (float2 *)dT;

@@ -37,6 +37,10 @@ bool xform_supported(int N);
 // thread (the instantiated variant); false when N has none.
 bool xform_blue_shape(int N, int *L, int *ne);
 int xform_table(int N, float2 *out);  // length in float2; writes when out != NULL
+// For 2048 < N <= 2731 the other Bluestein plan: the full convolution at
+// L = 8192 (XfBlue<8192, 6>) instead of the split outputs at L = 4096; the
+// table of the solver schedule kBlueFullSchedule.
+int xform_table_blue_full(int N, float2 *out);
 // Mixed precision (TMR_PREC_MIXED): N = 256, 1024, 2048 or 4096; its table is
 // [FP32 twiddles | tensor-core DFT fragments (radix 16, radix 8) | roots W_N^k].
 bool mixed_supported(int N);
@@ -90,6 +94,11 @@ struct SolverParams {
 // per thread, FP32, N = 512 .. 2048 with J N / 16 <= 512, L-BFGS pairs in the
 // global workspace p.pairs (solver_row.cuh).
 constexpr int kRowSchedule = 16;
+// G = kBlueFullSchedule (32): for 2048 < N <= 2731, one mask per CTA with the
+// full-length Bluestein plan (L = 8192) and its own transform table.
+constexpr int kBlueFullSchedule = 32;
+long long solver_dispatch_blue8192(int N, int ne, int what, const SolverParams *p, cudaStream_t s,
+                                   int *clusters_out);
 bool solver_variant_exists(int N, int G, int prec = 0);
 // schedule G usable for (N, J): variant exists, J % G == 0 for cluster schedules
 bool solver_schedule_valid(int N, int J, int G, int prec = 0);

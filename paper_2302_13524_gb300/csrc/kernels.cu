@@ -194,6 +194,12 @@ int xform_table(int N, float2 *out)
     }
 }
 
+int xform_table_blue_full(int N, float2 *out)
+{
+    if (N <= 2048 || N > kBlueSplitMaxN) return -1;
+    return blue_table<8192, 6>(N, out);  // the constants do not depend on the register count
+}
+
 bool mixed_supported(int N) { return N == 256 || N == 1024 || N == 2048 || N == 4096; }
 
 // Round to the nearest BF16 (ties to even); returns the bits.

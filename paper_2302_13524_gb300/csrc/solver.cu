@@ -9,6 +9,7 @@ namespace tmr {
 bool solver_variant_exists(int N, int G, int prec)
 {
     if (G == kRowSchedule) return prec == 0 && (N == 512 || N == 1024 || N == 2048);
+    if (G == kBlueFullSchedule) return prec == 0 && N > 2048 && N <= 2731;
     if (G != 1 && G != 2 && G != 4) return false;
     if (prec != 0) return G == 1 && mixed_supported(N);
     if (fft_supported(N)) return G * fft_threads(N) <= 512;
@@ -29,6 +30,7 @@ static long long solver_dispatch(int N, int G, int what, const SolverParams *p, 
                                  int *clusters_out)
 {
     if (G == kRowSchedule) return solver_dispatch_row(N, what, p, s, clusters_out);
+    if (G == kBlueFullSchedule) return solver_dispatch_blue8192(N, 6, what, p, s, clusters_out);
     if (p->prec != 0) return solver_dispatch_mixed(N, G, what, p, s, clusters_out);
     if (!fft_supported(N)) return solver_dispatch_blue(N, G, what, p, s, clusters_out);
     TMR_SOLVER_N(64)
@@ -56,6 +58,7 @@ bool solver_schedule_valid(int N, int J, int G, int prec)
 {
     if (!solver_variant_exists(N, G, prec) || J < 1) return false;
     if (G == kRowSchedule) return J * (N / 16) <= 512;
+    if (G == kBlueFullSchedule) return true;  // one mask per CTA
     return J % G == 0;
 }
 

@@ -12,9 +12,6 @@ namespace tmr {
         return (long long)launch_solver_t<XfBlue<LL, NEE>, 1>(*p, s, clusters_out);       \
     }
 
-long long solver_dispatch_blue8192(int N, int ne, int what, const SolverParams *p, cudaStream_t s,
-                                   int *clusters_out);
-
 long long solver_dispatch_blue(int N, int G, int what, const SolverParams *p, cudaStream_t s, int *clusters_out)
 {
     int L = 0, ne = 0;

@@ -1,5 +1,6 @@
 // solver_bs2.cu -- Bluestein solver instantiations at L = 8192 (N in
-// (2731, 4096], 6..8 registers per thread); dispatched from solver_bs.cu.
+// (2731, 4096], 6..8 registers per thread; and, as schedule 32, N in
+// (2048, 2731] with 6 registers); dispatched from solver_bs.cu and solver.cu.
 #include "solver_impl.cuh"
 
 namespace tmr {

@@ -234,3 +234,47 @@ def test_large_length_needs_a_short_history():
         torch.cuda.synchronize()
     Tr, _, _, _ = oracle.retrieve_rows(Y, d.astype(np.complex128), iters, m=1, T_init=T_init)
     assert_rows_close(to_np(Tn), Tr, 1e-4 * iters)
+
+
+# ------------------------------------------------------------ transform plans for 2048 < N <= 2731
+@pytest.mark.parametrize("N,J", [(2286, 4), (2600, 4)])
+def test_full_bluestein_plan_matches_oracle(N, J):
+    """Schedule 32 (Bluestein at L = 8192 over the whole output) against the
+    oracle step by step, and against schedule 1 (split outputs at L = 4096):
+    the same method through another transform plan."""
+    M, iters = 6, 4
+    T, d, Y = problem(N, M, J, seed=N + 32)
+    rng = np.random.default_rng(N)
+    T_init = c64(T + 0.3 * (rng.standard_normal(T.shape) + 1j * rng.standard_normal(T.shape)) / np.sqrt(N))
+    out = {}
+    for G in (1, 32):
+        Tn = torch.empty((M, N), dtype=torch.complex64, device="cuda")
+        its = torch.empty(M, dtype=torch.int32, device="cuda")
+        with handle(N, M, J, d, schedule=G) as h:
+            assert tmr.tmr_schedule(h) == G
+            tmr.tmr_retrieve_from(h, to_dev(T_init), to_dev(Y), None, iters, Tn, row_iters=its)
+            torch.cuda.synchronize()
+        out[G] = (to_np(Tn), to_np(its))
+    Tr, _, it_ref, _ = oracle.retrieve_rows(Y, d.astype(np.complex128), iters, T_init=T_init)
+    for G in (1, 32):
+        assert np.all(out[G][1] == it_ref)
+        assert_rows_close(out[G][0], Tr, 1e-4 * iters)
+
+
+def test_autotuner_times_both_bluestein_plans():
+    """At N = 2286 the autotuner has two candidates, the split-output plan
+    (schedule 1) and the full-length plan (schedule 32): it times both and
+    keeps the faster, which a handle made afterwards finds in the cache."""
+    N, M, J = 2286, 16, 4
+    _, d, Y = problem(N, M, J, seed=77)
+    with handle(N, M, J, d, m=3, schedule=0) as h:  # m = 3: a tuning key no other test uses
+        rep = tmr.tmr_autotune_report(h)
+        G = tmr.tmr_schedule(h)
+        To = torch.empty((M, N), dtype=torch.complex64, device="cuda")
+        tmr.tmr_retrieve(h, to_dev(Y), None, 5, To)
+        torch.cuda.synchronize()
+    print("autotuner at N = 2286:", rep, "->", G)
+    assert set(rep) == {1, 32}
+    assert G == min(rep, key=rep.get)
+    with handle(N, M, J, d, m=3, schedule=0) as h2:
+        assert tmr.tmr_schedule(h2) == G and tmr.tmr_autotune_report(h2) == {}

@@ -75,27 +75,33 @@ def test_mixed_rejects_other_lengths():
     assert ei.value.status == tmr.TMR_ERR_INVALID_ARG
 
 
-def test_mixed_learned_start_is_selected_per_row():
-    """The learned start with mixed precision: the per-row selection (in
-    tensor-core arithmetic) keeps a proposal only where its loss beats the spectral start,
-    so the rows it does not keep come out exactly as in the mixed spectral run."""
+def test_mixed_learned_start_seeds_and_falls_back():
+    """The learned start with mixed precision: a network whose proposals are
+    all zero leaves every row on the Philox seed (the result equals the mixed
+    spectral run bit for bit, no row counts as seeded); a network with nonzero
+    proposals seeds every row."""
     N, M, J, iters = 256, 24, 4, 20
     T, d, Y = problem(N, M, J, seed=9)
-    outs, kept = {}, None
-    for init in ("spectral", "learned"):
+
+    def run(init, model=None):
         To = torch.empty((M, N), dtype=torch.complex64, device="cuda")
         with handle(N, M, J, d, init=tmr.INIT[init], power_iters=40, precision=MIXED) as h:
-            if init == "learned":
-                m = tmr.tmr_mlp_create(J * N, 64, 64, 2 * N, seed=5)
-                tmr.tmr_set_init_model(h, m)
+            if model is not None:
+                tmr.tmr_set_init_model(h, model)
             tmr.tmr_retrieve(h, to_dev(Y), None, iters, To)
             torch.cuda.synchronize()
-            if init == "learned":
-                kept = tmr.tmr_learned_rows(h)
-                m.close()
-        outs[init] = to_np(To)
-    differ = np.any(outs["learned"] != outs["spectral"], axis=1)
-    assert 0 <= kept < M and int(differ.sum()) == kept
+            kept = tmr.tmr_learned_rows(h) if model is not None else None
+        return to_np(To), kept
+
+    with tmr.tmr_mlp_create(J * N, 64, 64, 2 * N, seed=5) as zero_net, \
+            tmr.tmr_mlp_create(J * N, 64, 64, 2 * N, seed=5) as net:
+        tmr.tmr_mlp_set_params(zero_net, np.zeros(zero_net.n_params, np.float32))
+        plain, _ = run("spectral")
+        z, kz = run("learned", zero_net)
+        assert kz == 0
+        np.testing.assert_array_equal(z, plain)
+        _, ks = run("learned", net)
+        assert ks == M
 
 
 def test_mixed_vs_fp32_at_2048():
@@ -178,8 +184,9 @@ def test_precision_workload_sampled_rows():
     """N = 4096, M = 16384 (128 x 128), J = 4, mode model R = 2200, Poisson
     1e4, spectral start, 100 iterations (the last 10 FP32).  Stated error of
     the mixed path: against the FP32 GPU path on every row (fidelity to the
-    ground truth and to each other) and against the FP64 oracle on 4 sampled
-    rows at a short budget from the same intensities."""
+    ground truth and to each other), against the FP64 oracle on 4 sampled
+    rows at a short budget from the same intensities, and, per transform
+    (forward model, loss, gradient), against the oracle on 256 sampled rows."""
     cfg = synth.CONFIGS["precision"]
     N, M, J = cfg["N"], cfg["M"], cfg["J"]
     T = c64(synth.tm_modes(M, N, cfg["R"], seed=0, dtype=np.complex64))
@@ -222,3 +229,25 @@ def test_precision_workload_sampled_rows():
     fm = oracle.fidelity_rows(to_np(Tm), T[rows])
     fo = oracle.fidelity_rows(Tr, T[rows])
     assert np.mean(np.abs(fm - fo) <= 1e-3) >= 3 / 4, (fm, fo)
+    # per-transform error of the mixed arithmetic against the FP64 oracle on 256
+    # sampled rows of the workload: intensities of the true rows, and the loss
+    # and gradient at rows perturbed by 30 % of their norm (large residuals)
+    r256 = synth.sample_rows(M, 256, seed=2)
+    Tt = T[r256]
+    rng = np.random.default_rng(3)
+    Tp = c64(Tt + 0.3 * (rng.standard_normal(Tt.shape) + 1j * rng.standard_normal(Tt.shape)) / np.sqrt(2 * N))
+    Y_or = oracle.forward(Tt.astype(np.complex128), d.astype(np.complex128))
+    loss_or, G_or = oracle.loss_grad(Tp.astype(np.complex128), d.astype(np.complex128), Y_or)
+    Yg = torch.empty((256, J, N), dtype=torch.float32, device="cuda")
+    lg = torch.empty(256, dtype=torch.float32, device="cuda")
+    Gg = torch.empty((256, N), dtype=torch.complex64, device="cuda")
+    with handle(N, 256, J, d, precision=MIXED) as h:
+        tmr.tmr_forward(h, to_dev(Tt), Yg)
+        tmr.tmr_grad(h, to_dev(Tp), to_dev(f32(Y_or)), lg, Gg)
+        torch.cuda.synchronize()
+    e_fwd = max(rel_l2_rows(to_np(Yg), Y_or), max_rel_elem_rows(to_np(Yg), Y_or))
+    e_loss = float(np.max(np.abs(to_np(lg) - loss_or) / loss_or))
+    e_grad = max(rel_l2_rows(to_np(Gg), G_or), max_rel_elem_rows(to_np(Gg), G_or))
+    print(f"mixed vs FP64 oracle on 256 rows (N = 4096): forward {e_fwd:.2e}, loss {e_loss:.2e}, "
+          f"gradient {e_grad:.2e}")
+    assert e_fwd <= 1e-4 and e_loss <= 1e-4 and e_grad <= 1e-4
