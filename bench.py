@@ -51,6 +51,9 @@ WORKLOADS = {
                       desc="precision N=4096 M=16384 (128x128) J=4 modes R=2200 Poisson 1e4"),
     # the step starts from camera frames: half-sampling and the 99.9 % fiber
     # mask (Sec. 2.2), then the plain retrieval of the rows inside the mask
+    # failed-row fraction against J with the 2D probing DFT (64 x 64 modes)
+    "jsweep": dict(N=4096, J=8, R=2200, ny=64, nx=64, photons=None, iters=200, tol=0.0,
+                   desc="jsweep: N=4096 (64x64 2D probing DFT), M=4096, J=3..8, noiseless"),
     "camera": dict(N=2048, J=4, R=1100, ny=128, nx=64, photons=3000.0, iters=100, tol=0.0,
                    camera=dict(radius=0.45, leak=1e-3, energy_frac=0.999),
                    desc="camera: 8192 uint16 probe frames + 50 defocus frames of 256x128 pixels, "
@@ -450,11 +453,58 @@ def second_half_arms(tmr, torch, synth, N, M, J, R, m, d, dop, photons, phase_it
     return out
 
 
+# ---------------------------------------------------------------- J-sweep (2D probing DFT)
+def run_jsweep(args):
+    """Failed-row fraction against the number of masks J = 3 .. 8 with the
+    paper's 2D probing DFT (Sec. 2.2: K the 2D DFT of the 64 x 64 phase
+    modes, N = 4096), noiseless data from a mode-model TM (R = 2200) on a
+    64 x 64 output grid, spectral start (100 power iterations) and 200 L-BFGS
+    iterations; a row fails when its fidelity to the truth is below 0.99.  The
+    paper's simulation (Sec. 3) swept M = 3 .. 9 masks on a measured TM; J = 9
+    is beyond this library's 8."""
+    import torch
+    import paper_2302_13524_gb300 as tmr
+    import synth
+    N, n1, M, R = 4096, 64, 4096, 2200
+    pits, iters = args.power_iters, 200 if args.iters == WORKLOADS[args.workload]["iters"] else args.iters
+    T = torch.from_numpy(synth.tm_modes(M, N, R, seed=0, dtype=np.complex64)).cuda()
+    out = []
+    for J in range(3, 9):
+        _, d = synth.mask_phases(J, N, seed=J)
+        dg = torch.from_numpy(np.ascontiguousarray(d, dtype=np.complex64)).cuda()
+        with tmr.tmr_create(N, M, J, dg, None, dict(probe_n1=n1, init="spectral", power_iters=pits,
+                                                      clip=2.0)) as h:
+            y = torch.empty((M, J, N), dtype=torch.float32, device="cuda")
+            tmr.tmr_forward(h, T, y)
+            To = torch.empty((M, N), dtype=torch.complex64, device="cuda")
+            tmr.tmr_retrieve(h, y, None, iters, To)  # warm
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            tmr.tmr_retrieve(h, y, None, iters, To)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+        f = fidelity_rows_t(To, T).float().cpu().numpy()
+        out.append({"J": J, "failed_frac": float(np.mean(f < 0.99)), "mean": float(f.mean()),
+                    "p1": float(np.percentile(f, 1)), "rows_per_s": M / (ms / 1e3), "ms": ms})
+        del y, To
+    line = {"metric": "failed-row fraction vs J (2D probing DFT)", "unit": "fraction", "n_gpus": 1,
+            "higher_is_better": False, "data": "synthetic, noiseless",
+            "config": {"workload": f"jsweep: N={N} as 64x64 2D DFT (probe_n1={n1}), M={M} (64x64), modes R={R}, "
+                                   f"noiseless, {pits} power + {iters} L-BFGS iterations, J = 3..8",
+                       "dtype": "f32"},
+            "value": out[-1]["failed_frac"], "sweep": out}
+    print(json.dumps(line))
+    return 0
+
+
 # ---------------------------------------------------------------- our arm
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "jsweep":
+        return run_jsweep(args)
     import torch
     rank, world, local = dist_env()
     if world > 1:

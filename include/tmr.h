@@ -137,6 +137,14 @@ typedef struct {
     int withhold_release;   /* test hook, 0 in normal use: 1 = the fit's grid barrier
                                is never released, so every wait runs out after
                                wait_spins polls (exercises the bounded wait)         */
+    int probe_n1;           /* 0 (default): K is the 1D DFT of length N.  n1 > 0: K is
+                               the paper's 2D DFT (Sec. 2.2, Eq. probingmatrix) of the
+                               row read as an n1 x (N/n1) array (element a*(N/n1) + b
+                               is row a, column b), its spectrum X[k1][k2] stored as
+                               pattern k1 + n1*k2 of each mask (y, forward, gradient,
+                               defocus fields).  FP32 only; N = 512 with n1 = 8 or 64,
+                               or N = 4096 with n1 = 8, 64 or 512 (the strides at which
+                               a pass of the register FFT starts); cluster schedules */
 } tmr_options;
 
 /* Fill *opt with the defaults above. */
@@ -306,8 +314,8 @@ void tmr_destroy(tmr_handle *h);
  * T_out complex64 [M][N], row_status / row_iters int32 [M] and row_loss
  * float32 [M] (each may be NULL).
  * opt: NULL for the defaults; workspace_limit, use_graph, schedule and tune_cache
- * are ignored (one mask per CTA); opt->precision must be TMR_PREC_FP32
- * (TMR_ERR_UNSUPPORTED otherwise).
+ * are ignored (one mask per CTA); opt->precision must be TMR_PREC_FP32 and
+ * opt->probe_n1 0 (TMR_ERR_UNSUPPORTED otherwise).
  * stream: cudaStream_t, NULL for the legacy default stream.
  *
  * Its only scratch (a row work counter and the FFT twiddle table) lives in

@@ -71,6 +71,7 @@ def lib():
             "orc_phase_fit": ([dp, dp, c_int, c_int, c_int, dp, c_dbl, c_int, c_int, dp, dp, ip,
                                dp], c_int),
             "orc_fidelity_rows": ([dp, dp, c_int, c_int, dp], c_int),
+            "orc_set_probe_2d": ([c_int, c_int], c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -110,6 +111,24 @@ def dft(x, sign: int = -1) -> np.ndarray:
     X = np.empty_like(x)
     assert lib().orc_dft(_p(x), _p(X), x.size, sign) == 0
     return X
+
+
+class probe_2d:
+    """Context in which the probing DFT K of every oracle call for rows of
+    length N is the 2D DFT of the row read as an n1 x (N / n1) array (paper:
+    "the 2D Fourier transform matrix for N_kx x 2N_ky"), its spectrum stored
+    column by column (pattern k1 + n1 k2).  Outside it K is the 1D DFT."""
+
+    def __init__(self, n1: int, N: int):
+        self.n1, self.N = int(n1), int(N)
+
+    def __enter__(self):
+        if lib().orc_set_probe_2d(self.n1, self.N) != 0:
+            raise ValueError("n1 must divide N")
+        return self
+
+    def __exit__(self, *a):
+        lib().orc_set_probe_2d(0, 0)
 
 
 def forward(T, masks, return_fields: bool = False):

@@ -104,23 +104,75 @@ int orc_dft(const double *x, double *X, int N, int sign)
 /* Probing operator Q and its adjoint (Eq. probingmatrix, Eq. optTMsmall2)    */
 /* ------------------------------------------------------------------------ */
 
-/* z = Q t : z[j*N + k] = F(d_j .* t)[k].  scratch: N entries. */
+/* The probing DFT K (Eq. probingmatrix): the 1D DFT of length N (default),
+ * or, after orc_set_probe_2d(n1, N), the 2D DFT of the vector read as an
+ * n1 x n2 array (n2 = N / n1; element a*n2 + b is row a, column b) -- the
+ * paper's "2D Fourier transform matrix for an N_kx x 2N_ky matrix".  The 2D
+ * spectrum X[k1][k2] is stored at pattern index k1 + n1*k2 (column by
+ * column).  A process-wide setting of this test oracle (read-only while a
+ * computation runs). */
+static int g_probe_n1 = 0, g_probe_N = 0;
+static cplx *g_tw1 = NULL, *g_tw2 = NULL;
+
+int orc_set_probe_2d(int n1, int N)
+{
+    free(g_tw1);
+    free(g_tw2);
+    g_tw1 = g_tw2 = NULL;
+    g_probe_n1 = g_probe_N = 0;
+    if (n1 == 0) return 0;
+    if (n1 < 1 || N <= 0 || N % n1) return -1;
+    g_probe_n1 = n1;
+    g_probe_N = N;
+    g_tw1 = make_twiddles(n1);
+    g_tw2 = make_twiddles(N / n1);
+    return 0;
+}
+
+/* Z[k1 + n1 k2] = sum_{a, b} s[a n2 + b] W_n1^(a k1 sign) W_n2^(b k2 sign) (forward
+ * layout), or, for the adjoint layout, out[a n2 + b] = the same double sum of
+ * V[k1 + n1 k2] with the conjugate kernel.  Separable: the n2-point sums along
+ * each row, then the n1-point sums along each column.  scratch: 2 N entries. */
+static void dft2_probe(const cplx *in, cplx *out, int N, int sign, int adjoint_layout, cplx *scratch)
+{
+    const int n1 = g_probe_n1, n2 = N / n1;
+    cplx *A = scratch, *col = scratch + N;  /* A[a][k2] (or A[k1][b]) */
+    if (!adjoint_layout) {
+        for (int a = 0; a < n1; a++) dft_naive(in + (size_t)a * n2, A + (size_t)a * n2, n2, sign, g_tw2);
+        for (int k2 = 0; k2 < n2; k2++) {
+            for (int a = 0; a < n1; a++) col[a] = A[(size_t)a * n2 + k2];
+            dft_naive(col, out + (size_t)n1 * k2, n1, sign, g_tw1);  /* out[k1 + n1 k2] */
+        }
+    } else {
+        /* in[k1 + n1 k2]: the n1-point sums over k1 for each k2 give A2[a][k2]
+           (held as A[k2 * n1 + a]), then the n2-point sums over k2 for each a */
+        for (int k2 = 0; k2 < n2; k2++) dft_naive(in + (size_t)n1 * k2, A + (size_t)n1 * k2, n1, sign, g_tw1);
+        for (int a = 0; a < n1; a++) {
+            for (int k2 = 0; k2 < n2; k2++) col[k2] = A[(size_t)n1 * k2 + a];
+            dft_naive(col, out + (size_t)a * n2, n2, sign, g_tw2);
+        }
+    }
+}
+
+/* z = Q t : z[j*N + k] = K(d_j .* t)[k].  scratch: 3 N entries. */
 static void apply_Q(const cplx *t, const cplx *d, int N, int J, const cplx *tw,
                     cplx *z, cplx *scratch)
 {
     for (int j = 0; j < J; j++) {
         for (int n = 0; n < N; n++) scratch[n] = d[(size_t)j * N + n] * t[n];
-        dft_naive(scratch, z + (size_t)j * N, N, -1, tw);
+        if (g_probe_n1 && g_probe_N == N) dft2_probe(scratch, z + (size_t)j * N, N, -1, 0, scratch + N);
+        else dft_naive(scratch, z + (size_t)j * N, N, -1, tw);
     }
 }
 
-/* out = Q^H v : out[n] = sum_j conj(d_j[n]) * (F^H v_j)[n].  scratch: N entries. */
+/* out = Q^H v : out[n] = sum_j conj(d_j[n]) * (K^H v_j)[n].  scratch: 3 N entries. */
 static void apply_QH(const cplx *v, const cplx *d, int N, int J, const cplx *tw,
                      cplx *out, cplx *scratch)
 {
     for (int n = 0; n < N; n++) out[n] = 0;
     for (int j = 0; j < J; j++) {
-        dft_naive(v + (size_t)j * N, scratch, N, +1, tw);
+        if (g_probe_n1 && g_probe_N == N) dft2_probe(v + (size_t)j * N, scratch, N, +1, 1, scratch + N);
+        else dft_naive(v + (size_t)j * N, scratch, N, +1, tw);
         for (int n = 0; n < N; n++) out[n] += conj(d[(size_t)j * N + n]) * scratch[n];
     }
 }
@@ -136,7 +188,7 @@ int orc_forward(const double *T, const double *masks, int M, int N, int J,
     size_t K = (size_t)J * N;
 #pragma omp parallel
     {
-        cplx *z = malloc(sizeof(cplx) * K), *sc = malloc(sizeof(cplx) * (size_t)N);
+        cplx *z = malloc(sizeof(cplx) * K), *sc = malloc(sizeof(cplx) * 3 * (size_t)N);
 #pragma omp for schedule(dynamic)
         for (int r = 0; r < M; r++) {
             apply_Q(Tc + (size_t)r * N, d, N, J, tw, z, sc);
@@ -159,7 +211,7 @@ int orc_adjoint(const double *V, const double *masks, int M, int N, int J, doubl
     size_t K = (size_t)J * N;
 #pragma omp parallel
     {
-        cplx *sc = malloc(sizeof(cplx) * (size_t)N);
+        cplx *sc = malloc(sizeof(cplx) * 3 * (size_t)N);
 #pragma omp for schedule(dynamic)
         for (int r = 0; r < M; r++)
             apply_QH((const cplx *)V + (size_t)r * K, d, N, J, tw, (cplx *)out + (size_t)r * N, sc);
@@ -201,7 +253,7 @@ int orc_loss_grad(const double *T, const double *masks, const double *Y, int M, 
 #pragma omp parallel
     {
         cplx *z = malloc(sizeof(cplx) * K), *rz = malloc(sizeof(cplx) * K);
-        cplx *sc = malloc(sizeof(cplx) * (size_t)N);
+        cplx *sc = malloc(sizeof(cplx) * 3 * (size_t)N);
 #pragma omp for schedule(dynamic)
         for (int r = 0; r < M; r++) {
             double f = loss_grad_row((const cplx *)T + (size_t)r * N, Y + (size_t)r * K, d, N, J, tw,
@@ -345,7 +397,7 @@ int orc_init(const double *Y, const double *masks, int M, int N, int J, const in
     size_t K = (size_t)J * N;
 #pragma omp parallel
     {
-        cplx *z = malloc(sizeof(cplx) * K), *sc = malloc(sizeof(cplx) * (size_t)N);
+        cplx *z = malloc(sizeof(cplx) * K), *sc = malloc(sizeof(cplx) * 3 * (size_t)N);
 #pragma omp for schedule(dynamic)
         for (int r = 0; r < M; r++)
             init_row(Y + (size_t)r * K, d, N, J, tw, init, seed, row_ids ? row_ids[r] : r,
@@ -572,7 +624,7 @@ static void solve_row(const double *y, const cplx *d, int N, int J, const cplx *
         return;
     }
     cplx *z = malloc(sizeof(cplx) * K), *w = malloc(sizeof(cplx) * K), *rz = malloc(sizeof(cplx) * K);
-    cplx *sc = malloc(sizeof(cplx) * (size_t)N), *g = malloc(sizeof(cplx) * (size_t)N);
+    cplx *sc = malloc(sizeof(cplx) * 3 * (size_t)N), *g = malloc(sizeof(cplx) * (size_t)N);
     cplx *gn = malloc(sizeof(cplx) * (size_t)N), *p = malloc(sizeof(cplx) * (size_t)N);
     cplx *tn = malloc(sizeof(cplx) * (size_t)N);
     double *r = malloc(sizeof(double) * K);
@@ -669,7 +721,7 @@ int orc_lbfgs_step(const double *y, const double *masks, int N, int J, const dou
     size_t K = (size_t)J * N;
     int n2 = 2 * N;
     cplx *z = malloc(sizeof(cplx) * K), *w = malloc(sizeof(cplx) * K), *rz = malloc(sizeof(cplx) * K);
-    cplx *sc = malloc(sizeof(cplx) * N), *g = malloc(sizeof(cplx) * N), *p = (cplx *)p_out;
+    cplx *sc = malloc(sizeof(cplx) * 3 * (size_t)N), *g = malloc(sizeof(cplx) * N), *p = (cplx *)p_out;
     double *r = calloc(K, sizeof(double)), *alpha = malloc(sizeof(double) * (np > 0 ? np : 1));
     loss_grad_row((const cplx *)t, y, d, N, J, tw, g, z, rz, sc);
     two_loop(n2, (const double *)g, S, Yh, np, (double *)p, alpha);

@@ -41,7 +41,8 @@ class tmr_options(ctypes.Structure):
                 ("phase_iters", ctypes.c_int), ("precision", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("workspace_limit", ctypes.c_size_t),
                 ("schedule", ctypes.c_int), ("tune_cache", ctypes.c_char_p),
-                ("wait_spins", ctypes.c_longlong), ("withhold_release", ctypes.c_int)]
+                ("wait_spins", ctypes.c_longlong), ("withhold_release", ctypes.c_int),
+                ("probe_n1", ctypes.c_int)]
 
 
 class tmr_defocus_op(ctypes.Structure):

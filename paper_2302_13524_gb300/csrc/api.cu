@@ -111,6 +111,7 @@ struct tmr_handle {
     bool last_had_fit = false;
     int G = 1;  // solver schedule: masks per CTA
     int prec = TMR_PREC_FP32;
+    int xk = 0;  // transform kind of the kernels: 0 FP32 1D DFT, 1 mixed, 2 FP32 2D probing DFT
     void *y16 = nullptr;   // mixed precision: FP16 intensities [M][J][N]
     float *ysc = nullptr;  // and their row scales [M]
     cudaStream_t own_stream = nullptr;  // created for graph capture when the caller gave none
@@ -242,7 +243,7 @@ tmr_status autotune(tmr_handle *h, int smem_optin, int *G_out, bool *timed)
     *timed = false;
     int cand[5], nc = 0;
     for (int G : {1, 2, 4, kRowSchedule, kBlueFullSchedule})
-        if (schedule_ok(h->N, h->J, h->opt.m, G, smem_optin, h->prec) && (G != kRowSchedule || h->pairs) &&
+        if (schedule_ok(h->N, h->J, h->opt.m, G, smem_optin, h->xk) && (G != kRowSchedule || h->pairs) &&
             (G != kBlueFullSchedule || h->tw_alt))
             cand[nc++] = G;
     if (nc == 0) {  // the forward model and gradient still work; tmr_retrieve will refuse
@@ -338,7 +339,7 @@ std::string tune_key(int dev, int N, int J, int m, int prec)
     cudaGetDeviceProperties(&prop, dev);
     char k[320];
     snprintf(k, sizeof(k), "%s|sm%d%d|N%d|J%d|m%d%s", prop.name, prop.major, prop.minor, N, J, m,
-             prec ? "|mixed" : "");
+             prec == 1 ? "|mixed" : (prec == 2 ? "|2d" : ""));
     for (char *c = k; *c; c++)
         if (*c == '"' || *c == '\\') *c = '_';
     return k;
@@ -366,6 +367,7 @@ void tmr_default_options(tmr_options *o)
     o->tune_cache = nullptr;
     o->wait_spins = 1LL << 24;
     o->withhold_release = 0;
+    o->probe_n1 = 0;
 }
 
 int tmr_schedule(const tmr_handle *h) { return h ? h->G : 0; }
@@ -444,6 +446,11 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
         return fail(TMR_ERR_INVALID_ARG, "opt.precision must be TMR_PREC_FP32 or TMR_PREC_MIXED");
     if (o.precision == TMR_PREC_MIXED && !mixed_supported(N))
         return fail(TMR_ERR_UNSUPPORTED, "TMR_PREC_MIXED needs N = 256, 1024, 2048 or 4096");
+    if (o.probe_n1 < 0) return fail(TMR_ERR_INVALID_ARG, "opt.probe_n1 must be >= 0");
+    if (o.probe_n1 != 0 && (o.precision != TMR_PREC_FP32 || N % o.probe_n1 != 0 || fft_table_2d(N, o.probe_n1, nullptr) < 0))
+        return fail(TMR_ERR_UNSUPPORTED, "the 2D probing DFT needs FP32 and N = 512 (n1 = 8 or 64) or N = 4096 "
+                                         "(n1 = 8, 64 or 512)");
+    const int xk = o.precision == TMR_PREC_MIXED ? 1 : (o.probe_n1 ? 2 : 0);
     if (!xform_supported(N))
         return fail(TMR_ERR_UNSUPPORTED, "N must be a power of two in 64..4096 or another length in 16..4096");
     if (J > kMaxMasks) return fail(TMR_ERR_UNSUPPORTED, "J must be at most 8");
@@ -460,7 +467,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
 
     int smem_optin = 0;
     TMR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
-    if (o.schedule != 0 && !schedule_ok(N, J, o.m, o.schedule, smem_optin, o.precision))
+    if (o.schedule != 0 && !schedule_ok(N, J, o.m, o.schedule, smem_optin, xk))
         return fail(TMR_ERR_UNSUPPORTED,
                     "opt.schedule must be 1, 2 or 4 (dividing J), 16 (one CTA per row) or 32 (full-length "
                     "Bluestein), and fit the device");
@@ -472,6 +479,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     h->opt = o;
     h->opt.tune_cache = nullptr;  // the caller's string is not kept
     h->prec = o.precision;
+    h->xk = xk;
     h->stream = (cudaStream_t)stream;
     if (!h->stream && o.use_graph) {
         // the legacy default stream cannot be captured: use a blocking stream
@@ -500,9 +508,10 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
             return cuda_fail(e, "copy masks");
         }
     }
-    const int twn = xform_table_prec(N, h->prec, nullptr);
+    const int twn = h->xk == 2 ? fft_table_2d(N, o.probe_n1, nullptr) : xform_table_prec(N, h->prec, nullptr);
     std::vector<float2> tw(twn > 0 ? twn : 1);
-    xform_table_prec(N, h->prec, tw.data());
+    if (h->xk == 2) fft_table_2d(N, o.probe_n1, tw.data());
+    else xform_table_prec(N, h->prec, tw.data());
     TRY(halloc(h, (void **)&h->tw, sizeof(float2) * tw.size(), "twiddles"));
     if (cudaMemcpy(h->tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
         tmr_destroy(h);
@@ -548,7 +557,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     // region per resident CTA, allocated when that schedule can run (and is
     // asked for or a candidate of the autotuner); under a workspace_limit that
     // it would exceed, the schedule is left out
-    if ((o.schedule == 0 || o.schedule == kRowSchedule) && schedule_ok(N, J, o.m, kRowSchedule, smem_optin, h->prec)) {
+    if ((o.schedule == 0 || o.schedule == kRowSchedule) && schedule_ok(N, J, o.m, kRowSchedule, smem_optin, h->xk)) {
         const int ctas = solver_row_max_ctas(N, J, o.m);
         const size_t bytes = sizeof(float2) * solver_row_pair_stride(N, o.m) * (size_t)(ctas > 0 ? ctas : 0);
         if (ctas > 0 && (!o.workspace_limit || h->held + bytes <= o.workspace_limit)) {
@@ -561,7 +570,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     }
     // the other Bluestein plan's table, when that schedule can run
     if ((o.schedule == 0 || o.schedule == kBlueFullSchedule) &&
-        schedule_ok(N, J, o.m, kBlueFullSchedule, smem_optin, h->prec)) {
+        schedule_ok(N, J, o.m, kBlueFullSchedule, smem_optin, h->xk)) {
         const int n = xform_table_blue_full(N, nullptr);
         std::vector<float2> t2(n > 0 ? n : 1);
         xform_table_blue_full(N, t2.data());
@@ -575,7 +584,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     if (o.schedule != 0) {
         h->G = o.schedule;
     } else {
-        const std::string key = tune_key(dev, N, J, o.m, h->prec);
+        const std::string key = tune_key(dev, N, J, o.m, h->xk);
         int G = 0;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -584,7 +593,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
             if (!G && o.tune_cache) {
                 auto fm = read_tune_file(o.tune_cache);
                 auto f = fm.find(key);
-                if (f != fm.end() && schedule_ok(N, J, o.m, f->second, smem_optin, h->prec)) G = f->second;
+                if (f != fm.end() && schedule_ok(N, J, o.m, f->second, smem_optin, h->xk)) G = f->second;
             }
             if (G == kRowSchedule && !h->pairs) G = 0;  // no pair workspace here: tune again
             if (G == kBlueFullSchedule && !h->tw_alt) G = 0;
@@ -623,7 +632,7 @@ tmr_status tmr_forward(tmr_handle *h, const void *T, float *Y)
     if ((st = stage(h, ST_TIN, T, sizeof(float2) * MN, true, &dT)) != TMR_OK) return st;
     if ((st = stage(h, ST_Y, Y, sizeof(float) * MK, false, &dY)) != TMR_OK) return st;
     if ((st = check_launch(launch_forward(h->N, h->M, h->J, (const float2 *)dT, h->masks, h->tw,
-                                          (float *)dY, h->stream, h->prec), "forward kernel")) != TMR_OK)
+                                          (float *)dY, h->stream, h->xk), "forward kernel")) != TMR_OK)
         return st;
     bool synced = false;
     if ((st = unstage(h, Y, dY, sizeof(float) * MK, &synced)) != TMR_OK) return st;
@@ -643,7 +652,7 @@ tmr_status tmr_grad(tmr_handle *h, const void *T, const float *Y, float *loss, v
     if (loss && (st = stage(h, ST_LOSS, loss, sizeof(float) * h->M, false, &dL)) != TMR_OK) return st;
     if (G && (st = stage(h, ST_TOUT, G, sizeof(float2) * MN, false, &dG)) != TMR_OK) return st;
     if ((st = check_launch(launch_grad(h->N, h->M, h->J, (const float2 *)dT, h->masks, h->tw,
-                                       (const float *)dY, (float *)dL, (float2 *)dG, h->stream, h->prec),
+                                       (const float *)dY, (float *)dL, (float2 *)dG, h->stream, h->xk),
                            "gradient kernel")) != TMR_OK)
         return st;
     bool synced = false;
@@ -696,7 +705,7 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
         int dev = 0, smem_optin = 0;
         TMR_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
         TMR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
-        if (!schedule_ok(h->N, h->J, h->opt.m, h->G, smem_optin, h->prec))
+        if (!schedule_ok(h->N, h->J, h->opt.m, h->G, smem_optin, h->xk))
             return fail(TMR_ERR_UNSUPPORTED,
                         "per-row state of this (N, J, m) does not fit in shared memory: lower opt.m");
     }
@@ -762,7 +771,7 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
     p.seed = h->opt.seed;
     p.clip = (float)h->opt.clip;
     p.tol = h->opt.tol;
-    p.prec = h->prec;
+    p.prec = h->xk;
     if (h->prec == TMR_PREC_MIXED) {
         if (!h->y16) {
             if ((st = halloc(h, &h->y16, 2 * (MK ? MK : 1), "FP16 intensities")) != TMR_OK) return st;
@@ -781,7 +790,7 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
         TMR_CUDA(launch_solver(h->N, h->G, p, h->stream, nullptr), "solver kernel");
         if (fit) {
             TMR_CUDA(launch_fields(h->N, h->M, h->J, h->Nd, (const float2 *)dT, h->masks, h->tw, h->Zd,
-                                   h->stream, h->prec),
+                                   h->stream, h->xk),
                      "fields kernel");
             tmr_status s2 = run_phase_fit(h, (const float2 *)dT, (const float *)dYd, h->phi, (float2 *)dT);
             if (s2 != TMR_OK) return s2;
@@ -856,7 +865,7 @@ tmr_status tmr_defocus_forward(tmr_handle *h, const void *T, float *Y_def)
     tmr_status st;
     if ((st = stage(h, ST_TIN, T, sizeof(float2) * MN, true, &dT)) != TMR_OK) return st;
     if ((st = stage(h, ST_YDEF, Y_def, sizeof(float) * (size_t)h->Nd * h->M, false, &dY)) != TMR_OK) return st;
-    TMR_CUDA(launch_fields(h->N, h->M, h->J, h->Nd, (const float2 *)dT, h->masks, h->tw, h->Zd, h->stream, h->prec),
+    TMR_CUDA(launch_fields(h->N, h->M, h->J, h->Nd, (const float2 *)dT, h->masks, h->tw, h->Zd, h->stream, h->xk),
              "fields kernel");
     TMR_CUDA(launch_defocus_forward(h->ny, h->nx, h->Nd, h->Zd, h->H, nullptr, nullptr, (float *)dY, h->stream),
              "defocus kernel");
@@ -878,7 +887,7 @@ tmr_status tmr_defocus_fit(tmr_handle *h, const void *T_est, const float *y_def,
     if ((st = stage(h, ST_YDEF, y_def, sizeof(float) * (size_t)h->Nd * h->M, true, &dY)) != TMR_OK) return st;
     if (phi && (st = stage(h, ST_PHI, phi, sizeof(double) * h->M, false, &dP)) != TMR_OK) return st;
     if (T_out && (st = stage(h, ST_TOUT, T_out, sizeof(float2) * MN, false, &dO)) != TMR_OK) return st;
-    TMR_CUDA(launch_fields(h->N, h->M, h->J, h->Nd, (const float2 *)dT, h->masks, h->tw, h->Zd, h->stream, h->prec),
+    TMR_CUDA(launch_fields(h->N, h->M, h->J, h->Nd, (const float2 *)dT, h->masks, h->tw, h->Zd, h->stream, h->xk),
              "fields kernel");
     if ((st = run_phase_fit(h, (const float2 *)dT, (const float *)dY, dP ? (double *)dP : h->phi,
                             (float2 *)dO)) != TMR_OK)

@@ -41,13 +41,18 @@ int xform_table(int N, float2 *out);  // length in float2; writes when out != NU
 // L = 8192 (XfBlue<8192, 6>) instead of the split outputs at L = 4096; the
 // table of the solver schedule kBlueFullSchedule.
 int xform_table_blue_full(int N, float2 *out);
+// The 2D probing DFT (N = 512 or 4096, n1 and N / n1 pass boundaries: 8, 64,
+// 512): the forward and adjoint twiddle tables and (n1, N/n1); -1 otherwise.
+// The kernels take it as transform kind 2 (the `prec` argument below).
+int fft_table_2d(int N, int n1, float2 *out);
 // Mixed precision (TMR_PREC_MIXED): N = 256, 1024, 2048 or 4096; its table is
 // [FP32 twiddles | tensor-core DFT fragments (radix 16, radix 8) | roots W_N^k].
 bool mixed_supported(int N);
 int xform_table_prec(int N, int prec, float2 *out);
 
 // ---- fused forward model and gradient (kernels.cu) -------------------------
-// prec: TMR_PREC_FP32 (FP32 transforms) or TMR_PREC_MIXED (tensor-core transforms)
+// prec: transform kind: TMR_PREC_FP32 (0, FP32, 1D probing DFT), TMR_PREC_MIXED
+// (1, tensor-core transforms) or 2 (FP32, 2D probing DFT, table fft_table_2d)
 cudaError_t launch_forward(int N, int M, int J, const float2 *T, const float2 *masks,
                            const float2 *tw, float *Y, cudaStream_t s, int prec = 0);
 cudaError_t launch_grad(int N, int M, int J, const float2 *T, const float2 *masks,
@@ -111,6 +116,8 @@ cudaError_t launch_solver(int N, int G, const SolverParams &p, cudaStream_t s, i
 long long solver_dispatch_blue(int N, int G, int what, const SolverParams *p, cudaStream_t s, int *clusters_out);
 // the one-CTA-per-row variants (solver_row.cu)
 long long solver_dispatch_row(int N, int what, const SolverParams *p, cudaStream_t s, int *ctas_out);
+// the 2D-probing-DFT variants (solver_2d.cu)
+long long solver_dispatch_2d(int N, int G, int what, const SolverParams *p, cudaStream_t s, int *clusters_out);
 // the mixed-precision variants (solver_mx.cu)
 long long solver_dispatch_mixed(int N, int G, int what, const SolverParams *p, cudaStream_t s, int *clusters_out);
 // Synthetic positive intensities for timing runs (autotuner).

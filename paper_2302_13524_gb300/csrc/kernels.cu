@@ -194,6 +194,39 @@ int xform_table(int N, float2 *out)
     }
 }
 
+// Tables of XfPow2D<N> (the 2D probing DFT, xform.cuh): the twiddles of
+// passes 1 .. P-2 with boundary B = n1 (forward) and B = N / n1 (adjoint):
+// W_{Ns R}^{r j} for passes with Ns < B, W_{(Ns/B) R}^{r (j div B)} for the
+// others; then the entry (n1, N / n1).
+template <int N>
+static int fft_table_2d_t(int n1, float2 *out)
+{
+    using Pl = FftPlan<N, N / fft_threads(N)>;
+    const int tws = Pl::tw_off(Pl::P - 1);
+    if (out) {
+        for (int half = 0; half < 2; half++) {
+            const int B = half == 0 ? n1 : N / n1;
+            for (int p = 1; p < Pl::P - 1; p++) {
+                const int R = Pl::radix(p), Ns = Pl::ns(p), off = Pl::tw_off(p);
+                for (int r = 1; r < R; r++)
+                    for (int j = 0; j < Ns; j++) {
+                        const double a = Ns >= B ? -2.0 * M_PI * (double)r * (double)(j / B) / ((double)(Ns / B) * R)
+                                                 : -2.0 * M_PI * (double)r * (double)j / ((double)Ns * R);
+                        out[half * tws + off + (r - 1) * Ns + j] = make_float2((float)std::cos(a), (float)std::sin(a));
+                    }
+            }
+        }
+        out[2 * tws] = make_float2((float)n1, (float)(N / n1));
+    }
+    return 2 * tws + 1;
+}
+
+int fft_table_2d(int N, int n1, float2 *out)
+{
+    if (!probe_2d_boundary(N, n1) || !probe_2d_boundary(N, N / n1)) return -1;
+    return N == 512 ? fft_table_2d_t<512>(n1, out) : fft_table_2d_t<4096>(n1, out);
+}
+
 int xform_table_blue_full(int N, float2 *out)
 {
     if (N <= 2048 || N > kBlueSplitMaxN) return -1;
@@ -291,10 +324,18 @@ int xform_table_prec(int N, int prec, float2 *out)
     }
 }
 
-// Calls f(Xf{}) with the transform policy of length N and precision prec.
+// Calls f(Xf{}) with the transform policy of length N and kind prec (0: FP32
+// with the 1D probing DFT, 1: mixed precision, 2: FP32 with the 2D probing DFT).
 template <class F>
 static cudaError_t dispatch_xf(int N, int prec, F &&f)
 {
+    if (prec == 2) {  // the 2D probing DFT
+        switch (N) {
+        case 512: return f(XfPow2D<512>{});
+        case 4096: return f(XfPow2D<4096>{});
+        default: return cudaErrorInvalidValue;
+        }
+    }
     if (prec != 0) {
         switch (N) {
         case 256: return f(XfMixed<256>{});

@@ -98,6 +98,8 @@ extern "C" tmr_status tmr_retrieve_rows_static(int N, int M, int J, const void *
         return fail(TMR_ERR_INVALID_ARG, "bad option");
     if (o.precision != TMR_PREC_FP32)
         return fail(TMR_ERR_UNSUPPORTED, "the static entry point runs the FP32 solver only (opt.precision)");
+    if (o.probe_n1 != 0)
+        return fail(TMR_ERR_UNSUPPORTED, "the static entry point uses the 1D probing DFT (opt.probe_n1 = 0)");
     const int twn = tmr::fft_table_len(N);
     if ((size_t)twn * sizeof(float2) + kCounterBytes > kStaticScratchBytes)
         return fail(TMR_ERR_UNSUPPORTED, "twiddle table larger than the static scratch");

@@ -87,6 +87,76 @@ struct XfPow2 {
     }
 };
 
+// XfPow2D<N>: the paper's 2D probing DFT (Eq. probingmatrix: K the 2D Fourier
+// transform of the row read as an n1 x n2 array, n1 n2 = N) through the same
+// register Stockham passes.  The Stockham passes whose stride Ns reaches n1
+// combine the length-n1 DFTs along the first index; with the twiddle of such
+// a pass taken as W_{(Ns/n1) R}^{r (j div n1)} instead of W_{Ns R}^{r j}
+// (the factors that couple the two indices dropped) the passes compute the 2D
+// DFT, spectrum X[k1][k2] at index k1 + n1 k2.  The adjoint reads its input in
+// that order, i.e. as an n2 x n1 array, so it runs the same passes with n2 in
+// place of n1.  n1 and n2 must both be strides at which a pass starts (the
+// products of the leading radices: 8 and 64 for N = 512; 8, 64, 512 for
+// N = 4096).  Constants: [ forward table (n1) | adjoint table (n2) | (n1, n2) ].
+template <int N_>
+struct XfPow2D {
+    static constexpr bool kBlue = false;
+    static constexpr int kN = N_;
+    static constexpr int NT = fft_threads(N_);
+    static constexpr int NE = N_ / NT;
+    static constexpr int LBUF = fft_buf_len(N_);
+    static constexpr int BUFS = N_ <= 2048 ? 2 : 1;
+    static constexpr int TWS = FftSmall<N_, NT>::TW_SMALL;  // one table
+    static constexpr int NCONST = 2 * TWS;
+    __host__ __device__ static constexpr int shared_consts(int n) { return NCONST; }
+
+    float2 dm[NE];
+    float2 wbf[1], wba[1];  // last-pass bases of the forward and the adjoint passes
+    int ph;
+
+    __device__ __forceinline__ static bool valid(int e, int tid, int n) { return true; }
+
+    // chirp: the (n1, n2) entry after the two tables
+    __device__ __forceinline__ void setup(const float2 *__restrict__ mask, const float2 *__restrict__ chirp,
+                                          int n, int tid)
+    {
+#pragma unroll
+        for (int e = 0; e < NE; e++) dm[e] = mask[tid + e * NT];
+        const int n1 = (int)chirp[0].x, n2 = (int)chirp[0].y;
+        // the last pass has stride N / NE >= n1, n2: twiddle base W_{N/B}^{tid div B}
+        double s, c;
+        sincospi(-2.0 * (double)(tid / n1) / (double)(N_ / n1), &s, &c);
+        wbf[0] = make_float2((float)c, (float)s);
+        sincospi(-2.0 * (double)(tid / n2) / (double)(N_ / n2), &s, &c);
+        wba[0] = make_float2((float)c, (float)s);
+        ph = 0;
+    }
+    __device__ __forceinline__ void fwd(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid)
+    {
+#pragma unroll
+        for (int e = 0; e < NE; e++) x[e] = cmul(x[e], dm[e]);
+        if constexpr (BUFS == 2) block_fft_pp<N_, NT, NE, -1>(x, buf, cst, wbf, tid, ph);
+        else block_fft_rb<N_, NT, -1>(x, buf, cst, wbf[0], tid);
+    }
+    __device__ __forceinline__ void adj(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid)
+    {
+        if constexpr (BUFS == 2) block_fft_pp<N_, NT, NE, +1>(x, buf, cst + TWS, wba, tid, ph);
+        else block_fft_rb<N_, NT, +1>(x, buf, cst + TWS, wba[0], tid);
+#pragma unroll
+        for (int e = 0; e < NE; e++) x[e] = cmulc(x[e], dm[e]);
+    }
+};
+
+// The strides at which a pass of the XfPow2 plan of length N starts
+// (products of the leading radices), excluding 1 and N.
+__host__ __device__ inline bool probe_2d_boundary(int N, int b)
+{
+    if (N != 512 && N != 4096) return false;  // plans with radix 8 in every pass
+    for (int s = 8; s < N; s *= 8)
+        if (s == b) return true;
+    return false;
+}
+
 template <int L_, int NE_>
 struct XfBlue {
     static constexpr bool kBlue = true;
