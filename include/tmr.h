@@ -93,17 +93,39 @@ enum {
  * either way. */
 enum { TMR_PREC_FP32 = 0, TMR_PREC_MIXED = 1 };
 
-/* Defocus operator of the phase-offset fit (Sec. 2.3).  The defocus field
- * of pattern n is D c_n with c_n[row] = (Q t_row)[n] (the first n_defocus
- * probe patterns) and D x = ifft2(H .* fft2(x)) on the ny x nx pixel grid.
- * H: device or host complex64 [ny][nx], or NULL for the quadratic phase
- * H[a][b] = exp(-i coef (ky_a^2 + kx_b^2)) on signed integer frequencies
- * (k = idx for 2 idx < n, else idx - n). */
+/* Defocus operator of the phase-offset fit (Sec. 2.3).  Two kinds.
+ *
+ * TMR_DEFOCUS_SAME_GRID (kind 0): the defocus field of pattern n is D c_n
+ * with c_n[row] = (Q t_row)[n] (the first n_defocus probe patterns) and
+ * D x = ifft2(H .* fft2(x)) on the ny x nx pixel grid; the defocus images are
+ * float [n_defocus][M].  H: device or host complex64 [ny][nx], or NULL for the
+ * quadratic phase H[a][b] = exp(-i coef (ky_a^2 + kx_b^2)) on signed integer
+ * frequencies (k = idx for 2 idx < n, else idx - n).
+ *
+ * TMR_DEFOCUS_ANGULAR_2X (kind 1, Eq. angularspectrum and Eq.
+ * forwarddefocusImage): n_defocus separate incident fields theta_n (complex64
+ * [n_defocus][N], `incident`, copied) give the fields c_n = T theta_n on the
+ * half-sampled ny x nx grid (c_n[row] = sum_k T[row][k] theta_n[k]), and the
+ * image of pattern n is |K2^H P diag(h) K1 c_n|^2 on the full 2ny x 2nx grid:
+ * K1 the 2D DFT of the half grid, h the angular-spectrum kernel
+ * exp(i 2 pi / wavelength sqrt(1 - (wavelength u)^2 - (wavelength v)^2) z_d)
+ * inside the pupil wavelength sqrt(u^2 + v^2) <= na (0 outside), with
+ * u = kx / (nx pixel), v = ky / (ny pixel) on signed frequencies, P the zero
+ * padding of the spectrum to the 2ny x 2nx grid and K2^H its inverse DFT
+ * divided by ny nx (so that with h = 1 the even full-grid pixels equal the
+ * half grid).  The images are float [n_defocus][4 M], each row-major
+ * 2ny x 2nx.  H non-NULL replaces the computed h ([ny][nx], FFT order).
+ * wavelength, pixel and z_d share one length unit. */
+enum { TMR_DEFOCUS_SAME_GRID = 0, TMR_DEFOCUS_ANGULAR_2X = 1 };
+
 typedef struct {
     int ny, nx;      /* ny * nx == M                                   */
-    const void *H;   /* copied at tmr_create; NULL = quadratic(coef)   */
-    double coef;     /* quadratic coefficient (0.05 in the workloads)  */
-    int n_defocus;   /* number of defocus patterns, 1 <= n_defocus <= J*N */
+    const void *H;   /* copied at tmr_create; NULL = made from the parameters */
+    double coef;     /* kind 0: quadratic coefficient (0.05 in the workloads) */
+    int n_defocus;   /* kind 0: 1..J*N; kind 1: 1..65536               */
+    int kind;        /* TMR_DEFOCUS_SAME_GRID (0) or TMR_DEFOCUS_ANGULAR_2X */
+    double wavelength, na, z_d, pixel;  /* kind 1: > 0, > 0, finite, > 0 */
+    const void *incident;  /* kind 1: device or host complex64 [n_defocus][N] */
 } tmr_defocus_op;
 
 typedef struct {
@@ -224,6 +246,12 @@ tmr_status tmr_defocus_fit(tmr_handle *h, const void *T_est, const float *y_def,
  * tmr_defocus_fit) ran out (opt.wait_spins), TMR_ERR_NUMERIC when a row of
  * the last retrieve reported non-finite values. */
 tmr_status tmr_sync(tmr_handle *h, double timeout_s);
+
+/* Loss g(phi) (Eq. optphase) at the phi of the last phase-offset fit and its
+ * accepted L-BFGS iterations (either pointer may be NULL); waits for the
+ * handle's stream.  UNSUPPORTED without a defocus operator, INVALID_ARG
+ * before the first fit. */
+tmr_status tmr_phase_fit_report(tmr_handle *h, double *loss, int *iters);
 
 /* Message describing the calling thread's last error ("" if none). */
 const char *tmr_last_error(void);

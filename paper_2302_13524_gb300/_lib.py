@@ -47,7 +47,12 @@ class tmr_options(ctypes.Structure):
 
 class tmr_defocus_op(ctypes.Structure):
     _fields_ = [("ny", ctypes.c_int), ("nx", ctypes.c_int), ("H", ctypes.c_void_p),
-                ("coef", ctypes.c_double), ("n_defocus", ctypes.c_int)]
+                ("coef", ctypes.c_double), ("n_defocus", ctypes.c_int), ("kind", ctypes.c_int),
+                ("wavelength", ctypes.c_double), ("na", ctypes.c_double), ("z_d", ctypes.c_double),
+                ("pixel", ctypes.c_double), ("incident", ctypes.c_void_p)]
+
+
+DEFOCUS_SAME_GRID, DEFOCUS_ANGULAR_2X = 0, 1
 
 
 def _load():
@@ -67,6 +72,7 @@ def _load():
         "tmr_defocus_forward": ([H, vp, fp], ctypes.c_int),
         "tmr_defocus_fit": ([H, vp, fp, dp, vp], ctypes.c_int),
         "tmr_sync": ([H, ctypes.c_double], ctypes.c_int),
+        "tmr_phase_fit_report": ([H, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "tmr_last_error": ([], ctypes.c_char_p),
         "tmr_workspace_bytes": ([H], ctypes.c_size_t),
         "tmr_schedule": ([H], ctypes.c_int),
@@ -164,9 +170,12 @@ def tmr_default_options(**overrides) -> tmr_options:
 class Handle:
     """Owns a tmr_handle; sizes are kept for argument checks."""
 
-    def __init__(self, raw, N, M, J, n_defocus):
+    def __init__(self, raw, N, M, J, n_defocus, defocus_kind=DEFOCUS_SAME_GRID):
         self.raw = raw
         self.N, self.M, self.J, self.n_defocus = N, M, J, n_defocus
+        self.defocus_kind = defocus_kind
+        # pixels of one defocus image: the grid (kind 0) or the 2ny x 2nx grid (kind 1)
+        self.defocus_pixels = M * (4 if defocus_kind == DEFOCUS_ANGULAR_2X else 1)
         self._keep = []
 
     def close(self):
@@ -188,15 +197,24 @@ class Handle:
 
 
 def tmr_create(N, M, J, masks, defocus_op=None, opt=None, stream=None) -> Handle:
-    """defocus_op: None or dict(ny, nx, n_defocus, coef=0.05, H=None)."""
+    """defocus_op: None, dict(ny, nx, n_defocus, coef=0.05, H=None) (the same-grid
+    operator), or dict(kind=1, ny, nx, n_defocus, wavelength, na, z_d, pixel,
+    incident [n_defocus, N] complex64, H=None) (angular spectrum, 2x padding)."""
     dop = None
     keep = []
     if defocus_op is not None:
+        kind = int(defocus_op.get("kind", DEFOCUS_SAME_GRID))
+        nd = int(defocus_op["n_defocus"])
         Hp = _ptr(defocus_op.get("H"), "c64", M, "H")
+        Ip = _ptr(defocus_op.get("incident"), "c64", nd * N, "incident")
         dop = tmr_defocus_op(int(defocus_op["ny"]), int(defocus_op["nx"]),
                              Hp.value if Hp is not None else None,
-                             float(defocus_op.get("coef", 0.05)), int(defocus_op["n_defocus"]))
+                             float(defocus_op.get("coef", 0.05)), nd, kind,
+                             float(defocus_op.get("wavelength", 0.0)), float(defocus_op.get("na", 0.0)),
+                             float(defocus_op.get("z_d", 0.0)), float(defocus_op.get("pixel", 0.0)),
+                             Ip.value if Ip is not None else None)
         keep.append(defocus_op.get("H"))
+        keep.append(defocus_op.get("incident"))
     if opt is None:
         opt = tmr_default_options()
     elif isinstance(opt, dict):
@@ -206,7 +224,8 @@ def tmr_create(N, M, J, masks, defocus_op=None, opt=None, stream=None) -> Handle
                         ctypes.byref(dop) if dop is not None else None, ctypes.byref(opt),
                         ctypes.c_void_p(stream) if stream else None)
     _check(st)
-    return Handle(raw, N, M, J, dop.n_defocus if dop is not None else 0)
+    return Handle(raw, N, M, J, dop.n_defocus if dop is not None else 0,
+                  dop.kind if dop is not None else DEFOCUS_SAME_GRID)
 
 
 def tmr_forward(h: Handle, T, Y):
@@ -221,7 +240,7 @@ def tmr_grad(h: Handle, T, Y, loss=None, G=None):
 def tmr_retrieve(h: Handle, y, y_def, iters, T_out, row_status=None, row_iters=None,
                  row_loss=None):
     _check(lib.tmr_retrieve(h.raw, _ptr(y, "f32", h.M * h.J * h.N, "y"),
-                            _ptr(y_def, "f32", h.n_defocus * h.M, "y_def"), int(iters),
+                            _ptr(y_def, "f32", h.n_defocus * h.defocus_pixels, "y_def"), int(iters),
                             _ptr(T_out, "c64", h.M * h.N, "T_out"),
                             _ptr(row_status, "i32", h.M, "row_status"),
                             _ptr(row_iters, "i32", h.M, "row_iters"),
@@ -232,7 +251,7 @@ def tmr_retrieve_from(h: Handle, T_init, y, y_def, iters, T_out, row_status=None
                       row_loss=None):
     _check(lib.tmr_retrieve_from(h.raw, _ptr(T_init, "c64", h.M * h.N, "T_init"),
                                  _ptr(y, "f32", h.M * h.J * h.N, "y"),
-                                 _ptr(y_def, "f32", h.n_defocus * h.M, "y_def"), int(iters),
+                                 _ptr(y_def, "f32", h.n_defocus * h.defocus_pixels, "y_def"), int(iters),
                                  _ptr(T_out, "c64", h.M * h.N, "T_out"),
                                  _ptr(row_status, "i32", h.M, "row_status"),
                                  _ptr(row_iters, "i32", h.M, "row_iters"),
@@ -241,12 +260,12 @@ def tmr_retrieve_from(h: Handle, T_init, y, y_def, iters, T_out, row_status=None
 
 def tmr_defocus_forward(h: Handle, T, Y_def):
     _check(lib.tmr_defocus_forward(h.raw, _ptr(T, "c64", h.M * h.N, "T"),
-                                   _ptr(Y_def, "f32", h.n_defocus * h.M, "Y_def")))
+                                   _ptr(Y_def, "f32", h.n_defocus * h.defocus_pixels, "Y_def")))
 
 
 def tmr_defocus_fit(h: Handle, T_est, y_def, phi=None, T_out=None):
     _check(lib.tmr_defocus_fit(h.raw, _ptr(T_est, "c64", h.M * h.N, "T_est"),
-                               _ptr(y_def, "f32", h.n_defocus * h.M, "y_def"),
+                               _ptr(y_def, "f32", h.n_defocus * h.defocus_pixels, "y_def"),
                                _ptr(phi, "f64", h.M, "phi"), _ptr(T_out, "c64", h.M * h.N, "T_out")))
 
 
@@ -269,6 +288,13 @@ def tmr_autotune_report(h: Handle) -> dict:
     ms = (ctypes.c_float * 8)()
     n = lib.tmr_autotune_report(h.raw, codes, ms, 8)
     return {int(codes[i]): float(ms[i]) for i in range(min(n, 8))}
+
+
+def tmr_phase_fit_report(h: Handle):
+    """(loss g(phi), accepted iterations) of the last phase-offset fit."""
+    loss, its = ctypes.c_double(), ctypes.c_int()
+    _check(lib.tmr_phase_fit_report(h.raw, ctypes.byref(loss), ctypes.byref(its)))
+    return loss.value, its.value
 
 
 def tmr_schedule(h: Handle) -> int:

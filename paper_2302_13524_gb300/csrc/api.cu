@@ -7,6 +7,7 @@
 //   solver (per-row Algorithm 1, persistent cluster kernel) -> row energies ->
 //   phase-offset fit (cooperative kernel) -> T_out = diag(e^{i phi}) T_est.
 #include <chrono>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <fstream>
@@ -84,7 +85,9 @@ struct tmr_handle {
     int N = 0, M = 0, J = 0;
     tmr_options opt{};
     bool has_defocus = false;
-    int ny = 0, nx = 0, Nd = 0;
+    int ny = 0, nx = 0, Nd = 0, dkind = 0;
+    bool fit_ran = false;
+    float2 *incident = nullptr;  // kind 1: [Nd][N] incident fields
     cudaStream_t stream = nullptr;
     size_t held = 0;
     // persistent device state
@@ -416,7 +419,7 @@ void tmr_destroy(tmr_handle *h)
     else cudaDeviceSynchronize();
     void *ptrs[] = {h->masks, h->tw, h->H, h->Zd, h->phi, h->pf_ws, h->pf_loss, h->wts, h->queue,
                     h->pf_sync, h->pf_err, h->pf_iters, h->status_scratch, h->iters_scratch,
-                    h->loss_scratch, h->Tcand, h->wins, h->y16, h->ysc, h->pairs, h->tw_alt};
+                    h->loss_scratch, h->Tcand, h->wins, h->y16, h->ysc, h->pairs, h->tw_alt, h->incident};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &b : h->stage)
@@ -459,10 +462,25 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     if (dop) {
         if (dop->ny <= 0 || dop->nx <= 0 || (long long)dop->ny * dop->nx != M)
             return fail(TMR_ERR_INVALID_ARG, "defocus grid ny*nx must equal M");
-        if (dop->n_defocus < 1 || dop->n_defocus > J * N)
-            return fail(TMR_ERR_INVALID_ARG, "n_defocus must be in 1..J*N");
-        if (!defocus_supported(dop->ny, dop->nx))
-            return fail(TMR_ERR_UNSUPPORTED, "defocus grid sides must be powers of two, grid <= 160 KB");
+        if (dop->kind == TMR_DEFOCUS_SAME_GRID) {
+            if (dop->n_defocus < 1 || dop->n_defocus > J * N)
+                return fail(TMR_ERR_INVALID_ARG, "n_defocus must be in 1..J*N");
+            if (!defocus_supported(dop->ny, dop->nx))
+                return fail(TMR_ERR_UNSUPPORTED, "defocus grid sides must be powers of two, grid <= 160 KB");
+        } else if (dop->kind == TMR_DEFOCUS_ANGULAR_2X) {
+            if (dop->n_defocus < 1 || dop->n_defocus > 65536)
+                return fail(TMR_ERR_INVALID_ARG, "n_defocus must be in 1..65536");
+            if (!dop->incident) return fail(TMR_ERR_INVALID_ARG, "the 2x defocus operator needs incident fields");
+            if (!dop->H && !(dop->wavelength > 0.0 && dop->pixel > 0.0 && dop->na > 0.0 && std::isfinite(dop->z_d) &&
+                             std::isfinite(dop->wavelength) && std::isfinite(dop->pixel) && std::isfinite(dop->na)))
+                return fail(TMR_ERR_INVALID_ARG, "wavelength, pixel and na must be positive and z_d finite");
+            if (!defocus2x_supported(dop->ny, dop->nx))
+                return fail(TMR_ERR_UNSUPPORTED,
+                            "2x defocus grid sides must be powers of two, three ny x (nx + 1) grids "
+                            "and the fit's scratch within 227 KB of shared memory");
+        } else {
+            return fail(TMR_ERR_INVALID_ARG, "unknown defocus kind");
+        }
     }
 
     int smem_optin = 0;
@@ -526,15 +544,27 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
         h->ny = dop->ny;
         h->nx = dop->nx;
         h->Nd = dop->n_defocus;
+        h->dkind = dop->kind;
         const size_t P = (size_t)M;
         TRY(halloc(h, (void **)&h->H, sizeof(float2) * P, "H"));
+        if (h->dkind == TMR_DEFOCUS_ANGULAR_2X) {
+            TRY(halloc(h, (void **)&h->incident, sizeof(float2) * (size_t)h->Nd * N, "incident fields"));
+            if (cudaMemcpy(h->incident, dop->incident, sizeof(float2) * (size_t)h->Nd * N, cudaMemcpyDefault) !=
+                cudaSuccess) {
+                tmr_destroy(h);
+                return fail(TMR_ERR_CUDA, "copy incident fields");
+            }
+        }
         if (dop->H) {
             if (cudaMemcpy(h->H, dop->H, sizeof(float2) * P, cudaMemcpyDefault) != cudaSuccess) {
                 tmr_destroy(h);
                 return fail(TMR_ERR_CUDA, "copy H");
             }
         } else {
-            cudaError_t e = launch_make_quadratic_H(h->ny, h->nx, dop->coef, h->H, nullptr);
+            cudaError_t e = h->dkind == TMR_DEFOCUS_ANGULAR_2X
+                                ? launch_make_H2x(h->ny, h->nx, dop->wavelength, dop->na, dop->z_d, dop->pixel, h->H,
+                                                  nullptr)
+                                : launch_make_quadratic_H(h->ny, h->nx, dop->coef, h->H, nullptr);
             if (e == cudaSuccess) e = cudaDeviceSynchronize();
             if (e != cudaSuccess) {
                 tmr_destroy(h);
@@ -662,6 +692,20 @@ tmr_status tmr_grad(tmr_handle *h, const void *T, const float *Y, float *loss, v
     return TMR_OK;
 }
 
+// floats of one set of defocus images: [Nd][M] (kind 0) or [Nd][4 M] (kind 1)
+static size_t ydef_floats(const tmr_handle *h)
+{
+    return (size_t)h->Nd * h->M * (h->dkind == TMR_DEFOCUS_ANGULAR_2X ? 4 : 1);
+}
+
+// Zd <- the fields c_n of T: probe patterns (kind 0) or incident fields (kind 1)
+static cudaError_t defocus_fields(tmr_handle *h, const float2 *dT)
+{
+    if (h->dkind == TMR_DEFOCUS_ANGULAR_2X)
+        return launch_incident_fields(h->M, h->N, h->Nd, dT, h->incident, h->Zd, h->stream);
+    return launch_fields(h->N, h->M, h->J, h->Nd, dT, h->masks, h->tw, h->Zd, h->stream, h->xk);
+}
+
 static tmr_status run_phase_fit(tmr_handle *h, const float2 *Tin, const float *dYdef, double *dphi,
                                 float2 *Tout)
 {
@@ -687,7 +731,9 @@ static tmr_status run_phase_fit(tmr_handle *h, const float2 *Tin, const float *d
     p.loss_out = h->pf_loss;
     p.wait_spins = h->opt.wait_spins;
     p.withhold_release = h->opt.withhold_release != 0;
+    p.kind = h->dkind;
     TMR_CUDA(launch_phase_fit(p, h->stream), "phase-fit kernel");
+    h->fit_ran = true;
     if (Tout) TMR_CUDA(launch_apply_phase(h->N, h->M, dphi, Tin, Tout, h->stream), "apply phase");
     return TMR_OK;
 }
@@ -714,7 +760,7 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
     void *dy, *dT, *dTin = nullptr, *dYd = nullptr, *dS, *dI, *dL;
     if ((st = stage(h, ST_Y, y, sizeof(float) * MK, true, &dy)) != TMR_OK) return st;
     if (T_init && (st = stage(h, ST_TIN, T_init, sizeof(float2) * MN, true, &dTin)) != TMR_OK) return st;
-    if (fit && (st = stage(h, ST_YDEF, y_def, sizeof(float) * (size_t)h->Nd * h->M, true, &dYd)) != TMR_OK)
+    if (fit && (st = stage(h, ST_YDEF, y_def, sizeof(float) * ydef_floats(h), true, &dYd)) != TMR_OK)
         return st;
     if ((st = stage(h, ST_TOUT, T_out, sizeof(float2) * MN, false, &dT)) != TMR_OK) return st;
     dS = h->status_scratch;
@@ -789,9 +835,7 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
         TMR_CUDA(cudaMemsetAsync(h->queue, 0, sizeof(unsigned) * 4, h->stream), "memset");
         TMR_CUDA(launch_solver(h->N, h->G, p, h->stream, nullptr), "solver kernel");
         if (fit) {
-            TMR_CUDA(launch_fields(h->N, h->M, h->J, h->Nd, (const float2 *)dT, h->masks, h->tw, h->Zd,
-                                   h->stream, h->xk),
-                     "fields kernel");
+            TMR_CUDA(defocus_fields(h, (const float2 *)dT), "fields kernel");
             tmr_status s2 = run_phase_fit(h, (const float2 *)dT, (const float *)dYd, h->phi, (float2 *)dT);
             if (s2 != TMR_OK) return s2;
         }
@@ -864,13 +908,14 @@ tmr_status tmr_defocus_forward(tmr_handle *h, const void *T, float *Y_def)
     void *dT, *dY;
     tmr_status st;
     if ((st = stage(h, ST_TIN, T, sizeof(float2) * MN, true, &dT)) != TMR_OK) return st;
-    if ((st = stage(h, ST_YDEF, Y_def, sizeof(float) * (size_t)h->Nd * h->M, false, &dY)) != TMR_OK) return st;
-    TMR_CUDA(launch_fields(h->N, h->M, h->J, h->Nd, (const float2 *)dT, h->masks, h->tw, h->Zd, h->stream, h->xk),
-             "fields kernel");
-    TMR_CUDA(launch_defocus_forward(h->ny, h->nx, h->Nd, h->Zd, h->H, nullptr, nullptr, (float *)dY, h->stream),
+    if ((st = stage(h, ST_YDEF, Y_def, sizeof(float) * ydef_floats(h), false, &dY)) != TMR_OK) return st;
+    TMR_CUDA(defocus_fields(h, (const float2 *)dT), "fields kernel");
+    TMR_CUDA(h->dkind == TMR_DEFOCUS_ANGULAR_2X
+                 ? launch_defocus_forward2x(h->ny, h->nx, h->Nd, h->Zd, h->H, (float *)dY, h->stream)
+                 : launch_defocus_forward(h->ny, h->nx, h->Nd, h->Zd, h->H, nullptr, nullptr, (float *)dY, h->stream),
              "defocus kernel");
     bool synced = false;
-    if ((st = unstage(h, Y_def, dY, sizeof(float) * (size_t)h->Nd * h->M, &synced)) != TMR_OK) return st;
+    if ((st = unstage(h, Y_def, dY, sizeof(float) * ydef_floats(h), &synced)) != TMR_OK) return st;
     if (synced) TMR_CUDA(cudaStreamSynchronize(h->stream), "sync");
     return TMR_OK;
 }
@@ -884,11 +929,10 @@ tmr_status tmr_defocus_fit(tmr_handle *h, const void *T_est, const float *y_def,
     void *dT, *dY, *dP = nullptr, *dO = nullptr;
     tmr_status st;
     if ((st = stage(h, ST_TIN, T_est, sizeof(float2) * MN, true, &dT)) != TMR_OK) return st;
-    if ((st = stage(h, ST_YDEF, y_def, sizeof(float) * (size_t)h->Nd * h->M, true, &dY)) != TMR_OK) return st;
+    if ((st = stage(h, ST_YDEF, y_def, sizeof(float) * ydef_floats(h), true, &dY)) != TMR_OK) return st;
     if (phi && (st = stage(h, ST_PHI, phi, sizeof(double) * h->M, false, &dP)) != TMR_OK) return st;
     if (T_out && (st = stage(h, ST_TOUT, T_out, sizeof(float2) * MN, false, &dO)) != TMR_OK) return st;
-    TMR_CUDA(launch_fields(h->N, h->M, h->J, h->Nd, (const float2 *)dT, h->masks, h->tw, h->Zd, h->stream, h->xk),
-             "fields kernel");
+    TMR_CUDA(defocus_fields(h, (const float2 *)dT), "fields kernel");
     if ((st = run_phase_fit(h, (const float2 *)dT, (const float *)dY, dP ? (double *)dP : h->phi,
                             (float2 *)dO)) != TMR_OK)
         return st;
@@ -898,6 +942,18 @@ tmr_status tmr_defocus_fit(tmr_handle *h, const void *T_est, const float *y_def,
     if (phi && (st = unstage(h, phi, dP, sizeof(double) * h->M, &synced)) != TMR_OK) return st;
     if (T_out && (st = unstage(h, T_out, dO, sizeof(float2) * MN, &synced)) != TMR_OK) return st;
     if (synced) TMR_CUDA(cudaStreamSynchronize(h->stream), "sync");
+    return TMR_OK;
+}
+
+tmr_status tmr_phase_fit_report(tmr_handle *h, double *loss, int *iters)
+{
+    tmr::set_last_error("");
+    if (!h) return fail(TMR_ERR_INVALID_ARG, "NULL handle");
+    if (!h->has_defocus) return fail(TMR_ERR_UNSUPPORTED, "handle has no defocus operator");
+    if (!h->fit_ran) return fail(TMR_ERR_INVALID_ARG, "no phase-offset fit has run on this handle");
+    TMR_CUDA(cudaStreamSynchronize(h->stream), "sync");
+    if (loss) TMR_CUDA(cudaMemcpy(loss, h->pf_loss, sizeof(double), cudaMemcpyDeviceToHost), "read loss");
+    if (iters) TMR_CUDA(cudaMemcpy(iters, h->pf_iters, sizeof(int), cudaMemcpyDeviceToHost), "read iterations");
     return TMR_OK;
 }
 

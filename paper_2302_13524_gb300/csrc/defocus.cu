@@ -228,6 +228,196 @@ cudaError_t launch_defocus_forward(int ny, int nx, int Nd, const float2 *Zd, con
 }
 
 // ---------------------------------------------------------------------------
+// The paper's defocus model (Sec. 2.3, Eq. angularspectrum, Eq.
+// forwarddefocusImage): fields c_n = TM_est e^{j theta_n} of separate incident
+// fields, A = K2^H P diag(h) K1 with the angular-spectrum kernel h and its NA
+// pupil on the half grid's frequencies, P the zero padding of the spectrum to
+// the 2ny x 2nx grid and K2^H the inverse DFT there (divided by ny nx, so that
+// with h = 1 the even full-grid pixels reproduce the half grid).  The padded
+// inverse is evaluated as four inverse DFTs of the half grid: the full-grid
+// pixel (2a + s, 2b + t) is
+//   (1 / (ny nx)) sum_{ky,kx} X[ky][kx] e^{i pi (ky s / ny + kx t / nx)} e^{2 pi i (ky a / ny + kx b / nx)}
+// (ky, kx the signed frequencies), i.e. the half-grid inverse of X times the
+// ramp ry^s rx^t, ry[ky] = e^{i pi ky / ny}, rx[kx] = e^{i pi kx / nx}; the
+// adjoint sums the four forward DFTs of the subgrids times the conjugate ramps.
+
+__global__ void k_make_H2x(int ny, int nx, double wavelength, double na, double zd, double pixel, float2 *H)
+{
+    const int P = ny * nx;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+        const int a = i / nx, b = i % nx;
+        const double ky = 2 * a < ny ? a : a - ny, kx = 2 * b < nx ? b : b - nx;
+        const double lu = wavelength * kx / (nx * pixel), lv = wavelength * ky / (ny * pixel);
+        const double rho2 = lu * lu + lv * lv;
+        if (sqrt(rho2) <= na) {
+            double s, c;
+            sincos(2.0 * M_PI / wavelength * sqrt(fmax(1.0 - rho2, 0.0)) * zd, &s, &c);
+            H[i] = make_float2((float)c, (float)s);
+        } else {
+            H[i] = make_float2(0.f, 0.f);
+        }
+    }
+}
+
+cudaError_t launch_make_H2x(int ny, int nx, double wavelength, double na, double zd, double pixel, float2 *H,
+                            cudaStream_t s)
+{
+    k_make_H2x<<<64, 256, 0, s>>>(ny, nx, wavelength, na, zd, pixel, H);
+    return cudaGetLastError();
+}
+
+// Zd[n][r] = sum_k T[r][k] inc[n][k] (FP32): a tiled complex product, 64 rows
+// x 32 fields per CTA, 16 x 16 threads with 4 x 2 outputs each, k in steps of 32.
+__global__ void __launch_bounds__(256) k_incident_fields(int M, int N, int Nd, const float2 *__restrict__ T,
+                                                         const float2 *__restrict__ inc, float2 *__restrict__ Zd)
+{
+    __shared__ float2 Ts[64][33], Is[32][33];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int r0 = blockIdx.x * 64, n0 = blockIdx.y * 32;
+    float2 acc[4][2];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 2; j++) acc[i][j] = make_float2(0.f, 0.f);
+    for (int k0 = 0; k0 < N; k0 += 32) {
+        for (int e = threadIdx.x; e < 64 * 32; e += 256) {
+            const int rr = e >> 5, kk = e & 31;
+            Ts[rr][kk] = (r0 + rr < M && k0 + kk < N) ? T[(size_t)(r0 + rr) * N + k0 + kk] : make_float2(0.f, 0.f);
+        }
+        for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+            const int nn = e >> 5, kk = e & 31;
+            Is[nn][kk] = (n0 + nn < Nd && k0 + kk < N) ? inc[(size_t)(n0 + nn) * N + k0 + kk] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < 32; kk++) {
+            float2 tv[4], iv[2];
+#pragma unroll
+            for (int i = 0; i < 4; i++) tv[i] = Ts[ty + 16 * i][kk];
+#pragma unroll
+            for (int j = 0; j < 2; j++) iv[j] = Is[tx + 16 * j][kk];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 2; j++) {
+                    acc[i][j].x = fmaf(tv[i].x, iv[j].x, fmaf(-tv[i].y, iv[j].y, acc[i][j].x));
+                    acc[i][j].y = fmaf(tv[i].x, iv[j].y, fmaf(tv[i].y, iv[j].x, acc[i][j].y));
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+            const int r = r0 + ty + 16 * i, n = n0 + tx + 16 * j;
+            if (r < M && n < Nd) Zd[(size_t)n * M + r] = acc[i][j];
+        }
+}
+
+cudaError_t launch_incident_fields(int M, int N, int Nd, const float2 *T, const float2 *inc, float2 *Zd,
+                                   cudaStream_t s)
+{
+    if (M == 0 || Nd == 0) return cudaSuccess;
+    dim3 grid((M + 63) / 64, (Nd + 31) / 32);
+    k_incident_fields<<<grid, 256, 0, s>>>(M, N, Nd, T, inc, Zd);
+    return cudaGetLastError();
+}
+
+// ramps of the four subgrids: ry[a] = e^{i pi ky(a) / ny}, rx[b] = e^{i pi kx(b) / nx}
+__device__ void make_ramps(float2 *ry, float2 *rx, int ny, int nx)
+{
+    for (int a = threadIdx.x; a < ny; a += blockDim.x) {
+        double s, c;
+        sincospi((double)(2 * a < ny ? a : a - ny) / ny, &s, &c);
+        ry[a] = make_float2((float)c, (float)s);
+    }
+    for (int b = threadIdx.x; b < nx; b += blockDim.x) {
+        double s, c;
+        sincospi((double)(2 * b < nx ? b : b - nx) / nx, &s, &c);
+        rx[b] = make_float2((float)c, (float)s);
+    }
+}
+
+__device__ __forceinline__ float2 ramp_st(int st, int a, int b, const float2 *ry, const float2 *rx)
+{
+    switch (st) {
+    case 0: return make_float2(1.f, 0.f);
+    case 1: return rx[b];
+    case 2: return ry[a];
+    default: return cmul(ry[a], rx[b]);
+    }
+}
+
+static size_t defocus2x_smem(int ny, int nx, int grids)
+{
+    return sizeof(float2) * ((size_t)grids * ny * (nx + 1) + ny / 2 + nx / 2 + ny + nx) + 64 * sizeof(double);
+}
+
+bool phase_fit2x_fits(int ny, int nx);
+
+bool defocus2x_supported(int ny, int nx)
+{
+    auto p2 = [](int v) { return v >= 2 && v <= 512 && (v & (v - 1)) == 0; };
+    return p2(ny) && p2(nx) && phase_fit2x_fits(ny, nx);
+}
+
+// Ydef[n][(2a + s) 2nx + 2b + t] = |A c_n|^2 at the full-grid pixels.
+__global__ void k_defocus_forward2x(int ny, int nx, int Nd, const float2 *__restrict__ Zd,
+                                    const float2 *__restrict__ H, float *__restrict__ Ydef)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int P = ny * nx, pitch = nx + 1, lx = __ffs(nx) - 1;
+    float2 *g = reinterpret_cast<float2 *>(smem_raw);
+    float2 *Xs = g + (size_t)ny * pitch;
+    float2 *twy = Xs + (size_t)ny * pitch, *twx = twy + ny / 2, *ry = twx + nx / 2, *rx = ry + ny;
+    make_tw(twy, ny);
+    make_tw(twx, nx);
+    make_ramps(ry, rx, ny, nx);
+    const float inv = 1.f / (float)P;
+    for (int n = blockIdx.x; n < Nd; n += gridDim.x) {
+        for (int i = threadIdx.x; i < P; i += blockDim.x) g[(i >> lx) * pitch + (i & (nx - 1))] = Zd[(size_t)n * P + i];
+        __syncthreads();
+        fft2_inplace(g, ny, nx, -1, twy, twx);
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            const int gi = (i >> lx) * pitch + (i & (nx - 1));
+            Xs[gi] = cmul(g[gi], H[i]);
+        }
+        __syncthreads();
+        for (int st = 0; st < 4; st++) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int a = i >> lx, b = i & (nx - 1), gi = a * pitch + b;
+                g[gi] = cmul(Xs[gi], ramp_st(st, a, b, ry, rx));
+            }
+            __syncthreads();
+            fft2_inplace(g, ny, nx, +1, twy, twx);
+            const int s = st >> 1, t = st & 1;
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int a = i >> lx, b = i & (nx - 1);
+                Ydef[(size_t)n * 4 * P + (size_t)(2 * a + s) * (2 * nx) + 2 * b + t] =
+                    cabs2(cscale(g[a * pitch + b], inv));
+            }
+            __syncthreads();
+        }
+    }
+}
+
+cudaError_t launch_defocus_forward2x(int ny, int nx, int Nd, const float2 *Zd, const float2 *H, float *Ydef,
+                                     cudaStream_t s)
+{
+    if (Nd == 0) return cudaSuccess;
+    const size_t sm = defocus2x_smem(ny, nx, 2);
+    cudaError_t e = cudaFuncSetAttribute(k_defocus_forward2x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = Nd < nsm ? Nd : nsm;
+    k_defocus_forward2x<<<grid, 512, sm, s>>>(ny, nx, Nd, Zd, H, Ydef);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Phase-offset fit.
 
 // bounded grid barrier; bar[0] arrival count, bar[1] generation.  A wait gives
@@ -360,16 +550,90 @@ __device__ void pf_coefficients(PFGram &G)
     G.gp = G.gmax > 0.0 ? -G.gg / G.gmax : 0.0;
 }
 
+// The 2x-padded operator's share of pf_eval for pattern n: on return g holds
+// A^H(w G) on the half grid, with w = A(c_n u) on the full grid and
+// G = I_n - |w|^2, and the loss of the pattern is added to fpl.  Xs and S are
+// two more grids: X h, and the accumulated cropped spectrum of w G.
+__device__ void pf_pattern2x(const PhaseFitParams &Pp, int n, float2 *g, float2 *Xs, float2 *S, const float2 *twy,
+                             const float2 *twx, const float2 *ry, const float2 *rx, float &fpl)
+{
+    const int ny = Pp.ny, nx = Pp.nx, P = ny * nx, pitch = nx + 1, lx = __ffs(nx) - 1;
+    const float *In = Pp.Ydef + (size_t)n * 4 * P;
+    const float inv = 1.0f / (float)P;
+    fft2_inplace(g, ny, nx, -1, twy, twx);
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int gi = (i >> lx) * pitch + (i & (nx - 1));
+        Xs[gi] = cmul(g[gi], Pp.H[i]);
+        S[gi] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int st = 0; st < 4; st++) {
+        const int s = st >> 1, t = st & 1;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            const int a = i >> lx, b = i & (nx - 1), gi = a * pitch + b;
+            g[gi] = cmul(Xs[gi], ramp_st(st, a, b, ry, rx));
+        }
+        __syncthreads();
+        fft2_inplace(g, ny, nx, +1, twy, twx);
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            const int a = i >> lx, b = i & (nx - 1), gi = a * pitch + b;
+            const float2 w = cscale(g[gi], inv);
+            const float Gv = In[(size_t)(2 * a + s) * (2 * nx) + 2 * b + t] - cabs2(w);
+            fpl = fmaf(Gv, Gv, fpl);
+            g[gi] = cscale(w, Gv);
+        }
+        __syncthreads();
+        fft2_inplace(g, ny, nx, -1, twy, twx);
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            const int a = i >> lx, b = i & (nx - 1), gi = a * pitch + b;
+            S[gi] = cadd(S[gi], cmulc(g[gi], ramp_st(st, a, b, ry, rx)));
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int gi = (i >> lx) * pitch + (i & (nx - 1));
+        g[gi] = cscale(cmulc(S[gi], Pp.H[i]), inv);
+    }
+    __syncthreads();
+    fft2_inplace(g, ny, nx, +1, twy, twx);
+}
+
 // Loss and gradient partials of this CTA's patterns for the phase table u:
 // part[blockIdx.x][:] (FP32, at most a few patterns per CTA) and fpart (FP64).
+// ex (kind 1 only): the grids Xs, S and the ramps ry, rx of pf_pattern2x.
+struct PFExtra {
+    float2 *Xs, *S;
+    const float2 *ry, *rx;
+};
+
 __device__ void pf_eval(const PhaseFitParams &Pp, const PFWork &W, float2 *g, const float2 *twy,
-                        const float2 *twx, double *red, double *out)
+                        const float2 *twx, double *red, double *out, const PFExtra &ex)
 {
     const int ny = Pp.ny, nx = Pp.nx, P = ny * nx, pitch = nx + 1, lx = __ffs(nx) - 1;
     auto at = [&](int k) { return (k >> lx) * pitch + (k & (nx - 1)); };
     float *part = W.part + (size_t)blockIdx.x * P;
     for (int k = threadIdx.x; k < P; k += blockDim.x) part[k] = 0.f;
     double fl = 0.0;
+    if (Pp.kind == 1) {
+        for (int n = blockIdx.x; n < Pp.Nd; n += gridDim.x) {
+            const float2 *cn = Pp.Zd + (size_t)n * P;
+            for (int k = threadIdx.x; k < P; k += blockDim.x) g[at(k)] = cmul(cn[k], __ldcg(W.u + k));
+            __syncthreads();
+            float fpl = 0.f;
+            pf_pattern2x(Pp, n, g, ex.Xs, ex.S, twy, twx, ex.ry, ex.rx, fpl);
+            fl += (double)fpl;
+            for (int k = threadIdx.x; k < P; k += blockDim.x) {
+                const float2 v = cmulc(g[at(k)], cn[k]);  // conj(c_n) A^H(w G)
+                const float2 cu = __ldcg(W.u + k);
+                part[k] += -4.f * fmaf(cu.x, v.y, -cu.y * v.x);  // -4 Im(conj(u) v)
+            }
+            __syncthreads();
+        }
+        double fv[1] = {fl};
+        block_sum<1, double>(fv, red, out);
+        if (threadIdx.x == 0) W.fpart[blockIdx.x] = out[0];
+        return;
+    }
     for (int n = blockIdx.x; n < Pp.Nd; n += gridDim.x) {
         const float2 *cn = Pp.Zd + (size_t)n * P;
         const float *In = Pp.Ydef + (size_t)n * P;
@@ -411,14 +675,18 @@ __global__ void __launch_bounds__(512) k_phase_fit(PhaseFitParams Pp)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ny = Pp.ny, nx = Pp.nx, P = ny * nx, m = Pp.m, nb = gridDim.x;
+    const int ngrid = Pp.kind == 1 ? 3 : 1;
     float2 *g = reinterpret_cast<float2 *>(smem_raw);
-    float2 *twy = g + (size_t)ny * (nx + 1), *twx = twy + ny / 2;
-    double *red = reinterpret_cast<double *>(twx + nx / 2 + 1);
+    float2 *twy = g + (size_t)ngrid * ny * (nx + 1), *twx = twy + ny / 2;
+    float2 *ry = twx + nx / 2, *rx = ry + ny;
+    double *red = reinterpret_cast<double *>(rx + nx + 1);
     double *out = red + 32 * kPfDots;
     __shared__ PFGram G;
     PFWork W = pf_carve(Pp.ws, P, m, nb);
     make_tw(twy, ny);
     make_tw(twx, nx);
+    PFExtra ex{g + (size_t)ny * (nx + 1), g + (size_t)2 * ny * (nx + 1), ry, rx};
+    if (Pp.kind == 1) make_ramps(ry, rx, ny, nx);
     const int tid = threadIdx.x, nt = blockDim.x;
     const int chunk = (P + nb - 1) / nb, k0 = min(P, blockIdx.x * chunk), k1 = min(P, k0 + chunk);
     double *Sg_ = W.S, *Yg_ = W.Y;
@@ -477,7 +745,7 @@ __global__ void __launch_bounds__(512) k_phase_fit(PhaseFitParams Pp)
         bail();
         return;
     }
-    pf_eval(Pp, W, g, twy, twx, red, out);
+    pf_eval(Pp, W, g, twy, twx, red, out, ex);
     if (!grid_sync(Pp.sync, Pp.err, Pp.wait_spins, Pp.withhold_release)) {
         bail();
         return;
@@ -541,7 +809,7 @@ __global__ void __launch_bounds__(512) k_phase_fit(PhaseFitParams Pp)
         bail();
         return;
     }
-            pf_eval(Pp, W, g, twy, twx, red, out);
+            pf_eval(Pp, W, g, twy, twx, red, out, ex);
             if (!grid_sync(Pp.sync, Pp.err, Pp.wait_spins, Pp.withhold_release)) {
         bail();
         return;
@@ -645,11 +913,22 @@ __global__ void __launch_bounds__(512) k_phase_fit(PhaseFitParams Pp)
     }
 }
 
+// dynamic shared memory of k_phase_fit: 1 grid (kind 0) or 3 (kind 1), the
+// twiddles, the ramps and the reduction scratch
+static size_t phase_fit_smem(int ny, int nx, int kind)
+{
+    const int ngrid = kind == 1 ? 3 : 1;
+    return sizeof(float2) * ((size_t)ngrid * ny * (nx + 1) + ny / 2 + nx / 2 + ny + nx + 1) +
+           sizeof(double) * (32 * kPfDots + kPfDots + 8) + 64;
+}
+
+bool phase_fit2x_fits(int ny, int nx) { return phase_fit_smem(ny, nx, 1) + sizeof(PFGram) + 1024 <= 227 * 1024; }
+
 cudaError_t launch_phase_fit(const PhaseFitParams &p, cudaStream_t s)
 {
     const int grid = phase_fit_grid(p.ny, p.nx, p.Nd);
     const int P = p.ny * p.nx;
-    const size_t sm = defocus_smem(p.ny, p.nx) + sizeof(double) * (32 * kPfDots + kPfDots + 8) + 2 * sizeof(float2);
+    const size_t sm = phase_fit_smem(p.ny, p.nx, p.kind);
     (void)P;
     cudaError_t e = cudaFuncSetAttribute(k_phase_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;

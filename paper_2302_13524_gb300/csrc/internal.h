@@ -156,10 +156,18 @@ struct PhaseFitParams {
     double *loss_out;    // [1]
     long long wait_spins;   // polls before a grid-barrier wait gives up
     bool withhold_release;  // test hook: the barrier is never released
+    int kind;               // 0: same-grid operator; 1: angular spectrum with 2x padding (Ydef [Nd][4P])
 };
 size_t phase_fit_workspace_doubles(int P, int Nd, int m, int grid);
 int phase_fit_grid(int ny, int nx, int Nd);
 bool defocus_supported(int ny, int nx);
+bool defocus2x_supported(int ny, int nx);
+cudaError_t launch_make_H2x(int ny, int nx, double wavelength, double na, double zd, double pixel, float2 *H,
+                            cudaStream_t s);
+cudaError_t launch_incident_fields(int M, int N, int Nd, const float2 *T, const float2 *inc, float2 *Zd,
+                                   cudaStream_t s);
+cudaError_t launch_defocus_forward2x(int ny, int nx, int Nd, const float2 *Zd, const float2 *H, float *Ydef,
+                                     cudaStream_t s);
 cudaError_t launch_phase_fit(const PhaseFitParams &p, cudaStream_t s);
 cudaError_t launch_defocus_forward(int ny, int nx, int Nd, const float2 *Zd, const float2 *H,
                                    const float2 *twy, const float2 *twx, float *Ydef,

@@ -18,8 +18,11 @@ class Retriever:
     """Retrieve an M x N transmission matrix from J masked-DFT intensity sets
     (Algorithm 1 per row, then the defocus phase-offset fit).
 
-    masks: complex64 tensor [J, N] (|d| = 1).  defocus: None or
-    dict(ny, nx, n_defocus, coef=0.05, H=None).  options: the fields of
+    masks: complex64 tensor [J, N] (|d| = 1).  defocus: None,
+    dict(ny, nx, n_defocus, coef=0.05, H=None) (same-grid operator, images
+    [n_defocus, M]) or dict(kind=1, ny, nx, n_defocus, wavelength, na, z_d,
+    pixel, incident) (angular spectrum with 2x padding, images
+    [n_defocus, 4 M] on the 2ny x 2nx grid).  options: the fields of
     tmr_options (m, init, seed, power_iters, clip, tol, phase_iters, precision,
     use_graph, workspace_limit, schedule, tune_cache).
     """
@@ -75,7 +78,7 @@ class Retriever:
                    iters=self._empty((self.M,), "i32"), loss=self._empty((self.M,), "f32"))
         y = self._check(y, "f32", (self.M, self.J, self.N), "y")
         if y_def is not None:
-            y_def = self._check(y_def, "f32", (self.h.n_defocus, self.M), "y_def")
+            y_def = self._check(y_def, "f32", (self.h.n_defocus, self.h.defocus_pixels), "y_def")
         if T_init is None:
             _lib.tmr_retrieve(self.h, y, y_def, iters, out["T"], out["status"], out["iters"], out["loss"])
         else:
@@ -84,8 +87,8 @@ class Retriever:
         return out
 
     def defocus_forward(self, T: torch.Tensor) -> torch.Tensor:
-        """Defocus-plane intensities [n_defocus, M] of the first n_defocus patterns (Eq. forwarddefocusImage)."""
-        Yd = self._empty((self.h.n_defocus, self.M), "f32")
+        """Defocus-plane intensities [n_defocus, M] (kind 0) or [n_defocus, 4 M] (kind 1) (Eq. forwarddefocusImage)."""
+        Yd = self._empty((self.h.n_defocus, self.h.defocus_pixels), "f32")
         _lib.tmr_defocus_forward(self.h, self._check(T, "c64", (self.M, self.N), "T"), Yd)
         return Yd
 
@@ -94,7 +97,7 @@ class Retriever:
         phi = self._empty((self.M,), "f64")
         T = self._empty((self.M, self.N), "c64")
         _lib.tmr_defocus_fit(self.h, self._check(T_est, "c64", (self.M, self.N), "T_est"),
-                             self._check(y_def, "f32", (self.h.n_defocus, self.M), "y_def"), phi, T)
+                             self._check(y_def, "f32", (self.h.n_defocus, self.h.defocus_pixels), "y_def"), phi, T)
         return phi, T
 
     def sync(self, timeout_s: float = 60.0):

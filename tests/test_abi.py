@@ -85,3 +85,33 @@ def test_preprocess_argument_errors_before_any_device_work():
     with pytest.raises(TypeError):
         import torch
         tmr.preprocess(torch.zeros((2, 4, 4), dtype=torch.int16))  # not on a GPU
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of tmr_options and tmr_defocus_op have the C
+    compiler's field offsets and sizes (a field added to the header but not to
+    the binding, or in another order, fails here)."""
+    import shutil
+    import subprocess
+    tmr = pytest.importorskip("paper_2302_13524_gb300")
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    import os
+    inc = os.path.dirname(tmr._lib.HEADER)
+    lines = []
+    for cname, cls in (("tmr_options", tmr._lib.tmr_options), ("tmr_defocus_op", tmr._lib.tmr_defocus_op)):
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"tmr.h\"\nint main(void){\n"
+                   + "\n".join(lines) + "\nreturn 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {(a, b): int(c) for a, b, c in (ln.split() for ln in out if ln)}
+    for cname, cls in (("tmr_options", tmr._lib.tmr_options), ("tmr_defocus_op", tmr._lib.tmr_defocus_op)):
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
