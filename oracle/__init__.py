@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.c")
 
-INIT = {"random": 0, "bp": 1, "spectral": 2, "given": 3}
+INIT = {"random": 0, "bp": 1, "spectral": 2, "given": 3, "lanczos": 4}
 ROW_MAXITER, ROW_CONVERGED, ROW_ZERO, ROW_NUMERIC = 0, 1, 2, 3
 
 

@@ -47,7 +47,7 @@ typedef double complex cplx;
 static double abs2(cplx x) { return creal(x) * creal(x) + cimag(x) * cimag(x); }
 
 enum { ROW_MAXITER = 0, ROW_CONVERGED = 1, ROW_ZERO = 2, ROW_NUMERIC = 3 };
-enum { INIT_RANDOM = 0, INIT_BP = 1, INIT_SPECTRAL = 2, INIT_GIVEN = 3 };
+enum { INIT_RANDOM = 0, INIT_BP = 1, INIT_SPECTRAL = 2, INIT_GIVEN = 3, INIT_LANCZOS = 4 };
 
 int orc_num_threads(void)
 {
@@ -341,6 +341,113 @@ static double rdot(const cplx *a, const cplx *b, int n)
     return s;
 }
 
+/* Eigenvalues and eigenvectors of a symmetric n x n matrix by the cyclic
+ * Jacobi method (rotations that zero one off-diagonal entry at a time, swept
+ * until the off-diagonal part vanishes).  A (row-major) is overwritten; on
+ * return ev[i] = A[i][i] and column i of V is its eigenvector. */
+static void jacobi_eig(int n, double *A, double *V, double *ev)
+{
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) V[i * n + j] = i == j ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 100; sweep++) {
+        double off = 0, dia = 0;
+        for (int p = 0; p < n; p++) {
+            dia += A[p * n + p] * A[p * n + p];
+            for (int q = p + 1; q < n; q++) off += A[p * n + q] * A[p * n + q];
+        }
+        if (off <= 1e-32 * dia || off == 0) break;
+        for (int p = 0; p < n; p++)
+            for (int q = p + 1; q < n; q++) {
+                double apq = A[p * n + q];
+                if (apq == 0) continue;
+                /* J = [[c, s], [-s, c]] in the (p, q) plane; A <- J^T A J with
+                 * t = s / c the smaller root of t^2 + 2 theta t - 1 = 0 */
+                double theta = (A[q * n + q] - A[p * n + p]) / (2 * apq);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1));
+                double c = 1 / sqrt(t * t + 1), s = t * c;
+                for (int k = 0; k < n; k++) {
+                    double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - s * akq;
+                    A[k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; k++) {
+                    double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - s * aqk;
+                    A[q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; k++) {
+                    double vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = c * vkp - s * vkq;
+                    V[k * n + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    for (int i = 0; i < n; i++) ev[i] = A[i * n + i];
+}
+
+/* The leading eigenvector of A = Q^H diag(tau) Q / (J N) by the Lanczos method
+ * (the spectral start's eigenvector in fewer products than the power
+ * iteration; not in the paper).  From v_0 = t / ||t||, step j forms
+ * w = A v_j, orthogonalises w against v_0 .. v_j by two passes of classical
+ * Gram-Schmidt (coefficients h_l = <v_l, w>, w <- w - sum_l h_l v_l), takes
+ * alpha_j = the real part of v_j's two coefficients and beta_j = ||w||, and
+ * stops after k steps or when beta_j <= 1e-6 alpha_0 (an invariant subspace);
+ * else v_{j+1} = w / beta_j.  The tridiagonal T (alpha on the diagonal, beta
+ * beside it) is diagonalised, and t <- sum_l s_l v_l with s the eigenvector of
+ * its largest eigenvalue, signed so that s_0 >= 0.  Work: z (K), sc (3N). */
+static void lanczos_row(const double *tau, const cplx *d, int N, int J, const cplx *tw, int k,
+                        cplx *t, cplx *z, cplx *sc)
+{
+    size_t K = (size_t)J * N;
+    cplx *V = malloc(sizeof(cplx) * (size_t)k * N), *w = malloc(sizeof(cplx) * (size_t)N);
+    cplx *h = malloc(sizeof(cplx) * (size_t)k);
+    double *al = calloc((size_t)k, sizeof(double)), *be = calloc((size_t)k, sizeof(double));
+    double nt = sqrt(norm2(t, N));
+    for (int n = 0; n < N; n++) V[n] = nt > 0 ? t[n] / nt : 0;
+    int kk = k;
+    for (int j = 0; j < k; j++) {
+        cplx *vj = V + (size_t)j * N;
+        apply_Q(vj, d, N, J, tw, z, sc);
+        for (size_t i = 0; i < K; i++) z[i] *= tau[i];
+        apply_QH(z, d, N, J, tw, w, sc);
+        for (int n = 0; n < N; n++) w[n] /= (double)J * N;
+        al[j] = 0;
+        for (int pass = 0; pass < 2; pass++) {
+            for (int l = 0; l <= j; l++) {
+                cplx s = 0;
+                for (int n = 0; n < N; n++) s += conj(V[(size_t)l * N + n]) * w[n];
+                h[l] = s;
+            }
+            for (int l = 0; l <= j; l++)
+                for (int n = 0; n < N; n++) w[n] -= h[l] * V[(size_t)l * N + n];
+            al[j] += creal(h[j]);
+        }
+        be[j] = sqrt(norm2(w, N));
+        if (j == k - 1 || !(be[j] > 1e-6 * al[0])) {
+            kk = j + 1;
+            break;
+        }
+        for (int n = 0; n < N; n++) V[(size_t)(j + 1) * N + n] = w[n] / be[j];
+    }
+    double *Tm = calloc((size_t)kk * kk, sizeof(double)), *E = malloc(sizeof(double) * kk * kk);
+    double *ev = malloc(sizeof(double) * kk);
+    for (int j = 0; j < kk; j++) {
+        Tm[j * kk + j] = al[j];
+        if (j + 1 < kk) Tm[j * kk + j + 1] = Tm[(j + 1) * kk + j] = be[j];
+    }
+    jacobi_eig(kk, Tm, E, ev);
+    int top = 0;
+    for (int j = 1; j < kk; j++)
+        if (ev[j] > ev[top]) top = j;
+    double sg = E[0 * kk + top] < 0 ? -1.0 : 1.0;
+    for (int n = 0; n < N; n++) {
+        cplx s = 0;
+        for (int l = 0; l < kk; l++) s += sg * E[l * kk + top] * V[(size_t)l * N + n];
+        t[n] = s;
+    }
+    free(V); free(w); free(h); free(al); free(be); free(Tm); free(E); free(ev);
+}
+
 /* t0 for one row.
  *  random   : Philox complex normal, rescaled to the Parseval norm
  *             ||t||^2 = sum(y) / (J N)  (Q^H Q = J N I for unit-modulus masks).
@@ -350,6 +457,8 @@ static double rdot(const cplx *a, const cplx *b, int n)
  *             A = Q^H diag(tau) Q / (J N), tau_i = min(y_i / mean(y), clip)
  *             (clip <= 0: tau = y / mean(y)), started from the random vector,
  *             then rescaled to the Parseval norm.
+ *  lanczos  : the same eigenvector by `power_iters` Lanczos steps from the
+ *             random vector (lanczos_row), then rescaled to the Parseval norm.
  * Work: z (K), sc (N). */
 static void init_row(const double *y, const cplx *d, int N, int J, const cplx *tw, int init,
                      uint64_t seed, int row, int power_iters, double clip, cplx *t, cplx *z,
@@ -366,6 +475,16 @@ static void init_row(const double *y, const cplx *d, int N, int J, const cplx *t
         return;
     }
     for (int n = 0; n < N; n++) t[n] = philox_cnormal(seed, (uint32_t)row, (uint32_t)n);
+    if (init == INIT_LANCZOS && power_iters > 0) {
+        double mean = sy / (double)K;
+        double *tau = malloc(sizeof(double) * K);
+        for (size_t i = 0; i < K; i++) {
+            tau[i] = mean > 0 ? y[i] / mean : 0.0;
+            if (clip > 0 && tau[i] > clip) tau[i] = clip;
+        }
+        lanczos_row(tau, d, N, J, tw, power_iters, t, z, sc);
+        free(tau);
+    }
     if (init == INIT_SPECTRAL) {
         double mean = sy / (double)K;
         for (int it = 0; it < power_iters; it++) {

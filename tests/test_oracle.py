@@ -189,6 +189,75 @@ def test_spectral_init_is_leading_eigenvector():
         assert abs(np.sum(abs(T0[r]) ** 2) - y.sum() / (J * N)) < 1e-10 * y.sum()
 
 
+def _krylov_ritz(A, v, k):
+    """Rayleigh-Ritz on span{v, A v, ..., A^(k-1) v}: the Krylov matrix built by
+    repeated products, an orthonormal basis by QR, the top eigenvector of the
+    projected matrix by eigh, mapped back (no Lanczos recurrence)."""
+    Kr = np.empty((v.size, k), complex)
+    x = v / np.linalg.norm(v)
+    for j in range(k):
+        Kr[:, j] = x
+        x = A @ x
+        x /= np.linalg.norm(x)
+    B, _ = np.linalg.qr(Kr)
+    w, S = np.linalg.eigh(B.conj().T @ A @ B)
+    return B @ S[:, -1]
+
+
+def test_lanczos_start_is_the_krylov_ritz_vector():
+    """k Lanczos steps give the Ritz vector of the k-dimensional Krylov space of
+    A = Q^H diag(tau) Q / (J N) from the Philox start, at the Parseval norm, with
+    Re<t, v_0> >= 0; k = N gives the leading eigenvector of A itself."""
+    rng = np.random.default_rng(40)
+    M, N, J, clip = 3, 16, 4, 2.0
+    _, d = synth.mask_phases(J, N, seed=41)
+    Y = oracle.forward(crandn(rng, M, N), d)
+    Q = dense_Q(d)
+    for k in (3, 6, 9):
+        T0 = oracle.init(Y, d, "lanczos", seed=2, power_iters=k, clip=clip)
+        for r in range(M):
+            y = Y[r].ravel()
+            tau = np.minimum(y / y.mean(), clip)
+            A = Q.conj().T @ (tau[:, None] * Q) / (J * N)
+            v0 = oracle.random_cnormal(2, r, N)
+            x = _krylov_ritz(A, v0, k)
+            fid = abs(np.vdot(x, T0[r])) / np.linalg.norm(T0[r])
+            assert fid > 1 - 1e-10, (k, r, fid)
+            assert np.real(np.vdot(v0, T0[r])) > 0
+            assert abs(np.sum(abs(T0[r]) ** 2) - y.sum() / (J * N)) < 1e-10 * y.sum()
+    T0 = oracle.init(Y, d, "lanczos", seed=2, power_iters=N, clip=clip)
+    for r in range(M):
+        y = Y[r].ravel()
+        tau = np.minimum(y / y.mean(), clip)
+        A = Q.conj().T @ (tau[:, None] * Q) / (J * N)
+        v = np.linalg.eigh(A)[1][:, -1]
+        assert abs(np.vdot(v, T0[r])) / np.linalg.norm(T0[r]) > 1 - 1e-9
+
+
+def test_lanczos_stops_on_an_invariant_subspace():
+    """Constant intensities make tau = 1 and A = Q^H Q / (J N) = I: the first
+    step finds beta_0 = 0, and the start is the random start itself."""
+    N, J = 32, 4
+    _, d = synth.mask_phases(J, N, seed=42)
+    Y = np.full((2, J, N), 3.0)
+    T_l = oracle.init(Y, d, "lanczos", seed=7, power_iters=8, row_ids=[4, 5])
+    T_r = oracle.init(Y, d, "random", seed=7, row_ids=[4, 5])
+    np.testing.assert_allclose(T_l, T_r, rtol=0, atol=1e-12)
+
+
+def test_lanczos_and_power_starts_agree_when_both_converge():
+    """Both starts approximate the same leading eigenvector: with enough steps
+    each is within 1e-9 of it, hence of the other (up to the global phase)."""
+    rng = np.random.default_rng(43)
+    M, N, J = 4, 32, 4
+    _, d = synth.mask_phases(J, N, seed=44)
+    Y = oracle.forward(crandn(rng, M, N), d)
+    T_p = oracle.init(Y, d, "spectral", seed=3, power_iters=4000)
+    T_l = oracle.init(Y, d, "lanczos", seed=3, power_iters=N)
+    f = oracle.fidelity_rows(T_l, T_p)
+    assert np.all(f > 1 - 1e-9), f
+
+
 def test_random_init_parseval_norm_and_rows():
     rng = np.random.default_rng(16)
     M, N, J = 4, 32, 4
