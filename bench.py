@@ -73,7 +73,10 @@ def parse():
                     help="mixed: FP16 intensities, BF16 pairs, tensor-core split-BF16 DFT "
                          "stages, last 10 iterations FP32 (N = 256 or 4096)")
     ap.add_argument("--iters", type=int, default=None, help="L-BFGS iterations (cap); default per workload")
-    ap.add_argument("--power-iters", type=int, default=100)
+    ap.add_argument("--start", default="lanczos", choices=["lanczos", "power"],
+                    help="spectral start: Lanczos steps (default) or the power iteration")
+    ap.add_argument("--power-iters", type=int, default=None,
+                    help="operator products of the spectral start (default 16 Lanczos steps, 100 power)")
     ap.add_argument("--phase-iters", type=int, default=100)
     ap.add_argument("--rows", type=int, default=None, help="override M (grid kept 128 wide)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -85,6 +88,9 @@ def parse():
     args = ap.parse_args()
     if args.iters is None:
         args.iters = WORKLOADS[args.workload]["iters"]
+    if args.power_iters is None:
+        args.power_iters = 16 if args.start == "lanczos" else 100
+    args.lanczos = 1 if args.start == "lanczos" else 0
     return args
 
 
@@ -117,25 +123,29 @@ def fft_flops(N: int) -> float:
     return 5.0 * N * math.log2(N)
 
 
-def solver_flops_per_row(N, J, m, iters, power_iters) -> float:
-    """Algorithmic FP32 flops of one row: power iterations, the gradient at the
-    start, and the L-BFGS iterations (two FFT batches each, elementwise work,
-    two-loop).  The FFT count follows the 5 N log2 N convention for every N,
-    also where the library evaluates a length-N DFT through longer FFTs
-    (Bluestein).  iters may be the sum of the iterations of several rows
-    (then add the start once per row)."""
+def solver_flops_per_row(N, J, m, iters, power_iters, lanczos=0) -> float:
+    """Algorithmic FP32 flops of one row: the spectral start's products with A
+    (power iterations or Lanczos steps), the gradient at the start, and the
+    L-BFGS iterations (two FFT batches each, elementwise work, two-loop).  A
+    Lanczos step j also orthogonalises against its j + 1 vectors by two
+    passes of a complex dot product and an update (32 (j + 1) N flops), in
+    all 16 k (k + 1) N for k steps.  The FFT count follows the 5 N log2 N
+    convention for every N, also where the library evaluates a length-N DFT
+    through longer FFTs (Bluestein).  iters may be the sum of the iterations
+    of several rows (then add the start once per row)."""
     K = J * N
     f_batch = J * fft_flops(N)
     f_power = 2 * f_batch + 16 * K
     f_eval = 2 * f_batch + 16 * K
     f_iter = 2 * f_batch + 30 * K + 16 * m * N
-    return power_iters * f_power + f_eval + iters * f_iter
+    f_gs = 16 * power_iters * (power_iters + 1) * N if lanczos else 0
+    return power_iters * f_power + f_gs + f_eval + iters * f_iter
 
 
-def solver_flops(N, J, m, row_iters, power_iters) -> float:
+def solver_flops(N, J, m, row_iters, power_iters, lanczos=0) -> float:
     """Algorithmic flops of a launch whose rows ran row_iters iterations each."""
     rows = len(row_iters)
-    start = solver_flops_per_row(N, J, m, 0, power_iters)
+    start = solver_flops_per_row(N, J, m, 0, power_iters, lanczos)
     per_iter = solver_flops_per_row(N, J, m, 1, 0) - solver_flops_per_row(N, J, m, 0, 0)
     return rows * start + per_iter * float(np.sum(row_iters))
 
@@ -201,7 +211,7 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- reference arm
-def cpu_oracle_sample(W, M, iters, power_iters, rows_n, seed=0, keep=None):
+def cpu_oracle_sample(W, M, iters, power_iters, rows_n, seed=0, keep=None, lanczos=0):
     """Time the FP64 oracle on rows_n sampled rows of workload W.  Returns
     (rows/s, seconds, threads, description); when keep is a dict it receives
     the sample (intensities rounded to float32, the masks, the true rows and
@@ -220,13 +230,14 @@ def cpu_oracle_sample(W, M, iters, power_iters, rows_n, seed=0, keep=None):
     Y = synth.shot_noise(Y, synth.photon_scale(Y.mean(), ph), seed=seed, row_ids=rows)
     Y = Y.astype(np.float32)  # the values a float32 caller would pass
     t0 = time.perf_counter()
-    Tr, _, _, _ = oracle.retrieve_rows(Y, d, iters, init="spectral", power_iters=power_iters,
-                                       clip=2.0, tol=W["tol"], seed=seed)
+    Tr, _, _, _ = oracle.retrieve_rows(Y, d, iters, init="lanczos" if lanczos else "spectral",
+                                       power_iters=power_iters, clip=2.0, tol=W["tol"], seed=seed)
     dt = time.perf_counter() - t0
     fid = oracle.fidelity_rows(Tr, T)
     if keep is not None:
         keep.update(Y=Y, d=d, T=T, Tr=Tr, fid=fid)
-    desc = (f"{len(rows)} sampled rows of the workload, Algorithm 1 only ({power_iters} power + "
+    desc = (f"{len(rows)} sampled rows of the workload, Algorithm 1 only ({power_iters} "
+            f"{'Lanczos' if lanczos else 'power'} + "
             f"{iters} L-BFGS iterations, naive O(N^2) DFT, FP64, OpenMP over rows); the global "
             f"phase-offset fit is not in the sample; mean fidelity {fid.mean():.4f}")
     return len(rows) / dt, dt, oracle.num_threads(), desc
@@ -242,7 +253,7 @@ def run_reference(args):
     vals = []
     for s in range(args.warmup + args.steps):
         v, dt, cores, desc = cpu_oracle_sample(W, M, args.iters, args.power_iters,
-                                               rows_per_step, seed=0)
+                                               rows_per_step, seed=0, lanczos=args.lanczos)
         if s >= args.warmup:
             vals.append((v, dt))
     value = float(np.mean([v for v, _ in vals]))
@@ -252,7 +263,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": W["desc"], "iters": args.iters, "power_iters": args.power_iters,
-                       "rows_per_step": rows_per_step},
+                       "start": args.start, "rows_per_step": rows_per_step},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -308,7 +319,7 @@ def sweep_to_099(tmr, torch, make_handle, y, y_def, Tg, ref_frac, stream, P_list
 
 
 def second_half_arms(tmr, torch, synth, N, M, J, R, m, d, dop, photons, phase_iters, stream, world, iters,
-                     power_iters, keep=None):
+                     power_iters, keep=None, lanczos=0):
     """The metric's second half on the learned-initialiser workload (the plain
     workload's fiber model drawn as a family: shared input mode basis V, own
     coupling and phases): the network (J N -> 1024 -> 1024 -> 2 N, GELU, BF16
@@ -317,7 +328,8 @@ def second_half_arms(tmr, torch, synth, N, M, J, R, m, d, dop, photons, phase_it
     phase-invariant loss), then four arms -- spectral and learned start, FP32
     and mixed precision -- run on the held-out fiber 101 with the phase fit:
     rows/s at the configured budget and the fastest (power, L-BFGS) budget that
-    meets the 0.99 bar.  Also the network's inference throughput against the
+    meets the 0.99 bar (the start: Lanczos steps when lanczos, else power
+    iterations).  Also the network's inference throughput against the
     measured BF16 peak, and (keep: the CPU-baseline sample) each arm's
     fidelity difference to the FP64 oracle on the oracle's sampled rows."""
     from paper_2302_13524_gb300 import learned_init as li
@@ -331,7 +343,7 @@ def second_half_arms(tmr, torch, synth, N, M, J, R, m, d, dop, photons, phase_it
         gen = torch.Generator(device="cuda")
         gen.manual_seed(4242)
         Xs, Ts = [], []
-        with tmr.tmr_create(N, M, J, dg, None, dict(init="spectral", power_iters=100, m=m),
+        with tmr.tmr_create(N, M, J, dg, None, dict(init="spectral", power_iters=16, lanczos=1, m=m),
                             stream=stream.cuda_stream) as hd:
             for f in cfg["train_fibers"]:
                 _, yf = li.fiber_data(hd, synth.tm_family_device(M, N, R, f, 0), photons, gen)
@@ -390,7 +402,7 @@ def second_half_arms(tmr, torch, synth, N, M, J, R, m, d, dop, photons, phase_it
 
         def opts(init, prec, P):
             return dict(init=init, power_iters=P, clip=2.0, m=m, phase_iters=phase_iters, precision=prec,
-                        use_graph=1)
+                        use_graph=1, lanczos=lanczos)
 
         def make(init, prec):
             def mk(P):
@@ -417,7 +429,10 @@ def second_half_arms(tmr, torch, synth, N, M, J, R, m, d, dop, photons, phase_it
                                  "frac_ge_0.99": float(np.mean(f >= 0.99))}}
             if seeded is not None:
                 arm["rows_seeded_by_network"] = int(seeded)
-            P_list = (100, 80, 60, 50, 40, 30) if init == "spectral" else (100, 80, 60, 50, 40, 30, 20)
+            if lanczos:
+                P_list = tuple(p for p in (16, 14, 12, 10, 8, 6, 4) if p <= power_iters)
+            else:
+                P_list = (100, 80, 60, 50, 40, 30) if init == "spectral" else (100, 80, 60, 50, 40, 30, 20)
             best, passing = sweep_to_099(tmr, torch, make(init, prec), y, y_def, Tg, ref_frac, stream, P_list,
                                          (10, 20, 30, 50, 75), world)
             arm["to_fidelity_0.99"] = best
@@ -540,7 +555,7 @@ def main():
     # host-buffer calls (the e2e leg) launch directly
     opt = dict(init="spectral", power_iters=args.power_iters, clip=2.0, m=m,
                phase_iters=args.phase_iters, seed=seed, tol=W["tol"], precision=args.precision,
-               use_graph=1)
+               use_graph=1, lanczos=args.lanczos)
     dop = dict(ny=ny, nx=nx, n_defocus=Nd, coef=0.05)
     h = tmr.tmr_create(N, M, J, dg, dop, opt, stream=stream.cuda_stream)
     sched = tmr.tmr_schedule(h)
@@ -684,7 +699,7 @@ def main():
     worked = status.cpu().numpy() != tmr.TMR_ROW_ZERO  # zero rows (outside a fiber mask) do no work
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
-    flops = solver_flops(N, J, m, its[worked], args.power_iters)
+    flops = solver_flops(N, J, m, its[worked], args.power_iters, args.lanczos)
     achieved = flops / (solver_ms / 1e3) / 1e12
     peak_max = fp32_peak_tflops(n_sm, 2070.0)
     # DRAM bytes of the solver, from one ncu capture of the current kernel
@@ -733,7 +748,7 @@ def main():
     if not args.no_sweep and args.iters > 10:
         ref_frac = float(np.mean(fid >= 0.99))
         tried = []
-        for pits in sorted({args.power_iters, 50, 30}, reverse=True):
+        for pits in sorted({args.power_iters} | ({12, 8} if args.lanczos else {50, 30}), reverse=True):
             if pits > args.power_iters:
                 continue
             hp = h if pits == args.power_iters else tmr.tmr_create(
@@ -766,7 +781,7 @@ def main():
         if tried:
             to099 = dict(max(tried, key=lambda r: r["value"]))
             to099["criterion"] = ("mean >= 0.99 and rows >= 0.99 within 0.5 % of the configured budget's; "
-                                  "fastest passing (power, L-BFGS) pair")
+                                  "fastest passing (start steps, L-BFGS) pair")
             to099["passing"] = [{k: r[k] for k in ("power_iters", "iters", "value")} for r in tried]
 
     # ---- end to end through the C ABI with host buffers ----
@@ -790,7 +805,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt, cores, desc = cpu_oracle_sample(W, M, args.iters, args.power_iters,
                                                rows_n=max(1, min(16, os.cpu_count() or 8)), seed=seed,
-                                               keep=keep)
+                                               keep=keep, lanczos=args.lanczos)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
                "seconds": dt}
         # the same sampled rows (oracle-made intensities) through the library with
@@ -820,7 +835,7 @@ def main():
         torch.cuda.empty_cache()
         arms = second_half_arms(tmr, torch, synth, N, M, J, R, m, d, dop, W["photons"], args.phase_iters,
                                 stream, world, args.iters, args.power_iters,
-                                keep=keep if cpu is not None else None)
+                                keep=keep if cpu is not None else None, lanczos=args.lanczos)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -830,6 +845,7 @@ def main():
                 "config": {"workload": W["desc"], "N": N, "M": M, "J": J, "grid": [ny, nx],
                            "R": R, "photons": W["photons"], "init": "spectral", "tol": W["tol"],
                            "precision": args.precision,
+                           "start": f"{args.power_iters} {'Lanczos steps' if args.lanczos else 'power iterations'}",
                            "power_iters": args.power_iters, "iters": args.iters, "m": m,
                            "row_iters_mean": float(its[worked].mean()), "row_iters_max": int(its.max()),
                            "rows_solved": int(worked.sum()),

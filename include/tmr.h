@@ -132,7 +132,7 @@ typedef struct {
     int m;                  /* L-BFGS memory, 1..6 (default 5)                       */
     int init;               /* TMR_INIT_* (default spectral)                         */
     unsigned long long seed;/* Philox key for random/spectral starts (default 0)     */
-    int power_iters;        /* spectral power iterations (default 100)               */
+    int power_iters;        /* spectral start: power iterations, or Lanczos steps (default 100) */
     double clip;            /* spectral intensity clip, <= 0: none (default 2.0)     */
     double tol;             /* early exit when |f_prev - f| / f_prev < tol; 0 = off  */
     int phase_iters;        /* L-BFGS iterations of the phase-offset fit (default 100) */
@@ -167,6 +167,20 @@ typedef struct {
                                defocus fields).  FP32 only; N = 512 with n1 = 8 or 64,
                                or N = 4096 with n1 = 8, 64 or 512 (the strides at which
                                a pass of the register FFT starts); cluster schedules */
+    int lanczos;            /* 0 (default): the spectral start runs power_iters power
+                               iterations.  1: it runs power_iters (1..16) Lanczos
+                               steps instead (the same leading eigenvector in far
+                               fewer operator products; not in the paper): each step
+                               one product with A, w orthogonalised against every
+                               earlier Lanczos vector by two passes of classical
+                               Gram-Schmidt, stop at an invariant subspace
+                               (beta_j <= 1e-6 alpha_0); the start is the Ritz vector
+                               of the largest eigenvalue of the tridiagonal,
+                               signed so that its first coefficient is >= 0.  The
+                               handle holds power_iters N complex64 per resident
+                               CTA (one CTA per row) or cluster, up to 2 per SM.
+                               Applies to TMR_INIT_SPECTRAL and TMR_INIT_LEARNED
+                               (the proposal seeds the first Lanczos vector). */
 } tmr_options;
 
 /* Fill *opt with the defaults above. */
@@ -342,8 +356,8 @@ void tmr_destroy(tmr_handle *h);
  * T_out complex64 [M][N], row_status / row_iters int32 [M] and row_loss
  * float32 [M] (each may be NULL).
  * opt: NULL for the defaults; workspace_limit, use_graph, schedule and tune_cache
- * are ignored (one mask per CTA); opt->precision must be TMR_PREC_FP32 and
- * opt->probe_n1 0 (TMR_ERR_UNSUPPORTED otherwise).
+ * are ignored (one mask per CTA); opt->precision must be TMR_PREC_FP32,
+ * opt->probe_n1 0 and opt->lanczos 0 (TMR_ERR_UNSUPPORTED otherwise).
  * stream: cudaStream_t, NULL for the legacy default stream.
  *
  * Its only scratch (a row work counter and the FFT twiddle table) lives in

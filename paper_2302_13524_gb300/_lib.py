@@ -42,7 +42,7 @@ class tmr_options(ctypes.Structure):
                 ("use_graph", ctypes.c_int), ("workspace_limit", ctypes.c_size_t),
                 ("schedule", ctypes.c_int), ("tune_cache", ctypes.c_char_p),
                 ("wait_spins", ctypes.c_longlong), ("withhold_release", ctypes.c_int),
-                ("probe_n1", ctypes.c_int)]
+                ("probe_n1", ctypes.c_int), ("lanczos", ctypes.c_int)]
 
 
 class tmr_defocus_op(ctypes.Structure):
@@ -156,7 +156,10 @@ def _ptr(x, dtype=None, count=None, name="array"):
 def tmr_default_options(**overrides) -> tmr_options:
     o = tmr_options()
     lib.tmr_default_options(ctypes.byref(o))
+    names = {f for f, _ in tmr_options._fields_}
     for k, v in overrides.items():
+        if k not in names:  # ctypes would keep a misspelled option as a plain attribute
+            raise TypeError(f"unknown option {k!r}")
         if k == "init" and isinstance(v, str):
             v = INIT[v]
         if k == "precision" and isinstance(v, str):

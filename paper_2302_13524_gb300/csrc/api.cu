@@ -101,6 +101,9 @@ struct tmr_handle {
     // L-BFGS pair workspace of the one-CTA-per-row schedule (pair_ctas regions)
     float2 *pairs = nullptr;
     int pair_ctas = 0;
+    // Lanczos vectors of the spectral start (krylov_units regions of power_iters N)
+    float2 *krylov = nullptr;
+    int krylov_units = 0;
     // transform table of the full-length Bluestein schedule (2048 < N <= 2731)
     float2 *tw_alt = nullptr;
     // what the autotuner timed when this handle was made (none: given or cached)
@@ -419,7 +422,8 @@ void tmr_destroy(tmr_handle *h)
     else cudaDeviceSynchronize();
     void *ptrs[] = {h->masks, h->tw, h->H, h->Zd, h->phi, h->pf_ws, h->pf_loss, h->wts, h->queue,
                     h->pf_sync, h->pf_err, h->pf_iters, h->status_scratch, h->iters_scratch,
-                    h->loss_scratch, h->Tcand, h->wins, h->y16, h->ysc, h->pairs, h->tw_alt, h->incident};
+                    h->loss_scratch, h->Tcand, h->wins, h->y16, h->ysc, h->pairs, h->tw_alt, h->incident,
+                    h->krylov};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &b : h->stage)
@@ -443,6 +447,9 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     if (o.m < 1 || o.m > kMaxMem) return fail(TMR_ERR_INVALID_ARG, "opt.m must be in 1..6");
     if (o.init < TMR_INIT_RANDOM || o.init > TMR_INIT_LEARNED) return fail(TMR_ERR_INVALID_ARG, "opt.init");
     if (o.power_iters < 0 || o.phase_iters < 0 || o.tol < 0) return fail(TMR_ERR_INVALID_ARG, "negative option");
+    if (o.lanczos != 0 && o.lanczos != 1) return fail(TMR_ERR_INVALID_ARG, "opt.lanczos must be 0 or 1");
+    if (o.lanczos && o.power_iters > kMaxLanczos)
+        return fail(TMR_ERR_INVALID_ARG, "opt.power_iters (Lanczos steps) must be at most 16 with opt.lanczos");
     if (o.wait_spins < 1 || o.wait_spins > (1LL << 40))
         return fail(TMR_ERR_INVALID_ARG, "opt.wait_spins must be in 1..2^40");
     if (o.precision != TMR_PREC_FP32 && o.precision != TMR_PREC_MIXED)
@@ -647,6 +654,22 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
         }
         h->G = G;
     }
+    // Lanczos vectors of the spectral start: one region per resident CTA of the
+    // one-CTA-per-row schedule, else per cluster (launches are capped at 2 per SM)
+    if (o.lanczos && o.power_iters > 0 && h->G > 0 &&
+        (o.init == TMR_INIT_SPECTRAL || o.init == TMR_INIT_LEARNED)) {
+        int nsm = 0;
+        TMR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "attr");
+        int units = h->G == kRowSchedule ? h->pair_ctas : 2 * nsm;
+        if (units > M) units = M > 0 ? M : 1;
+        const size_t bytes = sizeof(float2) * (size_t)units * o.power_iters * N;
+        if (o.workspace_limit && h->held + bytes > o.workspace_limit) {
+            tmr_destroy(h);
+            return fail(TMR_ERR_OOM, "Lanczos workspace exceeds workspace_limit");
+        }
+        TRY(halloc(h, (void **)&h->krylov, bytes, "Lanczos vectors"));
+        h->krylov_units = units;
+    }
 #undef TRY
     *out = h;
     return TMR_OK;
@@ -806,6 +829,9 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
     p.queue = h->queue;
     p.pairs = h->pairs;
     p.pair_ctas = h->pair_ctas;
+    p.lanczos = h->opt.lanczos;
+    p.krylov = h->krylov;
+    p.krylov_units = h->krylov_units;
     p.Nd = 0;
     p.M = h->M;
     p.N = h->N;

@@ -88,6 +88,9 @@ struct SolverParams {
     unsigned *queue;      // row work counter, zeroed before the launch
     float2 *pairs;        // one-CTA-per-row schedule: L-BFGS pairs, pair_ctas regions of
     int pair_ctas;        //   2 (m + 1) N float2 each (global memory), else unused
+    int lanczos;          // spectral start by power_iters Lanczos steps (else the power iteration)
+    float2 *krylov;       // Lanczos vectors: krylov_units regions of power_iters N float2, one per
+    int krylov_units;     //   CTA (one CTA per row) or cluster; launches use at most that many
     int N, Nd, M, J, iters, m, init, power_iters;
     int prec;             // TMR_PREC_FP32 or TMR_PREC_MIXED
     unsigned long long seed;
@@ -99,6 +102,9 @@ struct SolverParams {
 // per thread, FP32, N = 512 .. 2048 with J N / 16 <= 512, L-BFGS pairs in the
 // global workspace p.pairs (solver_row.cuh).
 constexpr int kRowSchedule = 16;
+// Lanczos steps of the spectral start at most: the 2 k values of a
+// Gram-Schmidt reduction fit one warp
+constexpr int kMaxLanczos = 16;
 // G = kBlueFullSchedule (32): for 2048 < N <= 2731, one mask per CTA with the
 // full-length Bluestein plan (L = 8192) and its own transform table.
 constexpr int kBlueFullSchedule = 32;

@@ -1,0 +1,240 @@
+// lanczos.cuh -- the spectral start's leading eigenvector by the Lanczos
+// method, shared by the per-row solvers.
+//
+// The spectral start wants the leading eigenvector of
+// A = Q^H diag(tau) Q / (J N) (tau = min(y / mean y, clip)).  The power
+// iteration needs about a hundred products with A on the mode-model rows; k
+// Lanczos steps (k <= 16) reach the same vector in k products: from
+// v_0 = t / ||t||, step j forms w = A v_j and orthogonalises it against every
+// v_0 .. v_j by two passes of classical Gram-Schmidt (coefficients
+// h_l = <v_l, w>); alpha_j is the real part of v_j's two coefficients,
+// beta_j = ||w||, and v_{j+1} = w / beta_j, until j = k - 1 or
+// beta_j <= 1e-6 alpha_0 (an invariant subspace).  The start is
+// t = sum_l s_l v_l with s the eigenvector of the largest eigenvalue of the
+// tridiagonal T (alpha on the diagonal, beta beside it), signed so that
+// s_0 >= 0.  The Lanczos vectors live in a global workspace region of the CTA
+// (or cluster); each thread reads back only the elements it wrote.
+#pragma once
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace tmr {
+
+// Eigenvalues of T below x (Sturm sequence of the LDL^T pivots).
+static __device__ __forceinline__ int sturm_below(const float *a, const float *b, int n, float x)
+{
+    int c = 0;
+    float d = 1.f;
+    for (int i = 0; i < n; i++) {
+        d = (a[i] - x) - (i > 0 ? b[i - 1] * b[i - 1] / d : 0.f);
+        if (d == 0.f) d = -1e-30f;
+        c += d < 0.f;
+    }
+    return c;
+}
+
+// s <- unit eigenvector of the largest eigenvalue of the symmetric tridiagonal
+// T (a[0..n) diagonal, b[i] = T[i][i+1]), s[0] >= 0.  Called by all 32 lanes
+// of one warp: the eigenvalue by multisection (each lane counts the
+// eigenvalues below one of 32 points of the Gershgorin interval, six rounds),
+// then two steps of inverse iteration with (T - lambda I) factored by Gaussian
+// elimination with partial pivoting on lane 0.
+static __device__ void tridiag_top_eigvec(const float *a, const float *b, int n, float *s)
+{
+    const int lane = threadIdx.x & 31;
+    if (n == 1) {
+        if (lane == 0) s[0] = 1.f;
+        __syncwarp();
+        return;
+    }
+    float lo = 3.4e38f, hi = -3.4e38f, scale = 0.f;
+    for (int i = 0; i < n; i++) {
+        const float r = (i > 0 ? fabsf(b[i - 1]) : 0.f) + (i < n - 1 ? fabsf(b[i]) : 0.f);
+        lo = fminf(lo, a[i] - r);
+        hi = fmaxf(hi, a[i] + r);
+        scale = fmaxf(scale, fabsf(a[i]) + r);
+    }
+    for (int round = 0; round < 6; round++) {
+        const float w = (hi - lo) / 33.f;
+        const float x = lo + w * (float)(lane + 1);
+        // lambda_max >= x exactly when fewer than n eigenvalues lie below x
+        const unsigned above = __ballot_sync(0xffffffffu, sturm_below(a, b, n, x) <= n - 1);
+        const int last = above ? 31 - __clz(above) : -1;  // the highest point still below lambda_max
+        const float nlo = last >= 0 ? lo + w * (float)(last + 1) : lo;
+        const float nhi = last < 31 ? lo + w * (float)(last + 2) : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    if (lane == 0) {
+        const float lam = 0.5f * (lo + hi), tiny = 1e-7f * (scale > 0.f ? scale : 1.f);
+        float x[kMaxLanczos], d[kMaxLanczos], du[kMaxLanczos], dl[kMaxLanczos], du2[kMaxLanczos];
+        for (int i = 0; i < n; i++) x[i] = 1.f;
+        for (int step = 0; step < 2; step++) {
+            for (int i = 0; i < n; i++) {
+                d[i] = a[i] - lam;
+                du[i] = i < n - 1 ? b[i] : 0.f;
+                dl[i] = i < n - 1 ? b[i] : 0.f;
+                du2[i] = 0.f;
+            }
+            // eliminate below the diagonal; a row swap brings the fill-in du2
+            for (int i = 0; i < n - 1; i++) {
+                if (fabsf(d[i]) >= fabsf(dl[i])) {
+                    if (d[i] == 0.f) d[i] = tiny;
+                    const float f = dl[i] / d[i];
+                    d[i + 1] -= f * du[i];
+                    x[i + 1] -= f * x[i];
+                } else {
+                    const float f = d[i] / dl[i];
+                    d[i] = dl[i];
+                    const float t = d[i + 1];
+                    d[i + 1] = du[i] - f * t;
+                    if (i < n - 2) {
+                        du2[i] = du[i + 1];
+                        du[i + 1] = -f * du[i + 1];
+                    }
+                    du[i] = t;
+                    const float r = x[i];
+                    x[i] = x[i + 1];
+                    x[i + 1] = r - f * x[i + 1];
+                }
+            }
+            if (d[n - 1] == 0.f) d[n - 1] = tiny;
+            x[n - 1] /= d[n - 1];
+            x[n - 2] = (x[n - 2] - du[n - 2] * x[n - 1]) / d[n - 2];
+            for (int i = n - 3; i >= 0; i--) x[i] = (x[i] - du[i] * x[i + 1] - du2[i] * x[i + 2]) / d[i];
+            float nrm = 0.f;
+            for (int i = 0; i < n; i++) nrm = fmaf(x[i], x[i], nrm);
+            const float inv = nrm > 0.f && isfinite(nrm) ? rsqrtf(nrm) : 0.f;
+            for (int i = 0; i < n; i++) x[i] *= inv;
+        }
+        const float sg = x[0] < 0.f ? -1.f : 1.f;
+        for (int i = 0; i < n; i++) s[i] = sg * x[i];
+    }
+    __syncwarp();
+}
+
+// The Lanczos start on this CTA's nloc elements (thread-strided by blockDim.x).
+//   ts   in: the seed vector; out: the Ritz vector (unit norm)
+//   gs   scratch, nloc elements
+//   V    Lanczos vectors: vector l's element i at V[l vs + i] (global)
+//   red  the row's reduction results (reduce writes its sums there)
+//   lz   48 floats of shared scratch (alpha, beta, s); all threads call.
+//   applyA()      gs <- A ts on the whole row (synchronises before and after)
+//   reduce(v, n)  sums v[0..n) over the row into red[0..n), then synchronises
+template <class ApplyA, class Reduce>
+__device__ void lanczos_start(int k, int nloc, float2 *ts, float2 *gs, float2 *V, size_t vs, const float *red,
+                              float *lz, ApplyA &&applyA, Reduce &&reduce)
+{
+    const int tid = threadIdx.x, BT = blockDim.x;
+    float *la = lz, *lb = lz + kMaxLanczos, *ls = lz + 2 * kMaxLanczos;
+    {
+        float pv[32] = {0.f};
+        for (int i = tid; i < nloc; i += BT) pv[0] += cabs2(ts[i]);
+        reduce(pv, 1);
+        const float nr = red[0];
+        const float inv = nr > 0.f ? rsqrtf(nr) : 0.f;
+        for (int i = tid; i < nloc; i += BT) {
+            const float2 v = cscale(ts[i], inv);
+            ts[i] = v;
+            V[i] = v;
+        }
+    }
+    int kk = k;
+    float alpha0 = 0.f;
+    for (int j = 0; j < k; j++) {
+        applyA();
+        // pass 1: h_l = <v_l, w>
+        float pv[32];
+#pragma unroll
+        for (int q = 0; q < 32; q++) pv[q] = 0.f;
+        for (int i = tid; i < nloc; i += BT) {
+            const float2 w = gs[i];
+#pragma unroll
+            for (int l = 0; l < kMaxLanczos; l++) {
+                if (l <= j) {
+                    const float2 v = V[(size_t)l * vs + i];
+                    pv[2 * l] = fmaf(v.x, w.x, fmaf(v.y, w.y, pv[2 * l]));
+                    pv[2 * l + 1] = fmaf(v.x, w.y, fmaf(-v.y, w.x, pv[2 * l + 1]));
+                }
+            }
+        }
+        reduce(pv, 2 * (j + 1));
+        const float a1 = red[2 * j];
+        // w <- w - sum h_l v_l, and pass 2: h'_l = <v_l, w>
+#pragma unroll
+        for (int q = 0; q < 32; q++) pv[q] = 0.f;
+        for (int i = tid; i < nloc; i += BT) {
+            float2 w = gs[i];
+#pragma unroll
+            for (int l = 0; l < kMaxLanczos; l++) {
+                if (l <= j) {
+                    const float2 v = V[(size_t)l * vs + i];
+                    const float hr = red[2 * l], hi = red[2 * l + 1];
+                    w.x -= hr * v.x - hi * v.y;
+                    w.y -= hr * v.y + hi * v.x;
+                }
+            }
+            gs[i] = w;
+#pragma unroll
+            for (int l = 0; l < kMaxLanczos; l++) {
+                if (l <= j) {
+                    const float2 v = V[(size_t)l * vs + i];  // again (L1): fewer live registers
+                    pv[2 * l] = fmaf(v.x, w.x, fmaf(v.y, w.y, pv[2 * l]));
+                    pv[2 * l + 1] = fmaf(v.x, w.y, fmaf(-v.y, w.x, pv[2 * l + 1]));
+                }
+            }
+        }
+        reduce(pv, 2 * (j + 1));
+        const float alpha = a1 + red[2 * j];
+        if (j == 0) alpha0 = alpha;
+        // w <- w - sum h'_l v_l and beta = ||w||
+#pragma unroll
+        for (int q = 0; q < 32; q++) pv[q] = 0.f;
+        for (int i = tid; i < nloc; i += BT) {
+            float2 w = gs[i];
+#pragma unroll
+            for (int l = 0; l < kMaxLanczos; l++) {
+                if (l <= j) {
+                    const float2 v = V[(size_t)l * vs + i];
+                    const float hr = red[2 * l], hi = red[2 * l + 1];
+                    w.x -= hr * v.x - hi * v.y;
+                    w.y -= hr * v.y + hi * v.x;
+                }
+            }
+            gs[i] = w;
+            pv[0] = fmaf(w.x, w.x, fmaf(w.y, w.y, pv[0]));
+        }
+        reduce(pv, 1);
+        const float beta = sqrtf(red[0]);
+        if (tid == 0) {
+            la[j] = alpha;
+            lb[j] = beta;
+        }
+        if (j == k - 1 || !(beta > 1e-6f * alpha0)) {
+            kk = j + 1;
+            break;
+        }
+        const float inv = 1.f / beta;
+        for (int i = tid; i < nloc; i += BT) {
+            const float2 v = cscale(gs[i], inv);
+            ts[i] = v;
+            V[(size_t)(j + 1) * vs + i] = v;
+        }
+    }
+    __syncthreads();
+    if (tid < 32) tridiag_top_eigvec(la, lb, kk, ls);
+    __syncthreads();
+    for (int i = tid; i < nloc; i += BT) {
+        float2 acc = make_float2(0.f, 0.f);
+        for (int l = 0; l < kk; l++) {
+            const float2 v = V[(size_t)l * vs + i];
+            acc.x = fmaf(ls[l], v.x, acc.x);
+            acc.y = fmaf(ls[l], v.y, acc.y);
+        }
+        ts[i] = acc;
+    }
+    __syncthreads();
+}
+
+}  // namespace tmr

@@ -96,6 +96,9 @@ extern "C" tmr_status tmr_retrieve_rows_static(int N, int M, int J, const void *
     if (o.m < 1 || o.m > tmr::kMaxMem) return fail(TMR_ERR_INVALID_ARG, "opt.m must be in 1..6");
     if (o.init < TMR_INIT_RANDOM || o.init > TMR_INIT_SPECTRAL || o.power_iters < 0 || o.tol < 0)
         return fail(TMR_ERR_INVALID_ARG, "bad option");
+    if (o.lanczos)
+        return fail(TMR_ERR_UNSUPPORTED, "the static entry point runs the power iteration (opt.lanczos = 0): "
+                                         "the Lanczos vectors need a workspace");
     if (o.precision != TMR_PREC_FP32)
         return fail(TMR_ERR_UNSUPPORTED, "the static entry point runs the FP32 solver only (opt.precision)");
     if (o.probe_n1 != 0)

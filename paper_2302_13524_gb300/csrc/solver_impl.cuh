@@ -51,6 +51,7 @@
 #include "common.cuh"
 #include "fft.cuh"
 #include "internal.h"
+#include "lanczos.cuh"
 #include "xform.cuh"
 
 namespace cg = cooperative_groups;
@@ -62,6 +63,8 @@ enum { INIT_RANDOM = 0, INIT_BP = 1, INIT_SPECTRAL = 2 };
 
 constexpr int kSlots = kMaxMem + 1;  // m+1 slots: the new pair never overwrites a live one
 constexpr int kParts = 32;           // values per reduction: one per lane of a warp
+// the Lanczos start keeps alpha, beta and s in Gram::SY, unused before the first pair
+static_assert(kSlots * kSlots >= 3 * kMaxLanczos, "Lanczos scratch in Gram::SY");
 static_assert(4 * kSlots + 3 <= kParts, "reduction width");
 // layout of the per-iteration dot products: 4 per age k (s_k.y, y_k.y, s_k.g,
 // y_k.g with the new y and g), then these three
@@ -725,7 +728,28 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
                         if (P.clip > 0.f && tv > P.clip) tv = P.clip;
                         tau[e] = tv;
                     }
-                    for (int it = 0; it < P.power_iters; it++) {
+                    if (P.lanczos) {
+                        auto applyA = [&]() {
+                            __syncthreads();
+                            push_slice_to_X(ts);
+                            cluster.sync();
+                            float2 x[E];
+                            load_X(x);
+                            __syncthreads();  // X is read before the FFT reuses it
+                            xf.fwd(x, buf, tws, ttid);
+#pragma unroll
+                            for (int e = 0; e < E; e++) x[e] = cscale(x[e], tau[e]);
+                            xf.adj(x, buf, tws, ttid);
+                            push_to_owners(x);
+                            cluster.sync();
+                            for (int i = tid; i < nmine; i += BT) gs[i] = slice_sum(i, 1.f / JN);
+                            __syncthreads();
+                        };
+                        float2 *V = P.krylov + (size_t)(blockIdx.x / JC) * P.power_iters * N + lo;
+                        lanczos_start(P.power_iters, nmine, ts, gs, V, (size_t)N, Gm.red, &Gm.SY[0][0], applyA,
+                                      cluster_sum);
+                    }
+                    for (int it = 0; it < (P.lanczos ? 0 : P.power_iters); it++) {
                         // t <- A t, A = Q^H diag(tau) Q / (J N); the norm is restored
                         // every 8th step and at the end (only the direction matters
                         // to the power iteration, and |A| <= clip bounds the growth)
@@ -1022,6 +1046,7 @@ cudaError_t launch_solver_t(const SolverParams &p, cudaStream_t s, int *clusters
     if (e != cudaSuccess) return e;
     if (maxc < 1) return cudaErrorInvalidConfiguration;
     int nc = maxc < p.M ? maxc : p.M;
+    if (p.lanczos && p.init == INIT_SPECTRAL && nc > p.krylov_units) nc = p.krylov_units;  // one region each
     if (nc < 1) nc = 1;
     cfg.gridDim = dim3(nc * JC);
     if (clusters_out) *clusters_out = nc;

@@ -237,7 +237,29 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
                 }
                 if (!seeded)
                     for (int i = tid; i < N; i += BT) ts[i] = philox_cnormal(P.seed, (uint32_t)row, (uint32_t)i);
-                if (P.init == INIT_SPECTRAL) {
+                if (P.init == INIT_SPECTRAL && P.lanczos) {
+                    const float mean = sumy / (float)K;
+                    auto applyA = [&]() {
+                        __syncthreads();
+                        float2 x[E];
+                        load_team(ts, x);
+                        fwd(x);
+#pragma unroll
+                        for (int e = 0; e < E; e++) {
+                            float tv = yt[ttid + e * NT] / mean;
+                            if (P.clip > 0.f && tv > P.clip) tv = P.clip;
+                            x[e] = cscale(x[e], tv);
+                        }
+                        adj(x);
+                        park(x);
+                        __syncthreads();
+                        for (int i = tid; i < N; i += BT) gs[i] = team_sum(i, 1.f / JN);
+                        __syncthreads();
+                    };
+                    float2 *V = P.krylov + (size_t)blockIdx.x * P.power_iters * N;
+                    lanczos_start(P.power_iters, N, ts, gs, V, (size_t)N, Gm.red, &Gm.SY[0][0], applyA,
+                                  block_reduce);
+                } else if (P.init == INIT_SPECTRAL) {
                     const float mean = sumy / (float)K;
                     for (int it = 0; it < P.power_iters; it++) {
                         // t <- A t, A = Q^H diag(tau) Q / (J N), tau = min(y / mean, clip);
@@ -495,6 +517,7 @@ cudaError_t launch_solver_row_t(const SolverParams &p, cudaStream_t s, int *ctas
     long long grid = (long long)occ * nsm;
     if (grid > p.M) grid = p.M;
     if (grid > p.pair_ctas) grid = p.pair_ctas;  // one pair region per CTA
+    if (p.lanczos && p.init == INIT_SPECTRAL && grid > p.krylov_units) grid = p.krylov_units;
     if (grid < 1) grid = 1;
     if (ctas_out) *ctas_out = (int)grid;
     k_solver_row<N><<<(int)grid, BT, sm, s>>>(p);
