@@ -662,7 +662,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
         TMR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "attr");
         int units = h->G == kRowSchedule ? h->pair_ctas : 2 * nsm;
         if (units > M) units = M > 0 ? M : 1;
-        const size_t bytes = sizeof(float2) * (size_t)units * o.power_iters * N;
+        const size_t bytes = sizeof(float2) * (size_t)units * lanczos_region(N, o.power_iters);
         if (o.workspace_limit && h->held + bytes > o.workspace_limit) {
             tmr_destroy(h);
             return fail(TMR_ERR_OOM, "Lanczos workspace exceeds workspace_limit");

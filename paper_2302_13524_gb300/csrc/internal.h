@@ -89,8 +89,8 @@ struct SolverParams {
     float2 *pairs;        // one-CTA-per-row schedule: L-BFGS pairs, pair_ctas regions of
     int pair_ctas;        //   2 (m + 1) N float2 each (global memory), else unused
     int lanczos;          // spectral start by power_iters Lanczos steps (else the power iteration)
-    float2 *krylov;       // Lanczos vectors: krylov_units regions of power_iters N float2, one per
-    int krylov_units;     //   CTA (one CTA per row) or cluster; launches use at most that many
+    float2 *krylov;       // Lanczos vectors: krylov_units regions of lanczos_region(N, power_iters)
+    int krylov_units;     //   float2, one per CTA (one CTA per row) or cluster; launches use at most that many
     int N, Nd, M, J, iters, m, init, power_iters;
     int prec;             // TMR_PREC_FP32 or TMR_PREC_MIXED
     unsigned long long seed;
@@ -105,6 +105,12 @@ constexpr int kRowSchedule = 16;
 // Lanczos steps of the spectral start at most: the 2 k values of a
 // Gram-Schmidt reduction fit one warp
 constexpr int kMaxLanczos = 16;
+// float2 per Lanczos workspace region (one CTA, or one cluster of up to 8
+// CTAs): k vectors of length N, then one kMaxLanczos^2 Gram matrix per CTA
+__host__ __device__ inline size_t lanczos_region(int N, int k)
+{
+    return (size_t)k * N + (size_t)8 * kMaxLanczos * kMaxLanczos;
+}
 // G = kBlueFullSchedule (32): for 2048 < N <= 2731, one mask per CTA with the
 // full-length Bluestein plan (L = 8192) and its own transform table.
 constexpr int kBlueFullSchedule = 32;

@@ -118,15 +118,33 @@ static __device__ void tridiag_top_eigvec(const float *a, const float *b, int n,
 //   ts   in: the seed vector; out: the Ritz vector (unit norm)
 //   gs   scratch, nloc elements
 //   V    Lanczos vectors: vector l's element i at V[l vs + i] (global)
+//   Gw   kMaxLanczos^2 complex64 of global scratch: the Gram matrix of the
+//        stored Lanczos vectors (row l at Gw + l kMaxLanczos)
 //   red  the row's reduction results (reduce writes its sums there)
-//   lz   48 floats of shared scratch (alpha, beta, s); all threads call.
+//   lz   48 floats of shared scratch (alpha, beta, s); hc 32 floats (h, then c)
 //   applyA()      gs <- A ts on the whole row (synchronises before and after)
 //   reduce(v, n)  sums v[0..n) over the row into red[0..n), then synchronises
+// All threads call.
+//
+// The second Gram-Schmidt pass is taken from the Gram matrix G = V^H V of the
+// stored vectors instead of a second sweep over them: with h = V^H w the
+// first pass's coefficients, the second pass's would be
+// V^H (w - V h) = h - G h, so w is updated once by c = h + (h - G h), which
+// with G_ll = 1 is c_l = h_l - sum_{m != l} G_lm h_m.  G's new column,
+// <v_l, v_j>, comes from the same sweep that forms h (each v_l is loaded once
+// for both dots), so each step reads the stored vectors twice (the h sweep
+// and the update) instead of four times.  In exact arithmetic this is the
+// two-pass update; in FP32 it keeps the Ritz vector as close to the FP64
+// two-pass result as the explicit second pass does (about 1e-6 relative on
+// the mode-model rows), where one pass alone drifts by up to 1e-2 at k = 16.
+// (Forming G's column in the update sweep instead, with the v_l held in
+// registers, saves a reduction but spills registers of the L-BFGS loop that
+// shares the kernel, which then runs 16 % slower.)
 template <class ApplyA, class Reduce>
-__device__ void lanczos_start(int k, int nloc, float2 *ts, float2 *gs, float2 *V, size_t vs, const float *red,
-                              float *lz, ApplyA &&applyA, Reduce &&reduce)
+__device__ void lanczos_start(int k, int nloc, float2 *ts, float2 *gs, float2 *V, size_t vs, float2 *Gw,
+                              const float *red, float *lz, float *hc, ApplyA &&applyA, Reduce &&reduce)
 {
-    const int tid = threadIdx.x, BT = blockDim.x;
+    const int tid = threadIdx.x, BT = blockDim.x, lane = tid & 31;
     float *la = lz, *lb = lz + kMaxLanczos, *ls = lz + 2 * kMaxLanczos;
     {
         float pv[32] = {0.f};
@@ -144,62 +162,74 @@ __device__ void lanczos_start(int k, int nloc, float2 *ts, float2 *gs, float2 *V
     float alpha0 = 0.f;
     for (int j = 0; j < k; j++) {
         applyA();
-        // pass 1: h_l = <v_l, w>
-        float pv[32];
+        float pv[32], pg[32];
 #pragma unroll
-        for (int q = 0; q < 32; q++) pv[q] = 0.f;
+        for (int q = 0; q < 32; q++) pv[q] = pg[q] = 0.f;
+#pragma unroll 2
         for (int i = tid; i < nloc; i += BT) {
-            const float2 w = gs[i];
+            const float2 w = gs[i], vj = ts[i];
 #pragma unroll
             for (int l = 0; l < kMaxLanczos; l++) {
                 if (l <= j) {
                     const float2 v = V[(size_t)l * vs + i];
                     pv[2 * l] = fmaf(v.x, w.x, fmaf(v.y, w.y, pv[2 * l]));
                     pv[2 * l + 1] = fmaf(v.x, w.y, fmaf(-v.y, w.x, pv[2 * l + 1]));
+                    if (l < j) {
+                        pg[2 * l] = fmaf(v.x, vj.x, fmaf(v.y, vj.y, pg[2 * l]));
+                        pg[2 * l + 1] = fmaf(v.x, vj.y, fmaf(-v.y, vj.x, pg[2 * l + 1]));
+                    }
                 }
             }
         }
         reduce(pv, 2 * (j + 1));
-        const float a1 = red[2 * j];
-        // w <- w - sum h_l v_l, and pass 2: h'_l = <v_l, w>
+        if (tid < 2 * (j + 1)) hc[tid] = red[tid];
+        if (j > 0) {
+            reduce(pg, 2 * j);
+            if (tid < 32) {
+                if (lane < j) Gw[lane * kMaxLanczos + j] = make_float2(red[2 * lane], red[2 * lane + 1]);
+                if (lane == j) {
 #pragma unroll
-        for (int q = 0; q < 32; q++) pv[q] = 0.f;
-        for (int i = tid; i < nloc; i += BT) {
-            float2 w = gs[i];
-#pragma unroll
-            for (int l = 0; l < kMaxLanczos; l++) {
-                if (l <= j) {
-                    const float2 v = V[(size_t)l * vs + i];
-                    const float hr = red[2 * l], hi = red[2 * l + 1];
-                    w.x -= hr * v.x - hi * v.y;
-                    w.y -= hr * v.y + hi * v.x;
-                }
-            }
-            gs[i] = w;
-#pragma unroll
-            for (int l = 0; l < kMaxLanczos; l++) {
-                if (l <= j) {
-                    const float2 v = V[(size_t)l * vs + i];  // again (L1): fewer live registers
-                    pv[2 * l] = fmaf(v.x, w.x, fmaf(v.y, w.y, pv[2 * l]));
-                    pv[2 * l + 1] = fmaf(v.x, w.y, fmaf(-v.y, w.x, pv[2 * l + 1]));
+                    for (int l = 0; l < kMaxLanczos; l++)
+                        if (l < j) Gw[j * kMaxLanczos + l] = make_float2(red[2 * l], -red[2 * l + 1]);
                 }
             }
         }
-        reduce(pv, 2 * (j + 1));
-        const float alpha = a1 + red[2 * j];
+        __syncwarp();
+        if (tid < 32) {
+            float2 c = make_float2(0.f, 0.f);
+            if (lane <= j) {
+                c = make_float2(hc[2 * lane], hc[2 * lane + 1]);
+#pragma unroll
+                for (int m = 0; m < kMaxLanczos; m++) {
+                    if (m <= j && m != lane) {
+                        const float2 g = Gw[lane * kMaxLanczos + m], hm = make_float2(hc[2 * m], hc[2 * m + 1]);
+                        c.x -= g.x * hm.x - g.y * hm.y;
+                        c.y -= g.x * hm.y + g.y * hm.x;
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane <= j) {
+                hc[2 * lane] = c.x;
+                hc[2 * lane + 1] = c.y;
+            }
+            if (lane == j) la[j] = c.x;
+        }
+        __syncthreads();
+        const float alpha = la[j];
         if (j == 0) alpha0 = alpha;
-        // w <- w - sum h'_l v_l and beta = ||w||
 #pragma unroll
         for (int q = 0; q < 32; q++) pv[q] = 0.f;
+#pragma unroll 2
         for (int i = tid; i < nloc; i += BT) {
             float2 w = gs[i];
 #pragma unroll
             for (int l = 0; l < kMaxLanczos; l++) {
                 if (l <= j) {
                     const float2 v = V[(size_t)l * vs + i];
-                    const float hr = red[2 * l], hi = red[2 * l + 1];
-                    w.x -= hr * v.x - hi * v.y;
-                    w.y -= hr * v.y + hi * v.x;
+                    const float cr = hc[2 * l], ci = hc[2 * l + 1];
+                    w.x -= cr * v.x - ci * v.y;
+                    w.y -= cr * v.y + ci * v.x;
                 }
             }
             gs[i] = w;
@@ -207,10 +237,7 @@ __device__ void lanczos_start(int k, int nloc, float2 *ts, float2 *gs, float2 *V
         }
         reduce(pv, 1);
         const float beta = sqrtf(red[0]);
-        if (tid == 0) {
-            la[j] = alpha;
-            lb[j] = beta;
-        }
+        if (tid == 0) lb[j] = beta;
         if (j == k - 1 || !(beta > 1e-6f * alpha0)) {
             kk = j + 1;
             break;
@@ -227,10 +254,13 @@ __device__ void lanczos_start(int k, int nloc, float2 *ts, float2 *gs, float2 *V
     __syncthreads();
     for (int i = tid; i < nloc; i += BT) {
         float2 acc = make_float2(0.f, 0.f);
-        for (int l = 0; l < kk; l++) {
-            const float2 v = V[(size_t)l * vs + i];
-            acc.x = fmaf(ls[l], v.x, acc.x);
-            acc.y = fmaf(ls[l], v.y, acc.y);
+#pragma unroll
+        for (int l = 0; l < kMaxLanczos; l++) {
+            if (l < kk) {
+                const float2 v = V[(size_t)l * vs + i];
+                acc.x = fmaf(ls[l], v.x, acc.x);
+                acc.y = fmaf(ls[l], v.y, acc.y);
+            }
         }
         ts[i] = acc;
     }

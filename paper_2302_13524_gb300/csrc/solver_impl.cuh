@@ -64,7 +64,8 @@ enum { INIT_RANDOM = 0, INIT_BP = 1, INIT_SPECTRAL = 2 };
 constexpr int kSlots = kMaxMem + 1;  // m+1 slots: the new pair never overwrites a live one
 constexpr int kParts = 32;           // values per reduction: one per lane of a warp
 // the Lanczos start keeps alpha, beta and s in Gram::SY, unused before the first pair
-static_assert(kSlots * kSlots >= 3 * kMaxLanczos, "Lanczos scratch in Gram::SY");
+static_assert(kSlots * kSlots >= 3 * kMaxLanczos && kSlots * kSlots >= 2 * kMaxLanczos,
+              "Lanczos scratch in Gram::SY and Gram::YY");
 static_assert(4 * kSlots + 3 <= kParts, "reduction width");
 // layout of the per-iteration dot products: 4 per age k (s_k.y, y_k.y, s_k.g,
 // y_k.g with the new y and g), then these three
@@ -583,9 +584,13 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
         float *pb = part + (size_t)sel * JC * kParts;
         sel ^= 1;
         if (nv <= 6) {
-            for (int k = 0; k < nv; k++) {
-                const float t = warp_sum(v[k]);
-                if (lane == 0) red[k * NW + warp] = t;
+            // constant indices only: a runtime index would move v to local memory
+#pragma unroll
+            for (int k = 0; k < 6; k++) {
+                if (k < nv) {
+                    const float t = warp_sum(v[k]);
+                    if (lane == 0) red[k * NW + warp] = t;
+                }
             }
         } else {
             warp_reduce32(v, lane);
@@ -745,9 +750,10 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
                             for (int i = tid; i < nmine; i += BT) gs[i] = slice_sum(i, 1.f / JN);
                             __syncthreads();
                         };
-                        float2 *V = P.krylov + (size_t)(blockIdx.x / JC) * P.power_iters * N + lo;
-                        lanczos_start(P.power_iters, nmine, ts, gs, V, (size_t)N, Gm.red, &Gm.SY[0][0], applyA,
-                                      cluster_sum);
+                        float2 *reg = P.krylov + (size_t)(blockIdx.x / JC) * lanczos_region(N, P.power_iters);
+                        float2 *Gw = reg + (size_t)P.power_iters * N + (size_t)jr * kMaxLanczos * kMaxLanczos;
+                        lanczos_start(P.power_iters, nmine, ts, gs, reg + lo, (size_t)N, Gw, Gm.red, &Gm.SY[0][0],
+                                      &Gm.YY[0][0], applyA, cluster_sum);
                     }
                     for (int it = 0; it < (P.lanczos ? 0 : P.power_iters); it++) {
                         // t <- A t, A = Q^H diag(tau) Q / (J N); the norm is restored

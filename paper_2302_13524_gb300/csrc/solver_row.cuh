@@ -148,9 +148,13 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
     // adds the NW warp sums of value k in warp order into Gm.red[k].
     auto block_reduce = [&](float (&v)[32], int nv) {
         if (nv <= 6) {
-            for (int k = 0; k < nv; k++) {
-                const float t = warp_sum(v[k]);
-                if (lane == 0) red[k * NW + warp] = t;
+            // constant indices only: a runtime index would move v to local memory
+#pragma unroll
+            for (int k = 0; k < 6; k++) {
+                if (k < nv) {
+                    const float t = warp_sum(v[k]);
+                    if (lane == 0) red[k * NW + warp] = t;
+                }
             }
         } else {
             warp_reduce32(v, lane);
@@ -256,9 +260,9 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
                         for (int i = tid; i < N; i += BT) gs[i] = team_sum(i, 1.f / JN);
                         __syncthreads();
                     };
-                    float2 *V = P.krylov + (size_t)blockIdx.x * P.power_iters * N;
-                    lanczos_start(P.power_iters, N, ts, gs, V, (size_t)N, Gm.red, &Gm.SY[0][0], applyA,
-                                  block_reduce);
+                    float2 *V = P.krylov + (size_t)blockIdx.x * lanczos_region(N, P.power_iters);
+                    lanczos_start(P.power_iters, N, ts, gs, V, (size_t)N, V + (size_t)P.power_iters * N, Gm.red,
+                                  &Gm.SY[0][0], &Gm.YY[0][0], applyA, block_reduce);
                 } else if (P.init == INIT_SPECTRAL) {
                     const float mean = sumy / (float)K;
                     for (int it = 0; it < P.power_iters; it++) {
