@@ -473,7 +473,8 @@ def run_jsweep(args):
     """Failed-row fraction against the number of masks J = 3 .. 8 with the
     paper's 2D probing DFT (Sec. 2.2: K the 2D DFT of the 64 x 64 phase
     modes, N = 4096), noiseless data from a mode-model TM (R = 2200) on a
-    64 x 64 output grid, spectral start (100 power iterations) and 200 L-BFGS
+    64 x 64 output grid, the spectral start of --start (16 Lanczos steps by
+    default) and 200 L-BFGS
     iterations; a row fails when its fidelity to the truth is below 0.99.  The
     paper's simulation (Sec. 3) swept M = 3 .. 9 masks on a measured TM; J = 9
     is beyond this library's 8."""
@@ -488,7 +489,7 @@ def run_jsweep(args):
         _, d = synth.mask_phases(J, N, seed=J)
         dg = torch.from_numpy(np.ascontiguousarray(d, dtype=np.complex64)).cuda()
         with tmr.tmr_create(N, M, J, dg, None, dict(probe_n1=n1, init="spectral", power_iters=pits,
-                                                      clip=2.0)) as h:
+                                                      clip=2.0, lanczos=args.lanczos)) as h:
             y = torch.empty((M, J, N), dtype=torch.float32, device="cuda")
             tmr.tmr_forward(h, T, y)
             To = torch.empty((M, N), dtype=torch.complex64, device="cuda")
@@ -506,7 +507,8 @@ def run_jsweep(args):
     line = {"metric": "failed-row fraction vs J (2D probing DFT)", "unit": "fraction", "n_gpus": 1,
             "higher_is_better": False, "data": "synthetic, noiseless",
             "config": {"workload": f"jsweep: N={N} as 64x64 2D DFT (probe_n1={n1}), M={M} (64x64), modes R={R}, "
-                                   f"noiseless, {pits} power + {iters} L-BFGS iterations, J = 3..8",
+                                   f"noiseless, {pits} {'Lanczos' if args.lanczos else 'power'} + {iters} "
+                                   f"L-BFGS iterations, J = 3..8",
                        "dtype": "f32"},
             "value": out[-1]["failed_frac"], "sweep": out}
     print(json.dumps(line))
