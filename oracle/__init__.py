@@ -72,6 +72,8 @@ def lib():
                                dp], c_int),
             "orc_fidelity_rows": ([dp, dp, c_int, c_int, dp], c_int),
             "orc_set_probe_2d": ([c_int, c_int], c_int),
+            "orc_set_cost": ([c_int], c_int),
+            "orc_amp_step": ([dp, dp, dp, ctypes.c_size_t], c_dbl),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -129,6 +131,28 @@ class probe_2d:
 
     def __exit__(self, *a):
         lib().orc_set_probe_2d(0, 0)
+
+
+class amplitude_cost:
+    """Context in which every oracle call uses the amplitude cost
+    f = sum (sqrt(y) - |Qt|)^2 (the Discussion's alternative for Poisson
+    noise) with its gradient 2 Q^H((|z| - a) z / |z|) and its line search
+    (orc_amp_step); outside it the paper's intensity cost (Eq. optTMsmall2)."""
+
+    def __enter__(self):
+        lib().orc_set_cost(1)
+        return self
+
+    def __exit__(self, *a):
+        lib().orc_set_cost(0)
+
+
+def amp_step(z, w, y) -> float:
+    """The amplitude cost's step along a line with fields z + alpha w."""
+    z = _c128(z).ravel()
+    w = _c128(w).ravel()
+    y = _f64(y).ravel()
+    return lib().orc_amp_step(_p(z), _p(w), _p(y), y.size)
 
 
 def forward(T, masks, return_fields: bool = False):

@@ -225,6 +225,22 @@ int orc_adjoint(const double *V, const double *masks, int M, int N, int J, doubl
  *   f(t) = || y - |Q t|^2 ||^2                           (Eq. optTMsmall2)
  *   g    = (df/dt)^H = -4 Q^H diag(Q t)(y - |Q t|^2)      (Eq. derivative)
  * with g packed as df/dRe(t) + i df/dIm(t).  Work: z, rz (K each), sc (N). */
+/* Cost of the per-row problem.  Intensity (Eq. optTMsmall2, the paper's):
+ * f = sum_i (y_i - |z_i|^2)^2, real gradient g = -4 Q^H (z .* r), r = y - |z|^2
+ * (Eq. derivative).  Amplitude (the Discussion's alternative for Poisson noise,
+ * after Yeh et al. 2015), after orc_set_cost(1): f = sum_i (a_i - |z_i|)^2 with
+ * a = sqrt(y), real gradient g = 2 Q^H ((|z| - a) z / |z|), the term taken as 0
+ * where z_i = 0.  (Real gradient: d f / d Re t + i d f / d Im t.)  A
+ * process-wide setting of this test oracle, like the probing DFT's. */
+static int g_cost = 0;
+
+int orc_set_cost(int cost)
+{
+    if (cost != 0 && cost != 1) return -1;
+    g_cost = cost;
+    return 0;
+}
+
 static double loss_grad_row(const cplx *t, const double *y, const cplx *d, int N, int J,
                             const cplx *tw, cplx *g, cplx *z, cplx *rz, cplx *sc)
 {
@@ -232,13 +248,19 @@ static double loss_grad_row(const cplx *t, const double *y, const cplx *d, int N
     apply_Q(t, d, N, J, tw, z, sc);
     double f = 0;
     for (size_t i = 0; i < K; i++) {
-        double r = y[i] - abs2(z[i]);
-        f += r * r;
-        rz[i] = z[i] * r;
+        if (g_cost == 1) {
+            double a = sqrt(y[i] > 0 ? y[i] : 0.0), m = cabs(z[i]);
+            f += (a - m) * (a - m);
+            rz[i] = m > 0 ? z[i] * ((m - a) / m) : 0;
+        } else {
+            double r = y[i] - abs2(z[i]);
+            f += r * r;
+            rz[i] = z[i] * r;
+        }
     }
     if (g) {
         apply_QH(rz, d, N, J, tw, g, sc);
-        for (int n = 0; n < N; n++) g[n] *= -4.0;
+        for (int n = 0; n < N; n++) g[n] *= g_cost == 1 ? 2.0 : -4.0;
     }
     return f;
 }
@@ -600,6 +622,71 @@ double orc_quartic_argmin(const double c[5])
 }
 
 /* The five coefficients of phi(alpha) from r, z, w (length K). */
+/* Line search of the amplitude cost along t + alpha p (fields z + alpha w,
+ * w = Q p): phi(alpha) = sum_i (a_i - |u_i|)^2 with u = z + alpha w, m = |u|.
+ * Half its derivatives: phi'/2 = sum (m - a) Re(conj(u) w) / m and
+ * phi''/2 = sum |w|^2 - a Im(conj(u) w)^2 / m^3 (a term with m = 0 adds |w|^2
+ * to the second and nothing to the first, as in the gradient).  phi is not a
+ * polynomial, so the step is the root of phi' found in two stages:
+ *   bracket: alpha = 1, 2, 4, ... (at most 40 doublings) until phi' >= 0,
+ *     the lower end the last point with phi' < 0 (alpha = 0 at first: p is a
+ *     descent direction); if phi' stays negative, the farthest point tried;
+ *   root: Newton steps from the lower end kept inside the bracket (the
+ *     midpoint when a step would leave it or phi'' <= 0), the bracket shrunk
+ *     by the sign of phi' at every point, until a step is below tol alpha.
+ * The oracle stops at tol = 1e-13 (at most 200 steps). */
+static void amp_derivs(const cplx *z, const cplx *w, const double *y, size_t K, double al, double *d1,
+                       double *d2)
+{
+    double s1 = 0, s2 = 0;
+    for (size_t i = 0; i < K; i++) {
+        double a = sqrt(y[i] > 0 ? y[i] : 0.0);
+        cplx u = z[i] + al * w[i], cw = conj(u) * w[i];
+        double m = cabs(u);
+        s2 += abs2(w[i]);
+        if (m > 0) {
+            s1 += (m - a) * creal(cw) / m;
+            s2 -= a * cimag(cw) * cimag(cw) / (m * m * m);
+        }
+    }
+    *d1 = s1;
+    *d2 = s2;
+}
+
+double orc_amp_step(const double *zr, const double *wr, const double *y, size_t K)
+{
+    const cplx *z = (const cplx *)zr, *w = (const cplx *)wr;
+    double lo = 0, hi = 0, d1lo, d2lo, d1, d2, al = 1;
+    amp_derivs(z, w, y, K, 0.0, &d1lo, &d2lo);
+    int bracketed = 0;
+    for (int k = 0; k <= 40; k++) {
+        amp_derivs(z, w, y, K, al, &d1, &d2);
+        if (!(d1 < 0)) {
+            hi = al;
+            bracketed = 1;
+            break;
+        }
+        lo = al;
+        d1lo = d1;
+        d2lo = d2;
+        al *= 2;
+    }
+    if (!bracketed) return lo;
+    double x = d2lo > 0 ? lo - d1lo / d2lo : NAN;
+    if (!(x > lo && x < hi)) x = 0.5 * (lo + hi);
+    for (int it = 0; it < 200; it++) {
+        amp_derivs(z, w, y, K, x, &d1, &d2);
+        if (d1 == 0) return x;
+        if (d1 < 0) lo = x;
+        else hi = x;
+        double xn = d2 > 0 ? x - d1 / d2 : NAN;
+        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        if (fabs(xn - x) <= 1e-13 * x) return xn;
+        x = xn;
+    }
+    return x;
+}
+
 static void quartic_coeffs(const double *r, const cplx *z, const cplx *w, size_t K, double c[5])
 {
     double s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;
@@ -766,12 +853,17 @@ static void solve_row(const double *y, const cplx *d, int N, int J, const cplx *
             np = 0;
             for (int n = 0; n < N; n++) p[n] = -g[n];
         }
-        /* exact line search along p; z = Q t is left by the last loss evaluation */
-        for (size_t i = 0; i < K; i++) r[i] = y[i] - abs2(z[i]);
+        /* line search along p; z = Q t is left by the last loss evaluation */
         apply_Q(p, d, N, J, tw, w, sc);
-        double c[5];
-        quartic_coeffs(r, z, w, K, c);
-        double alph = orc_quartic_argmin(c);
+        double alph;
+        if (g_cost == 1) {
+            alph = orc_amp_step((const double *)z, (const double *)w, y, K);
+        } else {
+            for (size_t i = 0; i < K; i++) r[i] = y[i] - abs2(z[i]);
+            double c[5];
+            quartic_coeffs(r, z, w, K, c);
+            alph = orc_quartic_argmin(c);
+        }
         if (!(alph != 0) || !isfinite(alph)) {
             status = isfinite(alph) ? ROW_CONVERGED : ROW_NUMERIC;
             break;
@@ -849,8 +941,14 @@ int orc_lbfgs_step(const double *y, const double *masks, int N, int J, const dou
     apply_Q((const cplx *)t, d, N, J, tw, z, sc);
     for (size_t i = 0; i < K; i++) r[i] = y[i] - abs2(z[i]);
     apply_Q(p, d, N, J, tw, w, sc);
-    quartic_coeffs(r, z, w, K, coef_out);
-    double al = orc_quartic_argmin(coef_out);
+    double al;
+    if (g_cost == 1) {  /* no quartic: its coefficients are returned as 0 */
+        for (int k = 0; k < 5; k++) coef_out[k] = 0;
+        al = orc_amp_step((const double *)z, (const double *)w, y, K);
+    } else {
+        quartic_coeffs(r, z, w, K, coef_out);
+        al = orc_quartic_argmin(coef_out);
+    }
     *alpha_out = al;
     for (int n = 0; n < N; n++) ((cplx *)t_out)[n] = ((const cplx *)t)[n] + al * p[n];
     *loss_out = loss_grad_row((const cplx *)t_out, y, d, N, J, tw, (cplx *)g_out, z, rz, sc);
