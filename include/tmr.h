@@ -181,7 +181,21 @@ typedef struct {
                                CTA (one CTA per row) or cluster, up to 2 per SM.
                                Applies to TMR_INIT_SPECTRAL and TMR_INIT_LEARNED
                                (the proposal seeds the first Lanczos vector). */
+    int cost;               /* TMR_COST_INTENSITY (default): Eq. optTMsmall2 with the
+                               exact quartic line search.  TMR_COST_AMPLITUDE: the
+                               Discussion's cost for Poisson noise,
+                               f = sum (sqrt(y) - |Q t|)^2, real gradient
+                               2 Q^H((|z| - sqrt(y)) z / |z|) (0 where z = 0), and a
+                               line search that brackets the first sign change of
+                               f'(t + al p) at al = 1, 2, 4, ... (40 doublings at
+                               most) and finds it by Newton steps kept inside the
+                               bracket (to 1e-6 al, 30 steps at most).  Applies to
+                               tmr_grad and tmr_retrieve (the row loss reported is
+                               this cost); the start and the defocus fit are
+                               unchanged. */
 } tmr_options;
+
+enum { TMR_COST_INTENSITY = 0, TMR_COST_AMPLITUDE = 1 };
 
 /* Fill *opt with the defaults above. */
 void tmr_default_options(tmr_options *opt);

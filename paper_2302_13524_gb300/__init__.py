@@ -6,7 +6,7 @@ C ABI of include/tmr.h); this package is its thin ctypes binding with the same
 function names.  Importing it fails when the library has not been built.
 """
 from ._lib import (  # noqa: F401
-    DEFOCUS_ANGULAR_2X, DEFOCUS_SAME_GRID, INIT, MLP, TMR_INIT_LEARNED, TMR_LOSS_MSE, TMR_LOSS_PHASE, TMR_ERR_CUDA, TMR_ERR_INVALID_ARG, TMR_ERR_NUMERIC, TMR_ERR_OOM, TMR_ERR_TIMEOUT,
+    DEFOCUS_ANGULAR_2X, DEFOCUS_SAME_GRID, TMR_COST_AMPLITUDE, TMR_COST_INTENSITY, INIT, MLP, TMR_INIT_LEARNED, TMR_LOSS_MSE, TMR_LOSS_PHASE, TMR_ERR_CUDA, TMR_ERR_INVALID_ARG, TMR_ERR_NUMERIC, TMR_ERR_OOM, TMR_ERR_TIMEOUT,
     TMR_ERR_UNSUPPORTED, TMR_INIT_BP, TMR_INIT_RANDOM, TMR_INIT_SPECTRAL, TMR_OK,
     TMR_PIX_F32, TMR_PIX_U16, TMR_PREC_FP32, TMR_PREC_MIXED, TMR_ROW_CONVERGED, TMR_ROW_MAXITER, TMR_ROW_NUMERIC, TMR_ROW_ZERO, Handle,
     LIB_PATH, TMRError, header_symbols, lib, tmr_create, tmr_default_options, tmr_defocus_fit,

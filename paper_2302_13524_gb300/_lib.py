@@ -21,6 +21,7 @@ TMR_INIT_RANDOM, TMR_INIT_BP, TMR_INIT_SPECTRAL, TMR_INIT_LEARNED = 0, 1, 2, 3
 TMR_ROW_MAXITER, TMR_ROW_CONVERGED, TMR_ROW_ZERO, TMR_ROW_NUMERIC = 0, 1, 2, 3
 TMR_PREC_FP32 = 0
 TMR_PREC_MIXED = 1
+TMR_COST_INTENSITY, TMR_COST_AMPLITUDE = 0, 1
 TMR_PIX_U16, TMR_PIX_F32 = 0, 1
 TMR_LOSS_MSE, TMR_LOSS_PHASE = 0, 1
 INIT = {"random": TMR_INIT_RANDOM, "bp": TMR_INIT_BP, "spectral": TMR_INIT_SPECTRAL,
@@ -42,7 +43,7 @@ class tmr_options(ctypes.Structure):
                 ("use_graph", ctypes.c_int), ("workspace_limit", ctypes.c_size_t),
                 ("schedule", ctypes.c_int), ("tune_cache", ctypes.c_char_p),
                 ("wait_spins", ctypes.c_longlong), ("withhold_release", ctypes.c_int),
-                ("probe_n1", ctypes.c_int), ("lanczos", ctypes.c_int)]
+                ("probe_n1", ctypes.c_int), ("lanczos", ctypes.c_int), ("cost", ctypes.c_int)]
 
 
 class tmr_defocus_op(ctypes.Structure):
@@ -162,6 +163,8 @@ def tmr_default_options(**overrides) -> tmr_options:
             raise TypeError(f"unknown option {k!r}")
         if k == "init" and isinstance(v, str):
             v = INIT[v]
+        if k == "cost" and isinstance(v, str):
+            v = {"intensity": TMR_COST_INTENSITY, "amplitude": TMR_COST_AMPLITUDE}[v]
         if k == "precision" and isinstance(v, str):
             v = {"fp32": TMR_PREC_FP32, "mixed": TMR_PREC_MIXED}[v]
         if k == "tune_cache" and isinstance(v, str):

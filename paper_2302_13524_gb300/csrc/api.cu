@@ -448,6 +448,8 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     if (o.init < TMR_INIT_RANDOM || o.init > TMR_INIT_LEARNED) return fail(TMR_ERR_INVALID_ARG, "opt.init");
     if (o.power_iters < 0 || o.phase_iters < 0 || o.tol < 0) return fail(TMR_ERR_INVALID_ARG, "negative option");
     if (o.lanczos != 0 && o.lanczos != 1) return fail(TMR_ERR_INVALID_ARG, "opt.lanczos must be 0 or 1");
+    if (o.cost != TMR_COST_INTENSITY && o.cost != TMR_COST_AMPLITUDE)
+        return fail(TMR_ERR_INVALID_ARG, "opt.cost must be TMR_COST_INTENSITY or TMR_COST_AMPLITUDE");
     if (o.lanczos && o.power_iters > kMaxLanczos)
         return fail(TMR_ERR_INVALID_ARG, "opt.power_iters (Lanczos steps) must be at most 16 with opt.lanczos");
     if (o.wait_spins < 1 || o.wait_spins > (1LL << 40))
@@ -705,7 +707,8 @@ tmr_status tmr_grad(tmr_handle *h, const void *T, const float *Y, float *loss, v
     if (loss && (st = stage(h, ST_LOSS, loss, sizeof(float) * h->M, false, &dL)) != TMR_OK) return st;
     if (G && (st = stage(h, ST_TOUT, G, sizeof(float2) * MN, false, &dG)) != TMR_OK) return st;
     if ((st = check_launch(launch_grad(h->N, h->M, h->J, (const float2 *)dT, h->masks, h->tw,
-                                       (const float *)dY, (float *)dL, (float2 *)dG, h->stream, h->xk),
+                                       (const float *)dY, (float *)dL, (float2 *)dG, h->stream, h->xk,
+                                       h->opt.cost),
                            "gradient kernel")) != TMR_OK)
         return st;
     bool synced = false;
@@ -830,6 +833,7 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
     p.pairs = h->pairs;
     p.pair_ctas = h->pair_ctas;
     p.lanczos = h->opt.lanczos;
+    p.cost = h->opt.cost;
     p.krylov = h->krylov;
     p.krylov_units = h->krylov_units;
     p.Nd = 0;

@@ -57,7 +57,7 @@ cudaError_t launch_forward(int N, int M, int J, const float2 *T, const float2 *m
                            const float2 *tw, float *Y, cudaStream_t s, int prec = 0);
 cudaError_t launch_grad(int N, int M, int J, const float2 *T, const float2 *masks,
                         const float2 *tw, const float *Y, float *loss, float2 *G, cudaStream_t s,
-                        int prec = 0);
+                        int prec = 0, int cost = 0);
 // c_n[r] = (Q T[r])[n] for n < Nd, written as Zd[n][r] (the defocus fields).
 cudaError_t launch_fields(int N, int M, int J, int Nd, const float2 *T, const float2 *masks,
                           const float2 *tw, float2 *Zd, cudaStream_t s, int prec = 0);
@@ -89,6 +89,7 @@ struct SolverParams {
     float2 *pairs;        // one-CTA-per-row schedule: L-BFGS pairs, pair_ctas regions of
     int pair_ctas;        //   2 (m + 1) N float2 each (global memory), else unused
     int lanczos;          // spectral start by power_iters Lanczos steps (else the power iteration)
+    int cost;             // COST_INTENSITY (Eq. optTMsmall2) or COST_AMPLITUDE (cost.cuh)
     float2 *krylov;       // Lanczos vectors: krylov_units regions of lanczos_region(N, power_iters)
     int krylov_units;     //   float2, one per CTA (one CTA per row) or cluster; launches use at most that many
     int N, Nd, M, J, iters, m, init, power_iters;

@@ -14,6 +14,7 @@
 #include <cuda_fp16.h>
 
 #include "common.cuh"
+#include "cost.cuh"
 #include "fft.cuh"
 #include "internal.h"
 #include "xform.cuh"
@@ -406,7 +407,7 @@ __global__ void __launch_bounds__(Xf::NT) k_grad(int N, const float2 *__restrict
                                                  const float2 *__restrict__ cg,
                                                  const float *__restrict__ Y,
                                                  float *__restrict__ loss,
-                                                 float2 *__restrict__ G, int J)
+                                                 float2 *__restrict__ G, int J, int cost)
 {
     constexpr int NT = Xf::NT, E = Xf::NE;
     extern __shared__ float2 smem[];
@@ -433,9 +434,14 @@ __global__ void __launch_bounds__(Xf::NT) k_grad(int N, const float2 *__restrict
         xf.fwd(v, buf, cst, tid);
 #pragma unroll
         for (int e = 0; e < E; e++) {
-            const float r = Xf::valid(e, tid, N) ? y[tid + e * NT] - cabs2(v[e]) : 0.f;
-            f = fmaf(r, r, f);
-            v[e] = cscale(v[e], r);
+            if (cost == COST_AMPLITUDE) {
+                const float c = Xf::valid(e, tid, N) ? cost_coef(cost, v[e], y[tid + e * NT], f) : 0.f;
+                v[e] = cscale(v[e], c);
+            } else {
+                const float r = Xf::valid(e, tid, N) ? y[tid + e * NT] - cabs2(v[e]) : 0.f;
+                f = fmaf(r, r, f);
+                v[e] = cscale(v[e], r);
+            }
         }
         xf.adj(v, buf, cst, tid);
 #pragma unroll
@@ -444,7 +450,7 @@ __global__ void __launch_bounds__(Xf::NT) k_grad(int N, const float2 *__restrict
     if (G) {
 #pragma unroll
         for (int e = 0; e < E; e++)
-            if (Xf::valid(e, tid, N)) G[(size_t)row * N + tid + e * NT] = cscale(acc[e], -4.f);
+            if (Xf::valid(e, tid, N)) G[(size_t)row * N + tid + e * NT] = cscale(acc[e], cost_grad_scale(cost));
     }
     float fv[1] = {f};
     block_sum<1>(fv, red, fsum);
@@ -528,14 +534,14 @@ cudaError_t launch_forward(int N, int M, int J, const float2 *T, const float2 *m
 
 cudaError_t launch_grad(int N, int M, int J, const float2 *T, const float2 *masks,
                         const float2 *tw, const float *Y, float *loss, float2 *G, cudaStream_t s,
-                        int prec)
+                        int prec, int cost)
 {
     if (M == 0) return cudaSuccess;
     return dispatch_xf(N, prec, [&](auto xf) {
         using XF = decltype(xf);
         const size_t sm = xf_kernel_smem<XF>(N);
         cudaFuncSetAttribute(k_grad<XF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_grad<XF><<<M, XF::NT, sm, s>>>(N, T, masks, tw, Y, loss, G, J);
+        k_grad<XF><<<M, XF::NT, sm, s>>>(N, T, masks, tw, Y, loss, G, J, cost);
         return cudaGetLastError();
     });
 }

@@ -96,6 +96,7 @@ extern "C" tmr_status tmr_retrieve_rows_static(int N, int M, int J, const void *
     if (o.m < 1 || o.m > tmr::kMaxMem) return fail(TMR_ERR_INVALID_ARG, "opt.m must be in 1..6");
     if (o.init < TMR_INIT_RANDOM || o.init > TMR_INIT_SPECTRAL || o.power_iters < 0 || o.tol < 0)
         return fail(TMR_ERR_INVALID_ARG, "bad option");
+    if (o.cost != TMR_COST_INTENSITY && o.cost != TMR_COST_AMPLITUDE) return fail(TMR_ERR_INVALID_ARG, "bad option");
     if (o.lanczos)
         return fail(TMR_ERR_UNSUPPORTED, "the static entry point runs the power iteration (opt.lanczos = 0): "
                                          "the Lanczos vectors need a workspace");
@@ -160,6 +161,7 @@ extern "C" tmr_status tmr_retrieve_rows_static(int N, int M, int J, const void *
     p.m = o.m;
     p.init = o.init;
     p.power_iters = o.power_iters;
+    p.cost = o.cost;
     p.seed = o.seed;
     p.clip = (float)o.clip;
     p.tol = o.tol;

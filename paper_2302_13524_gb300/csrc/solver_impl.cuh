@@ -50,6 +50,7 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "cost.cuh"
 #include "internal.h"
 #include "lanczos.cuh"
 #include "xform.cuh"
@@ -553,6 +554,7 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
     Xf xf;
     xf.setup(P.masks + (size_t)jm * N, P.tw + Xf::NCONST, N, ttid);
     auto valid = [&](int e) { return Xf::valid(e, ttid, N); };
+    const float gsc = cost_grad_scale(P.cost);  // the gradient's scale (-4 intensity, 2 amplitude)
     // x[e] = X[index of register e] (zero past the end)
     auto load_X = [&](float2 (&x)[E]) {
 #pragma unroll
@@ -811,8 +813,12 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
                     float pv[32] = {0.f};
 #pragma unroll
                     for (int e = 0; e < E; e++) {
-                        const float r = yv[e] - cabs2(x[e]);
-                        pv[0] = fmaf(r, r, pv[0]);
+                        if (P.cost == COST_AMPLITUDE) {
+                            if (valid(e)) cost_coef(P.cost, x[e], yv[e], pv[0]);
+                        } else {
+                            const float r = yv[e] - cabs2(x[e]);
+                            pv[0] = fmaf(r, r, pv[0]);
+                        }
                     }
                     cluster_sum(pv, 1);
                     fv[c] = Gm.red[0];
@@ -836,15 +842,19 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
                 float pv[32] = {0.f};
 #pragma unroll
                 for (int e = 0; e < E; e++) {
-                    const float r = yv[e] - cabs2(z[e]);
-                    pv[0] = fmaf(r, r, pv[0]);
-                    u[e] = cscale(z[e], r);
+                    if (P.cost == COST_AMPLITUDE) {
+                        u[e] = valid(e) ? cscale(z[e], cost_coef(P.cost, z[e], yv[e], pv[0])) : make_float2(0.f, 0.f);
+                    } else {
+                        const float r = yv[e] - cabs2(z[e]);
+                        pv[0] = fmaf(r, r, pv[0]);
+                        u[e] = cscale(z[e], r);
+                    }
                 }
                 xf.adj(u, buf, tws, ttid);
                 push_to_owners(u);
                 cluster.sync();
                 for (int i = tid; i < nmine; i += BT) {
-                    const float2 g = slice_sum(i, -4.f);
+                    const float2 g = slice_sum(i, gsc);
                     gs[i] = g;
                     pv[1] += cabs2(g);
                 }
@@ -912,8 +922,17 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
                 load_X(w);
                 __syncthreads();  // X is read before the FFT reuses it
                 xf.fwd(w, buf, tws, ttid);
-                // D: quartic coefficients
-                {
+                // D: the step -- the amplitude cost's line search, or the quartic's exact minimiser
+                if (P.cost == COST_AMPLITUDE) {
+                    const float al = amp_line_search(
+                        z, w, [&](int e) { return yv[e]; }, valid, cluster_sum, Gm.red, Gm.red + 16);
+                    if (tid == 0) {
+                        Gm.alpha = al;
+                        if (!isfinite(al)) { Gm.status = ROW_NUMERIC; Gm.stop = 1; }
+                        else if (al == 0.f) { Gm.status = ROW_CONVERGED; Gm.stop = 1; }
+                    }
+                    __syncthreads();
+                } else {
                     float pv[32] = {0.f};
 #pragma unroll
                     for (int e = 0; e < E; e++) {
@@ -945,9 +964,13 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
 #pragma unroll
                 for (int e = 0; e < E; e++) {
                     z[e] = make_float2(fmaf(al, w[e].x, z[e].x), fmaf(al, w[e].y, z[e].y));
-                    const float r = yv[e] - cabs2(z[e]);
-                    fpart = fmaf(r, r, fpart);
-                    u[e] = cscale(z[e], r);
+                    if (P.cost == COST_AMPLITUDE) {
+                        u[e] = valid(e) ? cscale(z[e], cost_coef(P.cost, z[e], yv[e], fpart)) : make_float2(0.f, 0.f);
+                    } else {
+                        const float r = yv[e] - cabs2(z[e]);
+                        fpart = fmaf(r, r, fpart);
+                        u[e] = cscale(z[e], r);
+                    }
                 }
                 for (int i = tid; i < nmine; i += BT) {
                     float2 s;
@@ -974,7 +997,7 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
 #pragma unroll
                     for (int k = 0; k < kSlots; k++) so[k] = Gm.slot[k <= np ? k : 0] * SL;
                     for (int i = tid; i < nmine; i += BT) {
-                        const float2 gn = slice_sum(i, -4.f);
+                        const float2 gn = slice_sum(i, gsc);
                         const HT yh = hist_store<HT>(csub(gn, gs[i]));
                         const float2 yn = hist_load(yh);  // the stored pair, as the Gram scalars see it
                         gs[i] = gn;
@@ -1011,7 +1034,8 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
             if (P.row_status) P.row_status[row] = Gm.status;
             if (P.row_iters) P.row_iters[row] = Gm.done;
             if (P.row_loss) {
-                const double f2 = (double)tsc * tsc * tsc * tsc;  // f scales as y^2 = t^4
+                // the intensity cost scales as y^2 = t^4, the amplitude cost as y = t^2
+                const double f2 = P.cost == COST_AMPLITUDE ? (double)tsc * tsc : (double)tsc * tsc * tsc * tsc;
                 P.row_loss[row] = early ? (Gm.status == ROW_ZERO ? 0.f : __int_as_float(0x7fc00000))
                                         : (float)((double)Gm.f * f2);
             }

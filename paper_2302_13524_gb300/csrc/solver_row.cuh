@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
     const int lane = tid & 31, warp = tid >> 5;
     const size_t K = (size_t)J * N;
     const float JN = (float)K;
+    const float gsc = cost_grad_scale(P.cost);  // the gradient's scale (-4 intensity, 2 amplitude)
 
     // ---- shared memory ----
     float2 *tws = reinterpret_cast<float2 *>(smem_raw);
@@ -318,8 +319,7 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
                     float pv[32] = {0.f};
 #pragma unroll
                     for (int e = 0; e < E; e++) {
-                        const float r = yt[ttid + e * NT] - cabs2(x[e]);
-                        pv[0] = fmaf(r, r, pv[0]);
+                        cost_coef(P.cost, x[e], yt[ttid + e * NT], pv[0]);
                     }
                     block_reduce(pv, 1);
                     fv[c] = Gm.red[0];
@@ -338,16 +338,12 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
                 float2 u[E];
                 float pv[32] = {0.f};
 #pragma unroll
-                for (int e = 0; e < E; e++) {
-                    const float r = yt[ttid + e * NT] - cabs2(z[e]);
-                    pv[0] = fmaf(r, r, pv[0]);
-                    u[e] = cscale(z[e], r);
-                }
+                for (int e = 0; e < E; e++) u[e] = cscale(z[e], cost_coef(P.cost, z[e], yt[ttid + e * NT], pv[0]));
                 adj(u);
                 park(u);
                 __syncthreads();
                 for (int i = tid; i < N; i += BT) {
-                    const float2 g = team_sum(i, -4.f);
+                    const float2 g = team_sum(i, gsc);
                     gs[i] = g;
                     pv[1] += cabs2(g);
                 }
@@ -401,8 +397,18 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
                 float2 w[E];
                 load_team(X, w);
                 fwd(w);
-                // D: quartic coefficients and the exact step
-                {
+                // D: the step -- the amplitude cost's line search, or the quartic's exact minimiser
+                if (P.cost == COST_AMPLITUDE) {
+                    const float al = amp_line_search(
+                        z, w, [&](int e) { return yt[ttid + e * NT]; }, [](int) { return true; }, block_reduce,
+                        Gm.red, Gm.red + 16);
+                    if (tid == 0) {
+                        Gm.alpha = al;
+                        if (!isfinite(al)) { Gm.status = ROW_NUMERIC; Gm.stop = 1; }
+                        else if (al == 0.f) { Gm.status = ROW_CONVERGED; Gm.stop = 1; }
+                    }
+                    __syncthreads();
+                } else {
                     float pv[32] = {0.f};
 #pragma unroll
                     for (int e = 0; e < E; e++) {
@@ -434,9 +440,7 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
 #pragma unroll
                 for (int e = 0; e < E; e++) {
                     z[e] = make_float2(fmaf(al, w[e].x, z[e].x), fmaf(al, w[e].y, z[e].y));
-                    const float r = yt[ttid + e * NT] - cabs2(z[e]);
-                    fpart = fmaf(r, r, fpart);
-                    u[e] = cscale(z[e], r);
+                    u[e] = cscale(z[e], cost_coef(P.cost, z[e], yt[ttid + e * NT], fpart));
                 }
                 adj(u);
                 park(u);
@@ -447,7 +451,7 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
 #pragma unroll
                     for (int k = 0; k < 32; k++) pv[k] = 0.f;
                     for (int i = tid; i < N; i += BT) {
-                        const float2 gn = team_sum(i, -4.f);
+                        const float2 gn = team_sum(i, gsc);
                         const float2 sn = cscale(X[i], al);
                         const float2 yn = csub(gn, gs[i]);
                         ts[i] = cadd(ts[i], sn);
@@ -489,7 +493,8 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
             if (P.row_status) P.row_status[row] = Gm.status;
             if (P.row_iters) P.row_iters[row] = Gm.done;
             if (P.row_loss) {
-                const double f2 = (double)tsc * tsc * tsc * tsc;  // f scales as y^2 = t^4
+                // the intensity cost scales as y^2 = t^4, the amplitude cost as y = t^2
+                const double f2 = P.cost == COST_AMPLITUDE ? (double)tsc * tsc : (double)tsc * tsc * tsc * tsc;
                 P.row_loss[row] = early ? (Gm.status == ROW_ZERO ? 0.f : __int_as_float(0x7fc00000))
                                         : (float)((double)Gm.f * f2);
             }
