@@ -235,9 +235,9 @@ void write_tune_file(const char *path, const std::map<std::string, int> &m)
     f << "\n}\n";
 }
 
-bool schedule_ok(int N, int J, int m, int G, int smem_optin, int prec = 0)
+bool schedule_ok(int N, int J, int m, int G, int smem_optin, int prec = 0, int cost = 0)
 {
-    if (G <= 0 || !solver_schedule_valid(N, J, G, prec)) return false;
+    if (G <= 0 || !solver_schedule_valid(N, J, G, prec) || !solver_cost_supported(N, G, prec, cost)) return false;
     const size_t b = solver_smem_bytes(N, J, m, G, prec);
     return b > 0 && b <= (size_t)smem_optin;
 }
@@ -249,7 +249,7 @@ tmr_status autotune(tmr_handle *h, int smem_optin, int *G_out, bool *timed)
     *timed = false;
     int cand[5], nc = 0;
     for (int G : {1, 2, 4, kRowSchedule, kBlueFullSchedule})
-        if (schedule_ok(h->N, h->J, h->opt.m, G, smem_optin, h->xk) && (G != kRowSchedule || h->pairs) &&
+        if (schedule_ok(h->N, h->J, h->opt.m, G, smem_optin, h->xk, h->opt.cost) && (G != kRowSchedule || h->pairs) &&
             (G != kBlueFullSchedule || h->tw_alt))
             cand[nc++] = G;
     if (nc == 0) {  // the forward model and gradient still work; tmr_retrieve will refuse
@@ -299,6 +299,7 @@ tmr_status autotune(tmr_handle *h, int smem_optin, int *G_out, bool *timed)
     p.m = h->opt.m;
     p.init = TMR_INIT_SPECTRAL;
     p.power_iters = 4;
+    p.cost = h->opt.cost;
     p.clip = 2.f;
     float best = 1e30f;
     int bestG = cand[0];
@@ -339,13 +340,13 @@ tmr_status autotune(tmr_handle *h, int smem_optin, int *G_out, bool *timed)
     return st;
 }
 
-std::string tune_key(int dev, int N, int J, int m, int prec)
+std::string tune_key(int dev, int N, int J, int m, int prec, int cost)
 {
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, dev);
     char k[320];
-    snprintf(k, sizeof(k), "%s|sm%d%d|N%d|J%d|m%d%s", prop.name, prop.major, prop.minor, N, J, m,
-             prec == 1 ? "|mixed" : (prec == 2 ? "|2d" : ""));
+    snprintf(k, sizeof(k), "%s|sm%d%d|N%d|J%d|m%d%s%s", prop.name, prop.major, prop.minor, N, J, m,
+             prec == 1 ? "|mixed" : (prec == 2 ? "|2d" : ""), cost == TMR_COST_AMPLITUDE ? "|amp" : "");
     for (char *c = k; *c; c++)
         if (*c == '"' || *c == '\\') *c = '_';
     return k;
@@ -494,7 +495,9 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
 
     int smem_optin = 0;
     TMR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
-    if (o.schedule != 0 && !schedule_ok(N, J, o.m, o.schedule, smem_optin, xk))
+    if (o.cost == TMR_COST_AMPLITUDE && xk != 0)
+        return fail(TMR_ERR_UNSUPPORTED, "the amplitude cost runs on the FP32 1D transforms (precision FP32, probe_n1 0)");
+    if (o.schedule != 0 && !schedule_ok(N, J, o.m, o.schedule, smem_optin, xk, o.cost))
         return fail(TMR_ERR_UNSUPPORTED,
                     "opt.schedule must be 1, 2 or 4 (dividing J), 16 (one CTA per row) or 32 (full-length "
                     "Bluestein), and fit the device");
@@ -596,7 +599,8 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     // region per resident CTA, allocated when that schedule can run (and is
     // asked for or a candidate of the autotuner); under a workspace_limit that
     // it would exceed, the schedule is left out
-    if ((o.schedule == 0 || o.schedule == kRowSchedule) && schedule_ok(N, J, o.m, kRowSchedule, smem_optin, h->xk)) {
+    if ((o.schedule == 0 || o.schedule == kRowSchedule) &&
+        schedule_ok(N, J, o.m, kRowSchedule, smem_optin, h->xk, o.cost)) {
         const int ctas = solver_row_max_ctas(N, J, o.m);
         const size_t bytes = sizeof(float2) * solver_row_pair_stride(N, o.m) * (size_t)(ctas > 0 ? ctas : 0);
         if (ctas > 0 && (!o.workspace_limit || h->held + bytes <= o.workspace_limit)) {
@@ -609,7 +613,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     }
     // the other Bluestein plan's table, when that schedule can run
     if ((o.schedule == 0 || o.schedule == kBlueFullSchedule) &&
-        schedule_ok(N, J, o.m, kBlueFullSchedule, smem_optin, h->xk)) {
+        schedule_ok(N, J, o.m, kBlueFullSchedule, smem_optin, h->xk, o.cost)) {
         const int n = xform_table_blue_full(N, nullptr);
         std::vector<float2> t2(n > 0 ? n : 1);
         xform_table_blue_full(N, t2.data());
@@ -623,7 +627,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     if (o.schedule != 0) {
         h->G = o.schedule;
     } else {
-        const std::string key = tune_key(dev, N, J, o.m, h->xk);
+        const std::string key = tune_key(dev, N, J, o.m, h->xk, o.cost);
         int G = 0;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -632,7 +636,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
             if (!G && o.tune_cache) {
                 auto fm = read_tune_file(o.tune_cache);
                 auto f = fm.find(key);
-                if (f != fm.end() && schedule_ok(N, J, o.m, f->second, smem_optin, h->xk)) G = f->second;
+                if (f != fm.end() && schedule_ok(N, J, o.m, f->second, smem_optin, h->xk, o.cost)) G = f->second;
             }
             if (G == kRowSchedule && !h->pairs) G = 0;  // no pair workspace here: tune again
             if (G == kBlueFullSchedule && !h->tw_alt) G = 0;
@@ -777,7 +781,7 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
         int dev = 0, smem_optin = 0;
         TMR_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
         TMR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
-        if (!schedule_ok(h->N, h->J, h->opt.m, h->G, smem_optin, h->xk))
+        if (!schedule_ok(h->N, h->J, h->opt.m, h->G, smem_optin, h->xk, h->opt.cost))
             return fail(TMR_ERR_UNSUPPORTED,
                         "per-row state of this (N, J, m) does not fit in shared memory: lower opt.m");
     }

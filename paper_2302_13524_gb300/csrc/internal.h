@@ -117,6 +117,12 @@ __host__ __device__ inline size_t lanczos_region(int N, int k)
 constexpr int kBlueFullSchedule = 32;
 long long solver_dispatch_blue8192(int N, int ne, int what, const SolverParams *p, cudaStream_t s,
                                    int *clusters_out);
+// The amplitude cost's solvers (p.cost == 1): one CTA per row (N = 512, 1024,
+// 2048), clusters with G = 1, 2, 4 for powers of two, and G = 1 for the
+// Bluestein lengths with L <= 4096 (other N: none).
+cudaError_t launch_solver_row_amp(int N, const SolverParams &p, cudaStream_t s, int *ctas_out);
+cudaError_t launch_solver_amp(int N, int G, const SolverParams &p, cudaStream_t s, int *clusters_out);
+bool solver_cost_supported(int N, int G, int prec, int cost);
 bool solver_variant_exists(int N, int G, int prec = 0);
 // schedule G usable for (N, J): variant exists, J % G == 0 for cluster schedules
 bool solver_schedule_valid(int N, int J, int G, int prec = 0);

@@ -26,6 +26,10 @@ bool solver_variant_exists(int N, int G, int prec)
     }
 #define TMR_SOLVER_N(NN) TMR_SOLVER_N_G(NN, 1) TMR_SOLVER_N_G(NN, 2) TMR_SOLVER_N_G(NN, 4)
 
+// N = 1024 .. 4096 (solver_p2.cu: a translation unit of its own, compiled in parallel)
+long long solver_dispatch_pow2_large(int N, int G, int what, const SolverParams *p, cudaStream_t s,
+                                     int *clusters_out);
+
 // what == 0: shared-memory bytes of the variant; what == 1: launch it.
 static long long solver_dispatch(int N, int G, int what, const SolverParams *p, cudaStream_t s,
                                  int *clusters_out)
@@ -39,9 +43,7 @@ static long long solver_dispatch(int N, int G, int what, const SolverParams *p, 
     TMR_SOLVER_N(128)
     TMR_SOLVER_N(256)
     TMR_SOLVER_N(512)
-    TMR_SOLVER_N(1024)
-    TMR_SOLVER_N(2048)
-    TMR_SOLVER_N(4096)
+    if (N >= 1024) return solver_dispatch_pow2_large(N, G, what, p, s, clusters_out);
     return what == 0 ? 0 : (long long)cudaErrorInvalidValue;
 }
 
@@ -68,6 +70,8 @@ cudaError_t launch_solver(int N, int G, const SolverParams &p, cudaStream_t s, i
 {
     if (p.M == 0) return cudaSuccess;
     if (!solver_schedule_valid(N, p.J, G, p.prec) || p.N != N) return cudaErrorInvalidValue;
+    if (!solver_cost_supported(N, G, p.prec, p.cost)) return cudaErrorInvalidValue;
+    if (p.cost == COST_AMPLITUDE && G != kRowSchedule) return launch_solver_amp(N, G, p, s, clusters_out);
     return (cudaError_t)solver_dispatch(N, G, 1, &p, s, clusters_out);
 }
 

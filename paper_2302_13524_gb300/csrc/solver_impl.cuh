@@ -508,7 +508,7 @@ __host__ __device__ size_t solver_smem(int N, int J, int m)
     return bytes + sizeof(Gram);
 }
 
-template <class Xf, int G>
+template <class Xf, int G, int COST = COST_INTENSITY>
 __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <= 256 && Xf::kN >= 256) ? 2 : 1)
     k_solver(SolverParams P)
 {
@@ -554,7 +554,7 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
     Xf xf;
     xf.setup(P.masks + (size_t)jm * N, P.tw + Xf::NCONST, N, ttid);
     auto valid = [&](int e) { return Xf::valid(e, ttid, N); };
-    const float gsc = cost_grad_scale(P.cost);  // the gradient's scale (-4 intensity, 2 amplitude)
+    const float gsc = cost_grad_scale(COST);  // the gradient's scale (-4 intensity, 2 amplitude)
     // x[e] = X[index of register e] (zero past the end)
     auto load_X = [&](float2 (&x)[E]) {
 #pragma unroll
@@ -813,8 +813,8 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
                     float pv[32] = {0.f};
 #pragma unroll
                     for (int e = 0; e < E; e++) {
-                        if (P.cost == COST_AMPLITUDE) {
-                            if (valid(e)) cost_coef(P.cost, x[e], yv[e], pv[0]);
+                        if constexpr (COST == COST_AMPLITUDE) {
+                            if (valid(e)) cost_coef(COST, x[e], yv[e], pv[0]);
                         } else {
                             const float r = yv[e] - cabs2(x[e]);
                             pv[0] = fmaf(r, r, pv[0]);
@@ -842,8 +842,8 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
                 float pv[32] = {0.f};
 #pragma unroll
                 for (int e = 0; e < E; e++) {
-                    if (P.cost == COST_AMPLITUDE) {
-                        u[e] = valid(e) ? cscale(z[e], cost_coef(P.cost, z[e], yv[e], pv[0])) : make_float2(0.f, 0.f);
+                    if constexpr (COST == COST_AMPLITUDE) {
+                        u[e] = valid(e) ? cscale(z[e], cost_coef(COST, z[e], yv[e], pv[0])) : make_float2(0.f, 0.f);
                     } else {
                         const float r = yv[e] - cabs2(z[e]);
                         pv[0] = fmaf(r, r, pv[0]);
@@ -923,7 +923,7 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
                 __syncthreads();  // X is read before the FFT reuses it
                 xf.fwd(w, buf, tws, ttid);
                 // D: the step -- the amplitude cost's line search, or the quartic's exact minimiser
-                if (P.cost == COST_AMPLITUDE) {
+                if constexpr (COST == COST_AMPLITUDE) {
                     const float al = amp_line_search(
                         z, w, [&](int e) { return yv[e]; }, valid, cluster_sum, Gm.red, Gm.red + 16);
                     if (tid == 0) {
@@ -964,8 +964,8 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
 #pragma unroll
                 for (int e = 0; e < E; e++) {
                     z[e] = make_float2(fmaf(al, w[e].x, z[e].x), fmaf(al, w[e].y, z[e].y));
-                    if (P.cost == COST_AMPLITUDE) {
-                        u[e] = valid(e) ? cscale(z[e], cost_coef(P.cost, z[e], yv[e], fpart)) : make_float2(0.f, 0.f);
+                    if constexpr (COST == COST_AMPLITUDE) {
+                        u[e] = valid(e) ? cscale(z[e], cost_coef(COST, z[e], yv[e], fpart)) : make_float2(0.f, 0.f);
                     } else {
                         const float r = yv[e] - cabs2(z[e]);
                         fpart = fmaf(r, r, fpart);
@@ -1035,7 +1035,7 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
             if (P.row_iters) P.row_iters[row] = Gm.done;
             if (P.row_loss) {
                 // the intensity cost scales as y^2 = t^4, the amplitude cost as y = t^2
-                const double f2 = P.cost == COST_AMPLITUDE ? (double)tsc * tsc : (double)tsc * tsc * tsc * tsc;
+                const double f2 = COST == COST_AMPLITUDE ? (double)tsc * tsc : (double)tsc * tsc * tsc * tsc;
                 P.row_loss[row] = early ? (Gm.status == ROW_ZERO ? 0.f : __int_as_float(0x7fc00000))
                                         : (float)((double)Gm.f * f2);
             }
@@ -1051,13 +1051,13 @@ __global__ void __launch_bounds__(SolverCfg<Xf, G>::BT, (SolverCfg<Xf, G>::BT <=
     }
 }
 
-template <class Xf, int G>
+template <class Xf, int G, int COST = COST_INTENSITY>
 cudaError_t launch_solver_t(const SolverParams &p, cudaStream_t s, int *clusters_out)
 {
     using C = SolverCfg<Xf, G>;
     const int JC = p.J / G;
     const size_t sm = solver_smem<Xf, G>(p.N, p.J, p.m);
-    cudaError_t e = cudaFuncSetAttribute(k_solver<Xf, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_solver<Xf, G, COST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -1072,7 +1072,7 @@ cudaError_t launch_solver_t(const SolverParams &p, cudaStream_t s, int *clusters
     cfg.numAttrs = 1;
     cfg.gridDim = dim3(JC);
     int maxc = 0;
-    e = cudaOccupancyMaxActiveClusters(&maxc, k_solver<Xf, G>, &cfg);
+    e = cudaOccupancyMaxActiveClusters(&maxc, k_solver<Xf, G, COST>, &cfg);
     if (e != cudaSuccess) return e;
     if (maxc < 1) return cudaErrorInvalidConfiguration;
     int nc = maxc < p.M ? maxc : p.M;
@@ -1080,7 +1080,7 @@ cudaError_t launch_solver_t(const SolverParams &p, cudaStream_t s, int *clusters
     if (nc < 1) nc = 1;
     cfg.gridDim = dim3(nc * JC);
     if (clusters_out) *clusters_out = nc;
-    return cudaLaunchKernelEx(&cfg, k_solver<Xf, G>, p);
+    return cudaLaunchKernelEx(&cfg, k_solver<Xf, G, COST>, p);
 }
 
 }  // namespace tmr

@@ -8,10 +8,12 @@ namespace tmr {
         if (what == 0) return (long long)row_smem<NN>(p->J, p->m);         \
         return (long long)launch_solver_row_t<NN>(*p, s, ctas_out);
 
-// what == 0: shared-memory bytes; what == 1: launch.
+// what == 0: shared-memory bytes; what == 1: launch (the amplitude cost's
+// kernels are instantiated in solver_row_amp.cu).
 long long solver_dispatch_row(int N, int what, const SolverParams *p, cudaStream_t s, int *ctas_out)
 {
     if (!row_variant_fits(N, p->J)) return what == 0 ? 0 : (long long)cudaErrorInvalidValue;
+    if (what == 1 && p->cost == COST_AMPLITUDE) return (long long)launch_solver_row_amp(N, *p, s, ctas_out);
     switch (N) {
         TMR_ROW_N(512)
         TMR_ROW_N(1024)

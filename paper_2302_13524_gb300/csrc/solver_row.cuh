@@ -62,7 +62,7 @@ __host__ __device__ size_t row_smem(int J, int m)
 // Pair workspace of one CTA, in float2: 2 (m + 1) vectors of length N.
 __host__ __device__ inline size_t row_pair_stride(int N, int m) { return (size_t)2 * (m + 1) * N; }
 
-template <int N>
+template <int N, int COST = COST_INTENSITY>
 __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
 {
     using C = RowCfg<N>;
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
     const int lane = tid & 31, warp = tid >> 5;
     const size_t K = (size_t)J * N;
     const float JN = (float)K;
-    const float gsc = cost_grad_scale(P.cost);  // the gradient's scale (-4 intensity, 2 amplitude)
+    const float gsc = cost_grad_scale(COST);  // the gradient's scale (-4 intensity, 2 amplitude)
 
     // ---- shared memory ----
     float2 *tws = reinterpret_cast<float2 *>(smem_raw);
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
                     float pv[32] = {0.f};
 #pragma unroll
                     for (int e = 0; e < E; e++) {
-                        cost_coef(P.cost, x[e], yt[ttid + e * NT], pv[0]);
+                        cost_coef(COST, x[e], yt[ttid + e * NT], pv[0]);
                     }
                     block_reduce(pv, 1);
                     fv[c] = Gm.red[0];
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
                 float2 u[E];
                 float pv[32] = {0.f};
 #pragma unroll
-                for (int e = 0; e < E; e++) u[e] = cscale(z[e], cost_coef(P.cost, z[e], yt[ttid + e * NT], pv[0]));
+                for (int e = 0; e < E; e++) u[e] = cscale(z[e], cost_coef(COST, z[e], yt[ttid + e * NT], pv[0]));
                 adj(u);
                 park(u);
                 __syncthreads();
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
                 load_team(X, w);
                 fwd(w);
                 // D: the step -- the amplitude cost's line search, or the quartic's exact minimiser
-                if (P.cost == COST_AMPLITUDE) {
+                if constexpr (COST == COST_AMPLITUDE) {
                     const float al = amp_line_search(
                         z, w, [&](int e) { return yt[ttid + e * NT]; }, [](int) { return true; }, block_reduce,
                         Gm.red, Gm.red + 16);
@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
 #pragma unroll
                 for (int e = 0; e < E; e++) {
                     z[e] = make_float2(fmaf(al, w[e].x, z[e].x), fmaf(al, w[e].y, z[e].y));
-                    u[e] = cscale(z[e], cost_coef(P.cost, z[e], yt[ttid + e * NT], fpart));
+                    u[e] = cscale(z[e], cost_coef(COST, z[e], yt[ttid + e * NT], fpart));
                 }
                 adj(u);
                 park(u);
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
             if (P.row_iters) P.row_iters[row] = Gm.done;
             if (P.row_loss) {
                 // the intensity cost scales as y^2 = t^4, the amplitude cost as y = t^2
-                const double f2 = P.cost == COST_AMPLITUDE ? (double)tsc * tsc : (double)tsc * tsc * tsc * tsc;
+                const double f2 = COST == COST_AMPLITUDE ? (double)tsc * tsc : (double)tsc * tsc * tsc * tsc;
                 P.row_loss[row] = early ? (Gm.status == ROW_ZERO ? 0.f : __int_as_float(0x7fc00000))
                                         : (float)((double)Gm.f * f2);
             }
@@ -510,18 +510,18 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
     }
 }
 
-template <int N>
+template <int N, int COST = COST_INTENSITY>
 cudaError_t launch_solver_row_t(const SolverParams &p, cudaStream_t s, int *ctas_out)
 {
     if (!row_variant_fits(N, p.J) || !p.pairs) return cudaErrorInvalidValue;
     const int BT = p.J * RowCfg<N>::NT;
     const size_t sm = row_smem<N>(p.J, p.m);
-    cudaError_t e = cudaFuncSetAttribute(k_solver_row<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_solver_row<N, COST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0, occ = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solver_row<N>, BT, sm)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solver_row<N, COST>, BT, sm)) != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     long long grid = (long long)occ * nsm;
     if (grid > p.M) grid = p.M;
@@ -529,7 +529,7 @@ cudaError_t launch_solver_row_t(const SolverParams &p, cudaStream_t s, int *ctas
     if (p.lanczos && p.init == INIT_SPECTRAL && grid > p.krylov_units) grid = p.krylov_units;
     if (grid < 1) grid = 1;
     if (ctas_out) *ctas_out = (int)grid;
-    k_solver_row<N><<<(int)grid, BT, sm, s>>>(p);
+    k_solver_row<N, COST><<<(int)grid, BT, sm, s>>>(p);
     return cudaGetLastError();
 }
 
