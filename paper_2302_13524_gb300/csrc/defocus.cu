@@ -8,7 +8,7 @@
 // with w_n = D(c_n .* u), G_n = I_n - |w_n|^2 (Eq. phasederive).
 //
 // The whole fit is one cooperative launch: each CTA owns a set of patterns and
-// transforms their grids in shared memory (in-place radix-2 2D FFTs, FP32);
+// transforms their grids in shared memory (in-place radix-8/16 2D FFTs, FP32);
 // loss and gradient partials are written per CTA and reduced in a fixed order
 // (deterministic); the L-BFGS state, the Armijo test and every reduction of the
 // fit are FP64.  CTAs meet at a grid barrier whose spin is bounded: on timeout
@@ -16,6 +16,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "fft.cuh"
 #include "internal.h"
 
 namespace tmr {
@@ -47,7 +48,6 @@ cudaError_t launch_make_quadratic_H(int ny, int nx, double coef, float2 *H, cuda
 // ---------------------------------------------------------------------------
 // shared-memory 2D FFT, in place, radix-2 decimation in time after a
 // bit-reversal permutation along each axis.  grid pitch = nx + 1 float2.
-__device__ __forceinline__ unsigned bitrev(unsigned v, int bits) { return __brev(v) >> (32 - bits); }
 
 // tw[k] = exp(-2 pi i k / n), k < n/2 (twy for ny, twx for nx), made once per CTA.
 __device__ void make_tw(float2 *tw, int n)
@@ -59,134 +59,154 @@ __device__ void make_tw(float2 *tw, int n)
     }
 }
 
-// Two consecutive radix-2 DIT stages (halves h and 2h) fused on the group
-// {b0, b0 + h, b0 + 2h, b0 + 3h}: stage one pairs (0, 1) and (2, 3) with
-// W_{2h}^k, stage two pairs (0, 2) with W_{4h}^k and (1, 3) with W_{4h}^{k+h}.
-__device__ __forceinline__ void dit2x2(float2 &x0, float2 &x1, float2 &x2, float2 &x3, float2 w1, float2 w2,
-                                       float2 w3)
+// ---------------------------------------------------------------------------
+// In-place 2D FFT of an ny x nx grid in shared memory (row pitch nx + 1).
+// Each axis of length n = 2^l runs as a few radix-R stages (R = 8, with one
+// radix-16, radix-4 or radix-2 stage first when l is not a multiple of 3):
+// the forward transform is decimation in frequency from natural order, so
+// the spectrum is left in digit-reversed order (spec_freq gives the frequency
+// at a position); the inverse is the mirror decimation in time from that
+// order back to natural order (unnormalised).  Every product with a spectrum
+// (the kernel h, the padding's ramps) indexes it through spec_freq, so no
+// reordering pass is needed.  Row stages map consecutive threads to
+// consecutive rows and column stages to consecutive columns: with the odd
+// pitch both touch shared memory without bank conflicts.
+
+// stage s has radix 2^lr(s): lr0 for the first stage, 3 (radix 8) after it
+struct AxisPlan {
+    int n, ln, lr0, ns;
+    __device__ int lr(int s) const { return s == 0 ? lr0 : 3; }
+};
+
+__device__ __forceinline__ AxisPlan axis_plan(int n)
 {
-    const float2 t1 = cmul(x1, w1), t3 = cmul(x3, w1);
-    const float2 a0 = cadd(x0, t1), a1 = csub(x0, t1), a2 = cadd(x2, t3), a3 = csub(x2, t3);
-    const float2 u2 = cmul(a2, w2), u3 = cmul(a3, w3);
-    x0 = cadd(a0, u2);
-    x2 = csub(a0, u2);
-    x1 = cadd(a1, u3);
-    x3 = csub(a1, u3);
+    AxisPlan P;
+    P.n = n;
+    P.ln = __ffs(n) - 1;
+    const int l = P.ln;
+    P.lr0 = l == 1 ? 1 : (l % 3 == 1 ? 4 : (l % 3 == 2 ? 2 : 3));
+    P.ns = 1 + (l - P.lr0) / 3;
+    return P;
 }
 
-__device__ void fft2_inplace(float2 *g, int ny, int nx, int sign, const float2 *twy, const float2 *twx)
+// frequency held at position pos after the forward stages: the digits of pos
+// in the stage radices (most significant first) are the frequency's digits
+// from the least significant up
+__device__ __forceinline__ int axis_freq(const AxisPlan &P, int pos)
 {
-    // ny, nx powers of two: every index below is a shift or a mask; stages are
-    // fused two at a time (one barrier per pair), an odd last stage alone
-    const int pitch = nx + 1;
-    const int lx = __ffs(nx) - 1, ly = __ffs(ny) - 1;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    auto tw = [sign](const float2 *t, int i) {
-        float2 w = t[i];
-        if (sign > 0) w.y = -w.y;
-        return w;
-    };
-    // rows: bit reversal
-    for (int i = tid; i < ny * nx; i += nt) {
-        const int a = i >> lx, b = i & (nx - 1);
-        const int rb = (int)bitrev((unsigned)b, lx);
-        if (rb > b) {
-            const float2 t = g[a * pitch + b];
-            g[a * pitch + b] = g[a * pitch + rb];
-            g[a * pitch + rb] = t;
+    int f = 0, lmul = 0, lspan = P.ln;
+    for (int s = 0; s < P.ns; s++) {
+        const int l = P.lr(s);
+        lspan -= l;
+        f |= ((pos >> lspan) & ((1 << l) - 1)) << lmul;
+        lmul += l;
+    }
+    return f;
+}
+
+// W_n^idx from the half table tw[k] = exp(-2 pi i k / n), k < n / 2, idx < n
+__device__ __forceinline__ float2 tw_full(const float2 *tw, int n, int idx)
+{
+    if (idx < n / 2) return tw[idx];
+    const float2 w = tw[idx - n / 2];
+    return make_float2(-w.x, -w.y);
+}
+
+// One forward (FWD) or inverse stage of radix R and length L on every line
+// of one axis.  Along rows (ROWS): element e of line a at a * pitch + e,
+// nlines = ny; along columns: element e of line x at e * pitch + x.
+template <int R, bool FWD, bool ROWS>
+__device__ void fft_stage(float2 *g, int n, int nlines, int pitch, int L, const float2 *tw)
+{
+    const int m = L / R, per = n / R, total = nlines * per;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int line = i % nlines, q = i / nlines;  // lines fastest
+        const int b = q / m, j = q - b * m;
+        const int e0 = b * L + j;
+        float2 *base = ROWS ? g + line * pitch + e0 : g + e0 * pitch + line;
+        const int es = ROWS ? m : m * pitch;
+        float2 x[R];
+#pragma unroll
+        for (int k = 0; k < R; k++) x[k] = base[k * es];
+        const int step = j * (n / L);
+        if (FWD) {
+            dft_small<R, -1>(x);
+#pragma unroll
+            for (int k = 1; k < R; k++) x[k] = cmul(x[k], tw_full(tw, n, step * k));
+        } else {
+#pragma unroll
+            for (int k = 1; k < R; k++) x[k] = cmulc(x[k], tw_full(tw, n, step * k));
+            dft_small<R, 1>(x);
         }
+#pragma unroll
+        for (int k = 0; k < R; k++) base[k * es] = x[k];
     }
     __syncthreads();
-    int lh = 0;
-    for (; lh + 1 < lx; lh += 2) {
-        const int h = 1 << lh;
-        for (int i = tid; i < ny * (nx / 4); i += nt) {
-            const int a = i >> (lx - 2), q = i & (nx / 4 - 1);
-            const int k = q & (h - 1);
-            const int b0 = ((q >> lh) << (lh + 2)) + k;
-            float2 *r = g + a * pitch + b0;
-            float2 x0 = r[0], x1 = r[h], x2 = r[2 * h], x3 = r[3 * h];
-            dit2x2(x0, x1, x2, x3, tw(twx, k << (lx - 1 - lh)), tw(twx, k << (lx - 2 - lh)),
-                   tw(twx, (k + h) << (lx - 2 - lh)));
-            r[0] = x0;
-            r[h] = x1;
-            r[2 * h] = x2;
-            r[3 * h] = x3;
+}
+
+template <bool FWD, bool ROWS>
+__device__ void fft_axis(float2 *g, const AxisPlan &P, int nlines, int pitch, const float2 *tw)
+{
+    // forward: stages 0 .. ns-1 (span shrinking); inverse: the reverse order
+    for (int t = 0; t < P.ns; t++) {
+        const int s = FWD ? t : P.ns - 1 - t;
+        int lL = P.ln;
+        for (int u = 0; u < s; u++) lL -= P.lr(u);
+        const int L = 1 << lL;
+        switch (1 << P.lr(s)) {
+        case 2: fft_stage<2, FWD, ROWS>(g, P.n, nlines, pitch, L, tw); break;
+        case 4: fft_stage<4, FWD, ROWS>(g, P.n, nlines, pitch, L, tw); break;
+        case 8: fft_stage<8, FWD, ROWS>(g, P.n, nlines, pitch, L, tw); break;
+        default: fft_stage<16, FWD, ROWS>(g, P.n, nlines, pitch, L, tw); break;
         }
-        __syncthreads();
-    }
-    if (lh < lx) {
-        const int half = 1 << lh;
-        for (int i = tid; i < ny * (nx / 2); i += nt) {
-            const int a = i >> (lx - 1), q = i & (nx / 2 - 1);
-            const int k = q & (half - 1);
-            const int b0 = ((q >> lh) << (lh + 1)) + k, b1 = b0 + half;
-            const float2 w = tw(twx, k << (lx - 1 - lh));
-            const float2 x0 = g[a * pitch + b0], x1 = cmul(g[a * pitch + b1], w);
-            g[a * pitch + b0] = cadd(x0, x1);
-            g[a * pitch + b1] = csub(x0, x1);
-        }
-        __syncthreads();
-    }
-    // columns
-    for (int i = tid; i < ny * nx; i += nt) {
-        const int a = i >> lx, b = i & (nx - 1);
-        const int ra = (int)bitrev((unsigned)a, ly);
-        if (ra > a) {
-            const float2 t = g[a * pitch + b];
-            g[a * pitch + b] = g[ra * pitch + b];
-            g[ra * pitch + b] = t;
-        }
-    }
-    __syncthreads();
-    lh = 0;
-    for (; lh + 1 < ly; lh += 2) {
-        const int h = 1 << lh;
-        for (int i = tid; i < (ny / 4) * nx; i += nt) {
-            const int q = i >> lx, b = i & (nx - 1);
-            const int k = q & (h - 1);
-            const int a0 = ((q >> lh) << (lh + 2)) + k;
-            float2 *c = g + a0 * pitch + b;
-            float2 x0 = c[0], x1 = c[h * pitch], x2 = c[2 * h * pitch], x3 = c[3 * h * pitch];
-            dit2x2(x0, x1, x2, x3, tw(twy, k << (ly - 1 - lh)), tw(twy, k << (ly - 2 - lh)),
-                   tw(twy, (k + h) << (ly - 2 - lh)));
-            c[0] = x0;
-            c[h * pitch] = x1;
-            c[2 * h * pitch] = x2;
-            c[3 * h * pitch] = x3;
-        }
-        __syncthreads();
-    }
-    if (lh < ly) {
-        const int half = 1 << lh;
-        for (int i = tid; i < (ny / 2) * nx; i += nt) {
-            const int q = i >> lx, b = i & (nx - 1);
-            const int k = q & (half - 1);
-            const int a0 = ((q >> lh) << (lh + 1)) + k, a1 = a0 + half;
-            const float2 w = tw(twy, k << (ly - 1 - lh));
-            const float2 x0 = g[a0 * pitch + b], x1 = cmul(g[a1 * pitch + b], w);
-            g[a0 * pitch + b] = cadd(x0, x1);
-            g[a1 * pitch + b] = csub(x0, x1);
-        }
-        __syncthreads();
     }
 }
+
+// forward 2D DFT (exp(-2 pi i ...)), natural order in, digit-reversed out
+__device__ void fft2_fwd(float2 *g, int ny, int nx, const float2 *twy, const float2 *twx)
+{
+    const AxisPlan Px = axis_plan(nx), Py = axis_plan(ny);
+    fft_axis<true, true>(g, Px, ny, nx + 1, twx);
+    fft_axis<true, false>(g, Py, nx, nx + 1, twy);
+}
+
+// unnormalised inverse 2D DFT, digit-reversed order in, natural out
+__device__ void fft2_inv(float2 *g, int ny, int nx, const float2 *twy, const float2 *twx)
+{
+    const AxisPlan Px = axis_plan(nx), Py = axis_plan(ny);
+    fft_axis<false, false>(g, Py, nx, nx + 1, twy);
+    fft_axis<false, true>(g, Px, ny, nx + 1, twx);
+}
+
+// natural frequencies (ky index, kx index) of the spectrum at grid position (a, b)
+struct SpecMap {
+    AxisPlan py, px;
+    __device__ void init(int ny, int nx)
+    {
+        py = axis_plan(ny);
+        px = axis_plan(nx);
+    }
+    __device__ int fy(int a) const { return axis_freq(py, a); }
+    __device__ int fx(int b) const { return axis_freq(px, b); }
+};
 
 // g <- D g (adjoint: D^H g), including the 1/P of the inverse transform.
 __device__ void defocus_apply_smem(float2 *g, int ny, int nx, const float2 *__restrict__ H,
                                    bool adjoint, const float2 *twy, const float2 *twx)
 {
     const int pitch = nx + 1, P = ny * nx, lx = __ffs(nx) - 1;
-    fft2_inplace(g, ny, nx, -1, twy, twx);
+    SpecMap sm;
+    sm.init(ny, nx);
+    fft2_fwd(g, ny, nx, twy, twx);
     const float inv = 1.0f / (float)P;
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         const int a = i >> lx, b = i & (nx - 1);
-        float2 h = H[i];
+        float2 h = H[sm.fy(a) * nx + sm.fx(b)];
         if (adjoint) h.y = -h.y;
         g[a * pitch + b] = cscale(cmul(g[a * pitch + b], h), inv);
     }
     __syncthreads();
-    fft2_inplace(g, ny, nx, +1, twy, twx);
+    fft2_inv(g, ny, nx, twy, twx);
 }
 
 static size_t defocus_smem(int ny, int nx)
@@ -374,23 +394,25 @@ __global__ void k_defocus_forward2x(int ny, int nx, int Nd, const float2 *__rest
     make_tw(twy, ny);
     make_tw(twx, nx);
     make_ramps(ry, rx, ny, nx);
+    SpecMap sm;
+    sm.init(ny, nx);
     const float inv = 1.f / (float)P;
     for (int n = blockIdx.x; n < Nd; n += gridDim.x) {
         for (int i = threadIdx.x; i < P; i += blockDim.x) g[(i >> lx) * pitch + (i & (nx - 1))] = Zd[(size_t)n * P + i];
         __syncthreads();
-        fft2_inplace(g, ny, nx, -1, twy, twx);
+        fft2_fwd(g, ny, nx, twy, twx);
         for (int i = threadIdx.x; i < P; i += blockDim.x) {
-            const int gi = (i >> lx) * pitch + (i & (nx - 1));
-            Xs[gi] = cmul(g[gi], H[i]);
+            const int a = i >> lx, b = i & (nx - 1), gi = a * pitch + b;
+            Xs[gi] = cmul(g[gi], H[sm.fy(a) * nx + sm.fx(b)]);
         }
         __syncthreads();
         for (int st = 0; st < 4; st++) {
             for (int i = threadIdx.x; i < P; i += blockDim.x) {
                 const int a = i >> lx, b = i & (nx - 1), gi = a * pitch + b;
-                g[gi] = cmul(Xs[gi], ramp_st(st, a, b, ry, rx));
+                g[gi] = cmul(Xs[gi], ramp_st(st, sm.fy(a), sm.fx(b), ry, rx));
             }
             __syncthreads();
-            fft2_inplace(g, ny, nx, +1, twy, twx);
+            fft2_inv(g, ny, nx, twy, twx);
             const int s = st >> 1, t = st & 1;
             for (int i = threadIdx.x; i < P; i += blockDim.x) {
                 const int a = i >> lx, b = i & (nx - 1);
@@ -560,10 +582,12 @@ __device__ void pf_pattern2x(const PhaseFitParams &Pp, int n, float2 *g, float2 
     const int ny = Pp.ny, nx = Pp.nx, P = ny * nx, pitch = nx + 1, lx = __ffs(nx) - 1;
     const float *In = Pp.Ydef + (size_t)n * 4 * P;
     const float inv = 1.0f / (float)P;
-    fft2_inplace(g, ny, nx, -1, twy, twx);
+    SpecMap sm;
+    sm.init(ny, nx);
+    fft2_fwd(g, ny, nx, twy, twx);
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        const int gi = (i >> lx) * pitch + (i & (nx - 1));
-        Xs[gi] = cmul(g[gi], Pp.H[i]);
+        const int a = i >> lx, b = i & (nx - 1), gi = a * pitch + b;
+        Xs[gi] = cmul(g[gi], Pp.H[sm.fy(a) * nx + sm.fx(b)]);
         S[gi] = make_float2(0.f, 0.f);
     }
     __syncthreads();
@@ -571,10 +595,10 @@ __device__ void pf_pattern2x(const PhaseFitParams &Pp, int n, float2 *g, float2 
         const int s = st >> 1, t = st & 1;
         for (int i = threadIdx.x; i < P; i += blockDim.x) {
             const int a = i >> lx, b = i & (nx - 1), gi = a * pitch + b;
-            g[gi] = cmul(Xs[gi], ramp_st(st, a, b, ry, rx));
+            g[gi] = cmul(Xs[gi], ramp_st(st, sm.fy(a), sm.fx(b), ry, rx));
         }
         __syncthreads();
-        fft2_inplace(g, ny, nx, +1, twy, twx);
+        fft2_inv(g, ny, nx, twy, twx);
         for (int i = threadIdx.x; i < P; i += blockDim.x) {
             const int a = i >> lx, b = i & (nx - 1), gi = a * pitch + b;
             const float2 w = cscale(g[gi], inv);
@@ -583,19 +607,19 @@ __device__ void pf_pattern2x(const PhaseFitParams &Pp, int n, float2 *g, float2 
             g[gi] = cscale(w, Gv);
         }
         __syncthreads();
-        fft2_inplace(g, ny, nx, -1, twy, twx);
+        fft2_fwd(g, ny, nx, twy, twx);
         for (int i = threadIdx.x; i < P; i += blockDim.x) {
             const int a = i >> lx, b = i & (nx - 1), gi = a * pitch + b;
-            S[gi] = cadd(S[gi], cmulc(g[gi], ramp_st(st, a, b, ry, rx)));
+            S[gi] = cadd(S[gi], cmulc(g[gi], ramp_st(st, sm.fy(a), sm.fx(b), ry, rx)));
         }
         __syncthreads();
     }
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        const int gi = (i >> lx) * pitch + (i & (nx - 1));
-        g[gi] = cscale(cmulc(S[gi], Pp.H[i]), inv);
+        const int a = i >> lx, b = i & (nx - 1), gi = a * pitch + b;
+        g[gi] = cscale(cmulc(S[gi], Pp.H[sm.fy(a) * nx + sm.fx(b)]), inv);
     }
     __syncthreads();
-    fft2_inplace(g, ny, nx, +1, twy, twx);
+    fft2_inv(g, ny, nx, twy, twx);
 }
 
 // Loss and gradient partials of this CTA's patterns for the phase table u:
