@@ -499,13 +499,14 @@ size_t phase_fit_workspace_doubles(int P, int Nd, int m, int grid)
 {
     (void)Nd;
     return (size_t)P * (4 + 2 * (m + 1)) + grid + (size_t)grid * kPfDots + ((size_t)grid * P + 1) / 2 +
-           (size_t)P + 64;
+           2 * (size_t)P + 64;
 }
 
 struct PFWork {
     double *phi, *p, *g, *phit, *S, *Y, *fpart, *pdot;
     float *part;
     float2 *u;
+    double *gsum;  // [P] the new gradient of an accepted step, summed over the CTAs' partials
 };
 
 __device__ PFWork pf_carve(double *ws, int P, int m, int grid)
@@ -521,7 +522,38 @@ __device__ PFWork pf_carve(double *ws, int P, int m, int grid)
     w.pdot = w.fpart + grid;
     w.part = reinterpret_cast<float *>(w.pdot + (size_t)grid * kPfDots);
     w.u = reinterpret_cast<float2 *>(w.pdot + (size_t)grid * kPfDots + ((size_t)grid * P + 1) / 2);
+    w.gsum = reinterpret_cast<double *>(w.u + P);
     return w;
+}
+
+// The cross-CTA sums of the fit, each in a fixed order (deterministic) and
+// spread over lanes so that no thread walks all nb partials in sequence.
+// out[k] = sum_b part[b P + k] for k in [k0, k1): 8 lanes per element, lane s
+// adding b = s, s + 8, ..., then an xor tree over the 8 lanes.
+__device__ void pf_part_sums(const float *part, int nb, int P, int k0, int k1, double *out)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int sub = lane & 7, slot = lane >> 3;
+    for (int base = k0 + 4 * warp; base < k1; base += 4 * nw) {
+        const int k = base + slot;
+        double s = 0.0;
+        if (k < k1)
+            for (int b = sub; b < nb; b += 8) s += (double)__ldcg(part + (size_t)b * P + k);
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        s += __shfl_xor_sync(0xffffffffu, s, 4);
+        if (sub == 0 && k < k1) out[k] = s;
+    }
+}
+
+// sum_b x[b] over b < nb by the lanes of one warp (lane-strided, xor tree):
+// every lane of every warp that calls it gets the same value
+__device__ __forceinline__ double warp_sum_nb(const double *x, int nb)
+{
+    double s = 0.0;
+    for (int b = threadIdx.x & 31; b < nb; b += 32) s += __ldcg(x + b);
+    for (int o = 1; o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
 }
 
 // L-BFGS scalars of the phase fit (FP64), replicated in every CTA; pairs by age.
@@ -733,13 +765,21 @@ __global__ void __launch_bounds__(512) k_phase_fit(PhaseFitParams Pp)
             W.pdot[(size_t)blockIdx.x * kPfDots + tid] = val;
         }
         if (!grid_sync(Pp.sync, Pp.err, Pp.wait_spins, Pp.withhold_release)) return false;
-        if (tid < kPfDots) {
+        {
+            // value vi by 16 lanes (b = sub, sub + 16, ...), then an xor tree
+            const int vi = tid >> 4, sub = tid & 15;
+            const bool is_max = vi == kPfDots - 2;
             double acc = 0.0;
-            for (int b = 0; b < nb; b++) {
-                const double x = __ldcg(W.pdot + (size_t)b * kPfDots + tid);
-                acc = (tid == kPfDots - 2) ? fmax(acc, x) : acc + x;
+            if (vi < kPfDots)
+                for (int b = sub; b < nb; b += 16) {
+                    const double x = __ldcg(W.pdot + (size_t)b * kPfDots + vi);
+                    acc = is_max ? fmax(acc, x) : acc + x;
+                }
+            for (int o = 1; o < 16; o <<= 1) {
+                const double y = __shfl_xor_sync(0xffffffffu, acc, o);
+                acc = is_max ? fmax(acc, y) : acc + y;
             }
-            G.red[tid] = acc;
+            if (sub == 0 && vi < kPfDots) G.red[vi] = acc;
         }
         __syncthreads();
         return true;
@@ -775,12 +815,12 @@ __global__ void __launch_bounds__(512) k_phase_fit(PhaseFitParams Pp)
         return;
     }
     {
+        pf_part_sums(W.part, nb, P, k0, k1, W.g);
+        __syncthreads();
         double v[kPfDots] = {0.0};
         double vmax = 0.0;
         for (int k = k0 + tid; k < k1; k += nt) {
-            double s = 0.0;
-            for (int b = 0; b < nb; b++) s += (double)__ldcg(W.part + (size_t)b * P + k);
-            W.g[k] = s;
+            const double s = W.g[k];
             v[4 * kPfSlots + 1] += s * s;
             vmax = fmax(vmax, fabs(s));
         }
@@ -789,10 +829,9 @@ __global__ void __launch_bounds__(512) k_phase_fit(PhaseFitParams Pp)
             return;
         }
     }
+    const double f_start = warp_sum_nb(W.fpart, nb);
     if (tid == 0) {
-        double f = 0.0;
-        for (int b = 0; b < nb; b++) f += __ldcg(W.fpart + b);
-        G.f = f;
+        G.f = f_start;
         G.gg = G.red[4 * kPfSlots + 1];
         G.gmax = G.red[kPfDots - 2];
         G.np = 0;
@@ -838,8 +877,7 @@ __global__ void __launch_bounds__(512) k_phase_fit(PhaseFitParams Pp)
         bail();
         return;
     }
-            ft = 0.0;
-            for (int b = 0; b < nb; b++) ft += __ldcg(W.fpart + b);
+            ft = warp_sum_nb(W.fpart, nb);
             if (ft <= f0 + 1e-4 * a * gp) {
                 accepted = true;
                 break;
@@ -850,11 +888,12 @@ __global__ void __launch_bounds__(512) k_phase_fit(PhaseFitParams Pp)
         // ---- accept: new gradient, pair and dot products on my chunk ----
         {
             const int np = G.np, ns = G.slot[np];
+            pf_part_sums(W.part, nb, P, k0, k1, W.gsum);
+            __syncthreads();
             double v[kPfDots] = {0.0};
             double vmax = 0.0;
             for (int k = k0 + tid; k < k1; k += nt) {
-                double gn = 0.0;
-                for (int b = 0; b < nb; b++) gn += (double)__ldcg(W.part + (size_t)b * P + k);
+                const double gn = W.gsum[k];
                 const double sv = W.phit[k] - W.phi[k], yv = gn - W.g[k];
                 Sg_[(size_t)ns * P + k] = sv;
                 Yg_[(size_t)ns * P + k] = yv;
