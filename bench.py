@@ -78,6 +78,9 @@ def parse():
     ap.add_argument("--power-iters", type=int, default=None,
                     help="operator products of the spectral start (default 16 Lanczos steps, 100 power)")
     ap.add_argument("--phase-iters", type=int, default=100)
+    ap.add_argument("--phase-tol", type=float, default=1e-4,
+                    help="stop the phase-offset fit once an accepted step lowers its loss by at most "
+                         "this fraction (0: only the iteration cap)")
     ap.add_argument("--rows", type=int, default=None, help="override M (grid kept 128 wide)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -319,7 +322,7 @@ def sweep_to_099(tmr, torch, make_handle, y, y_def, Tg, ref_frac, stream, P_list
 
 
 def second_half_arms(tmr, torch, synth, N, M, J, R, m, d, dop, photons, phase_iters, stream, world, iters,
-                     power_iters, keep=None, lanczos=0):
+                     power_iters, keep=None, lanczos=0, phase_tol=0.0):
     """The metric's second half on the learned-initialiser workload (the plain
     workload's fiber model drawn as a family: shared input mode basis V, own
     coupling and phases): the network (J N -> 1024 -> 1024 -> 2 N, GELU, BF16
@@ -402,7 +405,7 @@ def second_half_arms(tmr, torch, synth, N, M, J, R, m, d, dop, photons, phase_it
 
         def opts(init, prec, P):
             return dict(init=init, power_iters=P, clip=2.0, m=m, phase_iters=phase_iters, precision=prec,
-                        use_graph=1, lanczos=lanczos)
+                        use_graph=1, lanczos=lanczos, phase_tol=phase_tol)
 
         def make(init, prec):
             def mk(P):
@@ -557,7 +560,7 @@ def main():
     # host-buffer calls (the e2e leg) launch directly
     opt = dict(init="spectral", power_iters=args.power_iters, clip=2.0, m=m,
                phase_iters=args.phase_iters, seed=seed, tol=W["tol"], precision=args.precision,
-               use_graph=1, lanczos=args.lanczos)
+               use_graph=1, lanczos=args.lanczos, phase_tol=args.phase_tol)
     dop = dict(ny=ny, nx=nx, n_defocus=Nd, coef=0.05)
     h = tmr.tmr_create(N, M, J, dg, dop, opt, stream=stream.cuda_stream)
     sched = tmr.tmr_schedule(h)
@@ -837,7 +840,8 @@ def main():
         torch.cuda.empty_cache()
         arms = second_half_arms(tmr, torch, synth, N, M, J, R, m, d, dop, W["photons"], args.phase_iters,
                                 stream, world, args.iters, args.power_iters,
-                                keep=keep if cpu is not None else None, lanczos=args.lanczos)
+                                keep=keep if cpu is not None else None, lanczos=args.lanczos,
+                                phase_tol=args.phase_tol)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -851,7 +855,7 @@ def main():
                            "power_iters": args.power_iters, "iters": args.iters, "m": m,
                            "row_iters_mean": float(its[worked].mean()), "row_iters_max": int(its.max()),
                            "rows_solved": int(worked.sum()),
-                           "n_defocus": Nd, "phase_iters": args.phase_iters,
+                           "n_defocus": Nd, "phase_iters": args.phase_iters, "phase_tol": args.phase_tol,
                            "l2": f"inputs larger than L2 (y is {M * J * N * 4 >> 20} MB)",
                            "parallelism": f"{world} independent TMs, one per GPU"},
                 "schedule": {"code": sched, "layout": "one CTA per row (16 points per thread)" if sched == 16

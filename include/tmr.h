@@ -193,6 +193,11 @@ typedef struct {
                                tmr_grad and tmr_retrieve (the row loss reported is
                                this cost); the start and the defocus fit are
                                unchanged. */
+    double phase_tol;       /* 0 (default): the phase-offset fit runs phase_iters
+                               L-BFGS iterations or until a backtracking fails.
+                               > 0: it also stops after an accepted step that
+                               lowers g(phi) (Eq. optphase) by at most phase_tol
+                               g -- the loss has reached its noise floor. */
 } tmr_options;
 
 enum { TMR_COST_INTENSITY = 0, TMR_COST_AMPLITUDE = 1 };

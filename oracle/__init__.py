@@ -69,7 +69,7 @@ def lib():
             "orc_defocus_forward": ([dp, c_int, c_int, c_int, dp, c_dbl, dp, dp], c_int),
             "orc_phase_loss_grad": ([dp, dp, dp, c_int, c_int, c_int, dp, c_dbl, dp, dp], c_int),
             "orc_phase_fit": ([dp, dp, c_int, c_int, c_int, dp, c_dbl, c_int, c_int, dp, dp, ip,
-                               dp], c_int),
+                               dp, c_dbl], c_int),
             "orc_fidelity_rows": ([dp, dp, c_int, c_int, dp], c_int),
             "orc_set_probe_2d": ([c_int, c_int], c_int),
             "orc_set_cost": ([c_int], c_int),
@@ -313,8 +313,10 @@ def phase_loss_grad(phi, C, Ydef, grid, H=None, coef: float = 0.05):
 
 
 def phase_fit(C, Ydef, grid, H=None, coef: float = 0.05, iters: int = 100, m: int = 5,
-              weights=None):
-    """L-BFGS/Armijo fit of phi from phi = 0; returns (phi, iters_done, loss)."""
+              weights=None, tol: float = 0.0):
+    """L-BFGS/Armijo fit of phi from phi = 0; returns (phi, iters_done, loss).
+    tol > 0: stop after an accepted step that lowers the loss by at most tol
+    of its value."""
     C = _c128(C)
     Ydef = _f64(Ydef)
     ny, nx = grid
@@ -324,7 +326,7 @@ def phase_fit(C, Ydef, grid, H=None, coef: float = 0.05, iters: int = 100, m: in
     done = np.zeros(1, np.int32)
     loss = np.zeros(1)
     assert lib().orc_phase_fit(_p(C), _p(Ydef), C.shape[0], ny, nx, _p(Hc), coef, iters, m,
-                               _p(w), _p(phi), _ip(done), _p(loss)) == 0
+                               _p(w), _p(phi), _ip(done), _p(loss), float(tol)) == 0
     return phi, int(done[0]), loss[0]
 
 

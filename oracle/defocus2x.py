@@ -113,9 +113,10 @@ def loss_grad(phi, C, I, h):
     return g, grad
 
 
-def fit(C, I, h, iters: int = 100, m: int = 5, weights=None):
+def fit(C, I, h, iters: int = 100, m: int = 5, weights=None, tol: float = 0.0):
     """L-BFGS over phi from 0 with Armijo backtracking; phi shifted so that
-    arg sum_r w_r e^{j phi_r} = 0.  Returns (phi, g, iterations)."""
+    arg sum_r w_r e^{j phi_r} = 0.  tol > 0: stop after an accepted step that
+    lowers g by at most tol of its value.  Returns (phi, g, iterations)."""
     M = np.asarray(C).shape[1]
     phi = np.zeros(M)
     f, g = loss_grad(phi, C, I, h)
@@ -159,8 +160,11 @@ def fit(C, I, h, iters: int = 100, m: int = 5, weights=None):
             if len(S) > m:
                 S.pop(0)
                 Y.pop(0)
+        decrease = f - ft
         phi, f, g = phi + s, ft, gt
         done = it + 1
+        if tol > 0 and decrease <= tol * (f + decrease):
+            break
     w = np.ones(M) if weights is None else np.asarray(weights, dtype=float)
     phi = phi - np.angle(np.sum(w * np.exp(1j * phi)))
     return phi, f, done

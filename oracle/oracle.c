@@ -1145,9 +1145,12 @@ int orc_phase_loss_grad(const double *phi, const double *C, const double *Ydef, 
  * `iters` iterations, at a zero gradient or when backtracking fails.
  * Finally phi is shifted by a constant so that arg(sum_k w_k e^{i phi_k}) = 0
  * with weights w (NULL: w = 1). */
+/* tol > 0: stop after an accepted step whose decrease f_old - f_new is at
+ * most tol f_old (the loss has reached its floor); 0: only the iteration cap
+ * and a failed backtracking stop the fit. */
 int orc_phase_fit(const double *C, const double *Ydef, int Nd, int ny, int nx, const double *H,
                   double coef, int iters, int m, const double *weights, double *phi,
-                  int *iters_done, double *loss_out)
+                  int *iters_done, double *loss_out, double tol)
 {
     if (Nd < 0 || ny <= 0 || nx <= 0 || m <= 0) return -1;
     defocus_ctx c;
@@ -1194,8 +1197,10 @@ int orc_phase_fit(const double *C, const double *Ydef, int Nd, int ny, int nx, c
         if (accept_pair(sv, yv, P)) push_pair(S, Yh, &np, m, P, sv, yv);
         memcpy(phi, pt, sizeof(double) * P);
         memcpy(g, gn, sizeof(double) * P);
+        const double decrease = f - fn;
         f = fn;
         done = it + 1;
+        if (tol > 0 && decrease <= tol * (f + decrease)) break;
     }
     /* remove the free constant: arg(sum_k w_k e^{i phi_k}) = 0 */
     cplx acc = 0;

@@ -43,7 +43,8 @@ class tmr_options(ctypes.Structure):
                 ("use_graph", ctypes.c_int), ("workspace_limit", ctypes.c_size_t),
                 ("schedule", ctypes.c_int), ("tune_cache", ctypes.c_char_p),
                 ("wait_spins", ctypes.c_longlong), ("withhold_release", ctypes.c_int),
-                ("probe_n1", ctypes.c_int), ("lanczos", ctypes.c_int), ("cost", ctypes.c_int)]
+                ("probe_n1", ctypes.c_int), ("lanczos", ctypes.c_int), ("cost", ctypes.c_int),
+                ("phase_tol", ctypes.c_double)]
 
 
 class tmr_defocus_op(ctypes.Structure):

@@ -449,6 +449,8 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     if (o.init < TMR_INIT_RANDOM || o.init > TMR_INIT_LEARNED) return fail(TMR_ERR_INVALID_ARG, "opt.init");
     if (o.power_iters < 0 || o.phase_iters < 0 || o.tol < 0) return fail(TMR_ERR_INVALID_ARG, "negative option");
     if (o.lanczos != 0 && o.lanczos != 1) return fail(TMR_ERR_INVALID_ARG, "opt.lanczos must be 0 or 1");
+    if (!(o.phase_tol >= 0.0) || !std::isfinite(o.phase_tol))
+        return fail(TMR_ERR_INVALID_ARG, "opt.phase_tol must be finite and >= 0");
     if (o.cost != TMR_COST_INTENSITY && o.cost != TMR_COST_AMPLITUDE)
         return fail(TMR_ERR_INVALID_ARG, "opt.cost must be TMR_COST_INTENSITY or TMR_COST_AMPLITUDE");
     if (o.lanczos && o.power_iters > kMaxLanczos)
@@ -762,6 +764,7 @@ static tmr_status run_phase_fit(tmr_handle *h, const float2 *Tin, const float *d
     p.wait_spins = h->opt.wait_spins;
     p.withhold_release = h->opt.withhold_release != 0;
     p.kind = h->dkind;
+    p.tol = h->opt.phase_tol;
     TMR_CUDA(launch_phase_fit(p, h->stream), "phase-fit kernel");
     h->fit_ran = true;
     if (Tout) TMR_CUDA(launch_apply_phase(h->N, h->M, dphi, Tin, Tout, h->stream), "apply phase");

@@ -546,6 +546,33 @@ __device__ void pf_part_sums(const float *part, int nb, int P, int k0, int k1, d
     }
 }
 
+// Block sums of 32 values per thread (kPfDots): within each warp a
+// transposing xor tree leaves value l's warp sum in lane l (31 additions per
+// lane instead of 32 x 5), then 32 threads add the warps' sums in order.
+static_assert(kPfDots == 32, "block_sum32 reduces 32 values");
+__device__ void block_sum32(double (&v)[32], double *red, double *out)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+        const bool upper = (lane & h) != 0;
+#pragma unroll
+        for (int i = 0; i < h; i++) {
+            const double send = upper ? v[i] : v[i + h];
+            const double keep = upper ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+        }
+    }
+    red[lane * nw + warp] = v[0];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double s = 0.0;
+        for (int w = 0; w < nw; w++) s += red[threadIdx.x * nw + w];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
 // sum_b x[b] over b < nb by the lanes of one warp (lane-strided, xor tree):
 // every lane of every warp that calls it gets the same value
 __device__ __forceinline__ double warp_sum_nb(const double *x, int nb)
@@ -564,6 +591,7 @@ struct PFGram {
     double red[kPfDots];
     int slot[kPfSlots];
     int np, restart;
+    int floor_reached;  // the last accepted step lowered g by at most tol g (PhaseFitParams::tol)
 };
 
 // compact-form coefficients (one thread); restart = 1 selects p = -g / max|g|
@@ -750,7 +778,7 @@ __global__ void __launch_bounds__(512) k_phase_fit(PhaseFitParams Pp)
     // reduce kPfDots per-thread values over the grid: block sums to pdot[b], a
     // grid barrier, then every CTA adds the nb partials in order into G.red
     auto grid_dots = [&](double (&v)[kPfDots], double vmax) -> bool {
-        block_sum<kPfDots, double>(v, red, out);
+        block_sum32(v, red, out);
         __shared__ double mx[32];
         double mv = vmax;
         for (int o = 16; o > 0; o >>= 1) mv = fmax(mv, __shfl_xor_sync(0xffffffffu, mv, o));
@@ -832,6 +860,7 @@ __global__ void __launch_bounds__(512) k_phase_fit(PhaseFitParams Pp)
     const double f_start = warp_sum_nb(W.fpart, nb);
     if (tid == 0) {
         G.f = f_start;
+        G.floor_reached = 0;
         G.gg = G.red[4 * kPfSlots + 1];
         G.gmax = G.red[kPfDots - 2];
         G.np = 0;
@@ -926,6 +955,7 @@ __global__ void __launch_bounds__(512) k_phase_fit(PhaseFitParams Pp)
                 const double sy = t[4 * np + 0], yy = t[4 * np + 1], ss = t[4 * kPfSlots + 0];
                 G.gg = t[4 * kPfSlots + 1];
                 G.gmax = t[kPfDots - 2];
+                G.floor_reached = Pp.tol > 0.0 && G.f - ft <= Pp.tol * G.f;
                 G.f = ft;
                 if (sy > 1e-10 * sqrt(ss) * sqrt(yy) && sy > 0.0) {
                     G.rD[np] = 1.0 / sy;
@@ -951,6 +981,7 @@ __global__ void __launch_bounds__(512) k_phase_fit(PhaseFitParams Pp)
             __syncthreads();
         }
         done = it + 1;
+        if (G.floor_reached) break;
     }
 
     // ---- remove the free constant: arg(sum_k w_k e^{i phi_k}) = 0 ----

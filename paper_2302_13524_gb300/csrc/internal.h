@@ -176,6 +176,7 @@ struct PhaseFitParams {
     long long wait_spins;   // polls before a grid-barrier wait gives up
     bool withhold_release;  // test hook: the barrier is never released
     int kind;               // 0: same-grid operator; 1: angular spectrum with 2x padding (Ydef [Nd][4P])
+    double tol;             // > 0: stop after an accepted step lowering g by at most tol g
 };
 size_t phase_fit_workspace_doubles(int P, int Nd, int m, int grid);
 int phase_fit_grid(int ny, int nx, int Nd);

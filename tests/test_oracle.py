@@ -452,6 +452,33 @@ def test_phase_fit_recovers_planted_offsets():
     assert oracle.matrix_fidelity(T_est, T) < 0.5
 
 
+def test_phase_fit_tolerance_stops_at_the_first_small_decrease():
+    """tol > 0 stops after the first accepted step that lowers the loss by at
+    most tol of its value: the same fit capped at k iterations (tol = 0) gives
+    the loss after each step, and the stop is the first k where the decrease
+    falls below the bar (noisy images, so the loss levels off above zero)."""
+    M, N, J = 128, 16, 4
+    grid = (16, 8)
+    T = synth.tm_iid(M, N, seed=3)
+    _, d = synth.mask_phases(J, N, seed=3)
+    Nd = 24
+    Yd = oracle.defocus_forward(oracle.defocus_fields(T, d, Nd), grid)
+    rng = np.random.default_rng(27)
+    Yd = Yd * (1 + 0.02 * rng.standard_normal(Yd.shape))
+    T_est = np.exp(-1j * rng.uniform(-np.pi, np.pi, M))[:, None] * T
+    C = oracle.defocus_fields(T_est, d, Nd)
+    losses = [oracle.phase_fit(C, Yd, grid, iters=0)[2]]
+    for k in range(1, 41):
+        phi_k, done_k, loss_k = oracle.phase_fit(C, Yd, grid, iters=k)
+        assert done_k == k
+        losses.append(loss_k)
+    for tol in (0.1, 0.03, 0.02):
+        want = next(k for k in range(1, 41) if losses[k - 1] - losses[k] <= tol * losses[k - 1])
+        phi, done, loss = oracle.phase_fit(C, Yd, grid, iters=40, tol=tol)
+        assert done == want, (tol, done, want)
+        assert loss == losses[want]
+
+
 # ---------------------------------------------------------- learned-init MLP
 def test_mlp_gelu_matches_erf_definition():
     import math
