@@ -54,6 +54,10 @@ WORKLOADS = {
     # failed-row fraction against J with the 2D probing DFT (64 x 64 modes)
     "jsweep": dict(N=4096, J=8, R=2200, ny=64, nx=64, photons=None, iters=200, tol=0.0,
                    desc="jsweep: N=4096 (64x64 2D probing DFT), M=4096, J=3..8, noiseless"),
+    # the paper's Table 1 comparison: the probing operator by FFTs against the
+    # explicit dense matrix ("without FFT") on 1024 rows (32 x 32 pixels), J = 8
+    "dense": dict(N=4096, J=8, R=2200, ny=32, nx=32, photons=None, iters=100, tol=0.0,
+                  desc="dense: N=4096, M=1024 (32x32), J=8, modes R=2200, noiseless; FFT vs explicit Q"),
     "camera": dict(N=2048, J=4, R=1100, ny=128, nx=64, photons=3000.0, iters=100, tol=0.0,
                    camera=dict(radius=0.45, leak=1e-3, energy_frac=0.999),
                    desc="camera: 8192 uint16 probe frames + 50 defocus frames of 256x128 pixels, "
@@ -518,6 +522,73 @@ def run_jsweep(args):
     return 0
 
 
+# ---------------------------------------------------------------- Table 1: with and without FFT
+def run_dense(args):
+    """The paper's Table 1 restated on one GPU: the loss and gradient of all
+    rows (the work of an L-BFGS iteration that depends on how Q is applied)
+    through the FFT path and through the explicit dense Q (cuBLAS complex
+    products, FP32 and FP32 emulated on the tensor cores by BF16x9), on
+    1024 rows of an N = 4096 mode-model TM with J = 8 masks (the paper:
+    1024 rows, N = 8192, M = 8); plus the whole FFT retrieval of those rows.
+    Times are CUDA-event means after warm-up."""
+    import torch
+    import paper_2302_13524_gb300 as tmr
+    import synth
+    W = WORKLOADS["dense"]
+    N, J, R = W["N"], W["J"], W["R"]
+    M = W["ny"] * W["nx"]
+    T = torch.from_numpy(synth.tm_modes(M, N, R, seed=0, dtype=np.complex64)).cuda()
+    _, d = synth.mask_phases(J, N, seed=0)
+    dg = torch.from_numpy(np.ascontiguousarray(d, dtype=np.complex64)).cuda()
+    y = torch.empty((M, J, N), dtype=torch.float32, device="cuda")
+    T1 = (T * 1.05).contiguous()
+    loss = torch.empty(M, dtype=torch.float32, device="cuda")
+    G = torch.empty((M, N), dtype=torch.complex64, device="cuda")
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {}
+    with tmr.tmr_create(N, M, J, dg, None, dict(init="spectral", power_iters=args.power_iters,
+                                                lanczos=args.lanczos, clip=2.0)) as h:
+        tmr.tmr_forward(h, T, y)
+        out["fft"] = timed(lambda: tmr.tmr_grad(h, T1, y, loss, G))
+        To = torch.empty((M, N), dtype=torch.complex64, device="cuda")
+        retr_ms = timed(lambda: tmr.tmr_retrieve(h, y, None, args.iters, To), reps=2)
+    G_fft = G.clone()
+    errs = {}
+    for mode, name in ((1, "dense_fp32"), (2, "dense_bf16x9")):
+        try:
+            with tmr.tmr_create(N, M, J, dg, None, dict(dense=mode)) as h:
+                out[name] = timed(lambda: tmr.tmr_grad(h, T1, y, loss, G))
+                errs[name] = float(torch.max(torch.abs(G - G_fft)) / torch.max(torch.abs(G_fft)))
+        except tmr.TMRError as e:
+            out[name] = None
+            errs[name] = str(e)
+    gemm_flops = 2 * 8.0 * M * N * (J * N)  # two complex products per gradient
+    line = {"metric": "gradient evaluation of all rows: FFT vs dense Q (Table 1)", "unit": "ms",
+            "n_gpus": 1, "higher_is_better": False, "data": "synthetic, noiseless",
+            "config": {"workload": W["desc"], "dtype": "f32"},
+            "value": out["fft"], "eval_ms": out,
+            "speedup_fft_over_dense": {k: (v / out["fft"] if v else None) for k, v in out.items() if k != "fft"},
+            "dense_tflops": {k: (gemm_flops / (v / 1e3) / 1e12 if v else None) for k, v in out.items()
+                             if k != "fft"},
+            "dense_rel_error_vs_fft": errs,
+            "fft_retrieval_ms": retr_ms,
+            "fft_retrieval": f"{args.power_iters} {'Lanczos' if args.lanczos else 'power'} + {args.iters} "
+                             f"L-BFGS iterations"}
+    print(json.dumps(line))
+    return 0
+
+
 # ---------------------------------------------------------------- our arm
 def main():
     args = parse()
@@ -525,6 +596,8 @@ def main():
         return run_reference(args)
     if args.workload == "jsweep":
         return run_jsweep(args)
+    if args.workload == "dense":
+        return run_dense(args)
     import torch
     rank, world, local = dist_env()
     if world > 1:

@@ -198,6 +198,18 @@ typedef struct {
                                > 0: it also stops after an accepted step that
                                lowers g(phi) (Eq. optphase) by at most phase_tol
                                g -- the loss has reached its noise floor. */
+    int dense;              /* 0 (default): the probing operator by FFTs.  1 or 2: the
+                               paper's "without FFT" evaluation (Table 1) for
+                               tmr_forward and tmr_grad: Q (J N x N, complex64,
+                               Q[j N + k][n] = exp(-2 pi i k n / N) d_j[n]) is built
+                               on the device at the first call (8 J N^2 bytes, plus
+                               two J N x M scratch products), and Z = T Q^T and
+                               G = -4 (Z .* r) conj(Q) (amplitude cost: its
+                               coefficient) run as complex matrix products over
+                               all rows (cuBLAS): 1 = FP32, 2 = FP32 emulated on
+                               the tensor cores with three BF16 terms per operand.
+                               tmr_retrieve and the defocus calls return
+                               TMR_ERR_UNSUPPORTED; 1D DFT only (probe_n1 0). */
 } tmr_options;
 
 enum { TMR_COST_INTENSITY = 0, TMR_COST_AMPLITUDE = 1 };

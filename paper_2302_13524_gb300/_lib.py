@@ -44,7 +44,7 @@ class tmr_options(ctypes.Structure):
                 ("schedule", ctypes.c_int), ("tune_cache", ctypes.c_char_p),
                 ("wait_spins", ctypes.c_longlong), ("withhold_release", ctypes.c_int),
                 ("probe_n1", ctypes.c_int), ("lanczos", ctypes.c_int), ("cost", ctypes.c_int),
-                ("phase_tol", ctypes.c_double)]
+                ("phase_tol", ctypes.c_double), ("dense", ctypes.c_int)]
 
 
 class tmr_defocus_op(ctypes.Structure):

@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
                     raise RuntimeError(f"nvcc failed for {c[-3]}")
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcublas"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             print(r.stdout + r.stderr)

@@ -101,6 +101,8 @@ struct tmr_handle {
     // L-BFGS pair workspace of the one-CTA-per-row schedule (pair_ctas regions)
     float2 *pairs = nullptr;
     int pair_ctas = 0;
+    // the probing operator as a dense matrix (opt.dense), made on first use
+    DenseState dense;
     // Lanczos vectors of the spectral start (krylov_units regions of power_iters N)
     float2 *krylov = nullptr;
     int krylov_units = 0;
@@ -449,6 +451,9 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     if (o.init < TMR_INIT_RANDOM || o.init > TMR_INIT_LEARNED) return fail(TMR_ERR_INVALID_ARG, "opt.init");
     if (o.power_iters < 0 || o.phase_iters < 0 || o.tol < 0) return fail(TMR_ERR_INVALID_ARG, "negative option");
     if (o.lanczos != 0 && o.lanczos != 1) return fail(TMR_ERR_INVALID_ARG, "opt.lanczos must be 0 or 1");
+    if (o.dense < 0 || o.dense > 2) return fail(TMR_ERR_INVALID_ARG, "opt.dense must be 0, 1 or 2");
+    if (o.dense && o.probe_n1 != 0)
+        return fail(TMR_ERR_UNSUPPORTED, "the dense evaluation uses the 1D DFT (probe_n1 0)");
     if (!(o.phase_tol >= 0.0) || !std::isfinite(o.phase_tol))
         return fail(TMR_ERR_INVALID_ARG, "opt.phase_tol must be finite and >= 0");
     if (o.cost != TMR_COST_INTENSITY && o.cost != TMR_COST_AMPLITUDE)
@@ -683,6 +688,24 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     return TMR_OK;
 }
 
+// the dense operator's matrix and scratch (opt.dense), made at the first call
+static tmr_status dense_ready(tmr_handle *h)
+{
+    size_t bytes = 0;
+    const size_t need = (h->dense.Q ? 0 : sizeof(float2) * (size_t)h->J * h->N * h->N) +
+                        (h->dense.Z ? 0 : 2 * sizeof(float2) * (size_t)h->J * h->N * (h->M > 0 ? h->M : 1));
+    if (h->opt.workspace_limit && h->held + need > h->opt.workspace_limit)
+        return fail(TMR_ERR_OOM, "the dense operator's matrix exceeds workspace_limit");
+    const cudaError_t e = dense_prepare(h->dense, h->N, h->M, h->J, h->masks, h->stream, &bytes);
+    h->held += bytes;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(TMR_ERR_OOM, "dense operator matrix");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "dense operator");
+    return TMR_OK;
+}
+
 tmr_status tmr_forward(tmr_handle *h, const void *T, float *Y)
 {
     tmr::set_last_error("");
@@ -690,10 +713,16 @@ tmr_status tmr_forward(tmr_handle *h, const void *T, float *Y)
     const size_t MN = (size_t)h->M * h->N, MK = MN * h->J;
     void *dT, *dY;
     tmr_status st;
+    if (h->opt.dense && (st = dense_ready(h)) != TMR_OK) return st;
     if ((st = stage(h, ST_TIN, T, sizeof(float2) * MN, true, &dT)) != TMR_OK) return st;
     if ((st = stage(h, ST_Y, Y, sizeof(float) * MK, false, &dY)) != TMR_OK) return st;
-    if ((st = check_launch(launch_forward(h->N, h->M, h->J, (const float2 *)dT, h->masks, h->tw,
-                                          (float *)dY, h->stream, h->xk), "forward kernel")) != TMR_OK)
+    if (h->opt.dense) {
+        if ((st = check_launch(dense_forward(h->dense, h->opt.dense, h->N, h->M, h->J, (const float2 *)dT,
+                                             (float *)dY, h->stream),
+                               "dense forward")) != TMR_OK)
+            return st;
+    } else if ((st = check_launch(launch_forward(h->N, h->M, h->J, (const float2 *)dT, h->masks, h->tw,
+                                                 (float *)dY, h->stream, h->xk), "forward kernel")) != TMR_OK)
         return st;
     bool synced = false;
     if ((st = unstage(h, Y, dY, sizeof(float) * MK, &synced)) != TMR_OK) return st;
@@ -712,10 +741,16 @@ tmr_status tmr_grad(tmr_handle *h, const void *T, const float *Y, float *loss, v
     if ((st = stage(h, ST_Y, Y, sizeof(float) * MK, true, &dY)) != TMR_OK) return st;
     if (loss && (st = stage(h, ST_LOSS, loss, sizeof(float) * h->M, false, &dL)) != TMR_OK) return st;
     if (G && (st = stage(h, ST_TOUT, G, sizeof(float2) * MN, false, &dG)) != TMR_OK) return st;
-    if ((st = check_launch(launch_grad(h->N, h->M, h->J, (const float2 *)dT, h->masks, h->tw,
+    if (h->opt.dense) {
+        if ((st = dense_ready(h)) != TMR_OK) return st;
+        if ((st = check_launch(dense_grad(h->dense, h->opt.dense, h->N, h->M, h->J, (const float2 *)dT,
+                                          (const float *)dY, (float *)dL, (float2 *)dG, h->opt.cost, h->stream),
+                               "dense gradient")) != TMR_OK)
+            return st;
+    } else if ((st = check_launch(launch_grad(h->N, h->M, h->J, (const float2 *)dT, h->masks, h->tw,
                                        (const float *)dY, (float *)dL, (float2 *)dG, h->stream, h->xk,
                                        h->opt.cost),
-                           "gradient kernel")) != TMR_OK)
+                                              "gradient kernel")) != TMR_OK)
         return st;
     bool synced = false;
     if (loss && (st = unstage(h, loss, dL, sizeof(float) * h->M, &synced)) != TMR_OK) return st;
@@ -778,6 +813,7 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
     tmr::set_last_error("");
     if (!h || !y || !T_out) return fail(TMR_ERR_INVALID_ARG, "NULL argument");
     if (iters < 0) return fail(TMR_ERR_INVALID_ARG, "iters must be >= 0");
+    if (h->opt.dense) return fail(TMR_ERR_UNSUPPORTED, "the dense evaluation serves tmr_forward and tmr_grad only");
     const bool fit = y_def != nullptr;
     if (fit && !h->has_defocus) return fail(TMR_ERR_INVALID_ARG, "y_def given but the handle has no defocus operator");
     {
@@ -939,6 +975,7 @@ tmr_status tmr_retrieve_from(tmr_handle *h, const void *T_init, const float *y, 
 tmr_status tmr_defocus_forward(tmr_handle *h, const void *T, float *Y_def)
 {
     tmr::set_last_error("");
+    if (h && h->opt.dense) return fail(TMR_ERR_UNSUPPORTED, "the dense evaluation serves tmr_forward and tmr_grad only");
     if (!h || !T || !Y_def) return fail(TMR_ERR_INVALID_ARG, "NULL argument");
     if (!h->has_defocus) return fail(TMR_ERR_UNSUPPORTED, "handle has no defocus operator");
     const size_t MN = (size_t)h->M * h->N;
@@ -960,6 +997,7 @@ tmr_status tmr_defocus_forward(tmr_handle *h, const void *T, float *Y_def)
 tmr_status tmr_defocus_fit(tmr_handle *h, const void *T_est, const float *y_def, double *phi, void *T_out)
 {
     tmr::set_last_error("");
+    if (h && h->opt.dense) return fail(TMR_ERR_UNSUPPORTED, "the dense evaluation serves tmr_forward and tmr_grad only");
     if (!h || !T_est || !y_def) return fail(TMR_ERR_INVALID_ARG, "NULL argument");
     if (!h->has_defocus) return fail(TMR_ERR_UNSUPPORTED, "handle has no defocus operator");
     const size_t MN = (size_t)h->M * h->N;

@@ -29,7 +29,7 @@ __device__ __forceinline__ float cost_coef(int cost, float2 z, float y, float &f
     return r;
 }
 
-__device__ __forceinline__ float cost_grad_scale(int cost) { return cost == COST_AMPLITUDE ? 2.f : -4.f; }
+__host__ __device__ __forceinline__ float cost_grad_scale(int cost) { return cost == COST_AMPLITUDE ? 2.f : -4.f; }
 
 // Half the first and second derivatives of phi(al) = sum (a - |z + al w|)^2
 // for one element, added to d1 and d2 (a term with |u| = 0 adds |w|^2 to d2

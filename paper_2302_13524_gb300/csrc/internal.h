@@ -180,6 +180,20 @@ struct PhaseFitParams {
 };
 size_t phase_fit_workspace_doubles(int P, int Nd, int m, int grid);
 int phase_fit_grid(int ny, int nx, int Nd);
+// The probing operator as an explicit dense matrix (dense.cu, the paper's
+// "without FFT" evaluation): Q [J N][N] and cuBLAS, made on first use.
+// mode 1: FP32 complex products; 2: FP32 emulated on the tensor cores (BF16x9).
+struct DenseState {
+    void *blas = nullptr;  // cublasHandle_t
+    float2 *Q = nullptr, *Z = nullptr, *C = nullptr;
+    ~DenseState();
+    void release();
+};
+cudaError_t dense_prepare(DenseState &ds, int N, int M, int J, const float2 *masks, cudaStream_t s,
+                          size_t *bytes_out);
+cudaError_t dense_forward(DenseState &ds, int mode, int N, int M, int J, const float2 *T, float *Y, cudaStream_t s);
+cudaError_t dense_grad(DenseState &ds, int mode, int N, int M, int J, const float2 *T, const float *y, float *loss,
+                       float2 *G, int cost, cudaStream_t s);
 bool defocus_supported(int ny, int nx);
 bool defocus2x_supported(int ny, int nx);
 cudaError_t launch_make_H2x(int ny, int nx, double wavelength, double na, double zd, double pixel, float2 *H,
