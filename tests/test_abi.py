@@ -115,3 +115,23 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_arrays_on_another_gpu_are_refused():
+    """An array on a GPU other than the current one is refused with
+    INVALID_ARG before any kernel could touch it (only where two GPUs are
+    visible; one GPU or none: skipped)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available() or torch.cuda.device_count() < 2:
+        pytest.skip("needs two visible GPUs")
+    tmr = pytest.importorskip("paper_2302_13524_gb300")
+    import numpy as np
+    N, M, J = 64, 4, 4
+    d = torch.ones((J, N), dtype=torch.complex64, device="cuda:0")
+    with tmr.tmr_create(N, M, J, d) as h:
+        T_other = torch.zeros((M, N), dtype=torch.complex64, device="cuda:1")
+        Y = torch.empty((M, J, N), dtype=torch.float32, device="cuda:0")
+        with pytest.raises(tmr.TMRError) as ei:
+            tmr.tmr_forward(h, T_other, Y)
+        assert ei.value.status == tmr.TMR_ERR_INVALID_ARG
+    assert np.isfinite(0.0)
