@@ -125,7 +125,6 @@ def test_arrays_on_another_gpu_are_refused():
     if not torch.cuda.is_available() or torch.cuda.device_count() < 2:
         pytest.skip("needs two visible GPUs")
     tmr = pytest.importorskip("paper_2302_13524_gb300")
-    import numpy as np
     N, M, J = 64, 4, 4
     d = torch.ones((J, N), dtype=torch.complex64, device="cuda:0")
     with tmr.tmr_create(N, M, J, d) as h:
@@ -134,4 +133,3 @@ def test_arrays_on_another_gpu_are_refused():
         with pytest.raises(tmr.TMRError) as ei:
             tmr.tmr_forward(h, T_other, Y)
         assert ei.value.status == tmr.TMR_ERR_INVALID_ARG
-    assert np.isfinite(0.0)
