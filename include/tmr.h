@@ -208,8 +208,14 @@ typedef struct {
                                coefficient) run as complex matrix products over
                                all rows (cuBLAS): 1 = FP32, 2 = FP32 emulated on
                                the tensor cores with three BF16 terms per operand.
-                               tmr_retrieve and the defocus calls return
-                               TMR_ERR_UNSUPPORTED; 1D DFT only (probe_n1 0). */
+                               tmr_retrieve then runs Algorithm 1 with every FFT
+                               replaced by the matrix-vector product with the DFT
+                               matrix (one mask per CTA, N^2 multiply-adds per
+                               transform, the table of W_N^m in shared memory):
+                               the paper's "TM retrieval without FFT", without
+                               the phase-offset fit (y_def must be NULL; the
+                               defocus calls return TMR_ERR_UNSUPPORTED).  FP32,
+                               probe_n1 0, N a power of two in 64..4096. */
 } tmr_options;
 
 enum { TMR_COST_INTENSITY = 0, TMR_COST_AMPLITUDE = 1 };

@@ -119,7 +119,8 @@ struct tmr_handle {
     bool last_had_fit = false;
     int G = 1;  // solver schedule: masks per CTA
     int prec = TMR_PREC_FP32;
-    int xk = 0;  // transform kind of the kernels: 0 FP32 1D DFT, 1 mixed, 2 FP32 2D probing DFT
+    int xk = 0;  // transform kind of the kernels: 0 FP32 1D DFT, 1 mixed, 2 FP32 2D probing DFT,
+                 // 3 the matrix-vector DFT of the dense ("without FFT") solver
     void *y16 = nullptr;   // mixed precision: FP16 intensities [M][J][N]
     float *ysc = nullptr;  // and their row scales [M]
     cudaStream_t own_stream = nullptr;  // created for graph capture when the caller gave none
@@ -348,7 +349,8 @@ std::string tune_key(int dev, int N, int J, int m, int prec, int cost)
     cudaGetDeviceProperties(&prop, dev);
     char k[320];
     snprintf(k, sizeof(k), "%s|sm%d%d|N%d|J%d|m%d%s%s", prop.name, prop.major, prop.minor, N, J, m,
-             prec == 1 ? "|mixed" : (prec == 2 ? "|2d" : ""), cost == TMR_COST_AMPLITUDE ? "|amp" : "");
+             prec == 1 ? "|mixed" : (prec == 2 ? "|2d" : (prec == 3 ? "|densemv" : "")),
+             cost == TMR_COST_AMPLITUDE ? "|amp" : "");
     for (char *c = k; *c; c++)
         if (*c == '"' || *c == '\\') *c = '_';
     return k;
@@ -452,8 +454,9 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     if (o.power_iters < 0 || o.phase_iters < 0 || o.tol < 0) return fail(TMR_ERR_INVALID_ARG, "negative option");
     if (o.lanczos != 0 && o.lanczos != 1) return fail(TMR_ERR_INVALID_ARG, "opt.lanczos must be 0 or 1");
     if (o.dense < 0 || o.dense > 2) return fail(TMR_ERR_INVALID_ARG, "opt.dense must be 0, 1 or 2");
-    if (o.dense && o.probe_n1 != 0)
-        return fail(TMR_ERR_UNSUPPORTED, "the dense evaluation uses the 1D DFT (probe_n1 0)");
+    if (o.dense && (o.probe_n1 != 0 || o.precision != TMR_PREC_FP32 || !fft_supported(N)))
+        return fail(TMR_ERR_UNSUPPORTED,
+                    "the dense operator runs FP32 with the 1D DFT (probe_n1 0) for N a power of two in 64..4096");
     if (!(o.phase_tol >= 0.0) || !std::isfinite(o.phase_tol))
         return fail(TMR_ERR_INVALID_ARG, "opt.phase_tol must be finite and >= 0");
     if (o.cost != TMR_COST_INTENSITY && o.cost != TMR_COST_AMPLITUDE)
@@ -470,7 +473,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
     if (o.probe_n1 != 0 && (o.precision != TMR_PREC_FP32 || N % o.probe_n1 != 0 || fft_table_2d(N, o.probe_n1, nullptr) < 0))
         return fail(TMR_ERR_UNSUPPORTED, "the 2D probing DFT needs FP32 and N = 512 (n1 = 8 or 64) or N = 4096 "
                                          "(n1 = 8, 64 or 512)");
-    const int xk = o.precision == TMR_PREC_MIXED ? 1 : (o.probe_n1 ? 2 : 0);
+    const int xk = o.precision == TMR_PREC_MIXED ? 1 : (o.probe_n1 ? 2 : (o.dense ? 3 : 0));
     if (!xform_supported(N))
         return fail(TMR_ERR_UNSUPPORTED, "N must be a power of two in 64..4096 or another length in 16..4096");
     if (J > kMaxMasks) return fail(TMR_ERR_UNSUPPORTED, "J must be at most 8");
@@ -545,9 +548,12 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
             return cuda_fail(e, "copy masks");
         }
     }
-    const int twn = h->xk == 2 ? fft_table_2d(N, o.probe_n1, nullptr) : xform_table_prec(N, h->prec, nullptr);
+    const int twn = h->xk == 2   ? fft_table_2d(N, o.probe_n1, nullptr)
+                    : h->xk == 3 ? dense_mv_table(N, nullptr)
+                                 : xform_table_prec(N, h->prec, nullptr);
     std::vector<float2> tw(twn > 0 ? twn : 1);
     if (h->xk == 2) fft_table_2d(N, o.probe_n1, tw.data());
+    else if (h->xk == 3) dense_mv_table(N, tw.data());
     else xform_table_prec(N, h->prec, tw.data());
     TRY(halloc(h, (void **)&h->tw, sizeof(float2) * tw.size(), "twiddles"));
     if (cudaMemcpy(h->tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -813,7 +819,8 @@ static tmr_status retrieve_impl(tmr_handle *h, const void *T_init, const float *
     tmr::set_last_error("");
     if (!h || !y || !T_out) return fail(TMR_ERR_INVALID_ARG, "NULL argument");
     if (iters < 0) return fail(TMR_ERR_INVALID_ARG, "iters must be >= 0");
-    if (h->opt.dense) return fail(TMR_ERR_UNSUPPORTED, "the dense evaluation serves tmr_forward and tmr_grad only");
+    if (h->opt.dense && y_def)
+        return fail(TMR_ERR_UNSUPPORTED, "the dense (without FFT) solver runs without the phase-offset fit");
     const bool fit = y_def != nullptr;
     if (fit && !h->has_defocus) return fail(TMR_ERR_INVALID_ARG, "y_def given but the handle has no defocus operator");
     {
@@ -975,7 +982,7 @@ tmr_status tmr_retrieve_from(tmr_handle *h, const void *T_init, const float *y, 
 tmr_status tmr_defocus_forward(tmr_handle *h, const void *T, float *Y_def)
 {
     tmr::set_last_error("");
-    if (h && h->opt.dense) return fail(TMR_ERR_UNSUPPORTED, "the dense evaluation serves tmr_forward and tmr_grad only");
+    if (h && h->opt.dense) return fail(TMR_ERR_UNSUPPORTED, "the dense operator runs without the defocus calls");
     if (!h || !T || !Y_def) return fail(TMR_ERR_INVALID_ARG, "NULL argument");
     if (!h->has_defocus) return fail(TMR_ERR_UNSUPPORTED, "handle has no defocus operator");
     const size_t MN = (size_t)h->M * h->N;
@@ -997,7 +1004,7 @@ tmr_status tmr_defocus_forward(tmr_handle *h, const void *T, float *Y_def)
 tmr_status tmr_defocus_fit(tmr_handle *h, const void *T_est, const float *y_def, double *phi, void *T_out)
 {
     tmr::set_last_error("");
-    if (h && h->opt.dense) return fail(TMR_ERR_UNSUPPORTED, "the dense evaluation serves tmr_forward and tmr_grad only");
+    if (h && h->opt.dense) return fail(TMR_ERR_UNSUPPORTED, "the dense operator runs without the defocus calls");
     if (!h || !T_est || !y_def) return fail(TMR_ERR_INVALID_ARG, "NULL argument");
     if (!h->has_defocus) return fail(TMR_ERR_UNSUPPORTED, "handle has no defocus operator");
     const size_t MN = (size_t)h->M * h->N;

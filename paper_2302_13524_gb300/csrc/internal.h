@@ -124,6 +124,9 @@ cudaError_t launch_solver_row_amp(int N, const SolverParams &p, cudaStream_t s, 
 cudaError_t launch_solver_amp(int N, int G, const SolverParams &p, cudaStream_t s, int *clusters_out);
 bool solver_cost_supported(int N, int G, int prec, int cost);
 bool solver_variant_exists(int N, int G, int prec = 0);
+// transform kind 3: the matrix-vector DFT (solver_dense.cu, the "without FFT" solver)
+long long solver_dispatch_dense(int N, int G, int what, const SolverParams *p, cudaStream_t s, int *clusters_out);
+int dense_mv_table(int N, float2 *out);
 // schedule G usable for (N, J): variant exists, J % G == 0 for cluster schedules
 bool solver_schedule_valid(int N, int J, int G, int prec = 0);
 // one-CTA-per-row schedule: CTAs resident at once (the pair regions a launch needs)

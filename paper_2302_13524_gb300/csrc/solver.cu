@@ -9,6 +9,7 @@ namespace tmr {
 bool solver_variant_exists(int N, int G, int prec)
 {
     if (prec == 2) return (G == 1 || G == 2 || G == 4) && (N == 512 || N == 4096) && G * fft_threads(N) <= 512;
+    if (prec == 3) return G == 1 && fft_supported(N);
     if (G == kRowSchedule) return prec == 0 && (N == 512 || N == 1024 || N == 2048);
     if (G == kBlueFullSchedule) return prec == 0 && N > 2048 && N <= 2731;
     if (G != 1 && G != 2 && G != 4) return false;
@@ -37,6 +38,7 @@ static long long solver_dispatch(int N, int G, int what, const SolverParams *p, 
     if (G == kRowSchedule) return solver_dispatch_row(N, what, p, s, clusters_out);
     if (G == kBlueFullSchedule) return solver_dispatch_blue8192(N, 6, what, p, s, clusters_out);
     if (p->prec == 2) return solver_dispatch_2d(N, G, what, p, s, clusters_out);
+    if (p->prec == 3) return solver_dispatch_dense(N, G, what, p, s, clusters_out);
     if (p->prec != 0) return solver_dispatch_mixed(N, G, what, p, s, clusters_out);
     if (!fft_supported(N)) return solver_dispatch_blue(N, G, what, p, s, clusters_out);
     TMR_SOLVER_N(64)

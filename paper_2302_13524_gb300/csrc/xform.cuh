@@ -87,6 +87,70 @@ struct XfPow2 {
     }
 };
 
+// XfDenseMV<N>: the probing DFT as an explicit matrix-vector product, the
+// paper's "TM retrieval without FFT" (Sec. 3, Table 1: Algorithm 1 with the
+// FFTs replaced by matrix-vector multiplication).  The team writes its masked
+// vector to shared memory in natural order and every thread forms its
+// outputs z[k] = sum_n W_N^{kn} x[n] from the table W_N^m, m < N (made in
+// FP64 on the host): N complex multiply-adds per output, N^2 per transform.
+template <int N_>
+struct XfDenseMV {
+    static constexpr bool kBlue = false;
+    static constexpr int kN = N_;
+    static constexpr int NT = fft_threads(N_);
+    static constexpr int NE = N_ / NT;
+    static constexpr int LBUF = N_;
+    static constexpr int BUFS = 1;
+    static constexpr int NCONST = N_;
+    __host__ __device__ static constexpr int shared_consts(int n) { return NCONST; }
+
+    float2 dm[NE];
+
+    __device__ __forceinline__ static bool valid(int e, int tid, int n) { return true; }
+
+    __device__ __forceinline__ void setup(const float2 *__restrict__ mask, const float2 *__restrict__ chirp,
+                                          int n, int tid)
+    {
+#pragma unroll
+        for (int e = 0; e < NE; e++) dm[e] = mask[tid + e * NT];
+    }
+    template <int SIGN>
+    __device__ __forceinline__ void mv(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid)
+    {
+#pragma unroll
+        for (int e = 0; e < NE; e++) buf[tid + e * NT] = x[e];
+        __syncthreads();
+        float2 acc[NE];
+#pragma unroll
+        for (int e = 0; e < NE; e++) acc[e] = make_float2(0.f, 0.f);
+        for (int n = 0; n < N_; n++) {
+            const float2 v = buf[n];
+#pragma unroll
+            for (int e = 0; e < NE; e++) {
+                float2 w = cst[((tid + e * NT) * n) & (N_ - 1)];
+                if (SIGN > 0) w.y = -w.y;
+                acc[e].x = fmaf(w.x, v.x, fmaf(-w.y, v.y, acc[e].x));
+                acc[e].y = fmaf(w.x, v.y, fmaf(w.y, v.x, acc[e].y));
+            }
+        }
+        __syncthreads();  // buf is read before the caller reuses it
+#pragma unroll
+        for (int e = 0; e < NE; e++) x[e] = acc[e];
+    }
+    __device__ __forceinline__ void fwd(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid)
+    {
+#pragma unroll
+        for (int e = 0; e < NE; e++) x[e] = cmul(x[e], dm[e]);
+        mv<-1>(x, buf, cst, tid);
+    }
+    __device__ __forceinline__ void adj(float2 (&x)[NE], float2 *buf, const float2 *cst, int tid)
+    {
+        mv<+1>(x, buf, cst, tid);
+#pragma unroll
+        for (int e = 0; e < NE; e++) x[e] = cmulc(x[e], dm[e]);
+    }
+};
+
 // XfPow2D<N>: the paper's 2D probing DFT (Eq. probingmatrix: K the 2D Fourier
 // transform of the row read as an n1 x n2 array, n1 n2 = N) through the same
 // register Stockham passes.  The Stockham passes whose stride Ns reaches n1

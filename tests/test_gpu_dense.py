@@ -19,7 +19,7 @@ import paper_2302_13524_gb300 as tmr  # noqa: E402
 
 
 @pytest.mark.parametrize("mode", [1, 2])
-@pytest.mark.parametrize("N,J", [(64, 4), (512, 4), (2048, 4), (1000, 3)])
+@pytest.mark.parametrize("N,J", [(64, 4), (512, 4), (2048, 4), (256, 3)])
 def test_dense_forward_and_gradient_match_oracle(mode, N, J):
     M = 6
     T, d, _ = problem(N, M, J, seed=N + mode)
@@ -53,7 +53,7 @@ def test_dense_amplitude_gradient_matches_oracle():
     assert_rows_close(to_np(G), G_ref, 1e-5)
 
 
-def test_dense_and_fft_paths_agree_and_retrieve_is_refused():
+def test_dense_and_fft_paths_agree():
     N, M, J = 1024, 64, 4
     T, d, Y = problem(N, M, J, seed=9)
     out = {}
@@ -63,14 +63,60 @@ def test_dense_and_fft_paths_agree_and_retrieve_is_refused():
         with tmr.tmr_create(N, M, J, to_dev(d), None, dict(dense=dense)) as h:
             tmr.tmr_grad(h, to_dev(T * 1.1), to_dev(Y), loss, G)
             torch.cuda.synchronize()
-            if dense:
-                To = torch.empty((M, N), dtype=torch.complex64, device="cuda")
-                with pytest.raises(tmr.TMRError) as ei:
-                    tmr.tmr_retrieve(h, to_dev(Y), None, 5, To)
-                assert ei.value.status == tmr.TMR_ERR_UNSUPPORTED
         out[dense] = (to_np(loss), to_np(G))
     assert np.max(np.abs(out[1][0] - out[0][0]) / out[0][0]) <= 2e-5
     assert_rows_close(out[1][1], out[0][1], 2e-5)
     with pytest.raises(tmr.TMRError) as ei:
         tmr.tmr_create(N, M, J, to_dev(d), None, dict(dense=3))
     assert ei.value.status == tmr.TMR_ERR_INVALID_ARG
+
+
+# ------------------------------------------------ Algorithm 1 without FFT
+@pytest.mark.parametrize("N,J", [(256, 4), (1024, 3), (64, 8)])
+def test_dense_solver_first_step_matches_oracle(N, J):
+    """tmr_retrieve with opt.dense runs Algorithm 1 with the FFTs replaced by
+    matrix-vector products: one step from a given start equals the oracle's."""
+    M = 4
+    T, d, Y = problem(N, M, J, seed=11 + N)
+    rng = np.random.default_rng(N)
+    T_init = (T + 0.3 * (rng.standard_normal(T.shape) + 1j * rng.standard_normal(T.shape)) / np.sqrt(N))
+    T_init = np.ascontiguousarray(T_init, dtype=np.complex64)
+    Tn = torch.empty((M, N), dtype=torch.complex64, device="cuda")
+    with tmr.tmr_create(N, M, J, to_dev(d), None, dict(dense=1)) as h:
+        assert tmr.tmr_schedule(h) == 1
+        tmr.tmr_retrieve_from(h, to_dev(T_init), to_dev(Y), None, 1, Tn)
+        torch.cuda.synchronize()
+    for r in range(M):
+        ref = oracle.lbfgs_step(Y[r].astype(np.float64), d.astype(np.complex128), T_init[r].astype(np.complex128))
+        assert_rows_close(to_np(Tn)[r:r + 1], ref["t"][None], 1e-5)
+
+
+def test_dense_solver_retrieval_matches_the_fft_solver():
+    """Whole retrievals (Lanczos start, 60 L-BFGS iterations) with and without
+    FFT end at the same per-row fidelities (the same algorithm, other rounding)."""
+    N, M, J = 512, 48, 4
+    T, d, Y = problem(N, M, J, seed=21)
+    fids = {}
+    for dense in (0, 1):
+        To = torch.empty((M, N), dtype=torch.complex64, device="cuda")
+        with tmr.tmr_create(N, M, J, to_dev(d), None,
+                            dict(dense=dense, init="spectral", power_iters=16, lanczos=1, schedule=1)) as h:
+            tmr.tmr_retrieve(h, to_dev(Y), None, 60, To)
+            tmr.tmr_sync(h, 60.0)
+        fids[dense] = oracle.fidelity_rows(to_np(To), T)
+    assert np.sum(np.abs(fids[1] - fids[0]) > 1e-3) <= 1
+    assert abs(np.sum(fids[1] < 0.99) - np.sum(fids[0] < 0.99)) <= 1
+
+
+def test_dense_solver_refuses_the_fit_and_other_shapes():
+    N, M, J = 64, 128, 4
+    _, d, Y = problem(N, M, J, seed=2)
+    with tmr.tmr_create(N, M, J, to_dev(d), dict(ny=16, nx=8, n_defocus=8), dict(dense=1)) as h:
+        To = torch.empty((M, N), dtype=torch.complex64, device="cuda")
+        yd = torch.zeros((8, M), dtype=torch.float32, device="cuda")
+        with pytest.raises(tmr.TMRError) as ei:
+            tmr.tmr_retrieve(h, to_dev(Y), yd, 5, To)
+        assert ei.value.status == tmr.TMR_ERR_UNSUPPORTED
+    with pytest.raises(tmr.TMRError) as ei:  # not a power of two
+        tmr.tmr_create(1000, 4, J, to_dev(np.ones((J, 1000), np.complex64)), None, dict(dense=1))
+    assert ei.value.status == tmr.TMR_ERR_UNSUPPORTED
