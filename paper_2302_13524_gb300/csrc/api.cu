@@ -505,7 +505,7 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
 
     int smem_optin = 0;
     TMR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
-    if (o.cost == TMR_COST_AMPLITUDE && xk != 0)
+    if (o.cost == TMR_COST_AMPLITUDE && xk != 0 && xk != 3)
         return fail(TMR_ERR_UNSUPPORTED, "the amplitude cost runs on the FP32 1D transforms (precision FP32, probe_n1 0)");
     if (o.schedule != 0 && !schedule_ok(N, J, o.m, o.schedule, smem_optin, xk, o.cost))
         return fail(TMR_ERR_UNSUPPORTED,
