@@ -98,7 +98,8 @@ struct tmr_handle {
     int *pf_err = nullptr, *pf_iters = nullptr;
     int *status_scratch = nullptr, *iters_scratch = nullptr;
     float *loss_scratch = nullptr;
-    // L-BFGS pair workspace of the one-CTA-per-row schedule (pair_ctas regions)
+    // token allocation of the one-CTA-per-row schedule (its pairs are in tensor
+    // memory) and its resident CTA count
     float2 *pairs = nullptr;
     int pair_ctas = 0;
     // the probing operator as a dense matrix (opt.dense), made on first use
@@ -608,10 +609,11 @@ tmr_status tmr_create(tmr_handle **out, int N, int M, int J, const void *masks,
         TRY(halloc(h, (void **)&h->pf_loss, sizeof(double) * 4, "phase loss"));
         cudaMemset(h->pf_err, 0, sizeof(int) * 4);
     }
-    // the one-CTA-per-row schedule keeps its L-BFGS pairs in global memory: one
-    // region per resident CTA, allocated when that schedule can run (and is
-    // asked for or a candidate of the autotuner); under a workspace_limit that
-    // it would exceed, the schedule is left out
+    // the one-CTA-per-row schedule keeps its L-BFGS pairs in tensor memory; its
+    // resident CTA count (pair_ctas, which sizes the Lanczos workspace) is set
+    // when that schedule can run (and is asked for or a candidate of the
+    // autotuner), with a token allocation (solver_row_pair_stride is 0) that
+    // marks the schedule as runnable
     if ((o.schedule == 0 || o.schedule == kRowSchedule) &&
         schedule_ok(N, J, o.m, kRowSchedule, smem_optin, h->xk, o.cost)) {
         const int ctas = solver_row_max_ctas(N, J, o.m);

@@ -86,8 +86,8 @@ struct SolverParams {
     int judge_cand;       // per row, the proposal replaces the start when its loss is lower
     unsigned *cand_wins;  // rows whose proposed start was kept
     unsigned *queue;      // row work counter, zeroed before the launch
-    float2 *pairs;        // one-CTA-per-row schedule: L-BFGS pairs, pair_ctas regions of
-    int pair_ctas;        //   2 (m + 1) N float2 each (global memory), else unused
+    float2 *pairs;        // one-CTA-per-row schedule: non-null when it may run (its L-BFGS
+    int pair_ctas;        //   pairs are in tensor memory); pair_ctas = its resident CTAs
     int lanczos;          // spectral start by power_iters Lanczos steps (else the power iteration)
     int cost;             // COST_INTENSITY (Eq. optTMsmall2) or COST_AMPLITUDE (cost.cuh)
     float2 *krylov;       // Lanczos vectors: krylov_units regions of lanczos_region(N, power_iters)

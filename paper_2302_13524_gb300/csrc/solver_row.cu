@@ -25,15 +25,10 @@ long long solver_dispatch_row(int N, int what, const SolverParams *p, cudaStream
 template <int N>
 static int row_max_ctas_t(int J, int m)
 {
-    const size_t sm = row_smem<N>(J, m);
-    if (cudaFuncSetAttribute(k_solver_row<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    int dev = 0, nsm = 0, occ = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solver_row<N>, J * RowCfg<N>::NT, sm) != cudaSuccess) {
+    size_t sm = 0;
+    int occ = 0, dev = 0, nsm = 0;
+    if (row_launch_shape<N, COST_INTENSITY>(J, m, &sm, &occ) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }

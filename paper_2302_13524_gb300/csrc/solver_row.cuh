@@ -16,9 +16,12 @@
 //   * the masks and the row's intensities live in shared memory (the masks
 //     are copied once per CTA and shared by all its rows), next to full-length
 //     t, g and the direction p, and one exchange buffer per team;
-//   * the L-BFGS pairs (2 (m+1) vectors of N complex values) live in a
-//     workspace in global memory, one region per resident CTA (about 29 MB
-//     for 152 CTAs at N = 2048, m = 5), which stays in L2;
+//   * the L-BFGS pairs (2 (m + 1) vectors of N complex values, 192 KB at
+//     N = 2048, m = 5) live in the SM's tensor memory, which the FP32 solver
+//     has no other use for: each thread keeps the elements it owns in the
+//     A and G phases (i = tid + e BT) in columns of its own lane, so the two
+//     passes over the pairs of every iteration read tensor memory instead of
+//     L2;
 //   * every exchange and every reduction is inside the CTA: block barriers
 //     instead of cluster barriers, no distributed shared memory.
 // Rows come from the same atomic work counter; a persistent launch of one
@@ -26,6 +29,7 @@
 #pragma once
 
 #include "solver_impl.cuh"
+#include "tmem.cuh"
 
 namespace tmr {
 
@@ -59,8 +63,34 @@ __host__ __device__ size_t row_smem(int J, int m)
     return bytes + sizeof(Gram);
 }
 
-// Pair workspace of one CTA, in float2: 2 (m + 1) vectors of length N.
-__host__ __device__ inline size_t row_pair_stride(int N, int m) { return (size_t)2 * (m + 1) * N; }
+// Tensor-memory columns of one CTA.  Thread tid owns elements tid + e BT,
+// e < EPT = ceil(N / BT), of every pair; a warp's block of columns holds
+// (m + 1) slots x EPT elements x (s re, s im, y re, y im), and the up to four
+// warps that share a lane quarter take consecutive blocks.  The allocation is the next
+// power of two (at least 32); every row variant with m <= 6 needs at most 504
+// of the 512 columns.
+__host__ __device__ inline int row_tmem_block(int N, int J, int m)
+{
+    const int BT = J * (N / kRowPts);
+    const int ept = (N + BT - 1) / BT;
+    return 2 * ept * 2 * (m + 1);
+}
+__host__ __device__ inline int row_tmem_cols(int N, int J, int m)
+{
+    const int NW = J * (N / kRowPts) / 32;
+    const int need = (NW + 3) / 4 * row_tmem_block(N, J, m);
+    int c = 32;
+    while (c < need) c *= 2;
+    return c;
+}
+
+// No global pair workspace: the pairs are in tensor memory.
+__host__ __device__ inline size_t row_pair_stride(int N, int m)
+{
+    (void)N;
+    (void)m;
+    return 0;
+}
 
 template <int N, int COST = COST_INTENSITY>
 __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
@@ -90,9 +120,18 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
     float *red = ys + (size_t)J * N;                // [kParts][NW]
     Gram &Gm = *reinterpret_cast<Gram *>(
         smem_raw + ((reinterpret_cast<unsigned char *>(red + kParts * NW) - smem_raw + 15) & ~(size_t)15));
-    // L-BFGS pairs of this CTA in global memory: slot a of S at Sg + a N, of Y at Yg + a N
-    float2 *Sg = P.pairs + (size_t)blockIdx.x * row_pair_stride(N, m);
-    float2 *Yg = Sg + (size_t)(m + 1) * N;
+
+    // L-BFGS pairs in tensor memory: element e (i = tid + e BT) of the pair in
+    // slot a at columns tcol(a, e) .. + 3 (s, then y)
+    __shared__ uint32_t tmem_base;
+    const int ncols = row_tmem_cols(N, J, m);
+    if (warp == 0) tmem_alloc_warp(&tmem_base, (uint32_t)ncols);
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    const int EPT = (N + BT - 1) / BT;
+    const uint32_t tlane = tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * row_tmem_block(N, J, m));
+    auto tcol = [&](int a, int e) { return tlane + (uint32_t)(4 * (a * EPT + e)); };
 
     // twiddles of the passes between the first and the last:
     // tw_p[(r - 1) Ns + j] = exp(-2 pi i r j / (Ns R)) at tw_off(p)
@@ -366,10 +405,10 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
             // ---- L-BFGS iterations ----
             for (int it = 0; it < P.iters && !Gm.stop; it++) {
                 const int np = Gm.np;
-                int so[kSlots];  // slot offsets by age (same for the S and Y halves)
+                int so[kSlots];  // slots by age
 #pragma unroll
-                for (int k = 0; k < kSlots; k++) so[k] = Gm.slot[k <= np ? k : 0] * N;
-                const int sn_off = so[np < kSlots ? np : 0];  // the free slot (age np) of the new pair
+                for (int k = 0; k < kSlots; k++) so[k] = Gm.slot[k <= np ? k : 0];
+                const int sn_slot = so[np < kSlots ? np : 0];  // the free slot (age np) of the new pair
                 // A: direction p = -(gamma g + sum c1 s + sum c2 y) into X
                 {
                     const float gam = Gm.gamma;
@@ -379,17 +418,26 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
                         c1r[k] = k < np ? Gm.c1[k] : 0.f;
                         c2r[k] = k < np ? Gm.c2[k] : 0.f;
                     }
-                    for (int i = tid; i < N; i += BT) {
-                        float2 acc = cscale(gs[i], gam);
+                    // every thread runs all EPT steps (the tensor-memory loads
+                    // are warp-wide); steps past N only load
+                    for (int e = 0; e < EPT; e++) {
+                        const int i = tid + e * BT;
+                        const bool in = i < N;
+                        float2 acc = in ? cscale(gs[i], gam) : make_float2(0.f, 0.f);
 #pragma unroll
                         for (int k = 0; k < kSlots; k++) {
                             if (k < np) {
-                                const float2 sa = Sg[so[k] + i], ya = Yg[so[k] + i];
+                                uint32_t r[4];
+                                tmem_ld4(tcol(so[k], e), r);
+                                tmem_wait_ld();
+                                tmem_reg_ready(r);
+                                const float2 sa = make_float2(__uint_as_float(r[0]), __uint_as_float(r[1]));
+                                const float2 ya = make_float2(__uint_as_float(r[2]), __uint_as_float(r[3]));
                                 acc.x = fmaf(c1r[k], sa.x, fmaf(c2r[k], ya.x, acc.x));
                                 acc.y = fmaf(c1r[k], sa.y, fmaf(c2r[k], ya.y, acc.y));
                             }
                         }
-                        X[i] = make_float2(-acc.x, -acc.y);
+                        if (in) X[i] = make_float2(-acc.x, -acc.y);
                     }
                 }
                 __syncthreads();
@@ -450,18 +498,27 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
                     float pv[32];
 #pragma unroll
                     for (int k = 0; k < 32; k++) pv[k] = 0.f;
-                    for (int i = tid; i < N; i += BT) {
-                        const float2 gn = team_sum(i, gsc);
-                        const float2 sn = cscale(X[i], al);
-                        const float2 yn = csub(gn, gs[i]);
-                        ts[i] = cadd(ts[i], sn);
-                        gs[i] = gn;
-                        Sg[sn_off + i] = sn;
-                        Yg[sn_off + i] = yn;
+                    for (int e = 0; e < EPT; e++) {
+                        const int i = tid + e * BT;
+                        const bool in = i < N;
+                        float2 gn = make_float2(0.f, 0.f), sn = gn, yn = gn;
+                        if (in) {
+                            gn = team_sum(i, gsc);
+                            sn = cscale(X[i], al);
+                            yn = csub(gn, gs[i]);
+                            ts[i] = cadd(ts[i], sn);
+                            gs[i] = gn;
+                        }
+                        tmem_st4(tcol(sn_slot, e), sn.x, sn.y, yn.x, yn.y);
 #pragma unroll
                         for (int k = 0; k < kSlots; k++) {
                             if (k < np) {  // live pairs by age
-                                const float2 sa = Sg[so[k] + i], ya = Yg[so[k] + i];
+                                uint32_t r[4];
+                                tmem_ld4(tcol(so[k], e), r);
+                                tmem_wait_ld();
+                                tmem_reg_ready(r);
+                                const float2 sa = make_float2(__uint_as_float(r[0]), __uint_as_float(r[1]));
+                                const float2 ya = make_float2(__uint_as_float(r[2]), __uint_as_float(r[3]));
                                 pv[4 * k + 0] += cdotr(sa, yn);
                                 pv[4 * k + 1] += cdotr(ya, yn);
                                 pv[4 * k + 2] += cdotr(sa, gn);
@@ -476,6 +533,7 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
                         pv[kIdxSS] += cabs2(sn);
                         pv[kIdxGG] += cabs2(gn);
                     }
+                    tmem_wait_st();  // the new pair is read back from the next iteration on
                     pv[kIdxF] = fpart;
                     block_reduce(pv, kParts);
                     if (warp == 0) lbfgs_gram_update(Gm, lane, m, it, P.iters, P.tol);
@@ -508,24 +566,63 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
         }
         __syncthreads();
     }
+    tmem_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tmem_fence_after_sync();
+        tmem_dealloc_warp(tmem_base, (uint32_t)ncols);
+    }
+}
+
+// Shared memory and resident CTAs per SM of a launch.  Every CTA holds
+// row_tmem_cols columns of the SM's 512 for its whole life, so at most
+// 512 / cols CTAs may share an SM; where registers and shared memory would
+// let more in, the shared-memory request is raised until they do not, and no
+// allocation ever has to wait for another CTA's columns.
+template <int N, int COST>
+cudaError_t row_launch_shape(int J, int m, size_t *smem_out, int *per_sm_out)
+{
+    const int BT = J * RowCfg<N>::NT;
+    const int cap = 512 / row_tmem_cols(N, J, m);
+    size_t sm = row_smem<N>(J, m);
+    int dev = 0, occ = 0, sm_per_mp = 0, optin = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sm_per_mp, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+        return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    for (int pass = 0; pass < 2; pass++) {
+        if (sm > (size_t)optin) return cudaErrorInvalidConfiguration;
+        if ((e = cudaFuncSetAttribute(k_solver_row<N, COST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solver_row<N, COST>, BT, sm)) != cudaSuccess)
+            return e;
+        if (occ < 1) return cudaErrorInvalidConfiguration;
+        if (occ <= cap) break;
+        if (pass == 1) return cudaErrorInvalidConfiguration;
+        const size_t need = (size_t)sm_per_mp / (size_t)(cap + 1) + 1;
+        if (need > sm) sm = (need + 15) & ~(size_t)15;
+    }
+    *smem_out = sm;
+    *per_sm_out = occ;
+    return cudaSuccess;
 }
 
 template <int N, int COST = COST_INTENSITY>
 cudaError_t launch_solver_row_t(const SolverParams &p, cudaStream_t s, int *ctas_out)
 {
-    if (!row_variant_fits(N, p.J) || !p.pairs) return cudaErrorInvalidValue;
+    if (!row_variant_fits(N, p.J) || p.m < 1 || p.m > kMaxMem) return cudaErrorInvalidValue;
     const int BT = p.J * RowCfg<N>::NT;
-    const size_t sm = row_smem<N>(p.J, p.m);
-    cudaError_t e = cudaFuncSetAttribute(k_solver_row<N, COST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    size_t sm = 0;
+    int occ = 0, dev = 0, nsm = 0;
+    cudaError_t e = row_launch_shape<N, COST>(p.J, p.m, &sm, &occ);
     if (e != cudaSuccess) return e;
-    int dev = 0, nsm = 0, occ = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solver_row<N, COST>, BT, sm)) != cudaSuccess) return e;
-    if (occ < 1) return cudaErrorInvalidConfiguration;
     long long grid = (long long)occ * nsm;
     if (grid > p.M) grid = p.M;
-    if (grid > p.pair_ctas) grid = p.pair_ctas;  // one pair region per CTA
+    if (grid > p.pair_ctas) grid = p.pair_ctas;  // the resident CTAs the handle sized its workspaces for
     if (p.lanczos && p.init == INIT_SPECTRAL && grid > p.krylov_units) grid = p.krylov_units;
     if (grid < 1) grid = 1;
     if (ctas_out) *ctas_out = (int)grid;
