@@ -13,11 +13,14 @@
 // t = sum_l s_l v_l with s the eigenvector of the largest eigenvalue of the
 // tridiagonal T (alpha on the diagonal, beta beside it), signed so that
 // s_0 >= 0.  The Lanczos vectors live in a global workspace region of the CTA
-// (or cluster); each thread reads back only the elements it wrote.
+// (or cluster), or, for the one-CTA-per-row solver where they fit, in the
+// SM's tensor memory (lanczos_start_tmem); each thread reads back only the
+// elements it wrote.
 #pragma once
 
 #include "common.cuh"
 #include "internal.h"
+#include "tmem.cuh"
 
 namespace tmr {
 
@@ -114,6 +117,52 @@ static __device__ void tridiag_top_eigvec(const float *a, const float *b, int n,
     __syncwarp();
 }
 
+// Step j's update coefficients from the sweep's partial sums (all threads):
+// pv holds <v_l, w> for l <= j and pg <v_l, v_j> for l < j (re, im pairs);
+// the new Gram column goes to Gw, the coefficients c (see lanczos_start) to
+// hc and alpha_j to la[j].  Ends with a block barrier.
+template <class Reduce>
+__device__ __forceinline__ void lanczos_coefficients(int j, float (&pv)[32], float (&pg)[32], float2 *Gw,
+                                                     const float *red, float *la, float *hc, Reduce &&reduce)
+{
+    const int tid = threadIdx.x, lane = tid & 31;
+    reduce(pv, 2 * (j + 1));
+    if (tid < 2 * (j + 1)) hc[tid] = red[tid];
+    if (j > 0) {
+        reduce(pg, 2 * j);
+        if (tid < 32) {
+            if (lane < j) Gw[lane * kMaxLanczos + j] = make_float2(red[2 * lane], red[2 * lane + 1]);
+            if (lane == j) {
+#pragma unroll
+                for (int l = 0; l < kMaxLanczos; l++)
+                    if (l < j) Gw[j * kMaxLanczos + l] = make_float2(red[2 * l], -red[2 * l + 1]);
+            }
+        }
+    }
+    __syncwarp();
+    if (tid < 32) {
+        float2 c = make_float2(0.f, 0.f);
+        if (lane <= j) {
+            c = make_float2(hc[2 * lane], hc[2 * lane + 1]);
+#pragma unroll
+            for (int m = 0; m < kMaxLanczos; m++) {
+                if (m <= j && m != lane) {
+                    const float2 g = Gw[lane * kMaxLanczos + m], hm = make_float2(hc[2 * m], hc[2 * m + 1]);
+                    c.x -= g.x * hm.x - g.y * hm.y;
+                    c.y -= g.x * hm.y + g.y * hm.x;
+                }
+            }
+        }
+        __syncwarp();
+        if (lane <= j) {
+            hc[2 * lane] = c.x;
+            hc[2 * lane + 1] = c.y;
+        }
+        if (lane == j) la[j] = c.x;
+    }
+    __syncthreads();
+}
+
 // The Lanczos start on this CTA's nloc elements (thread-strided by blockDim.x).
 //   ts   in: the seed vector; out: the Ritz vector (unit norm)
 //   gs   scratch, nloc elements
@@ -144,7 +193,7 @@ template <class ApplyA, class Reduce>
 __device__ void lanczos_start(int k, int nloc, float2 *ts, float2 *gs, float2 *V, size_t vs, float2 *Gw,
                               const float *red, float *lz, float *hc, ApplyA &&applyA, Reduce &&reduce)
 {
-    const int tid = threadIdx.x, BT = blockDim.x, lane = tid & 31;
+    const int tid = threadIdx.x, BT = blockDim.x;
     float *la = lz, *lb = lz + kMaxLanczos, *ls = lz + 2 * kMaxLanczos;
     {
         float pv[32] = {0.f};
@@ -181,41 +230,7 @@ __device__ void lanczos_start(int k, int nloc, float2 *ts, float2 *gs, float2 *V
                 }
             }
         }
-        reduce(pv, 2 * (j + 1));
-        if (tid < 2 * (j + 1)) hc[tid] = red[tid];
-        if (j > 0) {
-            reduce(pg, 2 * j);
-            if (tid < 32) {
-                if (lane < j) Gw[lane * kMaxLanczos + j] = make_float2(red[2 * lane], red[2 * lane + 1]);
-                if (lane == j) {
-#pragma unroll
-                    for (int l = 0; l < kMaxLanczos; l++)
-                        if (l < j) Gw[j * kMaxLanczos + l] = make_float2(red[2 * l], -red[2 * l + 1]);
-                }
-            }
-        }
-        __syncwarp();
-        if (tid < 32) {
-            float2 c = make_float2(0.f, 0.f);
-            if (lane <= j) {
-                c = make_float2(hc[2 * lane], hc[2 * lane + 1]);
-#pragma unroll
-                for (int m = 0; m < kMaxLanczos; m++) {
-                    if (m <= j && m != lane) {
-                        const float2 g = Gw[lane * kMaxLanczos + m], hm = make_float2(hc[2 * m], hc[2 * m + 1]);
-                        c.x -= g.x * hm.x - g.y * hm.y;
-                        c.y -= g.x * hm.y + g.y * hm.x;
-                    }
-                }
-            }
-            __syncwarp();
-            if (lane <= j) {
-                hc[2 * lane] = c.x;
-                hc[2 * lane + 1] = c.y;
-            }
-            if (lane == j) la[j] = c.x;
-        }
-        __syncthreads();
+        lanczos_coefficients(j, pv, pg, Gw, red, la, hc, reduce);
         const float alpha = la[j];
         if (j == 0) alpha0 = alpha;
 #pragma unroll
@@ -265,6 +280,158 @@ __device__ void lanczos_start(int k, int nloc, float2 *ts, float2 *gs, float2 *V
         ts[i] = acc;
     }
     __syncthreads();
+}
+
+// The same start with the Lanczos vectors in tensor memory (one CTA per row,
+// nloc = N).  Thread tid keeps elements i = tid + e BT, e < ept, of every
+// vector in its own lane; vectors l .. l + 3 of element e sit in 8
+// consecutive columns from tv + 2 (e KM + l), KM = k rounded up to a multiple
+// of 4, so one 8-column load brings four of them.  Every thread runs all ept
+// steps of each sweep (the tensor-memory loads and stores are warp-wide);
+// steps past nloc move zeros.  The arithmetic and its order are those of
+// lanczos_start.
+template <class ApplyA, class Reduce>
+__device__ void lanczos_start_tmem(int k, int nloc, int ept, uint32_t tv, float2 *ts, float2 *gs, float2 *Gw,
+                                   const float *red, float *lz, float *hc, ApplyA &&applyA, Reduce &&reduce)
+{
+    const int tid = threadIdx.x, BT = blockDim.x;
+    const int KM = (k + 3) & ~3;
+    float *la = lz, *lb = lz + kMaxLanczos, *ls = lz + 2 * kMaxLanczos;
+    auto col = [&](int l, int e) { return tv + (uint32_t)(2 * (e * KM + l)); };
+    tmem_fence_after_sync();
+    {
+        float pv[32] = {0.f};
+        for (int i = tid; i < nloc; i += BT) pv[0] += cabs2(ts[i]);
+        reduce(pv, 1);
+        const float nr = red[0];
+        const float inv = nr > 0.f ? rsqrtf(nr) : 0.f;
+        for (int e = 0; e < ept; e++) {
+            const int i = tid + e * BT;
+            float2 v = make_float2(0.f, 0.f);
+            if (i < nloc) {
+                v = cscale(ts[i], inv);
+                ts[i] = v;
+            }
+            tmem_st2(col(0, e), v.x, v.y);
+        }
+        tmem_wait_st();
+    }
+    int kk = k;
+    float alpha0 = 0.f;
+    for (int j = 0; j < k; j++) {
+        applyA();
+        float pv[32], pg[32];
+#pragma unroll
+        for (int q = 0; q < 32; q++) pv[q] = pg[q] = 0.f;
+        for (int e = 0; e < ept; e++) {
+            const int i = tid + e * BT;
+            const bool in = i < nloc;
+            const float2 w = in ? gs[i] : make_float2(0.f, 0.f), vj = in ? ts[i] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int g = 0; g < kMaxLanczos / 4; g++) {
+                if (4 * g <= j) {
+                    uint32_t r[8];
+                    tmem_ld8(col(4 * g, e), r);
+                    tmem_wait_ld();
+                    tmem_reg_ready(r);
+                    if (in) {
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {
+                            const int l = 4 * g + q;
+                            if (l <= j) {
+                                const float2 v = make_float2(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
+                                pv[2 * l] = fmaf(v.x, w.x, fmaf(v.y, w.y, pv[2 * l]));
+                                pv[2 * l + 1] = fmaf(v.x, w.y, fmaf(-v.y, w.x, pv[2 * l + 1]));
+                                if (l < j) {
+                                    pg[2 * l] = fmaf(v.x, vj.x, fmaf(v.y, vj.y, pg[2 * l]));
+                                    pg[2 * l + 1] = fmaf(v.x, vj.y, fmaf(-v.y, vj.x, pg[2 * l + 1]));
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        lanczos_coefficients(j, pv, pg, Gw, red, la, hc, reduce);
+        const float alpha = la[j];
+        if (j == 0) alpha0 = alpha;
+#pragma unroll
+        for (int q = 0; q < 32; q++) pv[q] = 0.f;
+        for (int e = 0; e < ept; e++) {
+            const int i = tid + e * BT;
+            const bool in = i < nloc;
+            float2 w = in ? gs[i] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int g = 0; g < kMaxLanczos / 4; g++) {
+                if (4 * g <= j) {
+                    uint32_t r[8];
+                    tmem_ld8(col(4 * g, e), r);
+                    tmem_wait_ld();
+                    tmem_reg_ready(r);
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const int l = 4 * g + q;
+                        if (l <= j) {
+                            const float2 v = make_float2(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
+                            const float cr = hc[2 * l], ci = hc[2 * l + 1];
+                            w.x -= cr * v.x - ci * v.y;
+                            w.y -= cr * v.y + ci * v.x;
+                        }
+                    }
+                }
+            }
+            if (in) {
+                gs[i] = w;
+                pv[0] = fmaf(w.x, w.x, fmaf(w.y, w.y, pv[0]));
+            }
+        }
+        reduce(pv, 1);
+        const float beta = sqrtf(red[0]);
+        if (tid == 0) lb[j] = beta;
+        if (j == k - 1 || !(beta > 1e-6f * alpha0)) {
+            kk = j + 1;
+            break;
+        }
+        const float inv = 1.f / beta;
+        for (int e = 0; e < ept; e++) {
+            const int i = tid + e * BT;
+            float2 v = make_float2(0.f, 0.f);
+            if (i < nloc) {
+                v = cscale(gs[i], inv);
+                ts[i] = v;
+            }
+            tmem_st2(col(j + 1, e), v.x, v.y);
+        }
+        tmem_wait_st();
+    }
+    __syncthreads();
+    if (tid < 32) tridiag_top_eigvec(la, lb, kk, ls);
+    __syncthreads();
+    for (int e = 0; e < ept; e++) {
+        const int i = tid + e * BT;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int g = 0; g < kMaxLanczos / 4; g++) {
+            if (4 * g < kk) {
+                uint32_t r[8];
+                tmem_ld8(col(4 * g, e), r);
+                tmem_wait_ld();
+                tmem_reg_ready(r);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int l = 4 * g + q;
+                    if (l < kk) {
+                        acc.x = fmaf(ls[l], __uint_as_float(r[2 * q]), acc.x);
+                        acc.y = fmaf(ls[l], __uint_as_float(r[2 * q + 1]), acc.y);
+                    }
+                }
+            }
+        }
+        if (i < nloc) ts[i] = acc;
+    }
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
 }
 
 }  // namespace tmr

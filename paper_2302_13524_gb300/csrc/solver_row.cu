@@ -27,7 +27,10 @@ static int row_max_ctas_t(int J, int m)
 {
     size_t sm = 0;
     int occ = 0, dev = 0, nsm = 0;
-    if (row_launch_shape<N, COST_INTENSITY>(J, m, &sm, &occ) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+    // the largest tensor-memory need of the schedule (a 16-step Lanczos start)
+    // bounds the resident CTAs of every launch
+    const int klz = row_tmem_klz(N, J, true, kMaxLanczos);
+    if (row_launch_shape<N, COST_INTENSITY>(J, m, klz, &sm, &occ) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
         return 0;

@@ -21,7 +21,9 @@
 //     has no other use for: each thread keeps the elements it owns in the
 //     A and G phases (i = tid + e BT) in columns of its own lane, so the two
 //     passes over the pairs of every iteration read tensor memory instead of
-//     L2;
+//     L2; before the first pair exists, the same columns hold the vectors of
+//     the Lanczos start where they fit (k N complex values: 256 KB, all 512
+//     columns, at N = 2048, J = 4, k = 16), else those stay in global memory;
 //   * every exchange and every reduction is inside the CTA: block barriers
 //     instead of cluster barriers, no distributed shared memory.
 // Rows come from the same atomic work counter; a persistent launch of one
@@ -64,21 +66,31 @@ __host__ __device__ size_t row_smem(int J, int m)
 }
 
 // Tensor-memory columns of one CTA.  Thread tid owns elements tid + e BT,
-// e < EPT = ceil(N / BT), of every pair; a warp's block of columns holds
-// (m + 1) slots x EPT elements x (s re, s im, y re, y im), and the up to four
-// warps that share a lane quarter take consecutive blocks.  The allocation is the next
-// power of two (at least 32); every row variant with m <= 6 needs at most 504
-// of the 512 columns.
-__host__ __device__ inline int row_tmem_block(int N, int J, int m)
+// e < EPT = ceil(N / BT), of every pair and Lanczos vector.  A warp's block of
+// pair columns holds (m + 1) slots x EPT elements x (s re, s im, y re, y im);
+// its block of Lanczos columns EPT elements x KM vectors x (re, im), KM = k
+// rounded up to a multiple of 4; the up to four warps that share a lane
+// quarter take consecutive blocks.  Every row variant with m <= 6 needs at
+// most 504 columns for its pairs; the Lanczos vectors go to tensor memory when
+// their blocks fit in 512 columns (klz = k steps, else 0).  The allocation is
+// the next power of two of the larger need (at least 32).
+__host__ __device__ inline int row_ept(int N, int J) { return (N + J * (N / kRowPts) - 1) / (J * (N / kRowPts)); }
+__host__ __device__ inline int row_tmem_block(int N, int J, int m) { return 4 * row_ept(N, J) * (m + 1); }
+__host__ __device__ inline int row_tmem_lanczos_block(int N, int J, int k) { return 2 * row_ept(N, J) * ((k + 3) & ~3); }
+__host__ __device__ inline int row_quarter_warps(int N, int J) { return (J * (N / kRowPts) / 32 + 3) / 4; }
+__host__ __device__ inline int row_tmem_klz(int N, int J, bool lanczos_start, int k)
 {
-    const int BT = J * (N / kRowPts);
-    const int ept = (N + BT - 1) / BT;
-    return 2 * ept * 2 * (m + 1);
+    return lanczos_start && k >= 1 && k <= kMaxLanczos && row_quarter_warps(N, J) * row_tmem_lanczos_block(N, J, k) <= 512
+               ? k
+               : 0;
 }
-__host__ __device__ inline int row_tmem_cols(int N, int J, int m)
+__host__ __device__ inline int row_tmem_cols(int N, int J, int m, int klz)
 {
-    const int NW = J * (N / kRowPts) / 32;
-    const int need = (NW + 3) / 4 * row_tmem_block(N, J, m);
+    int need = row_quarter_warps(N, J) * row_tmem_block(N, J, m);
+    if (klz > 0) {
+        const int lz = row_quarter_warps(N, J) * row_tmem_lanczos_block(N, J, klz);
+        if (lz > need) need = lz;
+    }
     int c = 32;
     while (c < need) c *= 2;
     return c;
@@ -124,13 +136,15 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
     // L-BFGS pairs in tensor memory: element e (i = tid + e BT) of the pair in
     // slot a at columns tcol(a, e) .. + 3 (s, then y)
     __shared__ uint32_t tmem_base;
-    const int ncols = row_tmem_cols(N, J, m);
+    const int klz = row_tmem_klz(N, J, P.lanczos && P.init == INIT_SPECTRAL && !P.T_init, P.power_iters);
+    const int ncols = row_tmem_cols(N, J, m, klz);
     if (warp == 0) tmem_alloc_warp(&tmem_base, (uint32_t)ncols);
     tmem_fence_before_sync();
     __syncthreads();
     tmem_fence_after_sync();
     const int EPT = (N + BT - 1) / BT;
-    const uint32_t tlane = tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * row_tmem_block(N, J, m));
+    const uint32_t tquarter = tmem_base + ((uint32_t)(32 * (warp & 3)) << 16);
+    const uint32_t tlane = tquarter + (uint32_t)((warp >> 2) * row_tmem_block(N, J, m));
     auto tcol = [&](int a, int e) { return tlane + (uint32_t)(4 * (a * EPT + e)); };
 
     // twiddles of the passes between the first and the last:
@@ -301,8 +315,14 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
                         __syncthreads();
                     };
                     float2 *V = P.krylov + (size_t)blockIdx.x * lanczos_region(N, P.power_iters);
-                    lanczos_start(P.power_iters, N, ts, gs, V, (size_t)N, V + (size_t)P.power_iters * N, Gm.red,
-                                  &Gm.SY[0][0], &Gm.YY[0][0], applyA, block_reduce);
+                    if (klz)
+                        lanczos_start_tmem(klz, N, EPT,
+                                           tquarter + (uint32_t)((warp >> 2) * row_tmem_lanczos_block(N, J, klz)), ts,
+                                           gs, V + (size_t)P.power_iters * N, Gm.red, &Gm.SY[0][0], &Gm.YY[0][0],
+                                           applyA, block_reduce);
+                    else
+                        lanczos_start(P.power_iters, N, ts, gs, V, (size_t)N, V + (size_t)P.power_iters * N, Gm.red,
+                                      &Gm.SY[0][0], &Gm.YY[0][0], applyA, block_reduce);
                 } else if (P.init == INIT_SPECTRAL) {
                     const float mean = sumy / (float)K;
                     for (int it = 0; it < P.power_iters; it++) {
@@ -420,6 +440,7 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
                     }
                     // every thread runs all EPT steps (the tensor-memory loads
                     // are warp-wide); steps past N only load
+                    tmem_fence_after_sync();
                     for (int e = 0; e < EPT; e++) {
                         const int i = tid + e * BT;
                         const bool in = i < N;
@@ -534,6 +555,7 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
                         pv[kIdxGG] += cabs2(gn);
                     }
                     tmem_wait_st();  // the new pair is read back from the next iteration on
+                    tmem_fence_before_sync();
                     pv[kIdxF] = fpart;
                     block_reduce(pv, kParts);
                     if (warp == 0) lbfgs_gram_update(Gm, lane, m, it, P.iters, P.tol);
@@ -580,10 +602,10 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
 // let more in, the shared-memory request is raised until they do not, and no
 // allocation ever has to wait for another CTA's columns.
 template <int N, int COST>
-cudaError_t row_launch_shape(int J, int m, size_t *smem_out, int *per_sm_out)
+cudaError_t row_launch_shape(int J, int m, int klz, size_t *smem_out, int *per_sm_out)
 {
     const int BT = J * RowCfg<N>::NT;
-    const int cap = 512 / row_tmem_cols(N, J, m);
+    const int cap = 512 / row_tmem_cols(N, J, m, klz);
     size_t sm = row_smem<N>(J, m);
     int dev = 0, occ = 0, sm_per_mp = 0, optin = 0;
     cudaError_t e;
@@ -616,7 +638,8 @@ cudaError_t launch_solver_row_t(const SolverParams &p, cudaStream_t s, int *ctas
     const int BT = p.J * RowCfg<N>::NT;
     size_t sm = 0;
     int occ = 0, dev = 0, nsm = 0;
-    cudaError_t e = row_launch_shape<N, COST>(p.J, p.m, &sm, &occ);
+    const int klz = row_tmem_klz(N, p.J, p.lanczos && p.init == INIT_SPECTRAL && !p.T_init, p.power_iters);
+    cudaError_t e = row_launch_shape<N, COST>(p.J, p.m, klz, &sm, &occ);
     if (e != cudaSuccess) return e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;

@@ -50,6 +50,14 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4])
                  : "r"(taddr));
 }
 
+// Whole warp: eight consecutive columns of each thread's lane into r[0..7].
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
 // Whole warp: four values into four consecutive columns of each thread's lane.
 __device__ __forceinline__ void tmem_st4(uint32_t taddr, float a, float b, float c, float d)
 {
@@ -75,6 +83,10 @@ __device__ __forceinline__ void tmem_reg_ready(uint32_t (&r)[2]) { asm volatile(
 __device__ __forceinline__ void tmem_reg_ready(uint32_t (&r)[4])
 {
     asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]));
+}
+__device__ __forceinline__ void tmem_reg_ready(uint32_t (&r)[8])
+{
+    asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]));
 }
 
 }  // namespace tmr
