@@ -86,6 +86,9 @@ def parse():
                     help="stop the phase-offset fit once an accepted step lowers its loss by at most "
                          "this fraction (0: only the iteration cap)")
     ap.add_argument("--rows", type=int, default=None, help="override M (grid kept 128 wide)")
+    ap.add_argument("--schedule", type=int, default=0,
+                    help="solver schedule code (0: the autotuner's choice; a profiler's per-launch overhead "
+                         "can sway that choice, so profiled runs pin the schedule the plain run reports)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true", help="skip the short-budget sweep to the 0.99 bar")
@@ -648,6 +651,8 @@ def main():
     opt = dict(init="spectral", power_iters=args.power_iters, clip=2.0, m=m,
                phase_iters=args.phase_iters, seed=seed, tol=W["tol"], precision=args.precision,
                use_graph=1, lanczos=args.lanczos, phase_tol=args.phase_tol)
+    if args.schedule:
+        opt["schedule"] = args.schedule
     dop = dict(ny=ny, nx=nx, n_defocus=Nd, coef=0.05)
     h = tmr.tmr_create(N, M, J, dg, dop, opt, stream=stream.cuda_stream)
     sched = tmr.tmr_schedule(h)
@@ -796,16 +801,18 @@ def main():
     peak_max = fp32_peak_tflops(n_sm, 2070.0)
     # DRAM bytes of the solver, from one ncu capture of the current kernel
     # (dram__bytes_read.sum + dram__bytes_write.sum) on the plain workload at
-    # 4096 rows: k_solver_row<2048> read 139.70 MB and wrote 60.16 MB; traffic
-    # grows with the rows, so a full 8192-row launch moves twice that.  The
-    # cluster schedules were captured earlier at 138.0 + 42.7 MB per 4096 rows.
+    # 4096 rows with the 16-step Lanczos start: k_solver_row<2048> read
+    # 138.97 MB and wrote 42.11 MB; traffic grows with the rows, so a full
+    # 8192-row launch moves twice that.
     kname = (f"k_solver_row<{N}> (one CTA per row)" if sched == 16
              else f"k_solver<{'XfPow2' if N & (N - 1) == 0 else 'XfBlue'}, {sched}> (cluster of {J // max(sched, 1)} CTAs)")
     traffic, tbasis = None, "no capture of this kernel and workload"
-    if args.workload == "plain" and sched == 16 and args.precision == "fp32":
-        traffic = (139703808 + 60157184) * (M / 4096.0)
-        tbasis = ("ncu capture of k_solver_row<2048> at 4096 rows (139.70 MB read + 60.16 MB written), "
-                  "scaled by rows; algorithmic bytes per 4096 rows: y 134.2 MB read, T 33.6 MB written")
+    if (args.workload == "plain" and sched == 16 and args.precision == "fp32" and args.lanczos
+            and args.power_iters == 16):
+        traffic = (138965504 + 42113280) * (M / 4096.0)
+        tbasis = ("ncu capture of k_solver_row<2048> at 4096 rows (138.97 MB read + 42.11 MB written), "
+                  "scaled by rows; algorithmic bytes per 4096 rows: y 134.2 MB read, T 67.1 MB written "
+                  "(output rows still dirty in L2 at the kernel's end are written back after it)")
     roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak_max,
             "unit": "TFLOP/s", "frac": achieved / peak_max, "traffic": traffic,
             "traffic_basis": tbasis,
@@ -947,7 +954,7 @@ def main():
                            "parallelism": f"{world} independent TMs, one per GPU"},
                 "schedule": {"code": sched, "layout": "one CTA per row (16 points per thread)" if sched == 16
                              else f"{sched} masks per CTA, cluster of {J // max(sched, 1)} CTAs per row",
-                             "autotuned": True, "cuda_graph": True},
+                             "autotuned": not args.schedule, "cuda_graph": True},
                 "fidelity": {"mean": float(fid.mean()), "p1": float(np.percentile(fid, 1)),
                              "frac_ge_0.99": float(np.mean(fid >= 0.99)),
                              "matrix_after_phase_fit": mfid},

@@ -199,8 +199,10 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
         for (int e = 0; e < E; e++) x[e] = src[ttid + e * NT];
     };
     // Block-wide sums of nv <= 32 per-thread values: warp sums, then thread k
-    // adds the NW warp sums of value k in warp order into Gm.red[k].
-    auto block_reduce = [&](float (&v)[32], int nv) {
+    // adds the NW warp sums of value k in warp order into Gm.red[k].  With
+    // all = false only warp 0 (threads 0 .. 31) goes on to read the sums, so
+    // a warp barrier replaces the block barrier after them.
+    auto block_reduce = [&](float (&v)[32], int nv, bool all = true) {
         if (nv <= 6) {
             // constant indices only: a runtime index would move v to local memory
 #pragma unroll
@@ -220,7 +222,8 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
             for (int w = 0; w < NW; w++) acc += red[tid * NW + w];
             Gm.red[tid] = acc;
         }
-        __syncthreads();
+        if (all) __syncthreads();
+        else __syncwarp();
     };
 
     while (true) {
@@ -315,11 +318,12 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
                         __syncthreads();
                     };
                     float2 *V = P.krylov + (size_t)blockIdx.x * lanczos_region(N, P.power_iters);
+                    // (the direction p is not in use yet: its buffer X holds
+                    // the Gram matrix of the Lanczos vectors)
                     if (klz)
                         lanczos_start_tmem(klz, N, EPT,
                                            tquarter + (uint32_t)((warp >> 2) * row_tmem_lanczos_block(N, J, klz)), ts,
-                                           gs, V + (size_t)P.power_iters * N, Gm.red, &Gm.SY[0][0], &Gm.YY[0][0],
-                                           applyA, block_reduce);
+                                           gs, X, Gm.red, &Gm.SY[0][0], &Gm.YY[0][0], applyA, block_reduce);
                     else
                         lanczos_start(P.power_iters, N, ts, gs, V, (size_t)N, V + (size_t)P.power_iters * N, Gm.red,
                                       &Gm.SY[0][0], &Gm.YY[0][0], applyA, block_reduce);
@@ -490,7 +494,7 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
                         pv[3] = fmaf(4.f * a, b, pv[3]);
                         pv[4] = fmaf(b, b, pv[4]);
                     }
-                    block_reduce(pv, 5);
+                    block_reduce(pv, 5, false);
                     if (warp == 0) {
                         const float al = quartic_argmin_warp(Gm.red, lane);
                         if (lane == 0) {
@@ -557,7 +561,7 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
                     tmem_wait_st();  // the new pair is read back from the next iteration on
                     tmem_fence_before_sync();
                     pv[kIdxF] = fpart;
-                    block_reduce(pv, kParts);
+                    block_reduce(pv, kParts, false);
                     if (warp == 0) lbfgs_gram_update(Gm, lane, m, it, P.iters, P.tol);
                     __syncthreads();
                 }
