@@ -802,15 +802,15 @@ def main():
     # DRAM bytes of the solver, from one ncu capture of the current kernel
     # (dram__bytes_read.sum + dram__bytes_write.sum) on the plain workload at
     # 4096 rows with the 16-step Lanczos start: k_solver_row<2048> read
-    # 138.97 MB and wrote 42.11 MB; traffic grows with the rows, so a full
+    # 138.84 MB and wrote 42.29 MB; traffic grows with the rows, so a full
     # 8192-row launch moves twice that.
     kname = (f"k_solver_row<{N}> (one CTA per row)" if sched == 16
              else f"k_solver<{'XfPow2' if N & (N - 1) == 0 else 'XfBlue'}, {sched}> (cluster of {J // max(sched, 1)} CTAs)")
     traffic, tbasis = None, "no capture of this kernel and workload"
     if (args.workload == "plain" and sched == 16 and args.precision == "fp32" and args.lanczos
             and args.power_iters == 16):
-        traffic = (138965504 + 42113280) * (M / 4096.0)
-        tbasis = ("ncu capture of k_solver_row<2048> at 4096 rows (138.97 MB read + 42.11 MB written), "
+        traffic = (138835456 + 42292480) * (M / 4096.0)
+        tbasis = ("ncu capture of k_solver_row<2048> at 4096 rows (138.84 MB read + 42.29 MB written), "
                   "scaled by rows; algorithmic bytes per 4096 rows: y 134.2 MB read, T 67.1 MB written "
                   "(output rows still dirty in L2 at the kernel's end are written back after it)")
     roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak_max,

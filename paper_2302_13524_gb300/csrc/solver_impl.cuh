@@ -194,68 +194,23 @@ static __device__ float quartic_argmin_safe(const float *c)
 
 // The same minimiser from the closed-form roots of the cubic phi'(a) = 0
 // (Cardano's formula for one real root, the trigonometric form for three),
-// each polished by Newton steps on phi' in FP32; among the real roots the one
-// with the smallest phi wins (ties: the smallest positive root).  Falls back
-// to the bracketing search when c4 <= 0 or a root comes out non-finite.
-static __device__ float quartic_argmin(const float *c)
-{
-    const float c1 = c[1], c2 = c[2], c3 = c[3], c4 = c[4];
-    if (!(c4 > 0.f)) return quartic_argmin_safe(c);
-    auto g = [&](float a) { return fmaf(fmaf(fmaf(4.f * c4, a, 3.f * c3), a, 2.f * c2), a, c1); };
-    auto dg = [&](float a) { return fmaf(fmaf(12.f * c4, a, 6.f * c3), a, 2.f * c2); };
-    auto phi = [&](float a) { return a * fmaf(fmaf(fmaf(c4, a, c3), a, c2), a, c1); };
-    // phi'(a) / (4 c4) = a^3 + B a^2 + C a + D; a = x - B/3 gives x^3 + p x + q
-    const float inv = 1.f / c4;
-    const float B3 = 0.25f * c3 * inv;  // B / 3
-    const float C = 0.5f * c2 * inv, D = 0.25f * c1 * inv;
-    const float p = fmaf(-3.f * B3, B3, C);
-    const float q = fmaf(B3, fmaf(2.f * B3, B3, -C), D);
-    const float hp = p * (1.f / 3.f), hq = 0.5f * q;
-    const float disc = fmaf(hq, hq, hp * hp * hp);
-    float cand[3];
-    int nc;
-    if (disc > 0.f) {
-        const float u = cbrtf(-hq - copysignf(sqrtf(disc), hq));
-        cand[0] = (u != 0.f ? u - hp / u : 0.f) - B3;
-        nc = 1;
-    } else {
-        const float r = sqrtf(fmaxf(-hp, 0.f));
-        const float r3 = r * r * r;
-        const float arg = r3 > 0.f ? fminf(fmaxf(-hq / r3, -1.f), 1.f) : 0.f;
-        const float th = acosf(arg) * (1.f / 3.f);
-        const float tr = 2.0943951023931955f;  // 2 pi / 3
-        cand[0] = 2.f * r * cosf(th) - B3;
-        cand[1] = 2.f * r * cosf(th - tr) - B3;
-        cand[2] = 2.f * r * cosf(th + tr) - B3;
-        nc = 3;
-    }
-    float best = 0.f, bestv = 0.f;
-    for (int k = 0; k < nc; k++) {
-        float a = cand[k];
-        for (int it = 0; it < 4; it++) {
-            const float d = dg(a);
-            if (!(d != 0.f)) break;
-            const float na = a - g(a) / d;
-            if (!isfinite(na) || na == a) break;
-            a = na;
-        }
-        if (!isfinite(a)) return quartic_argmin_safe(c);
-        const float v = phi(a);
-        if (k == 0 || v < bestv || (v == bestv && a > 0.f && (best <= 0.f || a < best))) {
-            best = a;
-            bestv = v;
-        }
-    }
-    return best;
-}
-
-// quartic_argmin with the up to three Newton polishings on lanes 0..2 of a
-// warp (every lane of the warp calls it and gets the same result): the same
-// candidates, steps and selection, in the same order, as the one-thread form.
+// each polished by Newton steps on phi' in FP32, the up to three polishings on
+// lanes 0..2 of a warp (every lane of the warp calls it and gets the same
+// result); among the real roots the one with the smallest phi wins (ties: the
+// smallest positive root).  The roots are found for the variable b = 2^-k a,
+// with k such that 2^(4k) c4 lies in [1/2, 8): an exact power-of-two
+// substitution that keeps the coefficients near 1 when the step's fields are
+// tiny (late iterations), where 1 / c4 and the cubic's coefficients would
+// leave FP32 range.  Falls back to the bracketing search when c4 <= 0 or a
+// root comes out non-finite.
 static __device__ float quartic_argmin_warp(const float *c, int lane)
 {
-    const float c1 = c[1], c2 = c[2], c3 = c[3], c4 = c[4];
-    if (!(c4 > 0.f)) return quartic_argmin_safe(c);
+    if (!(c[4] > 0.f)) return quartic_argmin_safe(c);
+    int e;
+    frexpf(c[4], &e);  // c4 = f 2^e, f in [1/2, 1)
+    const int ks = -(e >> 2);  // -floor(e / 4)
+    const float c1 = ldexpf(c[1], ks), c2 = ldexpf(c[2], 2 * ks), c3 = ldexpf(c[3], 3 * ks),
+                c4 = ldexpf(c[4], 4 * ks);
     auto g = [&](float a) { return fmaf(fmaf(fmaf(4.f * c4, a, 3.f * c3), a, 2.f * c2), a, c1); };
     auto dg = [&](float a) { return fmaf(fmaf(12.f * c4, a, 6.f * c3), a, 2.f * c2); };
     auto phi = [&](float a) { return a * fmaf(fmaf(fmaf(c4, a, c3), a, c2), a, c1); };
@@ -309,7 +264,7 @@ static __device__ float quartic_argmin_warp(const float *c, int lane)
         }
     }
     if (bad) return quartic_argmin_safe(c);
-    return best;
+    return ldexpf(best, ks);
 }
 
 // Compact-form coefficients, run by one warp (lane i owns age i):
