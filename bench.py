@@ -92,6 +92,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true", help="skip the short-budget sweep to the 0.99 bar")
+    ap.add_argument("--no-batching", action="store_true",
+                    help="skip the batching workload's line that the default plain run measures in a child "
+                         "run (also skipped with --no-sweep, which profiled runs pass)")
     ap.add_argument("--no-arms", action="store_true",
                     help="skip the metric's second half (mixed precision and the learned start, "
                          "with the network trained in this run)")
@@ -113,6 +116,35 @@ def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
     t = torch.tensor([float(x)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def batching_child_line(timeout_s: float = 600.0) -> dict:
+    """The batching workload (N = 2286 through split-output Bluestein
+    transforms, per-row photon levels from 1e3 to 1e5, early exit at a relative
+    loss change of 1e-7, the whole matrix in one persistent launch replayed
+    from a captured graph) timed by a child run of this script on the same
+    GPU, 3 warm-up and 2 timed steps; the fields of its line that the default
+    plain line carries beside the headline."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--workload", "batching", "--steps", "2", "--warmup", "3",
+           "--no-cpu-baseline", "--no-e2e", "--no-sweep", "--no-arms"]
+    env = {k: v for k, v in os.environ.items()
+           if k not in ("RANK", "LOCAL_RANK", "WORLD_SIZE", "LOCAL_WORLD_SIZE", "MASTER_ADDR", "MASTER_PORT")}
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s, env=env)
+        lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+        if r.returncode != 0 or not lines:
+            return {"error": f"child exited {r.returncode}: {r.stderr.strip()[-300:]}"}
+        c = json.loads(lines[-1])
+        roof = c.get("roofline", {})
+        return {"workload": c["config"]["workload"], "value": c["value"], "unit": c["unit"],
+                "ms_per_step": c["ms_per_step"], "steps": c["steps"], "warmup": c["warmup"],
+                "row_iters_mean": c["config"].get("row_iters_mean"),
+                "row_iters_max": c["config"].get("row_iters_max"),
+                "schedule": c.get("schedule"), "fidelity": c.get("fidelity"),
+                "roofline": {k: roof.get(k) for k in ("kernel", "achieved", "peak", "unit", "frac", "solver_ms")},
+                "clocks": c.get("clocks"), "gpu_launches": c.get("gpu_launches")}
+    except (OSError, ValueError, KeyError, subprocess.TimeoutExpired) as e:
+        return {"error": f"{type(e).__name__}: {e}"[:300]}
 
 
 def job_rows_per_s(rows_per_rank: int, world: int, seconds: float) -> float:
@@ -936,6 +968,12 @@ def main():
                                 stream, world, args.iters, args.power_iters,
                                 keep=keep if cpu is not None else None, lanczos=args.lanczos,
                                 phase_tol=args.phase_tol)
+    batching = None
+    if (rank == 0 and world == 1 and args.workload == "plain" and args.rows is None and not args.no_batching
+            and not args.no_sweep):
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        batching = batching_child_line()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -965,6 +1003,8 @@ def main():
                 # + k_prep_rows, k_prep_energy, k_prep_select, k_prep_zero and
                 # k_half_sample for the camera workload)
                 "gpu_launches": ((6 if args.precision == "mixed" else 5) + (5 if cam else 0)) * args.steps}
+        if batching is not None:
+            line["batching"] = batching
         if arms is not None:
             line["learned_init_mixed"] = arms
             line["roofline"]["tensor_mlp"] = arms.get("tensor_roofline")
