@@ -143,8 +143,8 @@ typedef struct {
                                a cluster of J/G CTAs per row, 8 points per thread;
                                16 = one CTA per row (FP32, N = 512..2048 with
                                J N / 16 <= 512 threads, 16 points per thread, L-BFGS
-                               pairs in a global-memory workspace of 2 (m+1) N
-                               complex64 per resident CTA);
+                               pairs, and the Lanczos vectors where they fit, in the
+                               SM's tensor memory: no device workspace for them);
                                32 = for 2048 < N <= 2731, one mask per CTA with the
                                full-length Bluestein plan (FFTs of L = 8192) instead
                                of the split outputs at L = 4096 of schedule 1;
