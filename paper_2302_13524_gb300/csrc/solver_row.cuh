@@ -604,7 +604,9 @@ __global__ void __launch_bounds__(512, 1) k_solver_row(SolverParams P)
 // row_tmem_cols columns of the SM's 512 for its whole life, so at most
 // 512 / cols CTAs may share an SM; where registers and shared memory would
 // let more in, the shared-memory request is raised until they do not, and no
-// allocation ever has to wait for another CTA's columns.
+// allocation has to wait for the columns of another CTA of the same launch.
+// (A concurrent launch on another stream that holds tensor memory can delay
+// an allocation until its CTAs on that SM exit; they never wait on this one.)
 template <int N, int COST>
 cudaError_t row_launch_shape(int J, int m, int klz, size_t *smem_out, int *per_sm_out)
 {
